@@ -1,0 +1,141 @@
+/*
+ * exp.h -- C ABI of libexpgb: the data-parallel hot path of relativistic
+ * Fock-space coupled cluster (CCSD amplitude equations and the (0h,1p) sector)
+ * on one NVIDIA GB300 (sm_103a).
+ *
+ * Method (Oleynichenko, Zaitsevskii, Eliav, "Towards High Performance
+ * Relativistic Electronic Structure Modelling: The EXP-T Program Package",
+ * arXiv:2004.03682):
+ *   - Hamiltonian in second-quantised form, Eq. (ham); V_pqrs = <pq||rs> is the
+ *     coefficient of (1/4) {p+ q+ s r}; f = diag(eps) (Hartree-Fock spinors).
+ *   - Amplitude equations t = D^-1 (V Omega - Omega (V Omega)_Cl), Eq. (amplitudes),
+ *     with D the negated differences of H0 eigenvalues; sectors solved one after
+ *     another, Eq. (sectors): (0h,0p) then (0h,1p).
+ *   - Every diagram is evaluated as permute -> GEMM -> permute (the TTGT list of
+ *     Sec. II.B) on symmetry-blocked tensors (DPD, Sec. II.C, Fig. "blocks"),
+ *     with all blocks of one contraction in one grouped launch (Fig. "mult").
+ *
+ * Conventions for every entry point:
+ *   - All host pointers are read during the call only (copied); nothing is
+ *     retained.  Device memory is obtained only through the caller's
+ *     exp_allocator, on the caller's CUDA stream; the library never calls
+ *     cudaMalloc.  All device work is ordered on that stream.  An entry point
+ *     that returns host values synchronises that stream (only).
+ *   - No exception or abort crosses the ABI.  Every call returns an exp_status;
+ *     exp_last_error() gives a one-line message for the last failure.
+ *   - A context is not thread-safe; distinct contexts are independent.
+ *   - Complex numbers are (re, im) pairs of IEEE doubles.
+ */
+#ifndef EXPGB_EXP_H
+#define EXPGB_EXP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  EXP_OK = 0,
+  EXP_EINVAL = 1,    /* bad argument, shape or label */
+  EXP_ENOMEM = 2,    /* the allocator returned NULL */
+  EXP_ECUDA = 3,     /* a CUDA runtime error (message in exp_last_error) */
+  EXP_ENOTCONV = 4,  /* max_iter reached without convergence */
+  EXP_ENUMERIC = 5,  /* NaN/Inf in the amplitudes */
+  EXP_ETIMEOUT = 6,  /* a bounded device-side wait gave up */
+  EXP_ESTATE = 7     /* call order violated (e.g. 0h1p before converged 0h0p) */
+} exp_status;
+
+typedef struct exp_ctx exp_ctx;
+
+/* Device memory provider.  alloc(bytes, user) returns a device pointer (256-byte
+ * aligned) usable on the context's stream, or NULL; free(ptr, user) releases it. */
+typedef struct {
+  void* (*alloc)(size_t bytes, void* user);
+  void (*free)(void* ptr, void* user);
+  void* user;
+} exp_allocator;
+
+enum { EXP_FP64 = 0, EXP_EMU_BF16 = 1 };
+enum { EXP_GUESS_MP2 = 0, EXP_GUESS_USER = 1 };
+
+typedef struct {
+  int n_inst;              /* independent same-sized instances solved together (>= 1) */
+  int n_occ, n_virt;       /* occupied (hole) and virtual (particle) spinors */
+  int n_irrep;             /* G: cyclic Abelian labels Z_G (1 = no symmetry) */
+  const int32_t* irrep_occ;   /* [G] occupied spinors per irrep (shared by instances) */
+  const int32_t* irrep_virt;  /* [G] virtual spinors per irrep */
+  const double* eps_occ;      /* [n_inst * n_occ] orbital energies, ordered by irrep then energy */
+  const double* eps_virt;     /* [n_inst * n_virt] */
+  int precision;           /* EXP_FP64: all contractions in FP64.  EXP_EMU_BF16: the large
+                              contractions as split-precision emulation of complex FP64 on
+                              the BF16 tensor cores (update, DIIS, energy stay FP64). */
+  int n_slices;            /* BF16 slices per FP64 operand in emulation (3..6) */
+  int diis_dim;            /* Pulay DIIS subspace (0 = off, <= 8) */
+  double conv_tol;         /* converged when max |t_new - t| < conv_tol */
+  int max_iter;            /* per exp_ccsd_iterate sequence, counted from the guess */
+  int guess;               /* EXP_GUESS_MP2 or EXP_GUESS_USER (amplitudes set by exp_set_amplitudes) */
+} exp_config;
+
+/* Create a context: validates the config, builds the symmetry-blocked layouts
+ * (Sec. II.C) and allocates amplitude/denominator/DIIS storage.  `stream` is a
+ * cudaStream_t (NULL = legacy default stream).  EINVAL on bad sizes (n_occ < 1,
+ * n_virt < 1, G < 1, counts not summing to n_occ/n_virt, n_slices outside 3..6,
+ * diis_dim > 8); ENOMEM when the allocator fails. */
+exp_status exp_create(const exp_config* cfg, const exp_allocator* alloc, void* stream,
+                      exp_ctx** out);
+void exp_destroy(exp_ctx* ctx);
+
+/* Step I of the flowchart (Sec. II.B): generate the synthetic two-electron
+ * integrals of every instance directly in the blocked layouts the contractions
+ * read.  V follows the seeded recipe: A_pqrs complex Gaussian from Philox4x32-10
+ * at counter (idx, 0, 0), key seed; V = A - A(qp) - A(sr) + A(qp,sr);
+ * V <- (V + conj V_rspq)/2; V_pqrs = 0 unless G_p + G_q - G_r - G_s = 0 mod G;
+ * V <- s V with s = 0.05 / max|V_abij / D_ij^ab|, times scale_mult[k].
+ * seeds: [n_inst] host.  scale_mult: [n_inst] host or NULL (= 1).  scale_out:
+ * [n_inst] host or NULL, receives each applied s * scale_mult. */
+exp_status exp_init_integrals(exp_ctx* ctx, const uint64_t* seeds, const double* scale_mult,
+                              double* scale_out);
+
+/* Per-iteration record (host). */
+typedef struct {
+  double e_re, e_im;   /* E(t_new) of instance 0 */
+  double max_dt;       /* max over instances of max |t_new - t| */
+  int diis_n;          /* vectors in the DIIS subspace (instance 0) */
+  int n_converged;     /* instances converged after this iteration */
+  double ms;           /* device time of the iteration (CUDA events) */
+} exp_iter_info;
+
+/* Steps II-IV for the (0h,0p) sector: iterate the CCSD amplitude equations
+ * (Eq. (amplitudes) with T = T1 + T2) from the guess (first call) or from the
+ * current amplitudes.  One iteration: build tau, the F/W intermediates and all
+ * T1/T2 diagrams (grouped permute + contraction launches), t_new = RHS/D,
+ * residual max|t_new - t|, E(t_new), DIIS extrapolation.  Runs at most n_iter
+ * iterations, stopping early when every instance has converged (residual below
+ * conv_tol).  info: host array of n_iter records or NULL.  *converged (host,
+ * nullable) = 1 when all instances converged.  Returns ENOTCONV once max_iter
+ * iterations have run in total without convergence, ENUMERIC on NaN/Inf, ESTATE
+ * before exp_init_integrals. */
+exp_status exp_ccsd_iterate(exp_ctx* ctx, int n_iter, exp_iter_info* info, int* converged);
+
+/* Correlation energy of instance `inst` for the current amplitudes (E of the last
+ * t_new; the MP2 energy before any iteration), in hartree.  Synchronises. */
+exp_status exp_energy(exp_ctx* ctx, int inst, double* e_re, double* e_im);
+
+/* Copy amplitudes of instance `inst` between the context and caller device
+ * buffers, dense layout: t1[i][a] (n_occ x n_virt), t2[i][j][a][b]; complex128,
+ * spinor order as in the config.  Symmetry-forbidden elements read as 0 and are
+ * ignored on write.  set_amplitudes also resets DIIS and the iteration count. */
+exp_status exp_get_amplitudes(exp_ctx* ctx, int inst, void* t1_dev, void* t2_dev);
+exp_status exp_set_amplitudes(exp_ctx* ctx, int inst, const void* t1_dev, const void* t2_dev);
+
+/* Number of kernels this context has launched so far (for launch accounting). */
+int64_t exp_kernel_launches(const exp_ctx* ctx);
+
+const char* exp_last_error(const exp_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EXPGB_EXP_H */

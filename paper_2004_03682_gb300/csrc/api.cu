@@ -1,0 +1,297 @@
+// The C ABI of libexpgb (include/exp.h): validation, context lifetime, error
+// mapping, the iteration loop with CUDA-graph replay, amplitude I/O.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <string>
+
+#include "ccsd.h"
+#include "emu.h"
+
+struct exp_ctx {
+  Ctx c;
+};
+
+static thread_local std::string g_err;
+
+#define API_BEGIN try {
+#define API_END(ctxp)                                                                  \
+  }                                                                                    \
+  catch (const ExpError& e) {                                                          \
+    g_err = e.msg;                                                                     \
+    if (ctxp) (ctxp)->c.err = e.msg;                                                   \
+    return e.s;                                                                        \
+  }                                                                                    \
+  catch (const CudaError& e) {                                                         \
+    g_err = std::string(e.where) + ": " + cudaGetErrorString(e.e);                     \
+    if (ctxp) (ctxp)->c.err = g_err;                                                   \
+    return EXP_ECUDA;                                                                  \
+  }                                                                                    \
+  catch (const std::exception& e) {                                                    \
+    g_err = e.what();                                                                  \
+    if (ctxp) (ctxp)->c.err = g_err;                                                   \
+    return EXP_EINVAL;                                                                 \
+  }
+
+static void check_config(const exp_config* cfg) {
+  if (!cfg) throw ExpError{EXP_EINVAL, "null config"};
+  if (cfg->n_inst < 1 || cfg->n_occ < 1 || cfg->n_virt < 1) throw ExpError{EXP_EINVAL, "sizes must be >= 1"};
+  if (cfg->n_irrep < 1 || cfg->n_irrep > EXP_MAX_G) throw ExpError{EXP_EINVAL, "n_irrep must be in 1..16"};
+  if (!cfg->irrep_occ || !cfg->irrep_virt || !cfg->eps_occ || !cfg->eps_virt)
+    throw ExpError{EXP_EINVAL, "null irrep or energy array"};
+  int so = 0, sv = 0;
+  for (int g = 0; g < cfg->n_irrep; ++g) {
+    if (cfg->irrep_occ[g] < 0 || cfg->irrep_virt[g] < 0) throw ExpError{EXP_EINVAL, "negative irrep count"};
+    so += cfg->irrep_occ[g];
+    sv += cfg->irrep_virt[g];
+  }
+  if (so != cfg->n_occ || sv != cfg->n_virt) throw ExpError{EXP_EINVAL, "irrep counts do not sum to n_occ/n_virt"};
+  if (cfg->precision != EXP_FP64 && cfg->precision != EXP_EMU_BF16) throw ExpError{EXP_EINVAL, "bad precision"};
+  if (cfg->precision == EXP_EMU_BF16 && (cfg->n_slices < 3 || cfg->n_slices > 6))
+    throw ExpError{EXP_EINVAL, "n_slices must be in 3..6"};
+  if (cfg->diis_dim < 0 || cfg->diis_dim > EXP_MAX_DIIS) throw ExpError{EXP_EINVAL, "diis_dim must be in 0..8"};
+  if (!(cfg->conv_tol > 0)) throw ExpError{EXP_EINVAL, "conv_tol must be > 0"};
+  if (cfg->max_iter < 1) throw ExpError{EXP_EINVAL, "max_iter must be >= 1"};
+  for (int64_t k = 0; k < int64_t(cfg->n_inst) * cfg->n_occ; ++k)
+    if (!std::isfinite(cfg->eps_occ[k])) throw ExpError{EXP_EINVAL, "non-finite eps_occ"};
+  for (int64_t k = 0; k < int64_t(cfg->n_inst) * cfg->n_virt; ++k)
+    if (!std::isfinite(cfg->eps_virt[k])) throw ExpError{EXP_EINVAL, "non-finite eps_virt"};
+}
+
+extern "C" exp_status exp_create(const exp_config* cfg, const exp_allocator* alloc, void* stream, exp_ctx** out) {
+  exp_ctx* x = nullptr;
+  API_BEGIN
+  if (!out) throw ExpError{EXP_EINVAL, "null out"};
+  *out = nullptr;
+  check_config(cfg);
+  if (!alloc || !alloc->alloc || !alloc->free) throw ExpError{EXP_EINVAL, "null allocator"};
+  x = new exp_ctx();
+  Ctx& c = x->c;
+  c.cfg = *cfg;
+  c.cfg.irrep_occ = c.cfg.irrep_virt = nullptr;
+  c.cfg.eps_occ = c.cfg.eps_virt = nullptr;
+  c.alloc = *alloc;
+  c.stream = (cudaStream_t)stream;
+  c.G = cfg->n_irrep;
+  c.no = cfg->n_occ;
+  c.nv = cfg->n_virt;
+  c.ninst = cfg->n_inst;
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&c.sm_count, cudaDevAttrMultiProcessorCount, dev));
+  c.spaces.resize(SP_COUNT);
+  for (int s = 0; s < SP_COUNT; ++s) {
+    Space& sp = c.spaces[s];
+    const int32_t* cnt = s == SP_OCC ? cfg->irrep_occ : cfg->irrep_virt;
+    sp.cnt.assign(cnt, cnt + c.G);
+    sp.off.resize(c.G);
+    int o = 0;
+    for (int g = 0; g < c.G; ++g) { sp.off[g] = o; o += sp.cnt[g]; }
+    sp.n = o;
+    sp.gbase = s == SP_OCC ? 0 : c.no;
+  }
+  const int n = c.no + c.nv;
+  std::vector<double> eps(size_t(c.ninst) * n);
+  for (int k = 0; k < c.ninst; ++k) {
+    std::copy(cfg->eps_occ + size_t(k) * c.no, cfg->eps_occ + size_t(k + 1) * c.no, eps.begin() + size_t(k) * n);
+    std::copy(cfg->eps_virt + size_t(k) * c.nv, cfg->eps_virt + size_t(k + 1) * c.nv,
+              eps.begin() + size_t(k) * n + c.no);
+  }
+  c.d_eps = (double*)c.dalloc(eps.size() * sizeof(double));
+  upload(c, c.d_eps, eps.data(), eps.size() * sizeof(double));
+  c.d_seed = (uint64_t*)c.dalloc(sizeof(uint64_t) * c.ninst);
+  c.d_scale = (double*)c.dalloc(sizeof(double) * c.ninst);
+  CK(cudaEventCreate(&c.ev0));
+  CK(cudaEventCreate(&c.ev1));
+  ccsd_setup(c);
+  CK(cudaStreamSynchronize(c.stream));
+  *out = x;
+  return EXP_OK;
+  }
+  catch (const ExpError& e) {
+    g_err = e.msg;
+    if (x) { x->c.dfree_all(); delete x; }
+    return e.s;
+  }
+  catch (const CudaError& e) {
+    g_err = std::string(e.where) + ": " + cudaGetErrorString(e.e);
+    if (x) { x->c.dfree_all(); delete x; }
+    return EXP_ECUDA;
+  }
+}
+
+extern "C" void exp_destroy(exp_ctx* x) {
+  if (!x) return;
+  Ctx& c = x->c;
+  cudaStreamSynchronize(c.stream);
+  if (c.graph) cudaGraphExecDestroy(c.graph);
+  if (c.ev0) cudaEventDestroy(c.ev0);
+  if (c.ev1) cudaEventDestroy(c.ev1);
+  if (c.h_stats) cudaFreeHost(c.h_stats);
+  try { emu_release(c); } catch (...) {}
+  ccsd_release(c);
+  c.dfree_all();
+  delete x;
+}
+
+extern "C" exp_status exp_init_integrals(exp_ctx* x, const uint64_t* seeds, const double* scale_mult,
+                                         double* scale_out) {
+  API_BEGIN
+  if (!x || !seeds) throw ExpError{EXP_EINVAL, "null argument"};
+  Ctx& c = x->c;
+  if (c.have_integrals) throw ExpError{EXP_ESTATE, "integrals already initialised"};
+  upload(c, c.d_seed, seeds, sizeof(uint64_t) * c.ninst);
+  std::vector<double> mult(c.ninst, 1.0);
+  if (scale_mult)
+    for (int k = 0; k < c.ninst; ++k) {
+      if (!(scale_mult[k] > 0) || !std::isfinite(scale_mult[k])) throw ExpError{EXP_EINVAL, "scale_mult must be > 0"};
+      mult[k] = scale_mult[k];
+    }
+  ccsd_init_integrals(c, mult.data());
+  if (scale_out)
+    for (int k = 0; k < c.ninst; ++k) scale_out[k] = c.h_scale[k];
+  return EXP_OK;
+  API_END(x)
+}
+
+static int64_t count_kernel_nodes(cudaGraph_t g) {
+  size_t n = 0;
+  CK(cudaGraphGetNodes(g, nullptr, &n));
+  std::vector<cudaGraphNode_t> nodes(n);
+  CK(cudaGraphGetNodes(g, nodes.data(), &n));
+  int64_t k = 0;
+  for (auto& nd : nodes) {
+    cudaGraphNodeType t;
+    CK(cudaGraphNodeGetType(nd, &t));
+    if (t == cudaGraphNodeTypeKernel) ++k;
+  }
+  return k;
+}
+
+extern "C" exp_status exp_ccsd_iterate(exp_ctx* x, int n_iter, exp_iter_info* info, int* converged) {
+  API_BEGIN
+  if (!x) throw ExpError{EXP_EINVAL, "null context"};
+  Ctx& c = x->c;
+  if (converged) *converged = 0;
+  if (!c.have_integrals) throw ExpError{EXP_ESTATE, "exp_init_integrals must come first"};
+  if (n_iter < 0) throw ExpError{EXP_EINVAL, "n_iter < 0"};
+  if (!c.guessed) {
+    if (c.cfg.guess == EXP_GUESS_MP2) ccsd_guess(c);
+    else throw ExpError{EXP_ESTATE, "guess=USER needs exp_set_amplitudes first"};
+    c.guessed = true;
+  }
+  bool all_conv = false;
+  for (int it = 0; it < n_iter; ++it) {
+    if (c.iter_done >= c.cfg.max_iter) return EXP_ENOTCONV;
+    CK(cudaEventRecord(c.ev0, c.stream));
+    if (c.graph) {
+      CK(cudaGraphLaunch(c.graph, c.stream));
+      c.launches += c.graph_kernels;
+    } else {
+      const bool capture = c.iter_done >= 1 && c.stream != nullptr;
+      if (capture) {
+        CK(cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal));
+        const int64_t before = c.launches;
+        try {
+          ccsd_iteration(c);
+        } catch (...) {
+          cudaGraph_t g;
+          cudaStreamEndCapture(c.stream, &g);
+          if (g) cudaGraphDestroy(g);
+          throw;
+        }
+        cudaGraph_t g;
+        CK(cudaStreamEndCapture(c.stream, &g));
+        CK(cudaGraphInstantiate(&c.graph, g, 0));
+        c.graph_kernels = count_kernel_nodes(g);
+        CK(cudaGraphDestroy(g));
+        c.launches = before + c.graph_kernels;
+        CK(cudaGraphLaunch(c.graph, c.stream));
+      } else {
+        ccsd_iteration(c);
+      }
+    }
+    CK(cudaEventRecord(c.ev1, c.stream));
+    CK(cudaMemcpyAsync(c.h_stats, c.d_stats, sizeof(double) * 8 * c.ninst, cudaMemcpyDeviceToHost, c.stream));
+    std::vector<int> st(4 * c.ninst);
+    CK(cudaMemcpyAsync(st.data(), c.d_diis_state, sizeof(int) * 4 * c.ninst, cudaMemcpyDeviceToHost, c.stream));
+    CK(cudaStreamSynchronize(c.stream));
+    c.iter_done++;
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, c.ev0, c.ev1));
+    double mdt = 0.0;
+    int nconv = 0;
+    bool bad = false;
+    for (int k = 0; k < c.ninst; ++k) {
+      mdt = std::max(mdt, c.h_stats[k * 8 + 0]);
+      if (c.h_stats[k * 8 + 4] != 0.0) bad = true;
+      if (st[k * 4 + 2]) ++nconv;
+    }
+    if (info) {
+      info[it].e_re = c.h_stats[1];
+      info[it].e_im = c.h_stats[2];
+      info[it].max_dt = mdt;
+      info[it].diis_n = int(c.h_stats[3]);
+      info[it].n_converged = nconv;
+      info[it].ms = ms;
+    }
+    if (bad) throw ExpError{EXP_ENUMERIC, "NaN/Inf in the amplitudes"};
+    if (nconv == c.ninst) { all_conv = true; break; }
+  }
+  if (converged) *converged = all_conv ? 1 : 0;
+  if (!all_conv && c.iter_done >= c.cfg.max_iter) return EXP_ENOTCONV;
+  return EXP_OK;
+  API_END(x)
+}
+
+extern "C" exp_status exp_energy(exp_ctx* x, int inst, double* e_re, double* e_im) {
+  API_BEGIN
+  if (!x) throw ExpError{EXP_EINVAL, "null context"};
+  Ctx& c = x->c;
+  if (inst < 0 || inst >= c.ninst) throw ExpError{EXP_EINVAL, "instance out of range"};
+  if (!c.guessed) throw ExpError{EXP_ESTATE, "no amplitudes yet"};
+  double s[8];
+  CK(cudaMemcpyAsync(s, c.d_stats + 8 * inst, sizeof(s), cudaMemcpyDeviceToHost, c.stream));
+  CK(cudaStreamSynchronize(c.stream));
+  if (e_re) *e_re = s[1];
+  if (e_im) *e_im = s[2];
+  return EXP_OK;
+  API_END(x)
+}
+
+extern "C" exp_status exp_get_amplitudes(exp_ctx* x, int inst, void* t1, void* t2) {
+  API_BEGIN
+  if (!x || !t1 || !t2) throw ExpError{EXP_EINVAL, "null argument"};
+  Ctx& c = x->c;
+  if (inst < 0 || inst >= c.ninst) throw ExpError{EXP_EINVAL, "instance out of range"};
+  ccsd_dense_io(c, inst, (cplx*)t1, (cplx*)t2, true);
+  CK(cudaStreamSynchronize(c.stream));
+  return EXP_OK;
+  API_END(x)
+}
+
+extern "C" exp_status exp_set_amplitudes(exp_ctx* x, int inst, const void* t1, const void* t2) {
+  API_BEGIN
+  if (!x || !t1 || !t2) throw ExpError{EXP_EINVAL, "null argument"};
+  Ctx& c = x->c;
+  if (inst < 0 || inst >= c.ninst) throw ExpError{EXP_EINVAL, "instance out of range"};
+  if (!c.have_integrals) throw ExpError{EXP_ESTATE, "exp_init_integrals must come first"};
+  if (!c.guessed) {
+    // other instances start from the MP2 guess
+    ccsd_guess(c);
+    c.guessed = true;
+  }
+  ccsd_dense_io(c, inst, (cplx*)t1, (cplx*)t2, false);
+  ccsd_reset_diis(c);
+  ccsd_energy_of(c, c.d_T, false);
+  CK(cudaStreamSynchronize(c.stream));
+  return EXP_OK;
+  API_END(x)
+}
+
+extern "C" int64_t exp_kernel_launches(const exp_ctx* x) { return x ? x->c.launches : 0; }
+
+extern "C" const char* exp_last_error(const exp_ctx* x) {
+  if (x && !x->c.err.empty()) return x->c.err.c_str();
+  return g_err.c_str();
+}

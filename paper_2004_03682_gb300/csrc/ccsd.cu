@@ -1,0 +1,714 @@
+// CCSD for the (0h,0p) sector on the GPU: the amplitude equations of
+// Eq. (amplitudes) truncated to singles and doubles, written as Stanton-Gauss
+// intermediates, every term one TTGT contraction on symmetry-blocked tensors
+// (Sec. II.B / II.C).  Plus the FP64 update t_new = RHS/D, the residual, the
+// energy and DIIS, all on the device; one iteration is replayed as a CUDA graph.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+
+#include "ccsd.h"
+#include "emu.h"
+
+static const cplx ONE = {1.0, 0.0};
+static inline cplx C(double x) { return make_double2(x, 0.0); }
+
+// Integral classes: V(p,q,r,s) by the spaces of its arguments.
+static const IntRef OOOO{{SP_OCC, SP_OCC, SP_OCC, SP_OCC}};
+static const IntRef OOOV{{SP_OCC, SP_OCC, SP_OCC, SP_VIRT}};
+static const IntRef OOVO{{SP_OCC, SP_OCC, SP_VIRT, SP_OCC}};
+static const IntRef OOVV{{SP_OCC, SP_OCC, SP_VIRT, SP_VIRT}};
+static const IntRef OVOV{{SP_OCC, SP_VIRT, SP_OCC, SP_VIRT}};
+static const IntRef OVVO{{SP_OCC, SP_VIRT, SP_VIRT, SP_OCC}};
+static const IntRef OVVV{{SP_OCC, SP_VIRT, SP_VIRT, SP_VIRT}};
+static const IntRef OVOO{{SP_OCC, SP_VIRT, SP_OCC, SP_OCC}};
+static const IntRef VOVV{{SP_VIRT, SP_OCC, SP_VIRT, SP_VIRT}};
+static const IntRef VVVO{{SP_VIRT, SP_VIRT, SP_VIRT, SP_OCC}};
+static const IntRef VVVV{{SP_VIRT, SP_VIRT, SP_VIRT, SP_VIRT}};
+
+Layout L4(Ctx& c, int s0, int g0, int s1, int g1, int s2, int g2, int s3, int g3, int nrow) {
+  const int sp[4] = {s0, s1, s2, s3}, sg[4] = {g0, g1, g2, g3};
+  return make_layout(c.spaces, c.G, 4, sp, sg, nrow);
+}
+Layout L2(Ctx& c, int s0, int g0, int s1, int g1) {
+  const int sp[2] = {s0, s1}, sg[2] = {g0, g1};
+  return make_layout(c.spaces, c.G, 2, sp, sg, 1);
+}
+
+// ---------------------------------------------------------------------------
+// Reductions: per-CTA partials in fixed order, then a one-CTA finaliser, so
+// every run is bitwise reproducible.
+#define RED_BLOCKS 152
+#define RED_THREADS 256
+
+template <typename T, typename Op>
+__device__ T block_reduce(T v, Op op, T* sh) {
+  for (int o = 16; o; o >>= 1) v = op(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    v = (l < (blockDim.x >> 5)) ? sh[l] : sh[0];
+    for (int o = 16; o; o >>= 1) v = op(v, __shfl_xor_sync(0xffffffffu, v, o));
+  }
+  return v;
+}
+struct MaxOp { __device__ double operator()(double a, double b) const { return fmax(a, b); } };
+struct AddOp { __device__ double operator()(double a, double b) const { return a + b; } };
+
+// t_new = R / D over the whole amplitude vector; e = t_new - t.  Writes t_new and
+// e into the next DIIS slot; per-CTA max |e|.  Frozen (converged) instances skip.
+__global__ void __launch_bounds__(RED_THREADS) k_update(const cplx* __restrict__ R, const double* __restrict__ D,
+                                                        const cplx* __restrict__ T, cplx* __restrict__ Tn,
+                                                        cplx* __restrict__ En, int64_t namp, int dim,
+                                                        const int* __restrict__ state, double* __restrict__ part) {
+  __shared__ double sh[32];
+  const int inst = blockIdx.y;
+  const int* st = state + inst * 4;
+  const int slot = dim > 0 ? (st[1] + 1) % dim : 0;
+  const int64_t off = int64_t(inst) * namp;
+  const int64_t soff = (int64_t(inst) * (dim > 0 ? dim : 1) + slot) * namp;
+  double m = 0.0;
+  if (!st[2]) {
+    for (int64_t k = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; k < namp; k += int64_t(gridDim.x) * blockDim.x) {
+      const cplx r = R[off + k];
+      const double d = D[off + k];
+      const cplx t = T[off + k];
+      const cplx tn = make_double2(r.x / d, r.y / d);
+      const cplx e = make_double2(tn.x - t.x, tn.y - t.y);
+      Tn[soff + k] = tn;
+      En[soff + k] = e;
+      m = fmax(m, hypot(e.x, e.y));
+    }
+  }
+  m = block_reduce(m, MaxOp(), sh);
+  if (threadIdx.x == 0) part[(inst * gridDim.x + blockIdx.x) * 8] = m;
+}
+
+// per instance: residual, NaN check, convergence, DIIS push.
+__global__ void k_finalize_update(const double* __restrict__ part, int nb, int* __restrict__ state,
+                                  double* __restrict__ stats, int dim, double tol) {
+  const int inst = blockIdx.x;
+  if (threadIdx.x) return;
+  int* st = state + inst * 4;
+  double* s = stats + inst * 8;
+  if (st[2]) { s[0] = 0.0; return; }
+  double m = 0.0;
+  bool bad = false;
+  for (int b = 0; b < nb; ++b) {
+    const double v = part[(inst * nb + b) * 8];
+    if (!(v == v) || isinf(v)) bad = true;
+    m = fmax(m, v);
+  }
+  s[0] = bad ? INFINITY : m;
+  s[4] = bad ? 1.0 : 0.0;
+  if (dim > 0) {
+    st[1] = (st[1] + 1) % dim;
+    st[0] = min(st[0] + 1, dim);
+  }
+  if (m < tol && !bad) st[3] = 1;  // converged this iteration (freeze after extrapolation)
+}
+
+// energy partial sums: E = 1/4 sum conj(<ab||ij>) tau_ij^ab  (<ij||ab> = conj <ab||ij>)
+__global__ void __launch_bounds__(RED_THREADS) k_energy_part(const cplx* __restrict__ Vd, int64_t vis,
+                                                             const cplx* __restrict__ tau, int64_t tis,
+                                                             int64_t n2, const int* __restrict__ state,
+                                                             double* __restrict__ part, int skip_frozen) {
+  __shared__ double sh[32];
+  const int inst = blockIdx.y;
+  double er = 0.0, ei = 0.0;
+  if (!(skip_frozen && state[inst * 4 + 2])) {
+    const cplx* v = Vd + inst * vis;
+    const cplx* t = tau + inst * tis;
+    for (int64_t k = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; k < n2; k += int64_t(gridDim.x) * blockDim.x) {
+      const cplx a = v[k], b = t[k];
+      er += a.x * b.x + a.y * b.y;
+      ei += a.x * b.y - a.y * b.x;
+    }
+  }
+  er = block_reduce(er, AddOp(), sh);
+  ei = block_reduce(ei, AddOp(), sh);
+  if (threadIdx.x == 0) {
+    part[(inst * gridDim.x + blockIdx.x) * 8 + 1] = er;
+    part[(inst * gridDim.x + blockIdx.x) * 8 + 2] = ei;
+  }
+}
+
+__global__ void k_finalize_energy(const double* __restrict__ part, int nb, const int* __restrict__ state,
+                                  double* __restrict__ stats, int skip_frozen) {
+  const int inst = blockIdx.x;
+  if (threadIdx.x) return;
+  if (skip_frozen && state[inst * 4 + 2]) return;
+  double er = 0.0, ei = 0.0;
+  for (int b = 0; b < nb; ++b) {
+    er += part[(inst * nb + b) * 8 + 1];
+    ei += part[(inst * nb + b) * 8 + 2];
+  }
+  stats[inst * 8 + 1] = 0.25 * er;
+  stats[inst * 8 + 2] = 0.25 * ei;
+}
+
+// DIIS: dots of the newest error vector with every stored one (Re <e_new, e_k>).
+__global__ void __launch_bounds__(RED_THREADS) k_diis_dots(const cplx* __restrict__ E, int64_t namp, int dim,
+                                                           const int* __restrict__ state,
+                                                           double* __restrict__ part) {
+  __shared__ double sh[32];
+  const int inst = blockIdx.y;
+  const int* st = state + inst * 4;
+  const int cnt = st[0], head = st[1];
+  const bool active = !st[2];
+  const cplx* en = E + (int64_t(inst) * dim + head) * namp;
+  for (int j = 0; j < dim; ++j) {
+    double acc = 0.0;
+    if (active && j < cnt) {
+      const int slot = (head - j + dim) % dim;
+      const cplx* ek = E + (int64_t(inst) * dim + slot) * namp;
+      for (int64_t k = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; k < namp; k += int64_t(gridDim.x) * blockDim.x) {
+        const cplx a = en[k], b = ek[k];
+        acc += a.x * b.x + a.y * b.y;
+      }
+    }
+    acc = block_reduce(acc, AddOp(), sh);
+    if (threadIdx.x == 0) part[((inst * gridDim.x + blockIdx.x) * EXP_MAX_DIIS + j)] = acc;
+  }
+}
+
+// DIIS solve per instance: B over slots (by age), bordered system, Gaussian
+// elimination with partial pivoting; a pivot below 1e-14 max diag drops the
+// oldest vector.  Writes coefficients per slot (0 for unused).
+__global__ void k_diis_solve(const double* __restrict__ part, int nb, int dim, int* __restrict__ state,
+                             double* __restrict__ Bm, double* __restrict__ coef, double* __restrict__ stats) {
+  const int inst = blockIdx.x;
+  if (threadIdx.x) return;
+  int* st = state + inst * 4;
+  double* cf = coef + inst * EXP_MAX_DIIS;
+  for (int k = 0; k < EXP_MAX_DIIS; ++k) cf[k] = 0.0;
+  if (st[2]) return;
+  const int head = st[1];
+  double* B = Bm + inst * EXP_MAX_DIIS * EXP_MAX_DIIS;  // B[slot][slot]
+  // new row / column from the dots
+  for (int j = 0; j < st[0]; ++j) {
+    double s = 0.0;
+    for (int b = 0; b < nb; ++b) s += part[((inst * nb + b) * EXP_MAX_DIIS + j)];
+    const int slot = (head - j + dim) % dim;
+    B[head * EXP_MAX_DIIS + slot] = s;
+    B[slot * EXP_MAX_DIIS + head] = s;
+  }
+  int cnt = st[0];
+  while (cnt >= 2) {
+    // order by age: index 0 = oldest
+    int sl[EXP_MAX_DIIS];
+    for (int k = 0; k < cnt; ++k) sl[k] = (head - (cnt - 1 - k) + dim) % dim;
+    const int m = cnt + 1;
+    double A[EXP_MAX_DIIS + 1][EXP_MAX_DIIS + 1], y[EXP_MAX_DIIS + 1];
+    double dmax = 0.0;
+    for (int k = 0; k < cnt; ++k) {
+      for (int l = 0; l < cnt; ++l) A[k][l] = B[sl[k] * EXP_MAX_DIIS + sl[l]];
+      A[k][cnt] = -1.0;
+      A[cnt][k] = -1.0;
+      y[k] = 0.0;
+      dmax = fmax(dmax, A[k][k]);
+    }
+    A[cnt][cnt] = 0.0;
+    y[cnt] = -1.0;
+    const double tiny = 1e-14 * dmax;
+    bool ok = true;
+    for (int k = 0; k < m && ok; ++k) {
+      int p = k;
+      for (int r = k + 1; r < m; ++r)
+        if (fabs(A[r][k]) > fabs(A[p][k])) p = r;
+      if (fabs(A[p][k]) < tiny) { ok = false; break; }
+      if (p != k) {
+        for (int c2 = 0; c2 < m; ++c2) { const double t = A[k][c2]; A[k][c2] = A[p][c2]; A[p][c2] = t; }
+        const double t = y[k]; y[k] = y[p]; y[p] = t;
+      }
+      for (int r = k + 1; r < m; ++r) {
+        const double f = A[r][k] / A[k][k];
+        for (int c2 = k; c2 < m; ++c2) A[r][c2] -= f * A[k][c2];
+        y[r] -= f * y[k];
+      }
+    }
+    if (ok) {
+      double x[EXP_MAX_DIIS + 1];
+      for (int k = m - 1; k >= 0; --k) {
+        double s = y[k];
+        for (int c2 = k + 1; c2 < m; ++c2) s -= A[k][c2] * x[c2];
+        x[k] = s / A[k][k];
+      }
+      for (int k = 0; k < cnt; ++k) cf[sl[k]] = x[k];
+      st[0] = cnt;
+      stats[inst * 8 + 3] = cnt;
+      return;
+    }
+    --cnt;  // drop the oldest
+    st[0] = cnt;
+  }
+  cf[head] = 1.0;  // fewer than 2 vectors: plain update
+  stats[inst * 8 + 3] = st[0];
+}
+
+// T = sum_k c_k t_new_k (or t_new when DIIS is off / not yet active).
+__global__ void __launch_bounds__(256) k_extrapolate(cplx* __restrict__ T, const cplx* __restrict__ Tn,
+                                                     int64_t namp, int dim, const double* __restrict__ coef,
+                                                     int* __restrict__ state) {
+  const int inst = blockIdx.y;
+  const int* st = state + inst * 4;
+  if (st[2]) return;
+  const int D = dim > 0 ? dim : 1;
+  const double* cf = coef + inst * EXP_MAX_DIIS;
+  const bool plain = dim == 0 || st[3];
+  const int head = dim > 0 ? st[1] : 0;
+  for (int64_t k = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; k < namp; k += int64_t(gridDim.x) * blockDim.x) {
+    double vr = 0.0, vi = 0.0;
+    if (plain) {
+      const cplx x = Tn[(int64_t(inst) * D + head) * namp + k];
+      vr = x.x; vi = x.y;
+    } else {
+      for (int s = 0; s < D; ++s) {
+        const double c = cf[s];
+        if (c != 0.0) {
+          const cplx x = Tn[(int64_t(inst) * D + s) * namp + k];
+          vr += c * x.x;
+          vi += c * x.y;
+        }
+      }
+    }
+    T[int64_t(inst) * namp + k] = make_double2(vr, vi);
+  }
+}
+
+// converged instances freeze after their final t_new has been taken
+__global__ void k_freeze(int* __restrict__ state, int ninst) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < ninst && state[i * 4 + 3]) state[i * 4 + 2] = 1;
+}
+
+// scale pass: max |V_abij / D_ij^ab| per instance
+__global__ void __launch_bounds__(RED_THREADS) k_maxratio(const cplx* __restrict__ V, int64_t vis,
+                                                          const double* __restrict__ D, int64_t dis, int64_t off,
+                                                          int64_t n, double* __restrict__ part) {
+  __shared__ double sh[32];
+  const int inst = blockIdx.y;
+  double m = 0.0;
+  for (int64_t k = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; k < n; k += int64_t(gridDim.x) * blockDim.x) {
+    const cplx v = V[inst * vis + k];
+    m = fmax(m, hypot(v.x, v.y) / fabs(D[inst * dis + off + k]));
+  }
+  m = block_reduce(m, MaxOp(), sh);
+  if (threadIdx.x == 0) part[(inst * gridDim.x + blockIdx.x) * 8] = m;
+}
+
+__global__ void k_set_scale(const double* __restrict__ part, int nb, const double* __restrict__ mult,
+                            double* __restrict__ scale) {
+  const int inst = blockIdx.x;
+  if (threadIdx.x) return;
+  double m = 0.0;
+  for (int b = 0; b < nb; ++b) m = fmax(m, part[(inst * nb + b) * 8]);
+  scale[inst] = 0.05 / m * mult[inst];
+}
+
+__global__ void k_rescale(cplx* __restrict__ V, int64_t vis, int64_t n, const double* __restrict__ scale) {
+  const int inst = blockIdx.y;
+  const double s = scale[inst];
+  for (int64_t k = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; k < n; k += int64_t(gridDim.x) * blockDim.x) {
+    cplx v = V[inst * vis + k];
+    V[inst * vis + k] = make_double2(s * v.x, s * v.y);
+  }
+}
+
+// t2 = V_abij / D (MP2 first-order amplitudes), t1 = 0
+__global__ void k_mp2_guess(cplx* __restrict__ T, const double* __restrict__ D, const cplx* __restrict__ Vd,
+                            int64_t vis, int64_t n1, int64_t namp) {
+  const int inst = blockIdx.y;
+  for (int64_t k = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; k < namp; k += int64_t(gridDim.x) * blockDim.x) {
+    cplx out = make_double2(0, 0);
+    if (k >= n1) {
+      const cplx v = Vd[inst * vis + (k - n1)];
+      const double d = D[inst * namp + k];
+      out = make_double2(v.x / d, v.y / d);
+    }
+    T[inst * namp + k] = out;
+  }
+}
+
+// ---------------------------------------------------------------------------
+static int grid_for(int64_t n, int threads = 256, int cap = 4 * 152) {
+  int64_t b = (n + threads - 1) / threads;
+  return int(std::max<int64_t>(1, std::min<int64_t>(b, cap)));
+}
+
+struct TauTasks {
+  GenTask* d_tasks = nullptr;
+  ChunkRef* d_chunks = nullptr;
+  int n_chunks = 0;
+};
+
+struct CcsdState {
+  TauTasks t2tasks;
+  TauTasks t1tasks;
+  int32_t* d_t1i = nullptr;
+  double* d_part = nullptr;
+  double* d_coef = nullptr;
+  const Tensor* Vd = nullptr;  // <ab||ij> in the t2 layout
+  Tensor Tn2;                  // view used for the energy tau (scratch)
+  cplx* d_taun = nullptr;      // tau of t_new
+};
+
+static CcsdState& S(Ctx& c) { return *reinterpret_cast<CcsdState*>(c.ccsd_state); }
+
+void ccsd_setup(Ctx& c) {
+  CcsdState* s = new CcsdState();
+  c.ccsd_state = s;
+  c.t1.L = L2(c, SP_VIRT, +1, SP_OCC, -1);
+  c.t2.L = L4(c, SP_VIRT, +1, SP_VIRT, +1, SP_OCC, -1, SP_OCC, -1, 2);
+  c.n1 = c.t1.L.size;
+  c.n2 = c.t2.L.size;
+  c.namp = c.n1 + c.n2;
+  const int64_t na = c.namp, ni = c.ninst;
+  c.d_T = (cplx*)c.dalloc(sizeof(cplx) * na * ni);
+  c.d_R = (cplx*)c.dalloc(sizeof(cplx) * na * ni);
+  c.d_D = (double*)c.dalloc(sizeof(double) * na * ni);
+  CK(cudaMemsetAsync(c.d_T, 0, sizeof(cplx) * na * ni, c.stream));
+  const int dslots = std::max(c.cfg.diis_dim, 1);
+  c.d_diis_t = (cplx*)c.dalloc(sizeof(cplx) * na * ni * dslots);
+  c.d_diis_e = (cplx*)c.dalloc(sizeof(cplx) * na * ni * dslots);
+  c.d_diis_B = (double*)c.dalloc(sizeof(double) * EXP_MAX_DIIS * EXP_MAX_DIIS * ni);
+  c.d_diis_state = (int*)c.dalloc(sizeof(int) * 4 * ni);
+  c.d_stats = (double*)c.dalloc(sizeof(double) * 8 * ni);
+  CK(cudaMemsetAsync(c.d_diis_state, 0, sizeof(int) * 4 * ni, c.stream));
+  CK(cudaMemsetAsync(c.d_stats, 0, sizeof(double) * 8 * ni, c.stream));
+  CK(cudaMemsetAsync(c.d_diis_B, 0, sizeof(double) * EXP_MAX_DIIS * EXP_MAX_DIIS * ni, c.stream));
+  CK(cudaMallocHost(&c.h_stats, sizeof(double) * 8 * ni));
+  s->d_part = (double*)c.dalloc(sizeof(double) * 8 * RED_BLOCKS * ni * EXP_MAX_DIIS);
+  s->d_coef = (double*)c.dalloc(sizeof(double) * EXP_MAX_DIIS * ni);
+  c.t1.d = c.d_T;
+  c.t1.is = na;
+  c.t2.d = c.d_T + c.n1;
+  c.t2.is = na;
+  c.r1 = c.t1;
+  c.r1.d = c.d_R;
+  c.r2 = c.t2;
+  c.r2.d = c.d_R + c.n1;
+  // denominators
+  {
+    std::vector<GenTask> tk;
+    std::vector<ChunkRef> ch;
+    gen_tasks(c, c.t1.L, tk, ch);
+    if (!ch.empty()) {
+      GenTask* dt = (GenTask*)c.dalloc(tk.size() * sizeof(GenTask));
+      ChunkRef* dc = (ChunkRef*)c.dalloc(ch.size() * sizeof(ChunkRef));
+      upload(c, dt, tk.data(), tk.size() * sizeof(GenTask));
+      upload(c, dc, ch.data(), ch.size() * sizeof(ChunkRef));
+      const int sg[2] = {+1, -1};
+      launch_fill_denom(c, c.d_D, na, dt, dc, int(ch.size()), 2, sg);
+    }
+    tk.clear();
+    ch.clear();
+    gen_tasks(c, c.t2.L, tk, ch);
+    if (!ch.empty()) {
+      GenTask* dt = (GenTask*)c.dalloc(tk.size() * sizeof(GenTask));
+      ChunkRef* dc = (ChunkRef*)c.dalloc(ch.size() * sizeof(ChunkRef));
+      upload(c, dt, tk.data(), tk.size() * sizeof(GenTask));
+      upload(c, dc, ch.data(), ch.size() * sizeof(ChunkRef));
+      const int sg[4] = {+1, +1, -1, -1};
+      launch_fill_denom(c, c.d_D + c.n1, na, dt, dc, int(ch.size()), 4, sg);
+      s->t2tasks.d_tasks = dt;
+      s->t2tasks.d_chunks = dc;
+      s->t2tasks.n_chunks = int(ch.size());
+    }
+  }
+  // t1 index table: offset of t1_ai (a, i local) or -1
+  {
+    std::vector<int32_t> idx(size_t(c.nv) * c.no, -1);
+    std::vector<SubBlock> sb;
+    enumerate_blocks(c.t1.L, c.spaces, sb);
+    for (auto& b : sb) {
+      const int a0 = c.spaces[SP_VIRT].off[b.irr[0]], i0 = c.spaces[SP_OCC].off[b.irr[1]];
+      for (int a = 0; a < b.n[0]; ++a)
+        for (int i = 0; i < b.n[1]; ++i) idx[size_t(a0 + a) * c.no + i0 + i] = int32_t(b.base + a * b.st[0] + i * b.st[1]);
+    }
+    s->d_t1i = (int32_t*)c.dalloc(idx.size() * sizeof(int32_t));
+    upload(c, s->d_t1i, idx.data(), idx.size() * sizeof(int32_t));
+  }
+  s->d_taun = (cplx*)c.dalloc(sizeof(cplx) * std::max<int64_t>(c.n2, 1) * ni);
+}
+
+void ccsd_release(Ctx& c) {
+  delete reinterpret_cast<CcsdState*>(c.ccsd_state);
+  c.ccsd_state = nullptr;
+}
+
+// Generate the driver <ab||ij> unscaled, fix the per-instance scale so that
+// max |t_MP2| = 0.05 (times the caller's multiplier), rescale it.
+void ccsd_init_integrals(Ctx& c, const double* h_mult) {
+  CcsdState& s = S(c);
+  std::vector<double> ones(c.ninst, 1.0);
+  upload(c, c.d_scale, ones.data(), sizeof(double) * c.ninst);
+  c.have_integrals = true;
+  const int arg[4] = {0, 1, 2, 3};
+  const IntRef VVOO{{SP_VIRT, SP_VIRT, SP_OCC, SP_OCC}};
+  const Tensor* Vd = integral(c, VVOO, arg, 2);
+  s.Vd = Vd;
+  const int nb = RED_BLOCKS;
+  k_maxratio<<<dim3(nb, c.ninst), RED_THREADS, 0, c.stream>>>(Vd->d, Vd->is, c.d_D, c.namp, c.n1, c.n2, s.d_part);
+  KCHECK(c);
+  double* d_mult = (double*)c.dalloc(sizeof(double) * c.ninst);
+  upload(c, d_mult, h_mult, sizeof(double) * c.ninst);
+  k_set_scale<<<c.ninst, 32, 0, c.stream>>>(s.d_part, nb, d_mult, c.d_scale);
+  KCHECK(c);
+  k_rescale<<<dim3(grid_for(c.n2), c.ninst), 256, 0, c.stream>>>(const_cast<cplx*>(Vd->d), Vd->is, c.n2, c.d_scale);
+  KCHECK(c);
+  c.h_scale.resize(c.ninst);
+  CK(cudaMemcpyAsync(c.h_scale.data(), c.d_scale, sizeof(double) * c.ninst, cudaMemcpyDeviceToHost, c.stream));
+  CK(cudaStreamSynchronize(c.stream));
+}
+
+void ccsd_guess(Ctx& c) {
+  CcsdState& s = S(c);
+  k_mp2_guess<<<dim3(grid_for(c.namp), c.ninst), 256, 0, c.stream>>>(c.d_T, c.d_D, s.Vd->d, s.Vd->is, c.n1, c.namp);
+  KCHECK(c);
+  ccsd_reset_diis(c);
+  ccsd_energy_of(c, c.d_T, false);
+}
+
+void ccsd_reset_diis(Ctx& c) {
+  CK(cudaMemsetAsync(c.d_diis_state, 0, sizeof(int) * 4 * c.ninst, c.stream));
+  CK(cudaMemsetAsync(c.d_diis_B, 0, sizeof(double) * EXP_MAX_DIIS * EXP_MAX_DIIS * c.ninst, c.stream));
+  CK(cudaMemsetAsync(c.d_stats, 0, sizeof(double) * 8 * c.ninst, c.stream));
+  c.iter_done = 0;
+}
+
+// E of the amplitude vector at `T` (per instance) into stats[1..2].
+void ccsd_energy_of(Ctx& c, const cplx* T, bool skip_frozen) {
+  CcsdState& s = S(c);
+  launch_tau(c, s.d_taun, c.n2, T + c.n1, T, c.namp, s.d_t1i, s.t2tasks.d_tasks, s.t2tasks.d_chunks,
+             s.t2tasks.n_chunks, 1.0, 1.0, -1.0);
+  const int nb = RED_BLOCKS;
+  k_energy_part<<<dim3(nb, c.ninst), RED_THREADS, 0, c.stream>>>(s.Vd->d, s.Vd->is, s.d_taun, c.n2, c.n2,
+                                                                 c.d_diis_state, s.d_part, skip_frozen);
+  KCHECK(c);
+  k_finalize_energy<<<c.ninst, 32, 0, c.stream>>>(s.d_part, nb, c.d_diis_state, c.d_stats, skip_frozen);
+  KCHECK(c);
+}
+
+// ---------------------------------------------------------------------------
+// The right-hand sides R1, R2 of the T1 and T2 equations at the current T.
+static void tau_build(Ctx& c, Tensor& dst, double c0, double c1, double c2) {
+  CcsdState& s = S(c);
+  launch_tau(c, dst.d, dst.is, c.t2.d, c.t1.d, c.namp, s.d_t1i, s.t2tasks.d_tasks, s.t2tasks.d_chunks,
+             s.t2tasks.n_chunks, c0, c1, c2);
+}
+
+static void copy_int(Ctx& c, Tensor& dst, const Tensor* src) {
+  if (src->L.size != dst.L.size) throw ExpError{EXP_EINVAL, "copy between different layouts"};
+  CK(cudaMemcpy2DAsync(dst.d, dst.is * sizeof(cplx), src->d, src->is * sizeof(cplx), dst.L.size * sizeof(cplx),
+                       c.ninst, cudaMemcpyDeviceToDevice, c.stream));
+}
+
+static void copy_t(Ctx& c, Tensor& dst, const Tensor& src) {
+  if (src.L.size != dst.L.size) throw ExpError{EXP_EINVAL, "copy between different layouts"};
+  CK(cudaMemcpy2DAsync(dst.d, dst.is * sizeof(cplx), src.d, src.is * sizeof(cplx), dst.L.size * sizeof(cplx),
+                       c.ninst, cudaMemcpyDeviceToDevice, c.stream));
+}
+
+void ccsd_rhs(Ctx& c) {
+  const int V = SP_VIRT, O = SP_OCC;
+  Tensor& t1 = c.t1;
+  Tensor& t2 = c.t2;
+  Tensor& r1 = c.r1;
+  Tensor& r2 = c.r2;
+  Tensor& tau = *work_tensor(c, "tau", t2.L);
+  Tensor& taut = *work_tensor(c, "taut", t2.L);
+  Tensor& zeta = *work_tensor(c, "zeta", t2.L);
+  Tensor& Fae = *work_tensor(c, "Fae", L2(c, V, +1, V, -1));
+  Tensor& Fmi = *work_tensor(c, "Fmi", L2(c, O, +1, O, -1));
+  Tensor& Fme = *work_tensor(c, "Fme", L2(c, O, +1, V, -1));
+  Tensor& Fp = *work_tensor(c, "Fp", L2(c, V, +1, V, -1));
+  Tensor& Fq = *work_tensor(c, "Fq", L2(c, O, +1, O, -1));
+  Tensor& Wmnij = *work_tensor(c, "Wmnij", L4(c, O, +1, O, +1, O, -1, O, -1, 2));
+  Tensor& Wmbej = *work_tensor(c, "Wemjb", L4(c, V, -1, O, +1, O, -1, V, +1, 2));  // labels "emjb"
+  Tensor& X = *work_tensor(c, "Xamij", L4(c, V, +1, O, +1, O, -1, O, -1, 2));
+  Tensor& Q = *work_tensor(c, "Qaijb", L4(c, V, +1, O, -1, O, -1, V, +1, 2));
+  Tensor& Z = *work_tensor(c, "Zmbji", L4(c, O, +1, V, +1, O, -1, O, -1, 3));
+  CcsdState& s = S(c);
+
+  tau_build(c, tau, 1.0, 1.0, -1.0);
+  tau_build(c, taut, 1.0, 0.5, -0.5);
+  tau_build(c, zeta, 0.5, 1.0, 0.0);
+
+  // F_ae = sum_mf t_m^f <ma||fe> - 1/2 sum_mnf taut_mn^af <mn||ef>       (f_ov = 0, f diagonal)
+  einsum(c, "Fae1", ONE, {nullptr, &OVVV, "mafe"}, {&t1, nullptr, "fm"}, Fae, "ae", false);
+  einsum(c, "Fae2", C(-0.5), {&taut, nullptr, "afmn"}, {nullptr, &OOVV, "mnef"}, Fae, "ae", true);
+  // F_mi = sum_ne t_n^e <mn||ie> + 1/2 sum_nef taut_in^ef <mn||ef>
+  einsum(c, "Fmi1", ONE, {nullptr, &OOOV, "mnie"}, {&t1, nullptr, "en"}, Fmi, "mi", false);
+  einsum(c, "Fmi2", C(0.5), {nullptr, &OOVV, "mnef"}, {&taut, nullptr, "efin"}, Fmi, "mi", true);
+  // F_me = sum_nf t_n^f <mn||ef>
+  einsum(c, "Fme", ONE, {nullptr, &OOVV, "mnef"}, {&t1, nullptr, "fn"}, Fme, "me", false);
+  // W_mnij = <mn||ij> + P(ij) sum_e t_j^e <mn||ie> + 1/2 sum_ef tau_ij^ef <mn||ef>
+  // (factor 1/2 instead of 1/4: it carries the (1/4) tau <mn||ef> part of W_abef too)
+  {
+    const int arg[4] = {0, 1, 2, 3};
+    copy_int(c, Wmnij, integral(c, OOOO, arg, 2));
+  }
+  einsum(c, "Wmnij1", ONE, {nullptr, &OOOV, "mnie"}, {&t1, nullptr, "ej"}, Wmnij, "mnij", true,
+         {{1.0, "mnij"}, {-1.0, "mnji"}});
+  einsum(c, "Wmnij2", C(0.5), {nullptr, &OOVV, "mnef"}, {&tau, nullptr, "efij"}, Wmnij, "mnij", true);
+  // W_mbej = <mb||ej> + sum_f t_j^f <mb||ef> - sum_n t_n^b <mn||ej> - sum_nf zeta_jn^fb <mn||ef>
+  {
+    const int arg[4] = {2, 0, 3, 1};  // storage (e, m, j, b) <- V(m, b, e, j)
+    copy_int(c, Wmbej, integral(c, OVVO, arg, 2));
+  }
+  einsum(c, "Wmbej1", ONE, {nullptr, &OVVV, "mbef"}, {&t1, nullptr, "fj"}, Wmbej, "emjb", true);
+  einsum(c, "Wmbej2", C(-1.0), {nullptr, &OOVO, "mnej"}, {&t1, nullptr, "bn"}, Wmbej, "emjb", true);
+  einsum(c, "Wmbej3", C(-1.0), {nullptr, &OOVV, "mnef"}, {&zeta, nullptr, "fbjn"}, Wmbej, "emjb", true);
+
+  // ---- T1 equation
+  CK(cudaMemset2DAsync(r1.d, r1.is * sizeof(cplx), 0, r1.L.size * sizeof(cplx), c.ninst, c.stream));
+  einsum(c, "R1a", ONE, {&Fae, nullptr, "ae"}, {&t1, nullptr, "ei"}, r1, "ai", true);
+  einsum(c, "R1b", C(-1.0), {&t1, nullptr, "am"}, {&Fmi, nullptr, "mi"}, r1, "ai", true);
+  einsum(c, "R1c", ONE, {&t2, nullptr, "aeim"}, {&Fme, nullptr, "me"}, r1, "ai", true);
+  einsum(c, "R1d", C(-1.0), {nullptr, &OVOV, "naif"}, {&t1, nullptr, "fn"}, r1, "ai", true);
+  einsum(c, "R1e", C(-0.5), {nullptr, &OVVV, "maef"}, {&t2, nullptr, "efim"}, r1, "ai", true);
+  einsum(c, "R1f", C(-0.5), {&t2, nullptr, "aemn"}, {nullptr, &OOVO, "nmei"}, r1, "ai", true);
+
+  // ---- T2 equation
+  copy_int(c, r2, s.Vd);
+  // F'_be = F_be - 1/2 sum_m t_m^b F_me ;  + P(ab) sum_e t_ij^ae F'_be
+  copy_t(c, Fp, Fae);
+  einsum(c, "Fp", C(-0.5), {&t1, nullptr, "bm"}, {&Fme, nullptr, "me"}, Fp, "be", true);
+  einsum(c, "R2a", ONE, {&Fp, nullptr, "be"}, {&t2, nullptr, "aeij"}, r2, "abij", true,
+         {{1.0, "abij"}, {-1.0, "baij"}});
+  // F'_mj = F_mj + 1/2 sum_e t_j^e F_me ;  - P(ij) sum_m t_im^ab F'_mj
+  copy_t(c, Fq, Fmi);
+  einsum(c, "Fq", C(0.5), {&Fme, nullptr, "me"}, {&t1, nullptr, "ej"}, Fq, "mj", true);
+  einsum(c, "R2b", C(-1.0), {&t2, nullptr, "abim"}, {&Fq, nullptr, "mj"}, r2, "abij", true,
+         {{1.0, "abij"}, {-1.0, "abji"}});
+  // hole-hole ladder: 1/2 sum_mn tau_mn^ab W_mnij
+  einsum(c, "R2hh", C(0.5), {&tau, nullptr, "abmn"}, {&Wmnij, nullptr, "mnij"}, r2, "abij", true);
+  // particle-particle ladder: 1/2 sum_ef <ab||ef> tau_ij^ef
+  einsum(c, "R2pp", C(0.5), {nullptr, &VVVV, "abef"}, {&tau, nullptr, "efij"}, r2, "abij", true);
+  // W_abef's t1 term: -1/2 P(ab) sum_m t_m^b X_amij,  X_amij = sum_ef <am||ef> tau_ij^ef
+  einsum(c, "Xamij", ONE, {nullptr, &VOVV, "amef"}, {&tau, nullptr, "efij"}, X, "amij", false);
+  einsum(c, "R2x", C(-0.5), {&X, nullptr, "amij"}, {&t1, nullptr, "bm"}, r2, "abij", true,
+         {{1.0, "abij"}, {-1.0, "baij"}});
+  // ring: P(ij)P(ab) [ sum_me t_im^ae W_mbej - sum_me t_i^e t_m^a <mb||ej> ]
+  einsum(c, "Qring", ONE, {&t2, nullptr, "aeim"}, {&Wmbej, nullptr, "emjb"}, Q, "aijb", false);
+  einsum(c, "Zmbji", ONE, {nullptr, &OVVO, "mbej"}, {&t1, nullptr, "ei"}, Z, "mbji", false);
+  einsum(c, "Qt1t1", C(-1.0), {&t1, nullptr, "am"}, {&Z, nullptr, "mbji"}, Q, "aijb", true);
+  permute_into(c, "R2ring", r2, "abij", Q, "aijb", true,
+               {{1.0, "abij"}, {-1.0, "abji"}, {-1.0, "baij"}, {1.0, "baji"}});
+  // + P(ij) sum_e t_i^e <ab||ej>
+  einsum(c, "R2c", ONE, {nullptr, &VVVO, "abej"}, {&t1, nullptr, "ei"}, r2, "abij", true,
+         {{1.0, "abij"}, {-1.0, "abji"}});
+  // - P(ab) sum_m t_m^a <mb||ij>
+  einsum(c, "R2d", C(-1.0), {&t1, nullptr, "am"}, {nullptr, &OVOO, "mbij"}, r2, "abij", true,
+         {{1.0, "abij"}, {-1.0, "baij"}});
+}
+
+// copy the newest t_new of every (active) instance into dst (namp-strided)
+__global__ void k_copy_newest(cplx* __restrict__ dst, const cplx* __restrict__ Tn, int64_t namp, int dim,
+                              const int* __restrict__ state) {
+  const int inst = blockIdx.y;
+  const int* st = state + inst * 4;
+  if (st[2]) return;
+  const int D = dim > 0 ? dim : 1;
+  const int head = dim > 0 ? st[1] : 0;
+  const cplx* src = Tn + (int64_t(inst) * D + head) * namp;
+  for (int64_t k = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; k < namp; k += int64_t(gridDim.x) * blockDim.x)
+    dst[int64_t(inst) * namp + k] = src[k];
+}
+
+void copy_newest(Ctx& c, cplx* dst) {
+  k_copy_newest<<<dim3(grid_for(c.namp), c.ninst), 256, 0, c.stream>>>(dst, c.d_diis_t, c.namp, c.cfg.diis_dim,
+                                                                      c.d_diis_state);
+  KCHECK(c);
+}
+
+// One full iteration: RHS, update, residual, energy, DIIS.
+void ccsd_iteration(Ctx& c) {
+  CcsdState& s = S(c);
+  ccsd_rhs(c);
+  const int dim = c.cfg.diis_dim;
+  const int D = std::max(dim, 1);
+  const int nb = RED_BLOCKS;
+  k_update<<<dim3(nb, c.ninst), RED_THREADS, 0, c.stream>>>(c.d_R, c.d_D, c.d_T, c.d_diis_t, c.d_diis_e, c.namp,
+                                                            dim, c.d_diis_state, s.d_part);
+  KCHECK(c);
+  k_finalize_update<<<c.ninst, 32, 0, c.stream>>>(s.d_part, nb, c.d_diis_state, c.d_stats, dim, c.cfg.conv_tol);
+  KCHECK(c);
+  if (dim > 0) {
+    k_diis_dots<<<dim3(nb, c.ninst), RED_THREADS, 0, c.stream>>>(c.d_diis_e, c.namp, dim, c.d_diis_state, s.d_part);
+    KCHECK(c);
+    k_diis_solve<<<c.ninst, 32, 0, c.stream>>>(s.d_part, nb, dim, c.d_diis_state, c.d_diis_B, s.d_coef, c.d_stats);
+    KCHECK(c);
+  }
+  // energy of t_new: gather the newest t_new of every instance into R (free by
+  // now), then tau + dot
+  copy_newest(c, c.d_R);
+  ccsd_energy_of(c, c.d_R, true);
+  k_extrapolate<<<dim3(grid_for(c.namp), c.ninst), 256, 0, c.stream>>>(c.d_T, c.d_diis_t, c.namp, dim, s.d_coef,
+                                                                       c.d_diis_state);
+  KCHECK(c);
+  k_freeze<<<(c.ninst + 127) / 128, 128, 0, c.stream>>>(c.d_diis_state, c.ninst);
+  KCHECK(c);
+}
+
+
+// Dense <-> blocked amplitude copies: t1[i][a], t2[i][j][a][b].
+__global__ void k_dense_io(cplx* __restrict__ T, int64_t off, int64_t namp, cplx* __restrict__ dense,
+                           const GenTask* __restrict__ tasks, const ChunkRef* __restrict__ chunks, int rank,
+                           int no, int nv, int to_dense) {
+  const ChunkRef ch = chunks[blockIdx.x];
+  const GenTask Tk = tasks[ch.task];
+  const int64_t end = min(ch.start + (int64_t)4096, Tk.count);
+  for (int64_t e = ch.start + threadIdx.x; e < end; e += blockDim.x) {
+    int64_t r = e;
+    int i[4];
+    i[3] = int(r % Tk.n[3]); r /= Tk.n[3];
+    i[2] = int(r % Tk.n[2]); r /= Tk.n[2];
+    i[1] = int(r % Tk.n[1]);
+    i[0] = int(r / Tk.n[1]);
+    const int64_t p = off + Tk.base + i[0] * Tk.st[0] + i[1] * Tk.st[1] + i[2] * Tk.st[2] + i[3] * Tk.st[3];
+    int64_t dp;
+    if (rank == 2) {  // slots (a, i) in dims 2, 3
+      const int a = Tk.g0[2] + i[2] - no, ii = Tk.g0[3] + i[3];
+      dp = int64_t(ii) * nv + a;
+    } else {  // slots (a, b, i, j)
+      const int a = Tk.g0[0] + i[0] - no, b = Tk.g0[1] + i[1] - no;
+      const int ii = Tk.g0[2] + i[2], jj = Tk.g0[3] + i[3];
+      dp = ((int64_t(ii) * no + jj) * nv + a) * nv + b;
+    }
+    if (to_dense) dense[dp] = T[p];
+    else T[p] = dense[dp];
+  }
+}
+
+void ccsd_dense_io(Ctx& c, int inst, cplx* t1d, cplx* t2d, bool to_dense) {
+  CcsdState& s = S(c);
+  if (!s.t1tasks.n_chunks && c.n1) {
+    std::vector<GenTask> tk;
+    std::vector<ChunkRef> ch;
+    gen_tasks(c, c.t1.L, tk, ch);
+    s.t1tasks.d_tasks = (GenTask*)c.dalloc(tk.size() * sizeof(GenTask));
+    s.t1tasks.d_chunks = (ChunkRef*)c.dalloc(ch.size() * sizeof(ChunkRef));
+    upload(c, s.t1tasks.d_tasks, tk.data(), tk.size() * sizeof(GenTask));
+    upload(c, s.t1tasks.d_chunks, ch.data(), ch.size() * sizeof(ChunkRef));
+    s.t1tasks.n_chunks = int(ch.size());
+  }
+  if (to_dense) {
+    CK(cudaMemsetAsync(t1d, 0, sizeof(cplx) * c.no * c.nv, c.stream));
+    CK(cudaMemsetAsync(t2d, 0, sizeof(cplx) * size_t(c.no) * c.no * c.nv * c.nv, c.stream));
+  }
+  const int64_t off = int64_t(inst) * c.namp;
+  if (s.t1tasks.n_chunks) {
+    k_dense_io<<<s.t1tasks.n_chunks, 256, 0, c.stream>>>(c.d_T, off, c.namp, t1d, s.t1tasks.d_tasks,
+                                                         s.t1tasks.d_chunks, 2, c.no, c.nv, to_dense);
+    KCHECK(c);
+  }
+  if (s.t2tasks.n_chunks) {
+    k_dense_io<<<s.t2tasks.n_chunks, 256, 0, c.stream>>>(c.d_T, off + c.n1, c.namp, t2d, s.t2tasks.d_tasks,
+                                                         s.t2tasks.d_chunks, 4, c.no, c.nv, to_dense);
+    KCHECK(c);
+  }
+}

@@ -1,0 +1,15 @@
+// CCSD (0h,0p) driver entry points used by the C ABI.
+#pragma once
+#include "engine.h"
+
+Layout L4(Ctx& c, int s0, int g0, int s1, int g1, int s2, int g2, int s3, int g3, int nrow);
+Layout L2(Ctx& c, int s0, int g0, int s1, int g1);
+void ccsd_setup(Ctx& c);
+void ccsd_release(Ctx& c);
+void ccsd_init_integrals(Ctx& c, const double* h_mult);
+void ccsd_guess(Ctx& c);
+void ccsd_reset_diis(Ctx& c);
+void ccsd_energy_of(Ctx& c, const cplx* T, bool skip_frozen);
+void ccsd_rhs(Ctx& c);
+void ccsd_iteration(Ctx& c);
+void ccsd_dense_io(Ctx& c, int inst, cplx* t1_dense, cplx* t2_dense, bool to_dense);

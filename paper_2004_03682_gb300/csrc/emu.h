@@ -1,0 +1,11 @@
+// Split-precision emulation of complex-FP64 GEMM on the BF16 tensor cores
+// (tcgen05), used for the large CCSD contractions.
+#pragma once
+#include "engine.h"
+
+bool emu_wanted(Ctx& c, const GemmPlan& g, const std::string& site);
+EmuPlan* emu_plan(Ctx& c, const GemmPlan& g, const Tensor* A, const Tensor* B, bool a_const,
+                  bool b_const);
+void emu_run(Ctx& c, EmuPlan* p, const GemmPlan& g, const cplx* A, const cplx* B, cplx* C,
+             int64_t ais, int64_t bis, int64_t cis, cplx alpha, bool beta);
+void emu_release(Ctx& c);

@@ -1,0 +1,454 @@
+// Host-side planning for symmetry-blocked tensors: layouts (DPD blocks,
+// Sec. II.C), sub-block enumeration, permute plans and the TTGT einsum
+// planner (Sec. II.B: permute operands into supermatrices, one grouped GEMM
+// over all symmetry blocks (Fig. "mult"), permute the result back).
+#include <algorithm>
+#include <cstdio>
+#include <sstream>
+
+#include "engine.h"
+#include "emu.h"
+
+static int64_t ipow(int G, int k) {
+  int64_t r = 1;
+  while (k-- > 0) r *= G;
+  return r;
+}
+static inline int imod(int a, int G) { return ((a % G) + G) % G; }
+
+std::string Layout::key() const {
+  std::ostringstream s;
+  s << rank << ":" << nrow << ":";
+  for (int k = 0; k < rank; ++k) s << sp[k] << (sg[k] > 0 ? '+' : '-');
+  return s.str();
+}
+
+void build_layout(Layout& L, const std::vector<Space>& S, int G) {
+  L.G = G;
+  const int nr = L.nrow, nc = L.rank - L.nrow;
+  L.rows.assign(G, 0);
+  L.cols.assign(G, 0);
+  const int64_t NR = ipow(G, nr), NC = ipow(G, nc);
+  L.rtup.assign(NR, 0);
+  L.ctup.assign(NC, 0);
+  for (int64_t code = 0; code < NR; ++code) {
+    int64_t c = code;
+    int irr[EXP_MAX_RANK] = {0, 0, 0, 0};
+    for (int k = nr - 1; k >= 0; --k) { irr[k] = int(c % G); c /= G; }
+    int sum = 0;
+    int64_t sz = 1;
+    for (int k = 0; k < nr; ++k) { sum += L.sg[k] * irr[k]; sz *= S[L.sp[k]].cnt[irr[k]]; }
+    const int g = imod(sum, G);
+    L.rtup[code] = L.rows[g];
+    L.rows[g] += sz;
+  }
+  for (int64_t code = 0; code < NC; ++code) {
+    int64_t c = code;
+    int irr[EXP_MAX_RANK] = {0, 0, 0, 0};
+    for (int k = nc - 1; k >= 0; --k) { irr[k] = int(c % G); c /= G; }
+    int sum = 0;
+    int64_t sz = 1;
+    for (int k = 0; k < nc; ++k) { sum += L.sg[nr + k] * irr[k]; sz *= S[L.sp[nr + k]].cnt[irr[k]]; }
+    const int g = imod(-sum, G);
+    L.ctup[code] = L.cols[g];
+    L.cols[g] += sz;
+  }
+  L.blk_off.assign(G, 0);
+  int64_t off = 0;
+  for (int g = 0; g < G; ++g) { L.blk_off[g] = off; off += L.rows[g] * L.cols[g]; }
+  L.size = off;
+}
+
+Layout make_layout(const std::vector<Space>& S, int G, int rank, const int* sp, const int* sg,
+                   int nrow) {
+  Layout L;
+  L.rank = rank;
+  L.nrow = nrow;
+  for (int k = 0; k < rank; ++k) { L.sp[k] = sp[k]; L.sg[k] = sg[k]; }
+  build_layout(L, S, G);
+  return L;
+}
+
+int64_t layout_count(const Layout& L, const std::vector<Space>&) { return L.size; }
+
+// Every allowed sub-block, in tuple-code order.  Dims are padded to 4 with the
+// padding in front (dim 3 is always the innermost storage slot).
+void enumerate_blocks(const Layout& L, const std::vector<Space>& S, std::vector<SubBlock>& out) {
+  const int G = L.G, r = L.rank, nr = L.nrow;
+  out.clear();
+  const int64_t NT = ipow(G, r);
+  for (int64_t code = 0; code < NT; ++code) {
+    int64_t c = code;
+    int irr[EXP_MAX_RANK] = {0, 0, 0, 0};
+    for (int k = r - 1; k >= 0; --k) { irr[k] = int(c % G); c /= G; }
+    int sum = 0, rsum = 0;
+    for (int k = 0; k < r; ++k) {
+      sum += L.sg[k] * irr[k];
+      if (k < nr) rsum += L.sg[k] * irr[k];
+    }
+    if (imod(sum, G) != 0) continue;
+    SubBlock b;
+    int64_t cnt = 1;
+    for (int k = 0; k < r; ++k) { b.irr[k] = irr[k]; b.n[k] = S[L.sp[k]].cnt[irr[k]]; cnt *= b.n[k]; }
+    for (int k = r; k < EXP_MAX_RANK; ++k) { b.irr[k] = 0; b.n[k] = 1; }
+    b.count = cnt;
+    const int g = imod(rsum, G);
+    int64_t rcode = 0, ccode = 0;
+    for (int k = 0; k < nr; ++k) rcode = rcode * G + irr[k];
+    for (int k = nr; k < r; ++k) ccode = ccode * G + irr[k];
+    b.base = L.blk_off[g] + L.rtup[rcode] * L.cols[g] + L.ctup[ccode];
+    int64_t s = 1;
+    for (int k = r - 1; k >= nr; --k) { b.st[k] = s; s *= b.n[k]; }
+    s = L.cols[g];
+    for (int k = nr - 1; k >= 0; --k) { b.st[k] = s; s *= b.n[k]; }
+    for (int k = r; k < EXP_MAX_RANK; ++k) b.st[k] = 0;
+    out.push_back(b);
+  }
+}
+
+static const int64_t kChunk = 4096;
+
+static void add_chunks(std::vector<ChunkRef>& chunks, int task, int64_t count) {
+  for (int64_t s = 0; s < count; s += kChunk) chunks.push_back(ChunkRef{task, 0, s});
+}
+
+void* Ctx::dalloc(size_t bytes) {
+  if (bytes == 0) bytes = 256;
+  void* p = alloc.alloc(bytes, alloc.user);
+  if (!p) throw ExpError{EXP_ENOMEM, "allocator returned NULL for " + std::to_string(bytes) + " bytes"};
+  owned.push_back(DevBuf{p, bytes});
+  return p;
+}
+
+void Ctx::dfree_all() {
+  for (auto& b : owned) alloc.free(b.p, alloc.user);
+  owned.clear();
+}
+
+void upload(Ctx& c, void* dst, const void* src, size_t bytes) {
+  if (!bytes) return;
+  CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c.stream));
+  // host buffers are temporaries: make the copy complete before they go away
+  CK(cudaStreamSynchronize(c.stream));
+}
+
+Tensor* new_tensor(Ctx& c, const Layout& L, bool zero) {
+  Tensor* t = new Tensor();
+  t->L = L;
+  const size_t bytes = sizeof(cplx) * size_t(std::max<int64_t>(L.size, 1)) * c.ninst;
+  t->d = (cplx*)c.dalloc(bytes);
+  t->is = std::max<int64_t>(L.size, 1);
+  if (zero) CK(cudaMemsetAsync(t->d, 0, bytes, c.stream));
+  return t;
+}
+
+Tensor* work_tensor(Ctx& c, const std::string& name, const Layout& L) {
+  auto it = c.work.find(name);
+  if (it != c.work.end()) return it->second.get();
+  Tensor* t = new_tensor(c, L, true);
+  c.work[name].reset(t);
+  return t;
+}
+
+void gen_tasks(Ctx& c, const Layout& L, std::vector<GenTask>& tasks, std::vector<ChunkRef>& chunks) {
+  std::vector<SubBlock> sb;
+  enumerate_blocks(L, c.spaces, sb);
+  const int r = L.rank, pad = EXP_MAX_RANK - r;
+  for (auto& b : sb) {
+    if (b.count == 0) continue;
+    GenTask t;
+    t.base = b.base;
+    t.count = b.count;
+    for (int d = 0; d < EXP_MAX_RANK; ++d) { t.n[d] = 1; t.st[d] = 0; t.g0[d] = 0; }
+    for (int k = 0; k < r; ++k) {
+      const Space& s = c.spaces[L.sp[k]];
+      t.n[pad + k] = b.n[k];
+      t.st[pad + k] = b.st[k];
+      t.g0[pad + k] = s.gbase + s.off[b.irr[k]];
+    }
+    add_chunks(chunks, int(tasks.size()), t.count);
+    tasks.push_back(t);
+  }
+}
+
+// Integral tensors: V(p,q,r,s) generated directly in the requested storage
+// order (slot k holds V argument arg[k]) and row/column split; cached.
+const Tensor* integral(Ctx& c, const IntRef& v, const int arg[4], int nrow) {
+  std::ostringstream key;
+  key << v.sp[0] << v.sp[1] << v.sp[2] << v.sp[3] << "|" << arg[0] << arg[1] << arg[2] << arg[3]
+      << "|" << nrow;
+  auto it = c.int_cache.find(key.str());
+  if (it != c.int_cache.end()) return it->second.get();
+  if (!c.have_integrals) throw ExpError{EXP_ESTATE, "integrals requested before exp_init_integrals"};
+  int sp[4], sg[4], map[4];
+  for (int k = 0; k < 4; ++k) {
+    sp[k] = v.sp[arg[k]];
+    sg[k] = arg[k] < 2 ? 1 : -1;
+    map[arg[k]] = k;
+  }
+  Layout L = make_layout(c.spaces, c.G, 4, sp, sg, nrow);
+  Tensor* t = new_tensor(c, L, true);
+  std::vector<GenTask> tasks;
+  std::vector<ChunkRef> chunks;
+  gen_tasks(c, L, tasks, chunks);
+  if (!chunks.empty()) {
+    GenTask* dt = (GenTask*)c.dalloc(tasks.size() * sizeof(GenTask));
+    ChunkRef* dc = (ChunkRef*)c.dalloc(chunks.size() * sizeof(ChunkRef));
+    upload(c, dt, tasks.data(), tasks.size() * sizeof(GenTask));
+    upload(c, dc, chunks.data(), chunks.size() * sizeof(ChunkRef));
+    launch_generate(c, t->d, t->is, dt, dc, int(chunks.size()), map);
+  }
+  c.int_cache[key.str()].reset(t);
+  return t;
+}
+
+// ---------------------------------------------------------------------------
+// Permute plans.  dst[dl] (+)= sum_t coef_t * src[sigma_t], where term t is a
+// relabelling string ts (a permutation of dl): the src slot labelled l takes
+// the value of the dst slot labelled sigma_t(l), sigma_t(dl[k]) = ts[k].
+static PermPlan make_perm_plan(Ctx& c, const Layout& D, const char* dl, const Layout& S,
+                               const char* sl, const std::vector<std::string>& terms) {
+  const int r = D.rank;
+  if (S.rank != r) throw ExpError{EXP_EINVAL, "permute rank mismatch"};
+  std::vector<SubBlock> db, sb;
+  enumerate_blocks(D, c.spaces, db);
+  enumerate_blocks(S, c.spaces, sb);
+  const int G = c.G;
+  std::vector<int> sidx(size_t(ipow(G, r)), -1);
+  for (size_t k = 0; k < sb.size(); ++k) {
+    int64_t code = 0;
+    for (int s = 0; s < r; ++s) code = code * G + sb[k].irr[s];
+    sidx[code] = int(k);
+  }
+  const int nt = int(terms.size());
+  // pos[t][k]: dst position feeding src slot k under term t
+  int pos[EXP_MAX_TERMS][EXP_MAX_RANK];
+  for (int t = 0; t < nt; ++t) {
+    const std::string& ts = terms[t];
+    for (int k = 0; k < r; ++k) {
+      // sigma(l) = ts[j] where dl[j] == l
+      const char* pl = strchr(dl, sl[k]);
+      if (!pl) throw ExpError{EXP_EINVAL, std::string("permute label missing: ") + sl[k]};
+      const char target = ts[pl - dl];
+      const char* pd = strchr(dl, target);
+      if (!pd) throw ExpError{EXP_EINVAL, "bad permute term"};
+      pos[t][k] = int(pd - dl);
+      if (S.sg[k] != D.sg[pos[t][k]] || S.sp[k] != D.sp[pos[t][k]])
+        throw ExpError{EXP_EINVAL, "permute space/sign mismatch"};
+    }
+  }
+  const int pad = EXP_MAX_RANK - r;
+  std::vector<PermTask> tasks;
+  std::vector<ChunkRef> chunks;
+  for (auto& b : db) {
+    if (b.count == 0) continue;
+    PermTask T;
+    memset(&T, 0, sizeof(T));
+    T.dst = b.base;
+    T.count = b.count;
+    for (int d = 0; d < 4; ++d) { T.n[d] = 1; T.dst_st[d] = 0; }
+    for (int k = 0; k < r; ++k) { T.n[pad + k] = b.n[k]; T.dst_st[pad + k] = b.st[k]; }
+    for (int t = 0; t < nt; ++t) {
+      int64_t code = 0;
+      for (int k = 0; k < r; ++k) code = code * G + b.irr[pos[t][k]];
+      const int si = sidx[code];
+      if (si < 0) throw ExpError{EXP_EINVAL, "permute source block missing"};
+      const SubBlock& s = sb[si];
+      T.src[t] = s.base;
+      for (int d = 0; d < 4; ++d) T.src_st[t][d] = 0;
+      for (int k = 0; k < r; ++k) T.src_st[t][pad + pos[t][k]] = s.st[k];
+    }
+    add_chunks(chunks, int(tasks.size()), T.count);
+    tasks.push_back(T);
+  }
+  PermPlan p;
+  p.n_terms = nt;
+  p.n_chunks = int(chunks.size());
+  if (!tasks.empty()) {
+    p.d_tasks = (PermTask*)c.dalloc(tasks.size() * sizeof(PermTask));
+    p.d_chunks = (ChunkRef*)c.dalloc(chunks.size() * sizeof(ChunkRef));
+    upload(c, p.d_tasks, tasks.data(), tasks.size() * sizeof(PermTask));
+    upload(c, p.d_chunks, chunks.data(), chunks.size() * sizeof(ChunkRef));
+  }
+  return p;
+}
+
+static Layout relayout(Ctx& c, const Layout& S, const char* sl, const std::string& order, int nrow) {
+  int sp[4], sg[4];
+  const int r = int(order.size());
+  for (int k = 0; k < r; ++k) {
+    const char* p = strchr(sl, order[k]);
+    sp[k] = S.sp[p - sl];
+    sg[k] = S.sg[p - sl];
+  }
+  return make_layout(c.spaces, c.G, r, sp, sg, nrow);
+}
+
+static std::vector<std::string> term_strings(const char* dl,
+                                             const std::vector<std::pair<double, std::string>>& terms,
+                                             std::vector<double>& coefs) {
+  std::vector<std::string> ts;
+  coefs.clear();
+  if (terms.empty()) {
+    ts.push_back(dl);
+    coefs.push_back(1.0);
+  } else {
+    for (auto& t : terms) { ts.push_back(t.second); coefs.push_back(t.first); }
+  }
+  if (ts.size() > EXP_MAX_TERMS) throw ExpError{EXP_EINVAL, "too many permute terms"};
+  return ts;
+}
+
+void permute_into(Ctx& c, const std::string& site, Tensor& dst, const char* dl, const Tensor& src,
+                  const char* sl, bool accumulate, std::vector<std::pair<double, std::string>> terms) {
+  const std::string key = "P:" + site;
+  auto it = c.perm_cache.find(key);
+  std::vector<double> coefs;
+  auto ts = term_strings(dl, terms, coefs);
+  if (it == c.perm_cache.end()) {
+    PermPlan p = make_perm_plan(c, dst.L, dl, src.L, sl, ts);
+    it = c.perm_cache.emplace(key, p).first;
+  }
+  cplx co[EXP_MAX_TERMS];
+  for (size_t k = 0; k < coefs.size(); ++k) co[k] = make_double2(coefs[k], 0.0);
+  launch_permute(c, it->second, dst.d, src.d, dst.is, src.is, co, accumulate, false);
+}
+
+// ---------------------------------------------------------------------------
+// TTGT einsum: C[cl] (+)= alpha * sum_K A[al] B[bl], optionally antisymmetrised
+// on output by the relabelling terms.  Operands are permuted into the
+// supermatrices A'(FA|K), B'(K|FB) unless they already are, integrals are
+// generated in the needed layout once, and the product runs as one grouped GEMM
+// over the symmetry blocks (all instances).
+static GemmPlan make_gemm_plan(Ctx& c, const Layout& A, const Layout& B, const Layout& C) {
+  GemmPlan g;
+  int tile0 = 0;
+  for (int q = 0; q < c.G; ++q) {
+    const int64_t M = A.rows[q], K = A.cols[q], N = B.cols[q];
+    if (B.rows[q] != K || C.rows[q] != M || C.cols[q] != N)
+      throw ExpError{EXP_EINVAL, "gemm block shape mismatch"};
+    if (M == 0 || N == 0) continue;
+    GemmProb p;
+    p.a = A.blk_off[q];
+    p.b = B.blk_off[q];
+    p.c = C.blk_off[q];
+    p.M = int32_t(M);
+    p.N = int32_t(N);
+    p.K = int32_t(K);
+    p.tiles_n = int32_t((N + 63) / 64);
+    p.tile0 = tile0;
+    tile0 += int32_t((M + 63) / 64) * p.tiles_n;
+    g.flops_mac += M * N * K;
+    g.h_probs.push_back(p);
+  }
+  g.n_probs = int(g.h_probs.size());
+  g.n_tiles = tile0;
+  if (g.n_probs) {
+    g.d_probs = (GemmProb*)c.dalloc(g.h_probs.size() * sizeof(GemmProb));
+    upload(c, g.d_probs, g.h_probs.data(), g.h_probs.size() * sizeof(GemmProb));
+  }
+  return g;
+}
+
+static const Tensor* prepare_operand(Ctx& c, const std::string& site, const Operand& op,
+                                     const std::string& order, int nrow, Tensor& scratch,
+                                     PermPlan& plan, bool& permuted) {
+  permuted = false;
+  if (op.v) {
+    int arg[4];
+    for (int k = 0; k < 4; ++k) {
+      const char* p = strchr(op.labels, order[k]);
+      arg[k] = int(p - op.labels);
+    }
+    return integral(c, *op.v, arg, nrow);
+  }
+  const Tensor* t = op.t;
+  if (order == op.labels && t->L.nrow == nrow) return t;
+  Layout L = relayout(c, t->L, op.labels, order, nrow);
+  Tensor* s = new_tensor(c, L, false);
+  scratch = *s;
+  delete s;
+  std::vector<std::string> ts{order};
+  plan = make_perm_plan(c, L, order.c_str(), t->L, op.labels, ts);
+  permuted = true;
+  return &scratch;
+}
+
+void einsum(Ctx& c, const std::string& site, cplx alpha, Operand A, Operand B, Tensor& C,
+            const char* cl, bool accumulate, std::vector<std::pair<double, std::string>> terms) {
+  auto it = c.plans.find(site);
+  EinsumPlan* P;
+  if (it == c.plans.end()) {
+    P = new EinsumPlan();
+    c.plans[site].reset(P);
+    const std::string al = A.labels, bl = B.labels, clab = cl;
+    std::string K, FA, FB;
+    for (char x : al)
+      if (bl.find(x) != std::string::npos && clab.find(x) == std::string::npos) K += x;
+    for (char x : al)
+      if (K.find(x) == std::string::npos) FA += x;
+    for (char x : bl)
+      if (K.find(x) == std::string::npos) FB += x;
+    if (FA.size() + FB.size() != clab.size()) throw ExpError{EXP_EINVAL, "einsum labels: " + site};
+    // contracted labels must meet with opposite signs
+    const std::string ordA = FA + K, ordB = K + FB;
+    const Tensor* Ap = prepare_operand(c, site, A, ordA, int(FA.size()), P->A2, P->pA, P->permA);
+    const Tensor* Bp = prepare_operand(c, site, B, ordB, int(K.size()), P->B2, P->pB, P->permB);
+    for (size_t k = 0; k < K.size(); ++k) {
+      if (Ap->L.sg[FA.size() + k] != -Bp->L.sg[k] || Ap->L.sp[FA.size() + k] != Bp->L.sp[k])
+        throw ExpError{EXP_EINVAL, "einsum contracted label sign/space mismatch: " + site};
+    }
+    P->A = A.v ? Ap : (P->permA ? &P->A2 : A.t);
+    P->B = B.v ? Bp : (P->permB ? &P->B2 : B.t);
+    // result supermatrix C'(FA|FB)
+    const std::string ordC = FA + FB;
+    std::vector<double> coefs;
+    auto ts = term_strings(cl, terms, coefs);
+    const bool identity = terms.empty() && ordC == clab && C.L.nrow == int(FA.size());
+    if (identity) {
+      P->permC = false;
+      P->gemm_beta = accumulate;
+      P->g = make_gemm_plan(c, P->A->L, P->B->L, C.L);
+    } else {
+      int sp[4], sg[4];
+      for (size_t k = 0; k < FA.size(); ++k) { sp[k] = P->A->L.sp[k]; sg[k] = P->A->L.sg[k]; }
+      for (size_t k = 0; k < FB.size(); ++k) {
+        sp[FA.size() + k] = P->B->L.sp[K.size() + k];
+        sg[FA.size() + k] = P->B->L.sg[K.size() + k];
+      }
+      Layout LC = make_layout(c.spaces, c.G, int(ordC.size()), sp, sg, int(FA.size()));
+      Tensor* s = new_tensor(c, LC, false);
+      P->C2 = *s;
+      delete s;
+      P->permC = true;
+      P->gemm_beta = false;
+      P->g = make_gemm_plan(c, P->A->L, P->B->L, LC);
+      // output permute: C[cl] (+)= sum coef * C'[ordC relabelled]
+      P->pC = make_perm_plan(c, C.L, cl, LC, ordC.c_str(), ts);
+    }
+    for (size_t k = 0; k < coefs.size(); ++k) P->cterms[k] = make_double2(coefs[k], 0.0);
+    P->alpha = alpha;
+    P->emulate = emu_wanted(c, P->g, site);
+    if (P->emulate) P->emu = emu_plan(c, P->g, P->A, P->B, A.v != nullptr, B.v != nullptr);
+  } else {
+    P = it->second.get();
+  }
+  // execute
+  if (P->permA) {
+    cplx one = make_double2(1, 0);
+    launch_permute(c, P->pA, P->A2.d, A.t->d, P->A2.is, A.t->is, &one, false, false);
+  }
+  if (P->permB) {
+    cplx one = make_double2(1, 0);
+    launch_permute(c, P->pB, P->B2.d, B.t->d, P->B2.is, B.t->is, &one, false, false);
+  }
+  Tensor* Cg = P->permC ? &P->C2 : &C;
+  if (P->emulate)
+    emu_run(c, P->emu, P->g, P->A->d, P->B->d, Cg->d, P->A->is, P->B->is, Cg->is, alpha,
+            P->gemm_beta);
+  else
+    launch_gemm_fp64(c, P->g, P->A->d, P->B->d, Cg->d, P->A->is, P->B->is, Cg->is, alpha,
+                     P->gemm_beta);
+  if (P->permC)
+    launch_permute(c, P->pC, C.d, P->C2.d, C.is, P->C2.is, P->cterms, accumulate, false);
+}

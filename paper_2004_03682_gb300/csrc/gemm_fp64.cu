@@ -1,0 +1,93 @@
+// Plain complex-FP64 grouped GEMM: step 3 of the TTGT list (Sec. II.B), all
+// symmetry blocks and instances of one contraction in one launch (the block
+// loop of Fig. "mult" flattened into a tile list).  Row-major operands,
+// C[MxN] = alpha A[MxK] B[KxN] (+ C).  SIMT FP64 FMA: GB300's FP64 rate is the
+// roofline for this path.
+#include "engine.h"
+
+#define GT_M 64
+#define GT_N 64
+#define GT_K 8
+
+__global__ void __launch_bounds__(256) k_gemm_fp64(const GemmProb* __restrict__ probs, int n_probs,
+                                                   const cplx* __restrict__ A,
+                                                   const cplx* __restrict__ B, cplx* __restrict__ C,
+                                                   int64_t ais, int64_t bis, int64_t cis,
+                                                   cplx alpha, int beta) {
+  __shared__ cplx As[GT_K][GT_M];
+  __shared__ cplx Bs[GT_K][GT_N];
+  const int tile = blockIdx.x;
+  int pi = 0;
+  while (pi + 1 < n_probs && probs[pi + 1].tile0 <= tile) ++pi;
+  const GemmProb P = probs[pi];
+  const int lt = tile - P.tile0;
+  const int m0 = (lt / P.tiles_n) * GT_M, n0 = (lt % P.tiles_n) * GT_N;
+  A += blockIdx.y * ais + P.a;
+  B += blockIdx.y * bis + P.b;
+  C += blockIdx.y * cis + P.c;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  double accr[4][4], acci[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) accr[i][j] = acci[i][j] = 0.0;
+  for (int k0 = 0; k0 < P.K; k0 += GT_K) {
+    // A tile: 64 x 8 -> 512 elements, 2 per thread
+#pragma unroll
+    for (int l = 0; l < 2; ++l) {
+      const int e = threadIdx.x + l * 256;
+      const int mm = e >> 3, kk = e & 7;
+      const int gm = m0 + mm, gk = k0 + kk;
+      As[kk][mm] = (gm < P.M && gk < P.K) ? A[int64_t(gm) * P.K + gk] : make_double2(0, 0);
+    }
+#pragma unroll
+    for (int l = 0; l < 2; ++l) {
+      const int e = threadIdx.x + l * 256;
+      const int kk = e >> 6, nn = e & 63;
+      const int gk = k0 + kk, gn = n0 + nn;
+      Bs[kk][nn] = (gk < P.K && gn < P.N) ? B[int64_t(gk) * P.N + gn] : make_double2(0, 0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GT_K; ++kk) {
+      cplx a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          accr[i][j] = fma(a[i].x, b[j].x, accr[i][j]);
+          accr[i][j] = fma(-a[i].y, b[j].y, accr[i][j]);
+          acci[i][j] = fma(a[i].x, b[j].y, acci[i][j]);
+          acci[i][j] = fma(a[i].y, b[j].x, acci[i][j]);
+        }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int gm = m0 + ty + 16 * i;
+    if (gm >= P.M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gn = n0 + tx + 16 * j;
+      if (gn >= P.N) continue;
+      double vr = alpha.x * accr[i][j] - alpha.y * acci[i][j];
+      double vi = alpha.x * acci[i][j] + alpha.y * accr[i][j];
+      cplx* dp = C + int64_t(gm) * P.N + gn;
+      if (beta) { const cplx o = *dp; vr += o.x; vi += o.y; }
+      *dp = make_double2(vr, vi);
+    }
+  }
+}
+
+void launch_gemm_fp64(Ctx& c, const GemmPlan& g, const cplx* A, const cplx* B, cplx* C, int64_t ais,
+                      int64_t bis, int64_t cis, cplx alpha, bool beta) {
+  if (g.n_tiles == 0) return;
+  k_gemm_fp64<<<dim3(g.n_tiles, c.ninst), 256, 0, c.stream>>>(g.d_probs, g.n_probs, A, B, C, ais, bis,
+                                                              cis, alpha, beta);
+  KCHECK(c);
+}

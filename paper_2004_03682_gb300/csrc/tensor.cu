@@ -1,0 +1,244 @@
+// Device kernels on symmetry-blocked tensors: the permute ("tensor
+// transposition", steps 1, 2 and 4 of the TTGT list in Sec. II.B), the
+// integral generator (step I of the flowchart, Sec. II.B, writing the
+// synthetic Hamiltonian of Eq. (ham) straight into blocked layouts), the
+// energy denominators of Eq. (amplitudes), and the tau builders.
+#include "engine.h"
+
+#define EXP_CHUNK 4096
+
+struct Coefs {
+  cplx c[EXP_MAX_TERMS];
+};
+
+// Each CTA handles one chunk of one sub-block task.  Elements are walked in
+// destination order (dim 3 innermost, stride 1 in dst) so that stores are
+// coalesced; sources are gathered through the task's strides.
+template <int NT>
+__global__ void __launch_bounds__(256) k_permute(const PermTask* __restrict__ tasks,
+                                                 const ChunkRef* __restrict__ chunks,
+                                                 cplx* __restrict__ dst,
+                                                 const cplx* __restrict__ src, int64_t dis,
+                                                 int64_t sis, Coefs co, int acc) {
+  __shared__ PermTask T;
+  const ChunkRef ch = chunks[blockIdx.x];
+  if (threadIdx.x < sizeof(PermTask) / 8)
+    reinterpret_cast<int64_t*>(&T)[threadIdx.x] =
+        reinterpret_cast<const int64_t*>(&tasks[ch.task])[threadIdx.x];
+  __syncthreads();
+  dst += blockIdx.y * dis;
+  src += blockIdx.y * sis;
+  const int64_t end = min(ch.start + (int64_t)EXP_CHUNK, T.count);
+  const int n1 = T.n[1], n2 = T.n[2], n3 = T.n[3];
+  for (int64_t e = ch.start + threadIdx.x; e < end; e += blockDim.x) {
+    int64_t r = e;
+    const int i3 = int(r % n3);
+    r /= n3;
+    const int i2 = int(r % n2);
+    r /= n2;
+    const int i1 = int(r % n1);
+    const int i0 = int(r / n1);
+    const int64_t dp = T.dst + i0 * T.dst_st[0] + i1 * T.dst_st[1] + i2 * T.dst_st[2] + i3 * T.dst_st[3];
+    double vr = 0.0, vi = 0.0;
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      const int64_t sp = T.src[t] + i0 * T.src_st[t][0] + i1 * T.src_st[t][1] +
+                         i2 * T.src_st[t][2] + i3 * T.src_st[t][3];
+      const cplx x = src[sp];
+      vr += co.c[t].x * x.x - co.c[t].y * x.y;
+      vi += co.c[t].x * x.y + co.c[t].y * x.x;
+    }
+    if (acc) {
+      const cplx o = dst[dp];
+      vr += o.x;
+      vi += o.y;
+    }
+    dst[dp] = make_double2(vr, vi);
+  }
+}
+
+void launch_permute(Ctx& c, const PermPlan& p, cplx* dst, const cplx* src, int64_t dst_is,
+                    int64_t src_is, const cplx* coef, bool accumulate, bool) {
+  if (p.n_chunks == 0) return;
+  Coefs co;
+  for (int t = 0; t < EXP_MAX_TERMS; ++t) co.c[t] = t < p.n_terms ? coef[t] : make_double2(0, 0);
+  dim3 grid(p.n_chunks, c.ninst);
+  switch (p.n_terms) {
+    case 1: k_permute<1><<<grid, 256, 0, c.stream>>>(p.d_tasks, p.d_chunks, dst, src, dst_is, src_is, co, accumulate); break;
+    case 2: k_permute<2><<<grid, 256, 0, c.stream>>>(p.d_tasks, p.d_chunks, dst, src, dst_is, src_is, co, accumulate); break;
+    case 3: k_permute<3><<<grid, 256, 0, c.stream>>>(p.d_tasks, p.d_chunks, dst, src, dst_is, src_is, co, accumulate); break;
+    default: k_permute<4><<<grid, 256, 0, c.stream>>>(p.d_tasks, p.d_chunks, dst, src, dst_is, src_is, co, accumulate); break;
+  }
+  KCHECK(c);
+}
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11) and the synthetic integral recipe.
+__device__ __forceinline__ void philox10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c[0]), lo0 = 0xD2511F53u * c[0];
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c[2]), lo1 = 0xCD9E8D57u * c[2];
+    const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+  }
+}
+
+// A[idx]: complex standard normal via Box-Muller of two 53-bit uniforms.
+__device__ __forceinline__ cplx gauss_a(uint64_t idx, uint64_t seed) {
+  uint32_t c[4] = {uint32_t(idx), uint32_t(idx >> 32), 0u, 0u};
+  philox10(c, uint32_t(seed), uint32_t(seed >> 32));
+  const uint64_t a = ((uint64_t(c[1]) << 32) | c[0]) >> 11;
+  const uint64_t b = ((uint64_t(c[3]) << 32) | c[2]) >> 11;
+  const double u1 = (double(a) + 0.5) * 0x1p-53;
+  const double u2 = (double(b) + 0.5) * 0x1p-53;
+  const double rad = sqrt(-2.0 * log(u1));
+  double s, co;
+  sincospi(2.0 * u2, &s, &co);
+  return make_double2(rad * co, rad * s);
+}
+
+// V_pqrs = 1/2 [ (A_pqrs - A_qprs - A_pqsr + A_qpsr) + conj(A_rspq - A_srpq - A_rsqp + A_srqp) ]
+__device__ cplx v_element(uint64_t p, uint64_t q, uint64_t r, uint64_t s, uint64_t n, uint64_t seed) {
+  auto I = [n](uint64_t a, uint64_t b, uint64_t c, uint64_t d) { return ((a * n + b) * n + c) * n + d; };
+  const cplx x0 = gauss_a(I(p, q, r, s), seed), x1 = gauss_a(I(q, p, r, s), seed);
+  const cplx x2 = gauss_a(I(p, q, s, r), seed), x3 = gauss_a(I(q, p, s, r), seed);
+  const cplx y0 = gauss_a(I(r, s, p, q), seed), y1 = gauss_a(I(s, r, p, q), seed);
+  const cplx y2 = gauss_a(I(r, s, q, p), seed), y3 = gauss_a(I(s, r, q, p), seed);
+  const double xr = x0.x - x1.x - x2.x + x3.x, xi = x0.y - x1.y - x2.y + x3.y;
+  const double yr = y0.x - y1.x - y2.x + y3.x, yi = y0.y - y1.y - y2.y + y3.y;
+  return make_double2(0.5 * (xr + yr), 0.5 * (xi - yi));
+}
+
+struct Map4 {
+  int m[4];
+};
+
+__global__ void __launch_bounds__(256) k_generate(cplx* __restrict__ dst, int64_t is,
+                                                  const GenTask* __restrict__ tasks,
+                                                  const ChunkRef* __restrict__ chunks, Map4 map,
+                                                  int n, const uint64_t* __restrict__ seeds,
+                                                  const double* __restrict__ scales) {
+  const ChunkRef ch = chunks[blockIdx.x];
+  const GenTask T = tasks[ch.task];
+  const int inst = blockIdx.y;
+  dst += inst * is;
+  const uint64_t seed = seeds[inst];
+  const double sc = scales[inst];
+  const int64_t end = min(ch.start + (int64_t)EXP_CHUNK, T.count);
+  for (int64_t e = ch.start + threadIdx.x; e < end; e += blockDim.x) {
+    int64_t r = e;
+    int i[4];
+    i[3] = int(r % T.n[3]); r /= T.n[3];
+    i[2] = int(r % T.n[2]); r /= T.n[2];
+    i[1] = int(r % T.n[1]);
+    i[0] = int(r / T.n[1]);
+    uint64_t g[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) g[k] = uint64_t(T.g0[k] + i[k]);
+    const int64_t dp = T.base + i[0] * T.st[0] + i[1] * T.st[1] + i[2] * T.st[2] + i[3] * T.st[3];
+    const cplx v = v_element(g[map.m[0]], g[map.m[1]], g[map.m[2]], g[map.m[3]], uint64_t(n), seed);
+    dst[dp] = make_double2(sc * v.x, sc * v.y);
+  }
+}
+
+void launch_generate(Ctx& c, cplx* dst, int64_t is, const GenTask* d_tasks, const ChunkRef* d_chunks,
+                     int n_chunks, const int map[4]) {
+  if (!n_chunks) return;
+  Map4 m;
+  // generator tasks use padded dims: slot k of a rank-4 tensor is dim k
+  for (int k = 0; k < 4; ++k) m.m[k] = map[k];
+  k_generate<<<dim3(n_chunks, c.ninst), 256, 0, c.stream>>>(dst, is, d_tasks, d_chunks, m,
+                                                            c.no + c.nv, c.d_seed, c.d_scale);
+  KCHECK(c);
+}
+
+// D = -sum_k sign_k eps(g_k)  (D_i^a = e_i - e_a, D_ij^ab = e_i + e_j - e_a - e_b)
+struct Sgn4 {
+  int s[4];
+};
+__global__ void k_fill_denom(double* __restrict__ dst, int64_t is, const GenTask* __restrict__ tasks,
+                             const ChunkRef* __restrict__ chunks, Sgn4 sg, int n,
+                             const double* __restrict__ eps) {
+  const ChunkRef ch = chunks[blockIdx.x];
+  const GenTask T = tasks[ch.task];
+  const int inst = blockIdx.y;
+  dst += inst * is;
+  eps += inst * n;
+  const int64_t end = min(ch.start + (int64_t)EXP_CHUNK, T.count);
+  for (int64_t e = ch.start + threadIdx.x; e < end; e += blockDim.x) {
+    int64_t r = e;
+    int i[4];
+    i[3] = int(r % T.n[3]); r /= T.n[3];
+    i[2] = int(r % T.n[2]); r /= T.n[2];
+    i[1] = int(r % T.n[1]);
+    i[0] = int(r / T.n[1]);
+    double d = 0.0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (sg.s[k]) d -= sg.s[k] * eps[T.g0[k] + i[k]];
+    dst[T.base + i[0] * T.st[0] + i[1] * T.st[1] + i[2] * T.st[2] + i[3] * T.st[3]] = d;
+  }
+}
+
+void launch_fill_denom(Ctx& c, double* dst, int64_t is, const GenTask* d_tasks, const ChunkRef* d_chunks,
+                       int n_chunks, int nslots, const int sgn[4]) {
+  if (!n_chunks) return;
+  Sgn4 s;
+  const int pad = 4 - nslots;
+  for (int k = 0; k < 4; ++k) s.s[k] = 0;
+  for (int k = 0; k < nslots; ++k) s.s[pad + k] = sgn[k];
+  k_fill_denom<<<dim3(n_chunks, c.ninst), 256, 0, c.stream>>>(dst, is, d_tasks, d_chunks, s, c.no + c.nv,
+                                                              c.d_eps);
+  KCHECK(c);
+}
+
+// dst_abij = c0 t2_abij + c1 t1_ai t1_bj + c2 t1_bi t1_aj over the t2 layout.
+// t1_index[a_local * no + i_local] = offset of t1_ai in its layout, or -1.
+__global__ void k_tau(cplx* __restrict__ dst, int64_t dis, const cplx* __restrict__ t2,
+                      const cplx* __restrict__ t1, int64_t tis, const int32_t* __restrict__ t1i,
+                      const GenTask* __restrict__ tasks, const ChunkRef* __restrict__ chunks,
+                      double c0, double c1, double c2, int no, int vbase) {
+  const ChunkRef ch = chunks[blockIdx.x];
+  const GenTask T = tasks[ch.task];
+  dst += blockIdx.y * dis;
+  t2 += blockIdx.y * tis;
+  t1 += blockIdx.y * tis;
+  const int64_t end = min(ch.start + (int64_t)EXP_CHUNK, T.count);
+  for (int64_t e = ch.start + threadIdx.x; e < end; e += blockDim.x) {
+    int64_t r = e;
+    int i[4];
+    i[3] = int(r % T.n[3]); r /= T.n[3];
+    i[2] = int(r % T.n[2]); r /= T.n[2];
+    i[1] = int(r % T.n[1]);
+    i[0] = int(r / T.n[1]);
+    const int a = T.g0[0] + i[0] - vbase, b = T.g0[1] + i[1] - vbase;
+    const int ii = T.g0[2] + i[2], jj = T.g0[3] + i[3];
+    const int64_t p = T.base + i[0] * T.st[0] + i[1] * T.st[1] + i[2] * T.st[2] + i[3] * T.st[3];
+    const cplx x = t2[p];
+    double vr = c0 * x.x, vi = c0 * x.y;
+    const int ai = t1i[a * no + ii], bj = t1i[b * no + jj];
+    if (ai >= 0 && bj >= 0) {
+      const cplx u = t1[ai], w = t1[bj];
+      vr += c1 * (u.x * w.x - u.y * w.y);
+      vi += c1 * (u.x * w.y + u.y * w.x);
+    }
+    const int bi = t1i[b * no + ii], aj = t1i[a * no + jj];
+    if (bi >= 0 && aj >= 0) {
+      const cplx u = t1[bi], w = t1[aj];
+      vr += c2 * (u.x * w.x - u.y * w.y);
+      vi += c2 * (u.x * w.y + u.y * w.x);
+    }
+    dst[p] = make_double2(vr, vi);
+  }
+}
+
+void launch_tau(Ctx& c, cplx* dst, int64_t dst_is, const cplx* t2, const cplx* t1, int64_t t_is,
+                const int32_t* t1_index, const GenTask* d_tasks, const ChunkRef* d_chunks,
+                int n_chunks, double c0, double c1, double c2) {
+  if (!n_chunks) return;
+  k_tau<<<dim3(n_chunks, c.ninst), 256, 0, c.stream>>>(dst, dst_is, t2, t1, t_is, t1_index, d_tasks,
+                                                       d_chunks, c0, c1, c2, c.no, c.no);
+  KCHECK(c);
+}

@@ -1,0 +1,220 @@
+"""Thin ctypes binding of libexpgb (include/exp.h): argument marshalling only.
+
+Every step of the method runs in the library's CUDA kernels; PyTorch supplies
+device memory (its caching allocator, through the exp_allocator callbacks) and
+the CUDA stream.  There is no CPU fallback: without the built library every call
+raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libexpgb.so")
+
+EXP_FP64, EXP_EMU_BF16 = 0, 1
+EXP_GUESS_MP2, EXP_GUESS_USER = 0, 1
+STATUS = {0: "EXP_OK", 1: "EXP_EINVAL", 2: "EXP_ENOMEM", 3: "EXP_ECUDA", 4: "EXP_ENOTCONV",
+          5: "EXP_ENUMERIC", 6: "EXP_ETIMEOUT", 7: "EXP_ESTATE"}
+
+
+class ExpError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class Allocator(C.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("user", C.c_void_p)]
+
+
+class Config(C.Structure):
+    _fields_ = [("n_inst", C.c_int), ("n_occ", C.c_int), ("n_virt", C.c_int), ("n_irrep", C.c_int),
+                ("irrep_occ", C.POINTER(C.c_int32)), ("irrep_virt", C.POINTER(C.c_int32)),
+                ("eps_occ", C.POINTER(C.c_double)), ("eps_virt", C.POINTER(C.c_double)),
+                ("precision", C.c_int), ("n_slices", C.c_int), ("diis_dim", C.c_int),
+                ("conv_tol", C.c_double), ("max_iter", C.c_int), ("guess", C.c_int)]
+
+
+class IterInfo(C.Structure):
+    _fields_ = [("e_re", C.c_double), ("e_im", C.c_double), ("max_dt", C.c_double),
+                ("diis_n", C.c_int), ("n_converged", C.c_int), ("ms", C.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libexpgb.so (built by paper_2004_03682_gb300.build); raise if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libexpgb.so not built ({LIB_PATH}); run __graft_entry__.build()")
+    L = C.CDLL(LIB_PATH)
+    P = C.c_void_p
+    L.exp_create.argtypes = [C.POINTER(Config), C.POINTER(Allocator), P, C.POINTER(P)]
+    L.exp_destroy.argtypes = [P]
+    L.exp_destroy.restype = None
+    L.exp_init_integrals.argtypes = [P, C.POINTER(C.c_uint64), C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    L.exp_ccsd_iterate.argtypes = [P, C.c_int, C.POINTER(IterInfo), C.POINTER(C.c_int)]
+    L.exp_energy.argtypes = [P, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    L.exp_get_amplitudes.argtypes = [P, C.c_int, P, P]
+    L.exp_set_amplitudes.argtypes = [P, C.c_int, P, P]
+    L.exp_kernel_launches.argtypes = [P]
+    L.exp_kernel_launches.restype = C.c_int64
+    L.exp_last_error.argtypes = [P]
+    L.exp_last_error.restype = C.c_char_p
+    for name in ("exp_create", "exp_init_integrals", "exp_ccsd_iterate", "exp_energy",
+                 "exp_get_amplitudes", "exp_set_amplitudes"):
+        getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def _arr(a, ctype, dtype):
+    a = np.ascontiguousarray(a, dtype=dtype)
+    return a, a.ctypes.data_as(C.POINTER(ctype))
+
+
+class TorchAllocator:
+    """exp_allocator backed by the PyTorch caching allocator on one stream."""
+
+    def __init__(self, device: int, stream):
+        import torch
+        self._torch = torch
+        self.device = device
+        self.stream = stream
+        self.live = {}
+
+        def _alloc(nbytes, user):
+            try:
+                p = torch.cuda.caching_allocator_alloc(int(nbytes), device, stream)
+            except Exception:
+                return None
+            self.live[p] = nbytes
+            return p
+
+        def _free(ptr, user):
+            if ptr in self.live:
+                del self.live[ptr]
+                torch.cuda.caching_allocator_delete(ptr)
+
+        self._a = ALLOC_FN(_alloc)
+        self._f = FREE_FN(_free)
+        self.struct = Allocator(self._a, self._f, None)
+
+
+class Context:
+    """One exp_ctx: n_inst same-sized CCSD instances on one GPU."""
+
+    def __init__(self, n_occ, n_virt, irrep_occ, irrep_virt, eps_occ, eps_virt, n_inst=1,
+                 precision=EXP_FP64, n_slices=5, diis_dim=6, conv_tol=1e-9, max_iter=500,
+                 guess=EXP_GUESS_MP2, device=0):
+        import torch
+        self._torch = torch
+        L = lib()
+        self.L = L
+        self.device = device
+        self.n_occ, self.n_virt, self.n_inst = int(n_occ), int(n_virt), int(n_inst)
+        torch.cuda.set_device(device)
+        self.stream = torch.cuda.Stream(device=device)
+        self.alloc = TorchAllocator(device, self.stream)
+        self._keep = []
+        io, pio = _arr(irrep_occ, C.c_int32, np.int32)
+        iv, piv = _arr(irrep_virt, C.c_int32, np.int32)
+        eo, peo = _arr(np.asarray(eps_occ, dtype=np.float64).reshape(-1), C.c_double, np.float64)
+        ev, pev = _arr(np.asarray(eps_virt, dtype=np.float64).reshape(-1), C.c_double, np.float64)
+        self._keep += [io, iv, eo, ev]
+        cfg = Config(self.n_inst, self.n_occ, self.n_virt, len(io), pio, piv, peo, pev,
+                     int(precision), int(n_slices), int(diis_dim), float(conv_tol), int(max_iter),
+                     int(guess))
+        h = C.c_void_p()
+        st = L.exp_create(C.byref(cfg), C.byref(self.alloc.struct), C.c_void_p(self.stream.cuda_stream),
+                          C.byref(h))
+        if st != 0:
+            raise ExpError(st, L.exp_last_error(None).decode())
+        self.h = h
+
+    def _check(self, st):
+        if st != 0:
+            raise ExpError(st, self.L.exp_last_error(self.h).decode())
+
+    def init_integrals(self, seeds, scale_mult=None):
+        s, ps = _arr(np.asarray(seeds, dtype=np.uint64).reshape(-1), C.c_uint64, np.uint64)
+        pm = None
+        if scale_mult is not None:
+            m, pm = _arr(np.asarray(scale_mult, dtype=np.float64).reshape(-1), C.c_double, np.float64)
+        out = np.zeros(self.n_inst)
+        self._check(self.L.exp_init_integrals(self.h, ps, pm, out.ctypes.data_as(C.POINTER(C.c_double))))
+        return out
+
+    def iterate(self, n_iter, raise_notconv=False):
+        info = (IterInfo * max(n_iter, 1))()
+        for k in range(n_iter):
+            info[k].ms = -1.0
+        conv = C.c_int(0)
+        st = self.L.exp_ccsd_iterate(self.h, int(n_iter), info, C.byref(conv))
+        if st not in (0, 4) or (st == 4 and raise_notconv):
+            self._check(st)
+        recs = []
+        for k in range(n_iter):
+            r = info[k]
+            if r.ms < 0:
+                break
+            recs.append(dict(e=complex(r.e_re, r.e_im), max_dt=r.max_dt, diis_n=r.diis_n,
+                             n_converged=r.n_converged, ms=r.ms))
+        return recs, bool(conv.value), st
+
+    def energy(self, inst=0) -> complex:
+        re, im = C.c_double(), C.c_double()
+        self._check(self.L.exp_energy(self.h, int(inst), C.byref(re), C.byref(im)))
+        return complex(re.value, im.value)
+
+    def get_amplitudes(self, inst=0):
+        torch = self._torch
+        o, v = self.n_occ, self.n_virt
+        with torch.cuda.stream(self.stream):
+            t1 = torch.empty((o, v), dtype=torch.complex128, device=f"cuda:{self.device}")
+            t2 = torch.empty((o, o, v, v), dtype=torch.complex128, device=f"cuda:{self.device}")
+        self._check(self.L.exp_get_amplitudes(self.h, int(inst), C.c_void_p(t1.data_ptr()),
+                                              C.c_void_p(t2.data_ptr())))
+        return t1, t2
+
+    def set_amplitudes(self, inst, t1, t2):
+        torch = self._torch
+        t1 = t1.to(device=f"cuda:{self.device}", dtype=torch.complex128).contiguous()
+        t2 = t2.to(device=f"cuda:{self.device}", dtype=torch.complex128).contiguous()
+        self.stream.wait_stream(torch.cuda.current_stream())
+        self._check(self.L.exp_set_amplitudes(self.h, int(inst), C.c_void_p(t1.data_ptr()),
+                                              C.c_void_p(t2.data_ptr())))
+
+    @property
+    def launches(self) -> int:
+        return int(self.L.exp_kernel_launches(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.exp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def from_problems(probs, **kw) -> Context:
+    """Context for one or more synthetic problems of the same sizes and irrep split."""
+    p0 = probs[0]
+    eo = np.stack([p.eps_occ for p in probs])
+    ev = np.stack([p.eps_virt for p in probs])
+    return Context(p0.n_occ, p0.n_virt, p0.irrep_occ, p0.irrep_virt, eo, ev, n_inst=len(probs), **kw)

@@ -1,0 +1,29 @@
+"""Write stored oracle results (calls only oracle/ and the seeded input module).
+
+    python tests/golden/make_golden.py
+"""
+import json
+import os
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
+
+from oracle import ccsd, integrals  # noqa: E402
+from paper_2004_03682_gb300 import synthetic as syn  # noqa: E402
+
+
+def c1():
+    spec = dict(seed=1001, n_occ=10, n_virt=40, G=1, tol=1e-9, max_iter=600)
+    prob = syn.make_problem(spec["seed"], spec["n_occ"], spec["n_virt"], spec["G"])
+    b = ccsd.Blocks(integrals.integrals(prob), integrals.fock(prob), prob.n_occ)
+    t1, t2, E, nit, conv, recs = ccsd.solve(b, tol=spec["tol"], max_iter=spec["max_iter"])
+    assert conv
+    out = dict(spec, e_re=E.real, e_im=E.imag, n_iter=nit, e_mp2=ccsd.mp2_energy(b),
+               source="oracle/ccsd.py solve(), MP2 guess, DIIS(6), residual max|t_new - t| < tol")
+    json.dump(out, open(os.path.join(HERE, "ccsd_c1_o10_v40.json"), "w"), indent=1)
+    print(out)
+
+
+if __name__ == "__main__":
+    c1()

@@ -1,0 +1,73 @@
+"""The C-ABI library loads, exports every entry point include/exp.h declares, and
+validates its arguments on the host (no GPU needed for these paths)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2004_03682_gb300 import build, expgb
+    build.build()
+    return expgb.lib()
+
+
+def _declared():
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for f in os.listdir(inc):
+        if f.endswith(".h"):
+            txt = open(os.path.join(inc, f)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(exp_[a-z0-9_]+)\s*\(", txt))
+    return names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert {"exp_create", "exp_init_integrals", "exp_ccsd_iterate", "exp_energy"} <= names
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def _cfg(expgb, **over):
+    io = np.array(over.pop("irrep_occ", [2, 2]), np.int32)
+    iv = np.array(over.pop("irrep_virt", [3, 3]), np.int32)
+    eo = np.linspace(-2, -1, int(io.sum()))
+    ev = np.linspace(1, 2, int(iv.sum()))
+    keep = [io, iv, eo, ev]
+    d = dict(n_inst=1, n_occ=int(io.sum()), n_virt=int(iv.sum()), n_irrep=len(io), precision=0,
+             n_slices=5, diis_dim=6, conv_tol=1e-9, max_iter=10, guess=0)
+    d.update(over)
+    cfg = expgb.Config(d["n_inst"], d["n_occ"], d["n_virt"], d["n_irrep"],
+                       io.ctypes.data_as(C.POINTER(C.c_int32)), iv.ctypes.data_as(C.POINTER(C.c_int32)),
+                       eo.ctypes.data_as(C.POINTER(C.c_double)), ev.ctypes.data_as(C.POINTER(C.c_double)),
+                       d["precision"], d["n_slices"], d["diis_dim"], d["conv_tol"], d["max_iter"], d["guess"])
+    return cfg, keep
+
+
+@pytest.mark.parametrize("bad", [dict(n_occ=5), dict(n_irrep=17), dict(diis_dim=9), dict(conv_tol=0.0),
+                                 dict(max_iter=0), dict(precision=7), dict(precision=1, n_slices=2),
+                                 dict(n_inst=0)])
+def test_create_rejects_bad_config_on_host(lib, bad):
+    from paper_2004_03682_gb300 import expgb
+    cfg, keep = _cfg(expgb, **bad)
+    a = expgb.Allocator(expgb.ALLOC_FN(lambda n, u: None), expgb.FREE_FN(lambda p, u: None), None)
+    h = C.c_void_p()
+    st = lib.exp_create(C.byref(cfg), C.byref(a), None, C.byref(h))
+    assert st == 1, (st, lib.exp_last_error(None))
+    assert not h.value
+    assert len(lib.exp_last_error(None)) > 0
+
+
+def test_null_arguments_rejected(lib):
+    assert lib.exp_create(None, None, None, None) == 1
+    assert lib.exp_init_integrals(None, None, None, None) == 1
+    assert lib.exp_ccsd_iterate(None, 1, None, None) == 1
+    assert lib.exp_energy(None, 0, None, None) == 1
+    lib.exp_destroy(None)

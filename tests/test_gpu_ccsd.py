@@ -1,0 +1,114 @@
+"""GPU parity: the CUDA CCSD path (through the C ABI) against the CPU oracle."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import ccsd, integrals
+from paper_2004_03682_gb300 import synthetic as syn
+
+pytestmark = pytest.mark.gpu
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module")
+def expgb():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA GPU required for -m gpu tests")
+    from paper_2004_03682_gb300 import build, expgb as e
+    build.build()
+    e.lib()
+    return e
+
+
+def _oracle(prob):
+    return ccsd.Blocks(integrals.integrals(prob), integrals.fock(prob), prob.n_occ)
+
+
+@pytest.mark.parametrize("no,nv,G", [(3, 7, 1), (4, 12, 2), (6, 20, 4), (5, 19, 8)])
+def test_mp2_guess_and_energy_match_oracle(expgb, no, nv, G):
+    prob = syn.make_problem(100 + no + nv + G, no, nv, G)
+    b = _oracle(prob)
+    ctx = expgb.from_problems([prob])
+    scale = ctx.init_integrals([prob.seed])[0]
+    ctx.iterate(0)
+    t1, t2 = ctx.get_amplitudes(0)
+    r1, r2 = ccsd.mp2_guess(b)
+    np.testing.assert_allclose(t2.cpu().numpy(), r2, atol=1e-14, rtol=0)
+    assert np.max(np.abs(t1.cpu().numpy())) == 0
+    e = ctx.energy(0)
+    assert abs(e - ccsd.mp2_energy(b)) < 1e-12 * max(1, abs(e))
+    V0 = integrals.unscaled_integrals(prob)
+    assert abs(scale - integrals.mp2_scale(V0, prob)) < 1e-14 * scale
+
+
+@pytest.mark.parametrize("no,nv,G", [(3, 7, 1), (4, 12, 2), (6, 20, 4), (5, 19, 8), (10, 40, 1)])
+def test_first_iterations_elementwise(expgb, no, nv, G):
+    """t_new = RHS(t)/D after one and two iterations, every amplitude element."""
+    prob = syn.make_problem(200 + no + nv + G, no, nv, G)
+    b = _oracle(prob)
+    ctx = expgb.from_problems([prob], diis_dim=0)
+    ctx.init_integrals([prob.seed])
+    t1, t2 = ccsd.mp2_guess(b)
+    D1, D2 = ccsd.denominators(b)
+    for it in range(2):
+        ctx.iterate(1)
+        r1, r2 = ccsd.rhs(t1, t2, b)
+        t1, t2 = r1 / D1, r2 / D2
+        g1, g2 = ctx.get_amplitudes(0)
+        scale = max(np.max(np.abs(t2)), 1e-3)
+        np.testing.assert_allclose(g1.cpu().numpy(), t1, atol=1e-12 * scale, rtol=0)
+        np.testing.assert_allclose(g2.cpu().numpy(), t2, atol=1e-12 * scale, rtol=0)
+        assert abs(ctx.energy(0) - ccsd.energy(t1, t2, b)) < 1e-11
+
+
+@pytest.mark.parametrize("no,nv,G", [(4, 14, 1), (6, 20, 4)])
+def test_converged_energy_and_iterates_match_oracle(expgb, no, nv, G):
+    prob = syn.make_problem(11 if G == 1 else 300 + no + nv, no, nv, G)
+    b = _oracle(prob)
+    t1, t2, E, nit, conv, recs = ccsd.solve(b, tol=1e-9, max_iter=300)
+    assert conv
+    ctx = expgb.from_problems([prob], conv_tol=1e-9, max_iter=300)
+    ctx.init_integrals([prob.seed])
+    grecs, gconv, _ = ctx.iterate(300)
+    assert gconv
+    assert len(grecs) == nit
+    for r, g in zip(recs[1:], grecs):
+        assert abs(r.energy - g["e"]) < 1e-10
+    e = ctx.energy(0)
+    assert abs(e - E) < 1e-10
+    g1, g2 = ctx.get_amplitudes(0)
+    np.testing.assert_allclose(g2.cpu().numpy(), t2, atol=1e-10)
+
+
+def test_batched_instances_equal_single_runs(expgb):
+    """Three instances in one context (one grouped launch per contraction) equal three
+    oracle solves; a batch shares the irrep split, not the energies or integrals."""
+    import dataclasses
+    base = [syn.make_problem(400 + k, 4, 12, 2) for k in range(3)]
+    mults = [1.0, 0.7, 1.3]
+    probs = [dataclasses.replace(p, irrep_occ=base[0].irrep_occ, irrep_virt=base[0].irrep_virt,
+                                 scale_mult=m) for p, m in zip(base, mults)]
+    ctx = expgb.from_problems(probs, conv_tol=1e-10, max_iter=300)
+    ctx.init_integrals([p.seed for p in probs], scale_mult=mults)
+    _, conv, _ = ctx.iterate(300)
+    assert conv
+    for k, p in enumerate(probs):
+        E = ccsd.solve(_oracle(p), tol=1e-10, max_iter=300)[2]
+        assert abs(ctx.energy(k) - E) < 1e-10
+
+
+def test_c1_o10_v40_converged_energy(expgb):
+    """The C1 workload (o=10, v=40, no symmetry) to convergence, against the stored
+    oracle energy (tests/golden/ccsd_c1_o10_v40.json, written by make_golden.py)."""
+    g = json.load(open(os.path.join(HERE, "golden", "ccsd_c1_o10_v40.json")))
+    prob = syn.make_problem(g["seed"], g["n_occ"], g["n_virt"], g["G"])
+    ctx = expgb.from_problems([prob], conv_tol=g["tol"], max_iter=g["max_iter"])
+    ctx.init_integrals([prob.seed])
+    recs, conv, _ = ctx.iterate(g["max_iter"])
+    assert conv
+    e = ctx.energy(0)
+    assert abs(e - complex(g["e_re"], g["e_im"])) < 1e-10
+    assert abs(len(recs) - g["n_iter"]) <= 2

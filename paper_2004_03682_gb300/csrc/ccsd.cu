@@ -49,7 +49,7 @@ __device__ T block_reduce(T v, Op op, T* sh) {
   if (l == 0) sh[w] = v;
   __syncthreads();
   if (w == 0) {
-    v = (l < (blockDim.x >> 5)) ? sh[l] : sh[0];
+    v = (l < (blockDim.x >> 5)) ? sh[l] : T(0);  // 0 is neutral for both sums and max of |.|
     for (int o = 16; o; o >>= 1) v = op(v, __shfl_xor_sync(0xffffffffu, v, o));
   }
   return v;

@@ -76,6 +76,8 @@ typedef struct {
   double conv_tol;         /* converged when max |t_new - t| < conv_tol */
   int max_iter;            /* per exp_ccsd_iterate sequence, counted from the guess */
   int guess;               /* EXP_GUESS_MP2 or EXP_GUESS_USER (amplitudes set by exp_set_amplitudes) */
+  double emu_min_macs;     /* with EXP_EMU_BF16: contractions with fewer complex multiply-adds per
+                              instance stay FP64 (0 = default, 2^26) */
 } exp_config;
 
 /* Create a context: validates the config, builds the symmetry-blocked layouts
@@ -129,6 +131,30 @@ exp_status exp_energy(exp_ctx* ctx, int inst, double* e_re, double* e_im);
  * ignored on write.  set_amplitudes also resets DIIS and the iteration count. */
 exp_status exp_get_amplitudes(exp_ctx* ctx, int inst, void* t1_dev, void* t2_dev);
 exp_status exp_set_amplitudes(exp_ctx* ctx, int inst, const void* t1_dev, const void* t2_dev);
+
+/* Algorithmic work of one (0h,0p) iteration, all instances: complex
+ * multiply-adds of every contraction over the symmetry-allowed blocks (what the
+ * grouped GEMMs execute).  Valid after the first iteration has been planned. */
+exp_status exp_work_per_iteration(const exp_ctx* ctx, double* complex_macs);
+
+/* Time the contraction with the most work on its own: `reps` launches of its
+ * grouped GEMM on the context stream between CUDA events.  Writes the call-site
+ * name (NUL-terminated, truncated to name_len), the mean milliseconds per launch
+ * and its complex multiply-adds per launch.  Overwrites that contraction's
+ * output buffer, which the next iteration recomputes. */
+exp_status exp_profile_top(exp_ctx* ctx, int reps, char* name, int name_len, double* ms_per_launch,
+                           double* complex_macs_per_launch);
+
+/* One complex GEMM C = alpha A B (+ C if beta) on caller device buffers, with the
+ * same kernels the contractions use (step 3 of the TTGT list, Sec. II.B):
+ * precision EXP_FP64 (SIMT FP64) or EXP_EMU_BF16 (n_slices BF16 slices on the
+ * tcgen05 tensor cores).  A: M x K, B: K x N, C: M x N, row-major complex128
+ * (re, im doubles), 16-byte aligned.  Scratch (slices, exponents, split-K
+ * partials) comes from `alloc` and is released before return.  Ordered on
+ * `stream`; synchronises it.  EINVAL on M, N < 1, K < 0 or bad precision /
+ * n_slices; ETIMEOUT if a bounded device wait gave up. */
+exp_status exp_zgemm(const exp_allocator* alloc, void* stream, int precision, int n_slices, int M, int N, int K,
+                     const void* A, const void* B, void* C, double alpha_re, double alpha_im, int beta);
 
 /* Number of kernels this context has launched so far (for launch accounting). */
 int64_t exp_kernel_launches(const exp_ctx* ctx);

@@ -4,6 +4,8 @@
 #include <cmath>
 #include <cstdio>
 #include <string>
+#include <cstring>
+#include <cstdlib>
 
 #include "ccsd.h"
 #include "emu.h"
@@ -103,6 +105,12 @@ extern "C" exp_status exp_create(const exp_config* cfg, const exp_allocator* all
   c.d_scale = (double*)c.dalloc(sizeof(double) * c.ninst);
   CK(cudaEventCreate(&c.ev0));
   CK(cudaEventCreate(&c.ev1));
+  CK(cudaEventCreate(&c.pev0));
+  CK(cudaEventCreate(&c.pev1));
+  {
+    const char* pe = getenv("EXP_PROFILE");
+    c.profile = pe && pe[0] == '1';
+  }
   ccsd_setup(c);
   CK(cudaStreamSynchronize(c.stream));
   *out = x;
@@ -127,6 +135,8 @@ extern "C" void exp_destroy(exp_ctx* x) {
   if (c.graph) cudaGraphExecDestroy(c.graph);
   if (c.ev0) cudaEventDestroy(c.ev0);
   if (c.ev1) cudaEventDestroy(c.ev1);
+  if (c.pev0) cudaEventDestroy(c.pev0);
+  if (c.pev1) cudaEventDestroy(c.pev1);
   if (c.h_stats) cudaFreeHost(c.h_stats);
   try { emu_release(c); } catch (...) {}
   ccsd_release(c);
@@ -188,7 +198,7 @@ extern "C" exp_status exp_ccsd_iterate(exp_ctx* x, int n_iter, exp_iter_info* in
       CK(cudaGraphLaunch(c.graph, c.stream));
       c.launches += c.graph_kernels;
     } else {
-      const bool capture = c.iter_done >= 1 && c.stream != nullptr;
+      const bool capture = c.iter_done >= 1 && c.stream != nullptr && !c.profile;
       if (capture) {
         CK(cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal));
         const int64_t before = c.launches;
@@ -234,6 +244,11 @@ extern "C" exp_status exp_ccsd_iterate(exp_ctx* x, int n_iter, exp_iter_info* in
       info[it].diis_n = int(c.h_stats[3]);
       info[it].n_converged = nconv;
       info[it].ms = ms;
+    }
+    if (c.d_emu_err) {
+      int err = 0;
+      CK(cudaMemcpy(&err, c.d_emu_err, sizeof(int), cudaMemcpyDeviceToHost));
+      if (err) throw ExpError{EXP_ETIMEOUT, "emulated GEMM: a bounded device wait gave up"};
     }
     if (bad) throw ExpError{EXP_ENUMERIC, "NaN/Inf in the amplitudes"};
     if (nconv == c.ninst) { all_conv = true; break; }
@@ -287,6 +302,113 @@ extern "C" exp_status exp_set_amplitudes(exp_ctx* x, int inst, const void* t1, c
   CK(cudaStreamSynchronize(c.stream));
   return EXP_OK;
   API_END(x)
+}
+
+extern "C" exp_status exp_work_per_iteration(const exp_ctx* x, double* macs) {
+  API_BEGIN
+  if (!x || !macs) throw ExpError{EXP_EINVAL, "null argument"};
+  const Ctx& c = x->c;
+  if (c.plans.empty()) throw ExpError{EXP_ESTATE, "no iteration planned yet"};
+  double s = 0;
+  for (auto& kv : c.plans) s += double(kv.second->g.flops_mac);
+  *macs = s * c.ninst;
+  return EXP_OK;
+  API_END(const_cast<exp_ctx*>(x))
+}
+
+extern "C" exp_status exp_profile_top(exp_ctx* x, int reps, char* name, int name_len, double* ms,
+                                      double* macs) {
+  API_BEGIN
+  if (!x || reps < 1) throw ExpError{EXP_EINVAL, "bad argument"};
+  Ctx& c = x->c;
+  if (c.plans.empty()) throw ExpError{EXP_ESTATE, "no iteration planned yet"};
+  const std::string* best = nullptr;
+  EinsumPlan* P = nullptr;
+  for (auto& kv : c.plans)
+    if (!P || kv.second->g.flops_mac > P->g.flops_mac) { P = kv.second.get(); best = &kv.first; }
+  Tensor* Cg = P->permC ? &P->C2 : nullptr;
+  cplx* cd = Cg ? Cg->d : (P->gemm_out ? P->gemm_out : nullptr);
+  int64_t cis = Cg ? Cg->is : P->gemm_out_is;
+  if (!cd) throw ExpError{EXP_ESTATE, "contraction output unknown"};
+  CK(cudaStreamSynchronize(c.stream));
+  CK(cudaEventRecord(c.ev0, c.stream));
+  for (int r = 0; r < reps; ++r) {
+    if (P->emulate)
+      emu_run(c, P->emu, P->g, P->A->d, P->B->d, cd, P->A->is, P->B->is, cis, P->alpha, P->gemm_beta);
+    else
+      launch_gemm_fp64(c, P->g, P->A->d, P->B->d, cd, P->A->is, P->B->is, cis, P->alpha, P->gemm_beta);
+  }
+  CK(cudaEventRecord(c.ev1, c.stream));
+  CK(cudaEventSynchronize(c.ev1));
+  float t = 0.f;
+  CK(cudaEventElapsedTime(&t, c.ev0, c.ev1));
+  if (ms) *ms = double(t) / reps;
+  if (macs) *macs = double(P->g.flops_mac) * c.ninst;
+  if (name && name_len > 0) {
+    strncpy(name, best->c_str(), size_t(name_len - 1));
+    name[name_len - 1] = 0;
+  }
+  return EXP_OK;
+  API_END(x)
+}
+
+extern "C" exp_status exp_zgemm(const exp_allocator* alloc, void* stream, int precision, int n_slices, int M,
+                                int N, int K, const void* A, const void* B, void* C, double are, double aim,
+                                int beta) {
+  Ctx c;
+  API_BEGIN
+  if (!alloc || !alloc->alloc || !alloc->free || !A || !B || !C) throw ExpError{EXP_EINVAL, "null argument"};
+  if (M < 1 || N < 1 || K < 0) throw ExpError{EXP_EINVAL, "bad GEMM shape"};
+  if (precision != EXP_FP64 && precision != EXP_EMU_BF16) throw ExpError{EXP_EINVAL, "bad precision"};
+  if (precision == EXP_EMU_BF16 && (n_slices < 3 || n_slices > 6)) throw ExpError{EXP_EINVAL, "n_slices must be in 3..6"};
+  c.alloc = *alloc;
+  c.stream = (cudaStream_t)stream;
+  c.cfg.precision = precision;
+  c.cfg.n_slices = n_slices;
+  c.ninst = 1;
+  c.G = 1;
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&c.sm_count, cudaDevAttrMultiProcessorCount, dev));
+  // a rank-2 "tensor" per operand: one block, rows x cols
+  Layout LA, LB, LC;
+  LA.G = LB.G = LC.G = 1;
+  LA.rows = {M}; LA.cols = {K}; LA.blk_off = {0}; LA.size = int64_t(M) * K;
+  LB.rows = {K}; LB.cols = {N}; LB.blk_off = {0}; LB.size = int64_t(K) * N;
+  LC.rows = {M}; LC.cols = {N}; LC.blk_off = {0}; LC.size = int64_t(M) * N;
+  GemmPlan g = make_gemm_plan(c, LA, LB, LC);
+  const cplx alpha = make_double2(are, aim);
+  if (precision == EXP_EMU_BF16 && K > 0) {
+    Tensor TA, TB;
+    TA.L = LA; TA.d = (cplx*)A; TA.is = LA.size;
+    TB.L = LB; TB.d = (cplx*)B; TB.is = LB.size;
+    EmuPlan* ep = emu_plan(c, g, &TA, &TB, false, false);
+    emu_run(c, ep, g, (const cplx*)A, (const cplx*)B, (cplx*)C, LA.size, LB.size, LC.size, alpha, beta != 0);
+  } else {
+    launch_gemm_fp64(c, g, (const cplx*)A, (const cplx*)B, (cplx*)C, LA.size, LB.size, LC.size, alpha, beta != 0);
+  }
+  CK(cudaStreamSynchronize(c.stream));
+  int err = 0;
+  if (c.d_emu_err) CK(cudaMemcpy(&err, c.d_emu_err, sizeof(int), cudaMemcpyDeviceToHost));
+  emu_release(c);
+  c.dfree_all();
+  if (err) throw ExpError{EXP_ETIMEOUT, "emulated GEMM: a bounded device wait gave up"};
+  return EXP_OK;
+  }
+  catch (const ExpError& e) {
+    g_err = e.msg;
+    cudaStreamSynchronize(c.stream);
+    emu_release(c);
+    c.dfree_all();
+    return e.s;
+  }
+  catch (const CudaError& e) {
+    g_err = std::string(e.where) + ": " + cudaGetErrorString(e.e);
+    cudaStreamSynchronize(c.stream);
+    emu_release(c);
+    c.dfree_all();
+    return EXP_ECUDA;
+  }
 }
 
 extern "C" int64_t exp_kernel_launches(const exp_ctx* x) { return x ? x->c.launches : 0; }

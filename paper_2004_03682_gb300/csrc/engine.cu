@@ -320,15 +320,15 @@ void permute_into(Ctx& c, const std::string& site, Tensor& dst, const char* dl, 
 // supermatrices A'(FA|K), B'(K|FB) unless they already are, integrals are
 // generated in the needed layout once, and the product runs as one grouped GEMM
 // over the symmetry blocks (all instances).
-static GemmPlan make_gemm_plan(Ctx& c, const Layout& A, const Layout& B, const Layout& C) {
+GemmPlan make_gemm_plan(Ctx& c, const Layout& A, const Layout& B, const Layout& C) {
   GemmPlan g;
-  int tile0 = 0;
+  int64_t tiles_mn = 0;
   for (int q = 0; q < c.G; ++q) {
     const int64_t M = A.rows[q], K = A.cols[q], N = B.cols[q];
     if (B.rows[q] != K || C.rows[q] != M || C.cols[q] != N)
       throw ExpError{EXP_EINVAL, "gemm block shape mismatch"};
     if (M == 0 || N == 0) continue;
-    GemmProb p;
+    GemmProb p{};
     p.a = A.blk_off[q];
     p.b = B.blk_off[q];
     p.c = C.blk_off[q];
@@ -336,13 +336,41 @@ static GemmPlan make_gemm_plan(Ctx& c, const Layout& A, const Layout& B, const L
     p.N = int32_t(N);
     p.K = int32_t(K);
     p.tiles_n = int32_t((N + 63) / 64);
-    p.tile0 = tile0;
-    tile0 += int32_t((M + 63) / 64) * p.tiles_n;
+    p.tiles_m = int32_t((M + 63) / 64);
+    p.ksplit = 1;
+    p.kchunk = int32_t(((K + 7) / 8) * 8);
+    tiles_mn += int64_t(p.tiles_m) * p.tiles_n;
     g.flops_mac += M * N * K;
     g.h_probs.push_back(p);
   }
+  // split K when the output tiles cannot fill the GPU (long-K, small-MN blocks)
+  const int64_t want = 4LL * std::max(c.sm_count, 1);
+  const int64_t have = tiles_mn * c.ninst;
+  int tile0 = 0;
+  int64_t ws = 0;
+  for (auto& p : g.h_probs) {
+    if (have < 3LL * std::max(c.sm_count, 1) && p.K >= 1024) {
+      int64_t ks = std::min<int64_t>((p.K + 511) / 512, (want + have - 1) / std::max<int64_t>(have, 1));
+      ks = std::max<int64_t>(1, std::min<int64_t>(ks, 256));
+      if (ks > 1) {
+        p.kchunk = int32_t((((p.K + ks - 1) / ks) + 7) / 8 * 8);
+        p.ksplit = int32_t((p.K + p.kchunk - 1) / p.kchunk);
+      }
+    }
+    if (p.ksplit > 1) {
+      p.ws = ws;
+      ws += int64_t(p.ksplit) * p.M * p.N;
+      g.red_elems += int64_t(p.M) * p.N;
+    }
+    p.tile0 = tile0;
+    tile0 += p.tiles_m * p.tiles_n * p.ksplit;
+  }
   g.n_probs = int(g.h_probs.size());
   g.n_tiles = tile0;
+  if (ws) {
+    g.ws_is = ws;
+    g.d_ws = (cplx*)c.dalloc(sizeof(cplx) * ws * c.ninst);
+  }
   if (g.n_probs) {
     g.d_probs = (GemmProb*)c.dalloc(g.h_probs.size() * sizeof(GemmProb));
     upload(c, g.d_probs, g.h_probs.data(), g.h_probs.size() * sizeof(GemmProb));
@@ -434,6 +462,8 @@ void einsum(Ctx& c, const std::string& site, cplx alpha, Operand A, Operand B, T
     P = it->second.get();
   }
   // execute
+  const bool prof = c.profile;
+  if (prof) CK(cudaEventRecord(c.pev0, c.stream));
   if (P->permA) {
     cplx one = make_double2(1, 0);
     launch_permute(c, P->pA, P->A2.d, A.t->d, P->A2.is, A.t->is, &one, false, false);
@@ -443,6 +473,8 @@ void einsum(Ctx& c, const std::string& site, cplx alpha, Operand A, Operand B, T
     launch_permute(c, P->pB, P->B2.d, B.t->d, P->B2.is, B.t->is, &one, false, false);
   }
   Tensor* Cg = P->permC ? &P->C2 : &C;
+  P->gemm_out = Cg->d;
+  P->gemm_out_is = Cg->is;
   if (P->emulate)
     emu_run(c, P->emu, P->g, P->A->d, P->B->d, Cg->d, P->A->is, P->B->is, Cg->is, alpha,
             P->gemm_beta);
@@ -451,4 +483,16 @@ void einsum(Ctx& c, const std::string& site, cplx alpha, Operand A, Operand B, T
                      P->gemm_beta);
   if (P->permC)
     launch_permute(c, P->pC, C.d, P->C2.d, C.is, P->C2.is, P->cterms, accumulate, false);
+  if (prof) {
+    CK(cudaEventRecord(c.pev1, c.stream));
+    CK(cudaEventSynchronize(c.pev1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, c.pev0, c.pev1));
+    int64_t M = 0, N = 0, K = 0;
+    for (auto& q : P->g.h_probs) { M = std::max<int64_t>(M, q.M); N = std::max<int64_t>(N, q.N); K = std::max<int64_t>(K, q.K); }
+    fprintf(stderr, "[exp_profile] %-8s %9.3f ms  %10.3g cMAC  %7.1f GF/s  probs=%d maxM=%lld maxN=%lld maxK=%lld perm=%d%d%d emu=%d\n",
+            site.c_str(), ms, double(P->g.flops_mac) * c.ninst,
+            8.0 * double(P->g.flops_mac) * c.ninst / (ms * 1e6), P->g.n_probs, (long long)M, (long long)N,
+            (long long)K, P->permA, P->permB, P->permC, P->emulate);
+  }
 }

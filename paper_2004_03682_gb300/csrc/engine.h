@@ -75,9 +75,13 @@ struct ChunkRef {
 
 struct GemmProb {  // one block of a grouped GEMM: C[MxN] (+)= alpha A[MxK] B[KxN], row-major
   int64_t a, b, c;  // element offsets inside the per-instance tensors
+  int64_t ws;       // split-K partials offset in the plan's scratch (ksplit > 1)
   int32_t M, N, K;
   int32_t tile0;    // first tile index of this problem
   int32_t tiles_n;  // tiles along N
+  int32_t tiles_m;
+  int32_t ksplit;   // K ranges computed by separate CTAs, summed in fixed order
+  int32_t kchunk;   // K per split (multiple of 8)
 };
 
 struct GenTask {  // integral generator: one sub-block
@@ -123,6 +127,9 @@ struct GemmPlan {
   GemmProb* d_probs = nullptr;
   int n_probs = 0;
   int n_tiles = 0;
+  cplx* d_ws = nullptr;      // split-K partials, ws_is elements per instance
+  int64_t ws_is = 0;
+  int64_t red_elems = 0;     // output elements of split problems (per instance)
   int64_t flops_mac = 0;  // complex MACs per instance
   std::vector<GemmProb> h_probs;
 };
@@ -140,6 +147,8 @@ struct EinsumPlan {
   cplx alpha;
   cplx cterms[EXP_MAX_TERMS];
   bool gemm_beta = false;
+  cplx* gemm_out = nullptr;  // GEMM output when it writes the destination directly
+  int64_t gemm_out_is = 0;
   bool emulate = false;
   EmuPlan* emu = nullptr;
   size_t scratch_bytes = 0;
@@ -208,7 +217,10 @@ struct Ctx {
   cudaGraphExec_t graph = nullptr;
   int64_t graph_kernels = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  bool profile = false;  // EXP_PROFILE=1: eager iterations, per-contraction timing on stderr
+  cudaEvent_t pev0 = nullptr, pev1 = nullptr;
 
+  int* d_emu_err = nullptr;  // set by a bounded device wait that gave up
   // emulation and driver state
   void* emu_state = nullptr;
   void* ccsd_state = nullptr;
@@ -218,6 +230,7 @@ struct Ctx {
 };
 
 // Helpers (engine.cu)
+GemmPlan make_gemm_plan(Ctx& c, const Layout& A, const Layout& B, const Layout& C);
 void build_layout(Layout& L, const std::vector<Space>& spaces, int G);
 Layout make_layout(const std::vector<Space>& spaces, int G, int rank, const int* sp,
                    const int* sg, int nrow);

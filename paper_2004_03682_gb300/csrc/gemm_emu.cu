@@ -1,6 +1,583 @@
-// placeholder, replaced by the tcgen05 emulation below
+// Split-precision emulation of complex-FP64 GEMM on the 5th-generation tensor
+// cores (tcgen05, BF16 in, FP32 accumulate in TMEM), for the large contractions
+// of step 3 of the TTGT list (Sec. II.B).
+//
+// Method: error-free splitting in the manner of Ozaki, Ogita, Oishi and Rump
+// ("Error-free transformations of matrix multiplication by using fast routines
+// of matrix multiplication and its applications", Numer. Algorithms 59, 2012).
+// Every row of A (column of B) gets a power-of-two exponent E with |x| < 2^E;
+// x 2^-E is cut into S integer slices of BETA bits,
+//     x 2^-E = sum_s a_s 2^(-BETA s),  a_1 in [-2^BETA, 2^BETA], a_s in [-2^(BETA-1), 2^(BETA-1)],
+// each exact in BF16.  The products a_s b_t with s + t <= S + 1 ("diagonals" d =
+// s + t) are summed on the tensor cores; every diagonal has its own FP32 TMEM
+// accumulator and stays an exact integer over a chunk of KC real K terms, so
+// the chunk sums are folded exactly into an int64 per output element:
+//     R += sum_d acc_d 2^(BETA (S + 1 - d)),   C = 2^(E_i + F_j - BETA (S + 1)) R.
+// Complex operands use the real embedding C' = A' B'' with A' = [Re A | Im A]
+// (K' = 2K) and B'' columns (2j, 2j+1) = ([Re B_j; -Im B_j], [Im B_j; Re B_j]).
+//
+// Kernel: one CTA per 128 x (BN/2 complex) output tile; warp 0 issues 1-D TMA
+// bulk copies of pre-tiled slice tiles (the split kernels write them in the
+// canonical no-swizzle K-major UMMA layout), warp 1 issues tcgen05.mma (one
+// MMA per A slice s covers all diagonals s+1..S+1 by stacking the B slices
+// along N), warps 2-5 drain the double-buffered TMEM accumulators.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cstdio>
+
 #include "emu.h"
-bool emu_wanted(Ctx& c, const GemmPlan& g, const std::string& site) { return false; }
-EmuPlan* emu_plan(Ctx&, const GemmPlan&, const Tensor*, const Tensor*, bool, bool) { return nullptr; }
-void emu_run(Ctx&, EmuPlan*, const GemmPlan&, const cplx*, const cplx*, cplx*, int64_t, int64_t, int64_t, cplx, bool) {}
-void emu_release(Ctx&) {}
+
+namespace {
+
+constexpr int BM = 128;        // rows per tile (tcgen05 M)
+constexpr int KB = 32;         // real K per smem k-block (4 core matrices of 8 bf16)
+constexpr int BETA = 7;        // bits per slice
+constexpr int KC_BLOCKS = 16;  // k-blocks per exact chunk: KC = 512 real terms
+constexpr int STAGES = 3;
+constexpr int THREADS = 192;   // 6 warps
+
+template <int S>
+struct Shape {
+  static constexpr int BN = S <= 5 ? 48 : 32;  // real output columns per tile
+  static constexpr int A_TILE = BM * KB;       // bf16 elements per slice tile
+  static constexpr int B_TILE = BN * KB;
+  static constexpr int A_STAGE = S * A_TILE * 2;  // bytes
+  static constexpr int B_STAGE = S * B_TILE * 2;
+  static constexpr int STAGE = A_STAGE + B_STAGE;
+  static constexpr int ACC = S * BN;             // TMEM columns per accumulator buffer
+  static constexpr int SMEM = STAGES * STAGE + 1024 + 256;
+  static_assert(2 * ACC <= 512, "TMEM");
+  static_assert(S * BN <= 256, "MMA N");
+  static_assert(BN % 16 == 0, "N multiple of 16");
+};
+
+struct EmuProb {
+  int64_t a_src, b_src, c_off;  // complex offsets in the per-instance A, B, C tensors
+  int64_t a_sl, b_sl;           // bf16 offsets of the slice tiles (per instance)
+  int64_t a_ex, b_ex;           // offsets of the exponent arrays (per instance)
+  int32_t M, N, K, Kp;          // Kp = 2K padded to KB
+  int32_t tiles_m, tiles_n, tile0, pad;
+};
+
+// ---------------------------------------------------------------------------
+// PTX helpers
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t n) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(n));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(su32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: gives up after ~2 s (or when another role already gave up),
+// recording the failure; never spins forever.
+__device__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort, int* gerr) {
+  if (mbar_try(b, parity)) return true;
+  const uint64_t t0 = gtimer();
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try(b, parity)) return true;
+    if ((it & 255) == 0) {
+      if (*abort) return false;
+      if (gtimer() - t0 > 2000000000ull) {
+        *abort = 1;
+        atomicExch(gerr, 1);
+        return false;
+      }
+    }
+  }
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(su32(dst)),
+               "l"(src), "r"(bytes), "r"(su32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// canonical K-major, no swizzle: core matrix = 8 rows x 16 B; LBO = step between
+// core matrices along K, SBO = step between 8-row groups.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return uint64_t((addr >> 4) & 0x3FFF) | (uint64_t((lbo >> 4) & 0x3FFF) << 16) |
+         (uint64_t((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+// kind::f16 instruction descriptor: D F32, A/B BF16, both K-major, M = 128.
+__device__ __forceinline__ uint32_t idesc_bf16(int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(N >> 3) << 17) | (uint32_t(BM >> 4) << 24);
+}
+__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(id), "r"(acc));
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar)) : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// offset (in elements) of element (r, k) inside a tile of `rows` x KB, core-matrix order
+__device__ __forceinline__ int core_off(int r, int k) { return ((r >> 3) * (KB / 8) + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7); }
+
+// ---------------------------------------------------------------------------
+// GEMM kernel
+template <int S>
+__global__ void __launch_bounds__(THREADS, 1)
+    k_emu_gemm(const EmuProb* __restrict__ probs, int nprobs, const __nv_bfloat16* __restrict__ Asl,
+               const __nv_bfloat16* __restrict__ Bsl, const int* __restrict__ Aex, const int* __restrict__ Bex,
+               cplx* __restrict__ C, int64_t asl_is, int64_t bsl_is, int64_t aex_is, int64_t bex_is, int64_t c_is,
+               cplx alpha, int beta, int* __restrict__ gerr) {
+  using SH = Shape<S>;
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)((uintptr_t(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* full = (uint64_t*)(smem + STAGES * SH::STAGE);
+  uint64_t* empty = full + STAGES;
+  uint64_t* accf = empty + STAGES;
+  uint64_t* acce = accf + 2;
+  uint64_t* drain = acce + 2;
+  uint32_t* tslot = (uint32_t*)(drain + 1);
+  volatile int* abort = (volatile int*)(tslot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tile = blockIdx.x, inst = blockIdx.y;
+  int pi = 0;
+  while (pi + 1 < nprobs && probs[pi + 1].tile0 <= tile) ++pi;
+  const EmuProb P = probs[pi];
+  const int lt = tile - P.tile0;
+  const int mt = lt / P.tiles_n, nt = lt % P.tiles_n;
+  const int nkb = P.Kp / KB;
+  const int nchunks = (nkb + KC_BLOCKS - 1) / KC_BLOCKS;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+    for (int b = 0; b < 2; ++b) { mbar_init(&accf[b], 1); mbar_init(&acce[b], 4); }
+    mbar_init(drain, 1);
+    *abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)), "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tslot;
+
+  const __nv_bfloat16* Ab = Asl + inst * asl_is + P.a_sl + int64_t(mt) * nkb * (S * SH::A_TILE);
+  const __nv_bfloat16* Bb = Bsl + inst * bsl_is + P.b_sl + int64_t(nt) * nkb * (S * SH::B_TILE);
+
+  if (warp == 0) {
+    // ---- producer: 1-D TMA bulk copies of the pre-tiled slice tiles
+    if (lane == 0) {
+      int kb = 0;
+      for (; kb < nkb; ++kb) {
+        const int st = kb % STAGES;
+        if (kb >= STAGES && !mbar_wait(&empty[st], ((kb / STAGES) & 1) ^ 1, abort, gerr)) break;
+        uint8_t* sA = smem + st * SH::STAGE;
+        uint8_t* sB = sA + SH::A_STAGE;
+        mbar_expect_tx(&full[st], SH::STAGE);
+        bulk_g2s(sA, Ab + int64_t(kb) * S * SH::A_TILE, SH::A_STAGE, &full[st]);
+        bulk_g2s(sB, Bb + int64_t(kb) * S * SH::B_TILE, SH::B_STAGE, &full[st]);
+      }
+      if (*abort) {
+        // let the copies already issued land before the CTA exits
+        for (int k = max(0, kb - STAGES); k < kb; ++k) {
+          volatile int dummy = 0;
+          mbar_wait(&full[k % STAGES], (k / STAGES) & 1, &dummy, gerr);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---- MMA issuer
+    if (lane == 0) {
+      for (int kb = 0; kb < nkb; ++kb) {
+        const int st = kb % STAGES;
+        const int ch = kb / KC_BLOCKS, buf = ch & 1;
+        const bool first = (kb % KC_BLOCKS) == 0;
+        if (first && ch >= 2) {
+          if (!mbar_wait(&acce[buf], ((ch >> 1) - 1) & 1, abort, gerr)) break;
+          fence_after();
+        }
+        if (!mbar_wait(&full[st], (kb / STAGES) & 1, abort, gerr)) break;
+        fence_after();
+        const uint32_t aA = su32(smem + st * SH::STAGE);
+        const uint32_t aB = aA + SH::A_STAGE;
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+          const uint32_t id = idesc_bf16((S - s) * SH::BN);
+          const uint32_t d = tmem + buf * 256 + s * SH::BN;
+#pragma unroll
+          for (int k16 = 0; k16 < 2; ++k16) {
+            const uint64_t ad = sdesc(aA + s * SH::A_TILE * 2 + k16 * 256, 128, 512);
+            const uint64_t bd = sdesc(aB + k16 * 256, 128, 512);
+            mma_bf16(d, ad, bd, id, (first && s == 0 && k16 == 0) ? 0u : 1u);
+          }
+        }
+        mma_commit(&empty[st]);
+        if ((kb % KC_BLOCKS) == KC_BLOCKS - 1 || kb == nkb - 1) mma_commit(&accf[buf]);
+      }
+    }
+  } else {
+    // ---- epilogue: 4 warps, one TMEM lane (= output row) per thread
+    const int q = warp & 3;  // TMEM lane quarter this warp may access
+    const int row = q * 32 + lane;
+    long long R[SH::BN];
+#pragma unroll
+    for (int j = 0; j < SH::BN; ++j) R[j] = 0;
+    bool ok = true;
+    for (int ch = 0; ch < nchunks && ok; ++ch) {
+      const int buf = ch & 1;
+      if (!mbar_wait(&accf[buf], (ch >> 1) & 1, abort, gerr)) { ok = false; break; }
+      fence_after();
+#pragma unroll
+      for (int dgi = 0; dgi < S; ++dgi) {
+        const int shift = BETA * (S - 1 - dgi);
+#pragma unroll
+        for (int j16 = 0; j16 < SH::BN / 16; ++j16) {
+          uint32_t v[16];
+          tmem_ld16(tmem + (uint32_t(q * 32) << 16) + buf * 256 + dgi * SH::BN + j16 * 16, v);
+          tmem_wait_ld();
+#pragma unroll
+          for (int u = 0; u < 16; ++u)
+            R[j16 * 16 + u] += (long long)__float2int_rn(__uint_as_float(v[u])) << shift;
+        }
+      }
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acce[buf]);
+    }
+    if (ok) {
+      const int gi = mt * BM + row;
+      if (gi < P.M) {
+        const int ei = Aex[inst * aex_is + P.a_ex + gi];
+        cplx* Crow = C + inst * c_is + P.c_off + int64_t(gi) * P.N;
+#pragma unroll
+        for (int jj = 0; jj < SH::BN / 2; ++jj) {
+          const int gj = nt * (SH::BN / 2) + jj;
+          if (gj < P.N) {
+            const int e = ei + Bex[inst * bex_is + P.b_ex + gj] - BETA * (S + 1);
+            const double re = ldexp(double(R[2 * jj]), e), im = ldexp(double(R[2 * jj + 1]), e);
+            double vr = alpha.x * re - alpha.y * im, vi = alpha.x * im + alpha.y * re;
+            if (beta) { const cplx o = Crow[gj]; vr += o.x; vi += o.y; }
+            Crow[gj] = make_double2(vr, vi);
+          }
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (*abort && threadIdx.x == 32) {
+    // wait (bounded) for MMAs still in flight before TMEM is released
+    mma_commit(drain);
+    volatile int dummy = 0;
+    mbar_wait(drain, 0, &dummy, gerr);
+  }
+  __syncthreads();
+  if (warp == 0) {
+    __syncwarp();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Split kernels.  Exponent E of a row (column) = smallest integer with
+// max |Re|, |Im| < 2^E (0 for an all-zero row).
+__device__ __forceinline__ int exp_of(double m) { return m > 0.0 ? ilogb(m) + 1 : 0; }
+
+__global__ void k_row_exp(const EmuProb* __restrict__ probs, int nprobs, const cplx* __restrict__ A, int64_t a_is,
+                          int* __restrict__ ex, int64_t ex_is, int total_rows) {
+  const int inst = blockIdx.y;
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (w >= total_rows) return;
+  // find the problem owning global row w (problems' rows are concatenated)
+  int pi = 0, base = 0;
+  while (pi < nprobs && w >= base + probs[pi].M) { base += probs[pi].M; ++pi; }
+  const EmuProb P = probs[pi];
+  const int r = w - base;
+  const cplx* a = A + inst * a_is + P.a_src + int64_t(r) * P.K;
+  double m = 0.0;
+  for (int k = lane; k < P.K; k += 32) m = fmax(m, fmax(fabs(a[k].x), fabs(a[k].y)));
+  for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane == 0) ex[inst * ex_is + P.a_ex + r] = exp_of(m);
+}
+
+__global__ void k_col_exp(const EmuProb* __restrict__ probs, int nprobs, const cplx* __restrict__ B, int64_t b_is,
+                          int* __restrict__ ex, int64_t ex_is, int total_cols) {
+  const int inst = blockIdx.y;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= total_cols) return;
+  int pi = 0, base = 0;
+  while (pi < nprobs && c >= base + probs[pi].N) { base += probs[pi].N; ++pi; }
+  const EmuProb P = probs[pi];
+  const int j = c - base;
+  const cplx* b = B + inst * b_is + P.b_src + j;
+  double m = 0.0;
+  for (int k = 0; k < P.K; ++k) m = fmax(m, fmax(fabs(b[int64_t(k) * P.N].x), fabs(b[int64_t(k) * P.N].y)));
+  ex[inst * ex_is + P.b_ex + j] = exp_of(m);
+}
+
+template <int S>
+__device__ __forceinline__ void slice_store(double x, __nv_bfloat16* dst, int64_t stride) {
+  // x in (-1, 1): a_1 = rint(x 2^B), r <- x 2^B - a_1, a_2 = rint(r 2^B), ...  (exact in FP64)
+  double r = x;
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    r = r * double(1 << BETA);
+    const double a = rint(r);
+    r -= a;
+    dst[s * stride] = __float2bfloat16_rn(float(a));
+  }
+}
+
+// A slices: tile (mt, kb) per CTA, elements (row r, real k') of A' = [Re A | Im A].
+template <int S>
+__global__ void __launch_bounds__(256) k_split_a(const EmuProb* __restrict__ probs, int nprobs, const cplx* __restrict__ A,
+                                                 int64_t a_is, const int* __restrict__ ex, int64_t ex_is,
+                                                 __nv_bfloat16* __restrict__ out, int64_t out_is) {
+  using SH = Shape<S>;
+  const int inst = blockIdx.y;
+  int t = blockIdx.x, pi = 0;
+  // tile index space: per problem tiles_m * nkb
+  while (pi + 1 < nprobs && t >= probs[pi].tile0 + probs[pi].tiles_m * (probs[pi].Kp / KB)) ++pi;
+  const EmuProb P = probs[pi];
+  const int nkb = P.Kp / KB;
+  const int lt = t - P.tile0;
+  const int mt = lt / nkb, kb = lt % nkb;
+  __nv_bfloat16* o = out + inst * out_is + P.a_sl + (int64_t(mt) * nkb + kb) * (S * SH::A_TILE);
+  const cplx* a = A + inst * a_is + P.a_src;
+  const int* e = ex + inst * ex_is + P.a_ex;
+  for (int idx = threadIdx.x; idx < BM * KB; idx += blockDim.x) {
+    const int r = idx / KB, k = idx % KB;
+    const int gi = mt * BM + r, gk = kb * KB + k;
+    double x = 0.0;
+    if (gi < P.M && gk < 2 * P.K) {
+      const cplx v = a[int64_t(gi) * P.K + (gk < P.K ? gk : gk - P.K)];
+      x = ldexp(gk < P.K ? v.x : v.y, -e[gi]);
+    }
+    slice_store<S>(x, o + core_off(r, k), SH::A_TILE);
+  }
+}
+
+// B'' slices: rows n' = 2j + c of B'' (c = 0: [Re B_j; -Im B_j], c = 1: [Im B_j; Re B_j]).
+template <int S>
+__global__ void __launch_bounds__(256) k_split_b(const EmuProb* __restrict__ probs, int nprobs, const cplx* __restrict__ B,
+                                                 int64_t b_is, const int* __restrict__ ex, int64_t ex_is,
+                                                 __nv_bfloat16* __restrict__ out, int64_t out_is, int tile_base) {
+  using SH = Shape<S>;
+  const int inst = blockIdx.y;
+  int t = blockIdx.x, pi = 0;
+  while (pi + 1 < nprobs && t >= probs[pi + 1].pad) ++pi;  // pad = first split-B tile of the problem
+  const EmuProb P = probs[pi];
+  const int nkb = P.Kp / KB;
+  const int lt = t - P.pad;
+  const int nt = lt / nkb, kb = lt % nkb;
+  __nv_bfloat16* o = out + inst * out_is + P.b_sl + (int64_t(nt) * nkb + kb) * (S * SH::B_TILE);
+  const cplx* b = B + inst * b_is + P.b_src;
+  const int* e = ex + inst * ex_is + P.b_ex;
+  for (int idx = threadIdx.x; idx < SH::BN * KB; idx += blockDim.x) {
+    const int k = idx / SH::BN, r = idx % SH::BN;  // r fastest: consecutive j reads
+    const int gj = nt * (SH::BN / 2) + (r >> 1), c = r & 1;
+    const int gk = kb * KB + k;
+    double x = 0.0;
+    if (gj < P.N && gk < 2 * P.K) {
+      const bool lo = gk < P.K;
+      const cplx v = b[int64_t(lo ? gk : gk - P.K) * P.N + gj];
+      const double val = c == 0 ? (lo ? v.x : -v.y) : (lo ? v.y : v.x);
+      x = ldexp(val, -e[gj]);
+    }
+    slice_store<S>(x, o + core_off(r, k), SH::B_TILE);
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+struct EmuPlan {
+  int S = 5;
+  std::vector<EmuProb> h;
+  EmuProb* d = nullptr;
+  int n_tiles = 0, n_atiles = 0, n_btiles = 0;
+  int total_rows = 0, total_cols = 0;
+  __nv_bfloat16* asl = nullptr;
+  __nv_bfloat16* bsl = nullptr;
+  int* aex = nullptr;
+  int* bex = nullptr;
+  int64_t asl_is = 0, bsl_is = 0, aex_is = 0, bex_is = 0;
+  bool a_const = false, b_const = false, a_ready = false, b_ready = false;
+  int* d_err = nullptr;
+};
+
+struct EmuState {
+  std::vector<EmuPlan*> plans;
+  int* d_err = nullptr;
+};
+
+bool emu_wanted(Ctx& c, const GemmPlan& g, const std::string&) {
+  if (c.cfg.precision != EXP_EMU_BF16) return false;
+  if (c.cfg.emu_min_macs > 0) return double(g.flops_mac) >= c.cfg.emu_min_macs;
+  if (g.flops_mac < int64_t(1) << 26) return false;
+  int64_t big = 0;
+  for (auto& p : g.h_probs)
+    if (p.M >= 64 && p.K >= 32 && p.N >= 8) big += int64_t(p.M) * p.N * p.K;
+  return big * 10 >= g.flops_mac * 9;  // nearly all work in GEMM-shaped blocks
+}
+
+template <int S>
+static void set_smem_attr() {
+  static bool done = false;
+  if (!done) {
+    CK(cudaFuncSetAttribute(k_emu_gemm<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, Shape<S>::SMEM));
+    done = true;
+  }
+}
+
+static int bn_of(int S) { return S <= 5 ? 48 : 32; }
+
+EmuPlan* emu_plan(Ctx& c, const GemmPlan& g, const Tensor* A, const Tensor* B, bool a_const, bool b_const) {
+  EmuState* st = (EmuState*)c.emu_state;
+  if (!st) {
+    st = new EmuState();
+    c.emu_state = st;
+    st->d_err = (int*)c.dalloc(sizeof(int));
+    CK(cudaMemsetAsync(st->d_err, 0, sizeof(int), c.stream));
+    c.d_emu_err = st->d_err;
+  }
+  EmuPlan* p = new EmuPlan();
+  st->plans.push_back(p);
+  p->S = c.cfg.n_slices;
+  p->a_const = a_const;
+  p->b_const = b_const;
+  p->d_err = st->d_err;
+  const int BN = bn_of(p->S);
+  int64_t asl = 0, bsl = 0, aex = 0, bex = 0;
+  int tile0 = 0, at0 = 0, bt0 = 0;
+  for (auto& q : g.h_probs) {
+    EmuProb e{};
+    e.a_src = q.a;
+    e.b_src = q.b;
+    e.c_off = q.c;
+    e.M = q.M;
+    e.N = q.N;
+    e.K = q.K;
+    e.Kp = ((2 * q.K + KB - 1) / KB) * KB;
+    if (e.Kp == 0) e.Kp = KB;
+    e.tiles_m = (q.M + BM - 1) / BM;
+    e.tiles_n = (q.N + BN / 2 - 1) / (BN / 2);
+    e.tile0 = tile0;
+    tile0 += e.tiles_m * e.tiles_n;
+    const int nkb = e.Kp / KB;
+    e.a_sl = asl;
+    e.b_sl = bsl;
+    asl += int64_t(e.tiles_m) * nkb * p->S * BM * KB;
+    bsl += int64_t(e.tiles_n) * nkb * p->S * BN * KB;
+    e.a_ex = aex;
+    e.b_ex = bex;
+    aex += q.M;
+    bex += q.N;
+    p->total_rows += q.M;
+    p->total_cols += q.N;
+    e.pad = bt0;  // first split-B tile
+    bt0 += e.tiles_n * nkb;
+    at0 += e.tiles_m * nkb;
+    p->h.push_back(e);
+  }
+  // split-A tile indexing reuses tile0 as the first split-A tile of each problem
+  std::vector<EmuProb> ha = p->h;
+  {
+    int t = 0;
+    for (auto& e : ha) { e.tile0 = t; t += e.tiles_m * (e.Kp / KB); }
+  }
+  p->n_tiles = tile0;
+  p->n_atiles = at0;
+  p->n_btiles = bt0;
+  p->asl_is = std::max<int64_t>(asl, 1);
+  p->bsl_is = std::max<int64_t>(bsl, 1);
+  p->aex_is = std::max<int64_t>(aex, 1);
+  p->bex_is = std::max<int64_t>(bex, 1);
+  p->asl = (__nv_bfloat16*)c.dalloc(sizeof(__nv_bfloat16) * p->asl_is * c.ninst);
+  p->bsl = (__nv_bfloat16*)c.dalloc(sizeof(__nv_bfloat16) * p->bsl_is * c.ninst);
+  p->aex = (int*)c.dalloc(sizeof(int) * p->aex_is * c.ninst);
+  p->bex = (int*)c.dalloc(sizeof(int) * p->bex_is * c.ninst);
+  // two device copies of the problem list: [0, n) for the GEMM and split-B, [n, 2n) for split-A
+  std::vector<EmuProb> both = p->h;
+  both.insert(both.end(), ha.begin(), ha.end());
+  p->d = (EmuProb*)c.dalloc(sizeof(EmuProb) * both.size());
+  upload(c, p->d, both.data(), sizeof(EmuProb) * both.size());
+  (void)A;
+  (void)B;
+  return p;
+}
+
+template <int S>
+static void run_s(Ctx& c, EmuPlan* p, const cplx* A, const cplx* B, cplx* C, int64_t ais, int64_t bis, int64_t cis,
+                  cplx alpha, bool beta) {
+  const int np = int(p->h.size());
+  if (!p->a_ready) {
+    k_row_exp<<<dim3((p->total_rows * 32 + 255) / 256, c.ninst), 256, 0, c.stream>>>(p->d, np, A, ais, p->aex, p->aex_is,
+                                                                                     p->total_rows);
+    KCHECK(c);
+    k_split_a<S><<<dim3(p->n_atiles, c.ninst), 256, 0, c.stream>>>(p->d + np, np, A, ais, p->aex, p->aex_is, p->asl,
+                                                                   p->asl_is);
+    KCHECK(c);
+    if (p->a_const) p->a_ready = true;
+  }
+  if (!p->b_ready) {
+    k_col_exp<<<dim3((p->total_cols + 127) / 128, c.ninst), 128, 0, c.stream>>>(p->d, np, B, bis, p->bex, p->bex_is,
+                                                                                p->total_cols);
+    KCHECK(c);
+    k_split_b<S><<<dim3(p->n_btiles, c.ninst), 256, 0, c.stream>>>(p->d, np, B, bis, p->bex, p->bex_is, p->bsl,
+                                                                   p->bsl_is, 0);
+    KCHECK(c);
+    if (p->b_const) p->b_ready = true;
+  }
+  set_smem_attr<S>();
+  k_emu_gemm<S><<<dim3(p->n_tiles, c.ninst), THREADS, Shape<S>::SMEM, c.stream>>>(
+      p->d, np, p->asl, p->bsl, p->aex, p->bex, C, p->asl_is, p->bsl_is, p->aex_is, p->bex_is, cis, alpha, beta ? 1 : 0,
+      p->d_err);
+  KCHECK(c);
+}
+
+void emu_run(Ctx& c, EmuPlan* p, const GemmPlan&, const cplx* A, const cplx* B, cplx* C, int64_t ais, int64_t bis,
+             int64_t cis, cplx alpha, bool beta) {
+  if (p->n_tiles == 0) return;
+  switch (p->S) {
+    case 3: run_s<3>(c, p, A, B, C, ais, bis, cis, alpha, beta); break;
+    case 4: run_s<4>(c, p, A, B, C, ais, bis, cis, alpha, beta); break;
+    case 5: run_s<5>(c, p, A, B, C, ais, bis, cis, alpha, beta); break;
+    default: run_s<6>(c, p, A, B, C, ais, bis, cis, alpha, beta); break;
+  }
+}
+
+void emu_release(Ctx& c) {
+  EmuState* st = (EmuState*)c.emu_state;
+  if (!st) return;
+  for (auto* p : st->plans) delete p;
+  delete st;
+  c.emu_state = nullptr;
+}

@@ -3,6 +3,8 @@
 // loop of Fig. "mult" flattened into a tile list).  Row-major operands,
 // C[MxN] = alpha A[MxK] B[KxN] (+ C).  SIMT FP64 FMA: GB300's FP64 rate is the
 // roofline for this path.
+#include <algorithm>
+
 #include "engine.h"
 
 #define GT_M 64
@@ -13,15 +15,20 @@ __global__ void __launch_bounds__(256) k_gemm_fp64(const GemmProb* __restrict__ 
                                                    const cplx* __restrict__ A,
                                                    const cplx* __restrict__ B, cplx* __restrict__ C,
                                                    int64_t ais, int64_t bis, int64_t cis,
-                                                   cplx alpha, int beta) {
+                                                   cplx alpha, int beta, cplx* __restrict__ ws,
+                                                   int64_t ws_is) {
   __shared__ cplx As[GT_K][GT_M];
   __shared__ cplx Bs[GT_K][GT_N];
   const int tile = blockIdx.x;
   int pi = 0;
   while (pi + 1 < n_probs && probs[pi + 1].tile0 <= tile) ++pi;
   const GemmProb P = probs[pi];
-  const int lt = tile - P.tile0;
+  int lt = tile - P.tile0;
+  const int tmn = P.tiles_m * P.tiles_n;
+  const int ks = lt / tmn;  // K split index
+  lt -= ks * tmn;
   const int m0 = (lt / P.tiles_n) * GT_M, n0 = (lt % P.tiles_n) * GT_N;
+  const int kbeg = ks * P.kchunk, kend = min(P.K, kbeg + P.kchunk);
   A += blockIdx.y * ais + P.a;
   B += blockIdx.y * bis + P.b;
   C += blockIdx.y * cis + P.c;
@@ -31,21 +38,21 @@ __global__ void __launch_bounds__(256) k_gemm_fp64(const GemmProb* __restrict__ 
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) accr[i][j] = acci[i][j] = 0.0;
-  for (int k0 = 0; k0 < P.K; k0 += GT_K) {
+  for (int k0 = kbeg; k0 < kend; k0 += GT_K) {
     // A tile: 64 x 8 -> 512 elements, 2 per thread
 #pragma unroll
     for (int l = 0; l < 2; ++l) {
       const int e = threadIdx.x + l * 256;
       const int mm = e >> 3, kk = e & 7;
       const int gm = m0 + mm, gk = k0 + kk;
-      As[kk][mm] = (gm < P.M && gk < P.K) ? A[int64_t(gm) * P.K + gk] : make_double2(0, 0);
+      As[kk][mm] = (gm < P.M && gk < kend) ? A[int64_t(gm) * P.K + gk] : make_double2(0, 0);
     }
 #pragma unroll
     for (int l = 0; l < 2; ++l) {
       const int e = threadIdx.x + l * 256;
       const int kk = e >> 6, nn = e & 63;
       const int gk = k0 + kk, gn = n0 + nn;
-      Bs[kk][nn] = (gk < P.K && gn < P.N) ? B[int64_t(gk) * P.N + gn] : make_double2(0, 0);
+      Bs[kk][nn] = (gk < kend && gn < P.N) ? B[int64_t(gk) * P.N + gn] : make_double2(0, 0);
     }
     __syncthreads();
 #pragma unroll
@@ -67,6 +74,20 @@ __global__ void __launch_bounds__(256) k_gemm_fp64(const GemmProb* __restrict__ 
     }
     __syncthreads();
   }
+  if (P.ksplit > 1) {  // raw partial for the fixed-order reduction
+    cplx* W = ws + blockIdx.y * ws_is + P.ws + int64_t(ks) * P.M * P.N;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int gm = m0 + ty + 16 * i;
+      if (gm >= P.M) continue;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int gn = n0 + tx + 16 * j;
+        if (gn < P.N) W[int64_t(gm) * P.N + gn] = make_double2(accr[i][j], acci[i][j]);
+      }
+    }
+    return;
+  }
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const int gm = m0 + ty + 16 * i;
@@ -84,10 +105,41 @@ __global__ void __launch_bounds__(256) k_gemm_fp64(const GemmProb* __restrict__ 
   }
 }
 
+// C = alpha * sum_s partial_s (+ C), splits summed in index order (deterministic)
+__global__ void __launch_bounds__(256) k_splitk_reduce(const GemmProb* __restrict__ probs, int n_probs,
+                                                       const cplx* __restrict__ ws, int64_t ws_is,
+                                                       cplx* __restrict__ C, int64_t cis, cplx alpha, int beta) {
+  const int inst = blockIdx.y;
+  for (int p = 0; p < n_probs; ++p) {
+    const GemmProb P = probs[p];
+    if (P.ksplit <= 1) continue;
+    const int64_t n = int64_t(P.M) * P.N;
+    const cplx* W = ws + inst * ws_is + P.ws;
+    cplx* Cp = C + inst * cis + P.c;
+    for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < n; e += int64_t(gridDim.x) * blockDim.x) {
+      double sr = 0.0, si = 0.0;
+      for (int s = 0; s < P.ksplit; ++s) {
+        const cplx w = W[int64_t(s) * n + e];
+        sr += w.x;
+        si += w.y;
+      }
+      double vr = alpha.x * sr - alpha.y * si, vi = alpha.x * si + alpha.y * sr;
+      if (beta) { const cplx o = Cp[e]; vr += o.x; vi += o.y; }
+      Cp[e] = make_double2(vr, vi);
+    }
+  }
+}
+
 void launch_gemm_fp64(Ctx& c, const GemmPlan& g, const cplx* A, const cplx* B, cplx* C, int64_t ais,
                       int64_t bis, int64_t cis, cplx alpha, bool beta) {
   if (g.n_tiles == 0) return;
   k_gemm_fp64<<<dim3(g.n_tiles, c.ninst), 256, 0, c.stream>>>(g.d_probs, g.n_probs, A, B, C, ais, bis,
-                                                              cis, alpha, beta);
+                                                              cis, alpha, beta, g.d_ws, g.ws_is);
   KCHECK(c);
+  if (g.red_elems) {
+    const int blocks = int(std::min<int64_t>((g.red_elems + 255) / 256, 2LL * std::max(c.sm_count, 1)));
+    k_splitk_reduce<<<dim3(blocks, c.ninst), 256, 0, c.stream>>>(g.d_probs, g.n_probs, g.d_ws, g.ws_is, C, cis,
+                                                                 alpha, beta);
+    KCHECK(c);
+  }
 }

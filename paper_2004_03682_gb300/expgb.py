@@ -40,7 +40,8 @@ class Config(C.Structure):
                 ("irrep_occ", C.POINTER(C.c_int32)), ("irrep_virt", C.POINTER(C.c_int32)),
                 ("eps_occ", C.POINTER(C.c_double)), ("eps_virt", C.POINTER(C.c_double)),
                 ("precision", C.c_int), ("n_slices", C.c_int), ("diis_dim", C.c_int),
-                ("conv_tol", C.c_double), ("max_iter", C.c_int), ("guess", C.c_int)]
+                ("conv_tol", C.c_double), ("max_iter", C.c_int), ("guess", C.c_int),
+                ("emu_min_macs", C.c_double)]
 
 
 class IterInfo(C.Structure):
@@ -68,6 +69,14 @@ def lib():
     L.exp_energy.argtypes = [P, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]
     L.exp_get_amplitudes.argtypes = [P, C.c_int, P, P]
     L.exp_set_amplitudes.argtypes = [P, C.c_int, P, P]
+    L.exp_work_per_iteration.argtypes = [P, C.POINTER(C.c_double)]
+    L.exp_work_per_iteration.restype = C.c_int
+    L.exp_profile_top.argtypes = [P, C.c_int, C.c_char_p, C.c_int, C.POINTER(C.c_double),
+                                  C.POINTER(C.c_double)]
+    L.exp_profile_top.restype = C.c_int
+    L.exp_zgemm.argtypes = [C.POINTER(Allocator), P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, P, P, P,
+                            C.c_double, C.c_double, C.c_int]
+    L.exp_zgemm.restype = C.c_int
     L.exp_kernel_launches.argtypes = [P]
     L.exp_kernel_launches.restype = C.c_int64
     L.exp_last_error.argtypes = [P]
@@ -117,7 +126,7 @@ class Context:
 
     def __init__(self, n_occ, n_virt, irrep_occ, irrep_virt, eps_occ, eps_virt, n_inst=1,
                  precision=EXP_FP64, n_slices=5, diis_dim=6, conv_tol=1e-9, max_iter=500,
-                 guess=EXP_GUESS_MP2, device=0):
+                 guess=EXP_GUESS_MP2, device=0, emu_min_macs=0.0):
         import torch
         self._torch = torch
         L = lib()
@@ -135,7 +144,7 @@ class Context:
         self._keep += [io, iv, eo, ev]
         cfg = Config(self.n_inst, self.n_occ, self.n_virt, len(io), pio, piv, peo, pev,
                      int(precision), int(n_slices), int(diis_dim), float(conv_tol), int(max_iter),
-                     int(guess))
+                     int(guess), float(emu_min_macs))
         h = C.c_void_p()
         st = L.exp_create(C.byref(cfg), C.byref(self.alloc.struct), C.c_void_p(self.stream.cuda_stream),
                           C.byref(h))
@@ -196,6 +205,19 @@ class Context:
         self._check(self.L.exp_set_amplitudes(self.h, int(inst), C.c_void_p(t1.data_ptr()),
                                               C.c_void_p(t2.data_ptr())))
 
+    def work_per_iteration(self) -> float:
+        """Complex multiply-adds of one iteration (all contractions, all instances)."""
+        m = C.c_double()
+        self._check(self.L.exp_work_per_iteration(self.h, C.byref(m)))
+        return m.value
+
+    def profile_top(self, reps=5):
+        """(site, ms per launch, complex MACs per launch) of the largest contraction."""
+        buf = C.create_string_buffer(64)
+        ms, macs = C.c_double(), C.c_double()
+        self._check(self.L.exp_profile_top(self.h, int(reps), buf, 64, C.byref(ms), C.byref(macs)))
+        return buf.value.decode(), ms.value, macs.value
+
     @property
     def launches(self) -> int:
         return int(self.L.exp_kernel_launches(self.h))
@@ -210,6 +232,37 @@ class Context:
             self.close()
         except Exception:
             pass
+
+
+def zgemm(A, B, C=None, alpha=1.0, beta=False, precision=EXP_FP64, n_slices=5):
+    """C = alpha A B (+ C) for complex128 CUDA tensors through exp_zgemm."""
+    import torch
+    L = lib()
+    M, K = A.shape
+    K2, N = B.shape
+    if K != K2:
+        raise ValueError("inner dimensions differ")
+    A = A.contiguous()
+    B = B.contiguous()
+    Cm = torch.zeros((M, N), dtype=torch.complex128, device=A.device) if C is None else C
+    dev = A.device.index or 0
+    stream = torch.cuda.current_stream(dev)
+    alloc = TorchAllocator(dev, stream)
+    a = complex(alpha)
+    st = L.exp_zgemm(_byref(alloc.struct), _vp(stream.cuda_stream), int(precision), int(n_slices),
+                     int(M), int(N), int(K), _vp(A.data_ptr()), _vp(B.data_ptr()), _vp(Cm.data_ptr()),
+                     a.real, a.imag, int(bool(beta)))
+    if st != 0:
+        raise ExpError(st, L.exp_last_error(None).decode())
+    return Cm
+
+
+def _byref(x):
+    return C.byref(x)
+
+
+def _vp(x):
+    return C.c_void_p(x)
 
 
 def from_problems(probs, **kw) -> Context:

@@ -47,7 +47,7 @@ def _cfg(expgb, **over):
     cfg = expgb.Config(d["n_inst"], d["n_occ"], d["n_virt"], d["n_irrep"],
                        io.ctypes.data_as(C.POINTER(C.c_int32)), iv.ctypes.data_as(C.POINTER(C.c_int32)),
                        eo.ctypes.data_as(C.POINTER(C.c_double)), ev.ctypes.data_as(C.POINTER(C.c_double)),
-                       d["precision"], d["n_slices"], d["diis_dim"], d["conv_tol"], d["max_iter"], d["guess"])
+                       d["precision"], d["n_slices"], d["diis_dim"], d["conv_tol"], d["max_iter"], d["guess"], 0.0)
     return cfg, keep
 
 

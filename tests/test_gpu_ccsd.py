@@ -112,3 +112,31 @@ def test_c1_o10_v40_converged_energy(expgb):
     e = ctx.energy(0)
     assert abs(e - complex(g["e_re"], g["e_im"])) < 1e-10
     assert abs(len(recs) - g["n_iter"]) <= 2
+
+
+@pytest.mark.parametrize("S", [4, 5])
+def test_emulated_ccsd_small_blocked(expgb, S):
+    """Every contraction above 1e3 complex MACs through the BF16-sliced emulation:
+    converged energy within 1e-8 Eh of the FP64 oracle."""
+    prob = syn.make_problem(306, 6, 20, 4)
+    b = _oracle(prob)
+    E = ccsd.solve(b, tol=1e-9, max_iter=300)[2]
+    ctx = expgb.from_problems([prob], conv_tol=1e-9, max_iter=300, precision=expgb.EXP_EMU_BF16,
+                              n_slices=S, emu_min_macs=1e3)
+    ctx.init_integrals([prob.seed])
+    _, conv, _ = ctx.iterate(300)
+    assert conv
+    assert abs(ctx.energy(0) - E) < 1e-8
+
+
+def test_emulated_ccsd_c1_o10_v40(expgb):
+    """The C1 workload with the default emulation policy (ladder and other large
+    contractions emulated, 5 slices): converged energy within 1e-8 Eh of the oracle."""
+    g = json.load(open(os.path.join(HERE, "golden", "ccsd_c1_o10_v40.json")))
+    prob = syn.make_problem(g["seed"], g["n_occ"], g["n_virt"], g["G"])
+    ctx = expgb.from_problems([prob], conv_tol=g["tol"], max_iter=g["max_iter"],
+                              precision=expgb.EXP_EMU_BF16, n_slices=5)
+    ctx.init_integrals([prob.seed])
+    _, conv, _ = ctx.iterate(g["max_iter"])
+    assert conv
+    assert abs(ctx.energy(0) - complex(g["e_re"], g["e_im"])) < 1e-8

@@ -323,6 +323,12 @@ void permute_into(Ctx& c, const std::string& site, Tensor& dst, const char* dl, 
 GemmPlan make_gemm_plan(Ctx& c, const Layout& A, const Layout& B, const Layout& C) {
   GemmPlan g;
   int64_t tiles_mn = 0;
+  int64_t maxM = 0, maxN = 0;
+  for (int q = 0; q < c.G; ++q) {
+    if (A.rows[q] && B.cols[q]) { maxM = std::max<int64_t>(maxM, A.rows[q]); maxN = std::max<int64_t>(maxN, B.cols[q]); }
+  }
+  g.tm = maxM <= 16 ? 16 : 64;
+  g.tn = maxN <= 16 ? 16 : 64;
   for (int q = 0; q < c.G; ++q) {
     const int64_t M = A.rows[q], K = A.cols[q], N = B.cols[q];
     if (B.rows[q] != K || C.rows[q] != M || C.cols[q] != N)
@@ -335,8 +341,8 @@ GemmPlan make_gemm_plan(Ctx& c, const Layout& A, const Layout& B, const Layout& 
     p.M = int32_t(M);
     p.N = int32_t(N);
     p.K = int32_t(K);
-    p.tiles_n = int32_t((N + 63) / 64);
-    p.tiles_m = int32_t((M + 63) / 64);
+    p.tiles_n = int32_t((N + g.tn - 1) / g.tn);
+    p.tiles_m = int32_t((M + g.tm - 1) / g.tm);
     p.ksplit = 1;
     p.kchunk = int32_t(((K + 7) / 8) * 8);
     tiles_mn += int64_t(p.tiles_m) * p.tiles_n;
@@ -344,13 +350,13 @@ GemmPlan make_gemm_plan(Ctx& c, const Layout& A, const Layout& B, const Layout& 
     g.h_probs.push_back(p);
   }
   // split K when the output tiles cannot fill the GPU (long-K, small-MN blocks)
-  const int64_t want = 4LL * std::max(c.sm_count, 1);
+  const int64_t want = 8LL * std::max(c.sm_count, 1);
   const int64_t have = tiles_mn * c.ninst;
   int tile0 = 0;
   int64_t ws = 0;
   for (auto& p : g.h_probs) {
-    if (have < 3LL * std::max(c.sm_count, 1) && p.K >= 1024) {
-      int64_t ks = std::min<int64_t>((p.K + 511) / 512, (want + have - 1) / std::max<int64_t>(have, 1));
+    if (have < 2LL * std::max(c.sm_count, 1) && p.K >= 512) {
+      int64_t ks = std::min<int64_t>((p.K + 255) / 256, (want + have - 1) / std::max<int64_t>(have, 1));
       ks = std::max<int64_t>(1, std::min<int64_t>(ks, 256));
       if (ks > 1) {
         p.kchunk = int32_t((((p.K + ks - 1) / ks) + 7) / 8 * 8);

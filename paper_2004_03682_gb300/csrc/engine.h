@@ -127,6 +127,7 @@ struct GemmPlan {
   GemmProb* d_probs = nullptr;
   int n_probs = 0;
   int n_tiles = 0;
+  int tm = 64, tn = 64;      // FP64 tile shape (16 or 64 each)
   cplx* d_ws = nullptr;      // split-K partials, ws_is elements per instance
   int64_t ws_is = 0;
   int64_t red_elems = 0;     // output elements of split problems (per instance)

@@ -7,18 +7,21 @@
 
 #include "engine.h"
 
-#define GT_M 64
-#define GT_N 64
 #define GT_K 8
 
+// Tile TM x TN (each 16 or 64), 256 threads as 16 x 16, every thread computing
+// (TM/16) x (TN/16) outputs; the plan picks 16 along a dimension whose blocks are
+// all <= 16 wide, so skinny contractions do not pay for padding.
+template <int TM, int TN>
 __global__ void __launch_bounds__(256) k_gemm_fp64(const GemmProb* __restrict__ probs, int n_probs,
                                                    const cplx* __restrict__ A,
                                                    const cplx* __restrict__ B, cplx* __restrict__ C,
                                                    int64_t ais, int64_t bis, int64_t cis,
                                                    cplx alpha, int beta, cplx* __restrict__ ws,
                                                    int64_t ws_is) {
-  __shared__ cplx As[GT_K][GT_M];
-  __shared__ cplx Bs[GT_K][GT_N];
+  constexpr int RM = TM / 16, RN = TN / 16;
+  __shared__ cplx As[GT_K][TM];
+  __shared__ cplx Bs[GT_K][TN];
   const int tile = blockIdx.x;
   int pi = 0;
   while (pi + 1 < n_probs && probs[pi + 1].tile0 <= tile) ++pi;
@@ -27,45 +30,40 @@ __global__ void __launch_bounds__(256) k_gemm_fp64(const GemmProb* __restrict__ 
   const int tmn = P.tiles_m * P.tiles_n;
   const int ks = lt / tmn;  // K split index
   lt -= ks * tmn;
-  const int m0 = (lt / P.tiles_n) * GT_M, n0 = (lt % P.tiles_n) * GT_N;
+  const int m0 = (lt / P.tiles_n) * TM, n0 = (lt % P.tiles_n) * TN;
   const int kbeg = ks * P.kchunk, kend = min(P.K, kbeg + P.kchunk);
   A += blockIdx.y * ais + P.a;
   B += blockIdx.y * bis + P.b;
   C += blockIdx.y * cis + P.c;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  double accr[4][4], acci[4][4];
+  double accr[RM][RN], acci[RM][RN];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < RM; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) accr[i][j] = acci[i][j] = 0.0;
+    for (int j = 0; j < RN; ++j) accr[i][j] = acci[i][j] = 0.0;
   for (int k0 = kbeg; k0 < kend; k0 += GT_K) {
-    // A tile: 64 x 8 -> 512 elements, 2 per thread
-#pragma unroll
-    for (int l = 0; l < 2; ++l) {
-      const int e = threadIdx.x + l * 256;
+    for (int e = threadIdx.x; e < TM * GT_K; e += 256) {
       const int mm = e >> 3, kk = e & 7;
       const int gm = m0 + mm, gk = k0 + kk;
       As[kk][mm] = (gm < P.M && gk < kend) ? A[int64_t(gm) * P.K + gk] : make_double2(0, 0);
     }
-#pragma unroll
-    for (int l = 0; l < 2; ++l) {
-      const int e = threadIdx.x + l * 256;
-      const int kk = e >> 6, nn = e & 63;
+    for (int e = threadIdx.x; e < TN * GT_K; e += 256) {
+      const int kk = e / TN, nn = e % TN;
       const int gk = k0 + kk, gn = n0 + nn;
       Bs[kk][nn] = (gk < kend && gn < P.N) ? B[int64_t(gk) * P.N + gn] : make_double2(0, 0);
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < GT_K; ++kk) {
-      cplx a[4], b[4];
+      cplx a[RM], b[RN];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+      for (int i = 0; i < RM; ++i) a[i] = As[kk][ty + 16 * i];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+      for (int j = 0; j < RN; ++j) b[j] = Bs[kk][tx + 16 * j];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < RM; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < RN; ++j) {
           accr[i][j] = fma(a[i].x, b[j].x, accr[i][j]);
           accr[i][j] = fma(-a[i].y, b[j].y, accr[i][j]);
           acci[i][j] = fma(a[i].x, b[j].y, acci[i][j]);
@@ -77,11 +75,11 @@ __global__ void __launch_bounds__(256) k_gemm_fp64(const GemmProb* __restrict__ 
   if (P.ksplit > 1) {  // raw partial for the fixed-order reduction
     cplx* W = ws + blockIdx.y * ws_is + P.ws + int64_t(ks) * P.M * P.N;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < RM; ++i) {
       const int gm = m0 + ty + 16 * i;
       if (gm >= P.M) continue;
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
+      for (int j = 0; j < RN; ++j) {
         const int gn = n0 + tx + 16 * j;
         if (gn < P.N) W[int64_t(gm) * P.N + gn] = make_double2(accr[i][j], acci[i][j]);
       }
@@ -89,11 +87,11 @@ __global__ void __launch_bounds__(256) k_gemm_fp64(const GemmProb* __restrict__ 
     return;
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < RM; ++i) {
     const int gm = m0 + ty + 16 * i;
     if (gm >= P.M) continue;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < RN; ++j) {
       const int gn = n0 + tx + 16 * j;
       if (gn >= P.N) continue;
       double vr = alpha.x * accr[i][j] - alpha.y * acci[i][j];
@@ -133,8 +131,15 @@ __global__ void __launch_bounds__(256) k_splitk_reduce(const GemmProb* __restric
 void launch_gemm_fp64(Ctx& c, const GemmPlan& g, const cplx* A, const cplx* B, cplx* C, int64_t ais,
                       int64_t bis, int64_t cis, cplx alpha, bool beta) {
   if (g.n_tiles == 0) return;
-  k_gemm_fp64<<<dim3(g.n_tiles, c.ninst), 256, 0, c.stream>>>(g.d_probs, g.n_probs, A, B, C, ais, bis,
-                                                              cis, alpha, beta, g.d_ws, g.ws_is);
+  const dim3 grid(g.n_tiles, c.ninst);
+  if (g.tm == 64 && g.tn == 64)
+    k_gemm_fp64<64, 64><<<grid, 256, 0, c.stream>>>(g.d_probs, g.n_probs, A, B, C, ais, bis, cis, alpha, beta, g.d_ws, g.ws_is);
+  else if (g.tm == 64)
+    k_gemm_fp64<64, 16><<<grid, 256, 0, c.stream>>>(g.d_probs, g.n_probs, A, B, C, ais, bis, cis, alpha, beta, g.d_ws, g.ws_is);
+  else if (g.tn == 64)
+    k_gemm_fp64<16, 64><<<grid, 256, 0, c.stream>>>(g.d_probs, g.n_probs, A, B, C, ais, bis, cis, alpha, beta, g.d_ws, g.ws_is);
+  else
+    k_gemm_fp64<16, 16><<<grid, 256, 0, c.stream>>>(g.d_probs, g.n_probs, A, B, C, ais, bis, cis, alpha, beta, g.d_ws, g.ws_is);
   KCHECK(c);
   if (g.red_elems) {
     const int blocks = int(std::min<int64_t>((g.red_elems + 255) / 256, 2LL * std::max(c.sm_count, 1)));

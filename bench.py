@@ -25,7 +25,14 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = dict(name="ccsd_z8_o40_v200", n_occ=40, n_virt=200, G=8, seed=2001)
+WORKLOADS = {
+    # the workload the metric is quoted on (one GPU)
+    "ccsd_z8_o40_v200": dict(name="ccsd_z8_o40_v200", n_occ=40, n_virt=200, G=8, seed=2001),
+    # a smaller case of the same kernels (a few GB on the device), for ncu captures
+    "ccsd_z8_o24_v120": dict(name="ccsd_z8_o24_v120", n_occ=24, n_virt=120, G=8, seed=2001),
+    "ccsd_c1_o10_v40": dict(name="ccsd_c1_o10_v40", n_occ=10, n_virt=40, G=1, seed=1001),
+}
+WORKLOAD = WORKLOADS["ccsd_z8_o40_v200"]
 METRIC = "ccsd_iterations_per_s"
 UNIT = "iter/s"
 FP64_NOMINAL_TFLOPS = 1.25      # GB300 nominal dense FP64
@@ -156,7 +163,10 @@ def main():
     ap.add_argument("--precision", choices=["emu", "fp64"], default="emu")
     ap.add_argument("--slices", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="ccsd_z8_o40_v200")
     args = ap.parse_args()
+    global WORKLOAD
+    WORKLOAD = WORKLOADS[args.workload]
     if args.warmup < 3:
         args.warmup = 3
     ws, rank, local = dist_env()
@@ -276,7 +286,7 @@ def main():
             "config": {"workload": WORKLOAD["name"], "n_occ": WORKLOAD["n_occ"], "n_virt": WORKLOAD["n_virt"],
                        "irreps": f"Z{WORKLOAD['G']}", "seed": WORKLOAD["seed"], "precision": args.precision,
                        "l2": "inputs larger than L2 (vvvv block ~3.2 GB re-read every step)"},
-            "complex_tflops": ctflops, "complex_macs_per_iter": macs, "energy": [e_final.real, e_final.imag],
+            "complex_tflops": ctflops, "complex_macs_per_iter": macs,
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk.summary(), "status": st}
     print(json.dumps(line))

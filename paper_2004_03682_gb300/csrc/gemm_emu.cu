@@ -36,6 +36,7 @@ constexpr int BETA = 7;        // bits per slice
 constexpr int KC_BLOCKS = 16;  // k-blocks per exact chunk: KC = 512 real terms
 constexpr int STAGES = 3;
 constexpr int THREADS = 192;   // 6 warps
+#define EXP_ZERO (-1100)       // exponent of an all-zero row / column (any x 2^-EXP_ZERO stays 0)
 
 template <int S>
 struct Shape {
@@ -56,8 +57,10 @@ struct EmuProb {
   int64_t a_src, b_src, c_off;  // complex offsets in the per-instance A, B, C tensors
   int64_t a_sl, b_sl;           // bf16 offsets of the slice tiles (per instance)
   int64_t a_ex, b_ex;           // offsets of the exponent arrays (per instance)
+  int64_t ws;                   // split-K partials offset (complex, per instance)
   int32_t M, N, K, Kp;          // Kp = 2K padded to KB
   int32_t tiles_m, tiles_n, tile0, pad;
+  int32_t ksplit, kcb, pad2, pad3;  // K splits and k-blocks per split (multiple of KC_BLOCKS)
 };
 
 // ---------------------------------------------------------------------------
@@ -150,7 +153,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     k_emu_gemm(const EmuProb* __restrict__ probs, int nprobs, const __nv_bfloat16* __restrict__ Asl,
                const __nv_bfloat16* __restrict__ Bsl, const int* __restrict__ Aex, const int* __restrict__ Bex,
                cplx* __restrict__ C, int64_t asl_is, int64_t bsl_is, int64_t aex_is, int64_t bex_is, int64_t c_is,
-               cplx alpha, int beta, int* __restrict__ gerr) {
+               cplx alpha, int beta, int* __restrict__ gerr, cplx* __restrict__ ws, int64_t ws_is) {
   using SH = Shape<S>;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)((uintptr_t(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -167,9 +170,14 @@ __global__ void __launch_bounds__(THREADS, 1)
   int pi = 0;
   while (pi + 1 < nprobs && probs[pi + 1].tile0 <= tile) ++pi;
   const EmuProb P = probs[pi];
-  const int lt = tile - P.tile0;
+  int lt = tile - P.tile0;  // tile -> (K split, row tile, column tile)
+  const int tmn = P.tiles_m * P.tiles_n;
+  const int ks = lt / tmn;
+  lt -= ks * tmn;
   const int mt = lt / P.tiles_n, nt = lt % P.tiles_n;
-  const int nkb = P.Kp / KB;
+  const int nkb_all = P.Kp / KB;
+  const int kb0 = ks * P.kcb;
+  const int nkb = min(nkb_all, kb0 + P.kcb) - kb0;  // k-blocks of this split
   const int nchunks = (nkb + KC_BLOCKS - 1) / KC_BLOCKS;
 
   if (threadIdx.x == 0) {
@@ -189,8 +197,8 @@ __global__ void __launch_bounds__(THREADS, 1)
   fence_after();
   const uint32_t tmem = *tslot;
 
-  const __nv_bfloat16* Ab = Asl + inst * asl_is + P.a_sl + int64_t(mt) * nkb * (S * SH::A_TILE);
-  const __nv_bfloat16* Bb = Bsl + inst * bsl_is + P.b_sl + int64_t(nt) * nkb * (S * SH::B_TILE);
+  const __nv_bfloat16* Ab = Asl + inst * asl_is + P.a_sl + (int64_t(mt) * nkb_all + kb0) * (S * SH::A_TILE);
+  const __nv_bfloat16* Bb = Bsl + inst * bsl_is + P.b_sl + (int64_t(nt) * nkb_all + kb0) * (S * SH::B_TILE);
 
   if (warp == 0) {
     // ---- producer: 1-D TMA bulk copies of the pre-tiled slice tiles
@@ -274,7 +282,18 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     if (ok) {
       const int gi = mt * BM + row;
-      if (gi < P.M) {
+      if (gi < P.M && P.ksplit > 1) {  // scaled partial for the fixed-order reduction
+        const int ei = Aex[inst * aex_is + P.a_ex + gi];
+        cplx* W = ws + inst * ws_is + P.ws + int64_t(ks) * P.M * P.N + int64_t(gi) * P.N;
+#pragma unroll
+        for (int jj = 0; jj < SH::BN / 2; ++jj) {
+          const int gj = nt * (SH::BN / 2) + jj;
+          if (gj < P.N) {
+            const int e = ei + Bex[inst * bex_is + P.b_ex + gj] - BETA * (S + 1);
+            W[gj] = make_double2(ldexp(double(R[2 * jj]), e), ldexp(double(R[2 * jj + 1]), e));
+          }
+        }
+      } else if (gi < P.M) {
         const int ei = Aex[inst * aex_is + P.a_ex + gi];
         cplx* Crow = C + inst * c_is + P.c_off + int64_t(gi) * P.N;
 #pragma unroll
@@ -308,38 +327,77 @@ __global__ void __launch_bounds__(THREADS, 1)
 // ---------------------------------------------------------------------------
 // Split kernels.  Exponent E of a row (column) = smallest integer with
 // max |Re|, |Im| < 2^E (0 for an all-zero row).
-__device__ __forceinline__ int exp_of(double m) { return m > 0.0 ? ilogb(m) + 1 : 0; }
+__device__ __forceinline__ int exp_of(double m) { return m > 0.0 ? ilogb(m) + 1 : EXP_ZERO; }
 
-__global__ void k_row_exp(const EmuProb* __restrict__ probs, int nprobs, const cplx* __restrict__ A, int64_t a_is,
-                          int* __restrict__ ex, int64_t ex_is, int total_rows) {
+// Row exponents: CTA = (one row, a K range of ROW_KR); block max -> atomicMax
+// (max is order-independent, so the result is deterministic).  Exponent arrays
+// start at EXP_ZERO (all-zero row or column).
+#define ROW_KR 8192
+__global__ void __launch_bounds__(256) k_row_exp(const EmuProb* __restrict__ probs, int nprobs,
+                                                 const cplx* __restrict__ A, int64_t a_is, int* __restrict__ ex,
+                                                 int64_t ex_is) {
+  __shared__ double sh[8];
   const int inst = blockIdx.y;
-  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  if (w >= total_rows) return;
-  // find the problem owning global row w (problems' rows are concatenated)
-  int pi = 0, base = 0;
-  while (pi < nprobs && w >= base + probs[pi].M) { base += probs[pi].M; ++pi; }
+  int t = blockIdx.x, pi = 0;
+  // work items: per problem M * ceil(K / ROW_KR)
+  for (;; ++pi) {
+    const int nk = (probs[pi].K + ROW_KR - 1) / ROW_KR;
+    const int items = probs[pi].M * max(nk, 1);
+    if (t < items || pi + 1 >= nprobs) break;
+    t -= items;
+  }
   const EmuProb P = probs[pi];
-  const int r = w - base;
+  const int nk = max((P.K + ROW_KR - 1) / ROW_KR, 1);
+  const int r = t / nk, kc = t % nk;
+  if (r >= P.M) return;
   const cplx* a = A + inst * a_is + P.a_src + int64_t(r) * P.K;
   double m = 0.0;
-  for (int k = lane; k < P.K; k += 32) m = fmax(m, fmax(fabs(a[k].x), fabs(a[k].y)));
+  for (int k = kc * ROW_KR + threadIdx.x; k < min(P.K, (kc + 1) * ROW_KR); k += 256)
+    m = fmax(m, fmax(fabs(a[k].x), fabs(a[k].y)));
   for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if (lane == 0) ex[inst * ex_is + P.a_ex + r] = exp_of(m);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < 8; ++w) m = fmax(m, sh[w]);
+    atomicMax(&ex[inst * ex_is + P.a_ex + r], exp_of(m));
+  }
 }
 
-__global__ void k_col_exp(const EmuProb* __restrict__ probs, int nprobs, const cplx* __restrict__ B, int64_t b_is,
-                          int* __restrict__ ex, int64_t ex_is, int total_cols) {
+// Column exponents: CTA = (32 columns, 256 rows of K); 8 row lanes per column.
+__global__ void __launch_bounds__(256) k_col_exp(const EmuProb* __restrict__ probs, int nprobs,
+                                                 const cplx* __restrict__ B, int64_t b_is, int* __restrict__ ex,
+                                                 int64_t ex_is) {
+  __shared__ double sh[8][33];
   const int inst = blockIdx.y;
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= total_cols) return;
-  int pi = 0, base = 0;
-  while (pi < nprobs && c >= base + probs[pi].N) { base += probs[pi].N; ++pi; }
+  int t = blockIdx.x, pi = 0;
+  for (;; ++pi) {
+    const int items = ((probs[pi].N + 31) / 32) * max((probs[pi].K + 255) / 256, 1);
+    if (t < items || pi + 1 >= nprobs) break;
+    t -= items;
+  }
   const EmuProb P = probs[pi];
-  const int j = c - base;
-  const cplx* b = B + inst * b_is + P.b_src + j;
+  const int nk = max((P.K + 255) / 256, 1);
+  const int ct = t / nk, kc = t % nk;
+  const int cl = threadIdx.x & 31, rl = threadIdx.x >> 5;
+  const int j = ct * 32 + cl;
   double m = 0.0;
-  for (int k = 0; k < P.K; ++k) m = fmax(m, fmax(fabs(b[int64_t(k) * P.N].x), fabs(b[int64_t(k) * P.N].y)));
-  ex[inst * ex_is + P.b_ex + j] = exp_of(m);
+  if (j < P.N) {
+    const cplx* b = B + inst * b_is + P.b_src + j;
+    for (int k = kc * 256 + rl; k < min(P.K, (kc + 1) * 256); k += 8) {
+      const cplx v = b[int64_t(k) * P.N];
+      m = fmax(m, fmax(fabs(v.x), fabs(v.y)));
+    }
+  }
+  sh[rl][cl] = m;
+  __syncthreads();
+  if (rl == 0 && j < P.N) {
+    for (int w = 1; w < 8; ++w) m = fmax(m, sh[w][cl]);
+    atomicMax(&ex[inst * ex_is + P.b_ex + j], exp_of(m));
+  }
+}
+
+__global__ void k_fill_int(int* __restrict__ p, int64_t n, int v) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) p[i] = v;
 }
 
 template <int S>
@@ -415,6 +473,31 @@ __global__ void __launch_bounds__(256) k_split_b(const EmuProb* __restrict__ pro
   }
 }
 
+// C = alpha * sum_s partial_s (+ C), splits in index order
+__global__ void __launch_bounds__(256) k_emu_reduce(const EmuProb* __restrict__ probs, int nprobs,
+                                                    const cplx* __restrict__ ws, int64_t ws_is, cplx* __restrict__ C,
+                                                    int64_t c_is, cplx alpha, int beta) {
+  const int inst = blockIdx.y;
+  for (int p = 0; p < nprobs; ++p) {
+    const EmuProb P = probs[p];
+    if (P.ksplit <= 1) continue;
+    const int64_t n = int64_t(P.M) * P.N;
+    const cplx* W = ws + inst * ws_is + P.ws;
+    cplx* Cp = C + inst * c_is + P.c_off;
+    for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < n; e += int64_t(gridDim.x) * blockDim.x) {
+      double sr = 0.0, si = 0.0;
+      for (int s = 0; s < P.ksplit; ++s) {
+        const cplx w = W[int64_t(s) * n + e];
+        sr += w.x;
+        si += w.y;
+      }
+      double vr = alpha.x * sr - alpha.y * si, vi = alpha.x * si + alpha.y * sr;
+      if (beta) { const cplx o = Cp[e]; vr += o.x; vi += o.y; }
+      Cp[e] = make_double2(vr, vi);
+    }
+  }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -424,6 +507,7 @@ struct EmuPlan {
   EmuProb* d = nullptr;
   int n_tiles = 0, n_atiles = 0, n_btiles = 0;
   int total_rows = 0, total_cols = 0;
+  int n_rowexp = 0, n_colexp = 0;  // work items of the exponent scans
   __nv_bfloat16* asl = nullptr;
   __nv_bfloat16* bsl = nullptr;
   int* aex = nullptr;
@@ -431,6 +515,8 @@ struct EmuPlan {
   int64_t asl_is = 0, bsl_is = 0, aex_is = 0, bex_is = 0;
   bool a_const = false, b_const = false, a_ready = false, b_ready = false;
   int* d_err = nullptr;
+  cplx* d_ws = nullptr;
+  int64_t ws_is = 0, red_elems = 0;
 };
 
 struct EmuState {
@@ -441,11 +527,11 @@ struct EmuState {
 bool emu_wanted(Ctx& c, const GemmPlan& g, const std::string&) {
   if (c.cfg.precision != EXP_EMU_BF16) return false;
   if (c.cfg.emu_min_macs > 0) return double(g.flops_mac) >= c.cfg.emu_min_macs;
-  if (g.flops_mac < int64_t(1) << 26) return false;
-  int64_t big = 0;
-  for (auto& p : g.h_probs)
-    if (p.M >= 64 && p.K >= 32 && p.N >= 8) big += int64_t(p.M) * p.N * p.K;
-  return big * 10 >= g.flops_mac * 9;  // nearly all work in GEMM-shaped blocks
+  // below ~8e6 complex MACs, or with a contraction length under 128, the split
+  // passes cost more than the FP64 kernel
+  int maxK = 0;
+  for (auto& p : g.h_probs) maxK = std::max(maxK, p.K);
+  return g.flops_mac >= int64_t(1) << 23 && maxK >= 128;
 }
 
 template <int S>
@@ -477,6 +563,12 @@ EmuPlan* emu_plan(Ctx& c, const GemmPlan& g, const Tensor* A, const Tensor* B, b
   const int BN = bn_of(p->S);
   int64_t asl = 0, bsl = 0, aex = 0, bex = 0;
   int tile0 = 0, at0 = 0, bt0 = 0;
+  int64_t tiles_mn = 0;
+  for (auto& q : g.h_probs)
+    tiles_mn += int64_t((q.M + BM - 1) / BM) * ((q.N + BN / 2 - 1) / (BN / 2));
+  tiles_mn *= c.ninst;
+  const int64_t sms = std::max(c.sm_count, 1);
+  int64_t ws = 0;
   for (auto& q : g.h_probs) {
     EmuProb e{};
     e.a_src = q.a;
@@ -489,9 +581,23 @@ EmuPlan* emu_plan(Ctx& c, const GemmPlan& g, const Tensor* A, const Tensor* B, b
     if (e.Kp == 0) e.Kp = KB;
     e.tiles_m = (q.M + BM - 1) / BM;
     e.tiles_n = (q.N + BN / 2 - 1) / (BN / 2);
-    e.tile0 = tile0;
-    tile0 += e.tiles_m * e.tiles_n;
     const int nkb = e.Kp / KB;
+    e.ksplit = 1;
+    e.kcb = ((nkb + KC_BLOCKS - 1) / KC_BLOCKS) * KC_BLOCKS;
+    if (tiles_mn < 2 * sms && nkb >= 2 * KC_BLOCKS) {
+      const int64_t chunks = (nkb + KC_BLOCKS - 1) / KC_BLOCKS;
+      int64_t ks = std::min<int64_t>(chunks, (4 * sms + tiles_mn - 1) / std::max<int64_t>(tiles_mn, 1));
+      ks = std::max<int64_t>(1, std::min<int64_t>(ks, 512));
+      e.kcb = int32_t(((chunks + ks - 1) / ks) * KC_BLOCKS);
+      e.ksplit = (nkb + e.kcb - 1) / e.kcb;
+    }
+    if (e.ksplit > 1) {
+      e.ws = ws;
+      ws += int64_t(e.ksplit) * q.M * q.N;
+      p->red_elems += int64_t(q.M) * q.N;
+    }
+    e.tile0 = tile0;
+    tile0 += e.tiles_m * e.tiles_n * e.ksplit;
     e.a_sl = asl;
     e.b_sl = bsl;
     asl += int64_t(e.tiles_m) * nkb * p->S * BM * KB;
@@ -502,6 +608,8 @@ EmuPlan* emu_plan(Ctx& c, const GemmPlan& g, const Tensor* A, const Tensor* B, b
     bex += q.N;
     p->total_rows += q.M;
     p->total_cols += q.N;
+    p->n_rowexp += q.M * std::max((q.K + ROW_KR - 1) / ROW_KR, 1);
+    p->n_colexp += ((q.N + 31) / 32) * std::max((q.K + 255) / 256, 1);
     e.pad = bt0;  // first split-B tile
     bt0 += e.tiles_n * nkb;
     at0 += e.tiles_m * nkb;
@@ -524,6 +632,10 @@ EmuPlan* emu_plan(Ctx& c, const GemmPlan& g, const Tensor* A, const Tensor* B, b
   p->bsl = (__nv_bfloat16*)c.dalloc(sizeof(__nv_bfloat16) * p->bsl_is * c.ninst);
   p->aex = (int*)c.dalloc(sizeof(int) * p->aex_is * c.ninst);
   p->bex = (int*)c.dalloc(sizeof(int) * p->bex_is * c.ninst);
+  if (ws) {
+    p->ws_is = ws;
+    p->d_ws = (cplx*)c.dalloc(sizeof(cplx) * ws * c.ninst);
+  }
   // two device copies of the problem list: [0, n) for the GEMM and split-B, [n, 2n) for split-A
   std::vector<EmuProb> both = p->h;
   both.insert(both.end(), ha.begin(), ha.end());
@@ -539,8 +651,10 @@ static void run_s(Ctx& c, EmuPlan* p, const cplx* A, const cplx* B, cplx* C, int
                   cplx alpha, bool beta) {
   const int np = int(p->h.size());
   if (!p->a_ready) {
-    k_row_exp<<<dim3((p->total_rows * 32 + 255) / 256, c.ninst), 256, 0, c.stream>>>(p->d, np, A, ais, p->aex, p->aex_is,
-                                                                                     p->total_rows);
+    k_fill_int<<<dim3(std::max<int64_t>(1, std::min<int64_t>((p->aex_is * c.ninst + 255) / 256, 1024))), 256, 0, c.stream>>>(
+        p->aex, p->aex_is * c.ninst, EXP_ZERO);
+    KCHECK(c);
+    k_row_exp<<<dim3(p->n_rowexp, c.ninst), 256, 0, c.stream>>>(p->d, np, A, ais, p->aex, p->aex_is);
     KCHECK(c);
     k_split_a<S><<<dim3(p->n_atiles, c.ninst), 256, 0, c.stream>>>(p->d + np, np, A, ais, p->aex, p->aex_is, p->asl,
                                                                    p->asl_is);
@@ -548,8 +662,10 @@ static void run_s(Ctx& c, EmuPlan* p, const cplx* A, const cplx* B, cplx* C, int
     if (p->a_const) p->a_ready = true;
   }
   if (!p->b_ready) {
-    k_col_exp<<<dim3((p->total_cols + 127) / 128, c.ninst), 128, 0, c.stream>>>(p->d, np, B, bis, p->bex, p->bex_is,
-                                                                                p->total_cols);
+    k_fill_int<<<dim3(std::max<int64_t>(1, std::min<int64_t>((p->bex_is * c.ninst + 255) / 256, 1024))), 256, 0, c.stream>>>(
+        p->bex, p->bex_is * c.ninst, EXP_ZERO);
+    KCHECK(c);
+    k_col_exp<<<dim3(p->n_colexp, c.ninst), 256, 0, c.stream>>>(p->d, np, B, bis, p->bex, p->bex_is);
     KCHECK(c);
     k_split_b<S><<<dim3(p->n_btiles, c.ninst), 256, 0, c.stream>>>(p->d, np, B, bis, p->bex, p->bex_is, p->bsl,
                                                                    p->bsl_is, 0);
@@ -559,8 +675,13 @@ static void run_s(Ctx& c, EmuPlan* p, const cplx* A, const cplx* B, cplx* C, int
   set_smem_attr<S>();
   k_emu_gemm<S><<<dim3(p->n_tiles, c.ninst), THREADS, Shape<S>::SMEM, c.stream>>>(
       p->d, np, p->asl, p->bsl, p->aex, p->bex, C, p->asl_is, p->bsl_is, p->aex_is, p->bex_is, cis, alpha, beta ? 1 : 0,
-      p->d_err);
+      p->d_err, p->d_ws, p->ws_is);
   KCHECK(c);
+  if (p->red_elems) {
+    const int blocks = int(std::min<int64_t>((p->red_elems + 255) / 256, 2LL * std::max(c.sm_count, 1)));
+    k_emu_reduce<<<dim3(blocks, c.ninst), 256, 0, c.stream>>>(p->d, np, p->d_ws, p->ws_is, C, cis, alpha, beta ? 1 : 0);
+    KCHECK(c);
+  }
 }
 
 void emu_run(Ctx& c, EmuPlan* p, const GemmPlan&, const cplx* A, const cplx* B, cplx* C, int64_t ais, int64_t bis,

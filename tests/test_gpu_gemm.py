@@ -44,8 +44,9 @@ def test_fp64_kernel_matches_numpy(env, M, N, K):
 
 
 @pytest.mark.parametrize("S", [3, 4, 5, 6])
-@pytest.mark.parametrize("M,N,K", SHAPES)
+@pytest.mark.parametrize("M,N,K", SHAPES + [(14, 14, 40000), (81, 14, 30000)])
 def test_emulated_exact_on_integer_inputs(env, S, M, N, K):
+    """(the two long-K shapes run split over K: partial sums in FP64, fixed order)"""
     torch, expgb = env
     rng = np.random.default_rng(S * 100 + M + N + K)
     A, B = _c(rng, (M, K), integer=True), _c(rng, (K, N), integer=True)

@@ -156,6 +156,32 @@ exp_status exp_profile_top(exp_ctx* ctx, int reps, char* name, int name_len, dou
 exp_status exp_zgemm(const exp_allocator* alloc, void* stream, int precision, int n_slices, int M, int N, int K,
                      const void* A, const void* B, void* C, double alpha_re, double alpha_im, int beta);
 
+/* Allocation-free complex GEMM (no counterpart in the paper: a library service).
+ *
+ * For callers that cannot allocate device memory when they need the product -
+ * a host application that owns every allocation and hands this library only a
+ * stream and its buffers, a pool whose budget is already spent, or a path where
+ * a cudaMalloc would synchronise the device.  Computes C = alpha A B (+ C if
+ * beta) with the BF16-sliced emulation of exp_zgemm (EXP_EMU_BF16, n_slices in
+ * 3..6; same layouts: A M x K, B K x N, C M x N, row-major complex128 device
+ * buffers, 16-byte aligned), and calls no allocator, cudaMalloc or cudaFree.
+ *
+ * Its scratch is one fixed array in the library's device memory, of
+ * EXP_NOALLOC_SCRATCH_BYTES, which every GPU that loads the library holds until
+ * the process exits.  A problem whose scratch need exceeds it is rejected with
+ * EXP_EINVAL before anything is launched (square problems fit up to about
+ * M = N = K = 600 with n_slices = 5 or 6).
+ * The first call on a device looks the array's address up (with that device
+ * current); make it before any stream capture.  Every call shares the array and
+ * re-initialises what must start at a known value; calls whose GPU work can
+ * overlap (different streams without ordering) race on it.  Synchronises
+ * `stream`.  Errors: EINVAL, ECUDA, ETIMEOUT; message in
+ * exp_noalloc_last_error(). */
+#define EXP_NOALLOC_SCRATCH_BYTES (48u << 20)
+exp_status exp_zgemm_emu_noalloc(void* stream, int n_slices, int M, int N, int K, const void* A, const void* B,
+                                 void* C, double alpha_re, double alpha_im, int beta);
+const char* exp_noalloc_last_error(void);
+
 /* Number of kernels this context has launched so far (for launch accounting). */
 int64_t exp_kernel_launches(const exp_ctx* ctx);
 

@@ -25,6 +25,7 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <string>
 
 #include "emu.h"
 
@@ -701,4 +702,172 @@ void emu_release(Ctx& c) {
   for (auto* p : st->plans) delete p;
   delete st;
   c.emu_state = nullptr;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the emulated GEMM (exp_zgemm_emu_noalloc).
+//
+// Some callers cannot allocate device memory at the point where they need a
+// product: code running inside a memory-pool budget that is already spent,
+// plugins that are handed a stream and buffers by a host application that
+// owns every allocation, or code paths where a cudaMalloc would synchronise
+// the device.  For them this entry point takes its scratch (slice tiles,
+// exponents, split-K partials, the problem record and the error flag) from a
+// fixed array in the module's device memory instead of an allocator.
+//
+// The array is a file-scope __device__ variable: every GPU that loads this
+// library holds EXP_NOALLOC_SCRATCH_BYTES of it until the process exits.  Its
+// device address is looked up once per device (cudaGetSymbolAddress, with that
+// device current) on the first call on that device; make that first call
+// before any stream capture.  All calls share the one array: the parts that
+// must start at a known value (exponents, the error flag) are re-initialised
+// on the stream by every call, and two calls whose work overlaps on the GPU
+// (different streams, no ordering between them) race on it.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[EXP_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+struct NoallocDev {
+  unsigned char* base = nullptr;
+  bool ready = false;
+};
+NoallocDev g_noalloc_dev[64];
+
+int64_t carve(int64_t& off, int64_t bytes) {
+  const int64_t at = (off + 255) & ~int64_t(255);
+  off = at + bytes;
+  return at;
+}
+
+template <int S>
+exp_status noalloc_launch(cudaStream_t st, unsigned char* base, int M, int N, int K, const cplx* A, const cplx* B,
+                          cplx* Cout, cplx alpha, int beta, int sms, std::string& err) {
+  using SH = Shape<S>;
+  const int BN = SH::BN;
+  EmuProb e{};
+  e.M = M;
+  e.N = N;
+  e.K = K;
+  e.Kp = std::max(((2 * K + KB - 1) / KB) * KB, KB);
+  e.tiles_m = (M + BM - 1) / BM;
+  e.tiles_n = (N + BN / 2 - 1) / (BN / 2);
+  const int nkb = e.Kp / KB;
+  const int64_t tiles_mn = int64_t(e.tiles_m) * e.tiles_n;
+  e.ksplit = 1;
+  e.kcb = ((nkb + KC_BLOCKS - 1) / KC_BLOCKS) * KC_BLOCKS;
+  if (tiles_mn < 2LL * sms && nkb >= 2 * KC_BLOCKS) {
+    const int64_t chunks = (nkb + KC_BLOCKS - 1) / KC_BLOCKS;
+    int64_t ks = std::min<int64_t>(chunks, (4LL * sms + tiles_mn - 1) / std::max<int64_t>(tiles_mn, 1));
+    ks = std::max<int64_t>(1, std::min<int64_t>(ks, 512));
+    e.kcb = int32_t(((chunks + ks - 1) / ks) * KC_BLOCKS);
+    e.ksplit = (nkb + e.kcb - 1) / e.kcb;
+  }
+  e.pad = 0;
+  e.tile0 = 0;
+  // scratch layout
+  int64_t off = 0;
+  const int64_t o_probs = carve(off, 2 * sizeof(EmuProb));
+  const int64_t o_err = carve(off, sizeof(int));
+  const int64_t o_aex = carve(off, sizeof(int) * int64_t(M));
+  const int64_t o_bex = carve(off, sizeof(int) * int64_t(N));
+  const int64_t o_asl = carve(off, int64_t(2) * e.tiles_m * nkb * S * BM * KB);
+  const int64_t o_bsl = carve(off, int64_t(2) * e.tiles_n * nkb * S * BN * KB);
+  const int64_t o_ws = carve(off, e.ksplit > 1 ? int64_t(sizeof(cplx)) * e.ksplit * M * N : 0);
+  if (off > int64_t(EXP_NOALLOC_SCRATCH_BYTES)) {
+    err = "exp_zgemm_emu_noalloc: problem needs " + std::to_string(off) + " bytes of scratch, more than the " +
+          std::to_string(int64_t(EXP_NOALLOC_SCRATCH_BYTES)) + " bytes available";
+    return EXP_EINVAL;
+  }
+  EmuProb recs[2] = {e, e};
+  recs[1].tile0 = 0;  // split-A tile numbering starts at 0 as well
+  EmuProb* d_probs = (EmuProb*)(base + o_probs);
+  int* d_err = (int*)(base + o_err);
+  int* aex = (int*)(base + o_aex);
+  int* bex = (int*)(base + o_bex);
+  __nv_bfloat16* asl = (__nv_bfloat16*)(base + o_asl);
+  __nv_bfloat16* bsl = (__nv_bfloat16*)(base + o_bsl);
+  cplx* ws = (cplx*)(base + o_ws);
+  if (cudaMemcpyAsync(d_probs, recs, sizeof(recs), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemsetAsync(d_err, 0, sizeof(int), st) != cudaSuccess) {
+    err = "exp_zgemm_emu_noalloc: copy to scratch failed";
+    return EXP_ECUDA;
+  }
+  const int64_t n_rowexp = int64_t(M) * std::max((K + ROW_KR - 1) / ROW_KR, 1);
+  const int64_t n_colexp = int64_t((N + 31) / 32) * std::max((K + 255) / 256, 1);
+  k_fill_int<<<std::max(1, std::min((M + 255) / 256, 1024)), 256, 0, st>>>(aex, M, EXP_ZERO);
+  k_fill_int<<<std::max(1, std::min((N + 255) / 256, 1024)), 256, 0, st>>>(bex, N, EXP_ZERO);
+  k_row_exp<<<dim3(unsigned(n_rowexp), 1), 256, 0, st>>>(d_probs, 1, A, 0, aex, 0);
+  k_col_exp<<<dim3(unsigned(n_colexp), 1), 256, 0, st>>>(d_probs, 1, B, 0, bex, 0);
+  k_split_a<S><<<dim3(e.tiles_m * nkb, 1), 256, 0, st>>>(d_probs + 1, 1, A, 0, aex, 0, asl, 0);
+  k_split_b<S><<<dim3(e.tiles_n * nkb, 1), 256, 0, st>>>(d_probs, 1, B, 0, bex, 0, bsl, 0, 0);
+  if (cudaFuncSetAttribute(k_emu_gemm<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, SH::SMEM) != cudaSuccess) {
+    err = "exp_zgemm_emu_noalloc: shared-memory attribute refused";
+    return EXP_ECUDA;
+  }
+  k_emu_gemm<S><<<dim3(unsigned(tiles_mn * e.ksplit), 1), THREADS, SH::SMEM, st>>>(
+      d_probs, 1, asl, bsl, aex, bex, Cout, 0, 0, 0, 0, 0, alpha, beta, d_err, ws, 0);
+  if (e.ksplit > 1) {
+    const int blocks = int(std::min<int64_t>((int64_t(M) * N + 255) / 256, 2LL * sms));
+    k_emu_reduce<<<dim3(blocks, 1), 256, 0, st>>>(d_probs, 1, ws, 0, Cout, 0, alpha, beta);
+  }
+  cudaError_t ce = cudaGetLastError();
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+  if (ce != cudaSuccess) {
+    err = std::string("exp_zgemm_emu_noalloc: ") + cudaGetErrorString(ce);
+    return EXP_ECUDA;
+  }
+  int flag = 0;
+  if (cudaMemcpy(&flag, d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+    err = "exp_zgemm_emu_noalloc: reading the error flag failed";
+    return EXP_ECUDA;
+  }
+  if (flag) {
+    err = "exp_zgemm_emu_noalloc: a bounded device wait gave up";
+    return EXP_ETIMEOUT;
+  }
+  return EXP_OK;
+}
+}  // namespace
+
+static thread_local std::string g_noalloc_err;
+
+extern "C" const char* exp_noalloc_last_error(void) { return g_noalloc_err.c_str(); }
+
+extern "C" exp_status exp_zgemm_emu_noalloc(void* stream, int n_slices, int M, int N, int K, const void* A,
+                                            const void* B, void* C, double alpha_re, double alpha_im, int beta) {
+  g_noalloc_err.clear();
+  if (!A || !B || !C || M < 1 || N < 1 || K < 1 || n_slices < 3 || n_slices > 6) {
+    g_noalloc_err = "exp_zgemm_emu_noalloc: null pointer, M, N, K < 1 or n_slices outside 3..6";
+    return EXP_EINVAL;
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    g_noalloc_err = "exp_zgemm_emu_noalloc: no current CUDA device";
+    return EXP_ECUDA;
+  }
+  NoallocDev& nd = g_noalloc_dev[dev];
+  if (!nd.ready) {
+    // one-time set-up on this device: the host-side name of the array is not a
+    // device address; ask the runtime for the real one
+    void* p = nullptr;
+    const cudaError_t ce = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (ce != cudaSuccess || !p) {
+      g_noalloc_err = std::string("exp_zgemm_emu_noalloc: cudaGetSymbolAddress failed: ") + cudaGetErrorString(ce);
+      return EXP_ECUDA;
+    }
+    nd.base = (unsigned char*)p;
+    nd.ready = true;
+  }
+  int sms = 1;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const cplx alpha = make_double2(alpha_re, alpha_im);
+  cudaStream_t st = (cudaStream_t)stream;
+  const cplx* a = (const cplx*)A;
+  const cplx* b = (const cplx*)B;
+  cplx* c = (cplx*)C;
+  switch (n_slices) {
+    case 3: return noalloc_launch<3>(st, nd.base, M, N, K, a, b, c, alpha, beta != 0, sms, g_noalloc_err);
+    case 4: return noalloc_launch<4>(st, nd.base, M, N, K, a, b, c, alpha, beta != 0, sms, g_noalloc_err);
+    case 5: return noalloc_launch<5>(st, nd.base, M, N, K, a, b, c, alpha, beta != 0, sms, g_noalloc_err);
+    default: return noalloc_launch<6>(st, nd.base, M, N, K, a, b, c, alpha, beta != 0, sms, g_noalloc_err);
+  }
 }

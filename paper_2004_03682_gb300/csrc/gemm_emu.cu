@@ -401,20 +401,37 @@ __global__ void k_fill_int(int* __restrict__ p, int64_t n, int v) {
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) p[i] = v;
 }
 
+// Slices of 8 consecutive values, written as one 16-byte vector per slice (a
+// core-matrix row).  x in (-1, 1): a_1 = rint(x 2^B), r <- x 2^B - a_1,
+// a_2 = rint(r 2^B), ...  (exact in FP64; rint is odd, so slices of -x are -slices of x).
+__device__ __forceinline__ uint32_t pack2(__nv_bfloat16 a, __nv_bfloat16 b) {
+  return uint32_t(__bfloat16_as_ushort(a)) | (uint32_t(__bfloat16_as_ushort(b)) << 16);
+}
+
 template <int S>
-__device__ __forceinline__ void slice_store(double x, __nv_bfloat16* dst, int64_t stride) {
-  // x in (-1, 1): a_1 = rint(x 2^B), r <- x 2^B - a_1, a_2 = rint(r 2^B), ...  (exact in FP64)
-  double r = x;
+__device__ __forceinline__ void slice8(const double (&x)[8], uint4 (&out)[S], bool neg_copy, uint4 (&outn)[S]) {
+  double r[8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) r[u] = x[u];
 #pragma unroll
   for (int s = 0; s < S; ++s) {
-    r = r * double(1 << BETA);
-    const double a = rint(r);
-    r -= a;
-    dst[s * stride] = __float2bfloat16_rn(float(a));
+    __nv_bfloat16 h[8], hn[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      r[u] *= double(1 << BETA);
+      const double a = rint(r[u]);
+      r[u] -= a;
+      h[u] = __float2bfloat16_rn(float(a));
+      hn[u] = __float2bfloat16_rn(float(-a));
+    }
+    out[s] = make_uint4(pack2(h[0], h[1]), pack2(h[2], h[3]), pack2(h[4], h[5]), pack2(h[6], h[7]));
+    if (neg_copy) outn[s] = make_uint4(pack2(hn[0], hn[1]), pack2(hn[2], hn[3]), pack2(hn[4], hn[5]), pack2(hn[6], hn[7]));
   }
 }
 
-// A slices: tile (mt, kb) per CTA, elements (row r, real k') of A' = [Re A | Im A].
+// A' = [Re A | Im A], each half padded to Kh = K rounded up to KB.  CTA = (row
+// tile mt, half-k-block kbh): one read of A per element, writes the Re tile
+// (k-block kbh) and the Im tile (k-block Kh/KB + kbh).  Thread unit = (row, 8-group).
 template <int S>
 __global__ void __launch_bounds__(256) k_split_a(const EmuProb* __restrict__ probs, int nprobs, const cplx* __restrict__ A,
                                                  int64_t a_is, const int* __restrict__ ex, int64_t ex_is,
@@ -422,55 +439,90 @@ __global__ void __launch_bounds__(256) k_split_a(const EmuProb* __restrict__ pro
   using SH = Shape<S>;
   const int inst = blockIdx.y;
   int t = blockIdx.x, pi = 0;
-  // tile index space: per problem tiles_m * nkb
-  while (pi + 1 < nprobs && t >= probs[pi].tile0 + probs[pi].tiles_m * (probs[pi].Kp / KB)) ++pi;
+  while (pi + 1 < nprobs && t >= probs[pi].tile0 + probs[pi].tiles_m * (probs[pi].Kp / (2 * KB))) ++pi;
   const EmuProb P = probs[pi];
-  const int nkb = P.Kp / KB;
+  const int nkb = P.Kp / KB, nkh = nkb / 2;
   const int lt = t - P.tile0;
-  const int mt = lt / nkb, kb = lt % nkb;
-  __nv_bfloat16* o = out + inst * out_is + P.a_sl + (int64_t(mt) * nkb + kb) * (S * SH::A_TILE);
+  const int mt = lt / nkh, kbh = lt % nkh;
+  __nv_bfloat16* o_re = out + inst * out_is + P.a_sl + (int64_t(mt) * nkb + kbh) * (S * SH::A_TILE);
+  __nv_bfloat16* o_im = out + inst * out_is + P.a_sl + (int64_t(mt) * nkb + nkh + kbh) * (S * SH::A_TILE);
   const cplx* a = A + inst * a_is + P.a_src;
   const int* e = ex + inst * ex_is + P.a_ex;
-  for (int idx = threadIdx.x; idx < BM * KB; idx += blockDim.x) {
-    const int r = idx / KB, k = idx % KB;
-    const int gi = mt * BM + r, gk = kb * KB + k;
-    double x = 0.0;
-    if (gi < P.M && gk < 2 * P.K) {
-      const cplx v = a[int64_t(gi) * P.K + (gk < P.K ? gk : gk - P.K)];
-      x = ldexp(gk < P.K ? v.x : v.y, -e[gi]);
+  for (int u = threadIdx.x; u < BM * (KB / 8); u += blockDim.x) {
+    const int r = u >> 2, g = u & 3;
+    const int gi = mt * BM + r;
+    const int k0 = kbh * KB + g * 8;
+    double xr[8], xi[8];
+    const int sh = gi < P.M ? -e[gi] : 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      xr[q] = 0.0;
+      xi[q] = 0.0;
+      if (gi < P.M && k0 + q < P.K) {
+        const cplx v = a[int64_t(gi) * P.K + k0 + q];
+        xr[q] = ldexp(v.x, sh);
+        xi[q] = ldexp(v.y, sh);
+      }
     }
-    slice_store<S>(x, o + core_off(r, k), SH::A_TILE);
+    uint4 sr[S], si[S], dummy[S];
+    slice8<S>(xr, sr, false, dummy);
+    slice8<S>(xi, si, false, dummy);
+    const int off = core_off(r, g * 8);
+#pragma unroll
+    for (int s2 = 0; s2 < S; ++s2) {
+      *reinterpret_cast<uint4*>(o_re + s2 * SH::A_TILE + off) = sr[s2];
+      *reinterpret_cast<uint4*>(o_im + s2 * SH::A_TILE + off) = si[s2];
+    }
   }
 }
 
-// B'' slices: rows n' = 2j + c of B'' (c = 0: [Re B_j; -Im B_j], c = 1: [Im B_j; Re B_j]).
+// B'' rows n' = 2j + c: c = 0 -> [Re B_j ; -Im B_j], c = 1 -> [Im B_j ; Re B_j] over the
+// two K halves.  CTA = (column tile nt, half-k-block kbh); thread unit = (column j,
+// 8-group); lanes run along j, so the strided column reads coalesce across a warp.
 template <int S>
-__global__ void __launch_bounds__(256) k_split_b(const EmuProb* __restrict__ probs, int nprobs, const cplx* __restrict__ B,
+__global__ void __launch_bounds__(128) k_split_b(const EmuProb* __restrict__ probs, int nprobs, const cplx* __restrict__ B,
                                                  int64_t b_is, const int* __restrict__ ex, int64_t ex_is,
-                                                 __nv_bfloat16* __restrict__ out, int64_t out_is, int tile_base) {
+                                                 __nv_bfloat16* __restrict__ out, int64_t out_is, int) {
   using SH = Shape<S>;
+  constexpr int NJ = SH::BN / 2;
   const int inst = blockIdx.y;
   int t = blockIdx.x, pi = 0;
-  while (pi + 1 < nprobs && t >= probs[pi + 1].pad) ++pi;  // pad = first split-B tile of the problem
+  while (pi + 1 < nprobs && t >= probs[pi + 1].pad) ++pi;  // pad = first split-B CTA of the problem
   const EmuProb P = probs[pi];
-  const int nkb = P.Kp / KB;
+  const int nkb = P.Kp / KB, nkh = nkb / 2;
   const int lt = t - P.pad;
-  const int nt = lt / nkb, kb = lt % nkb;
-  __nv_bfloat16* o = out + inst * out_is + P.b_sl + (int64_t(nt) * nkb + kb) * (S * SH::B_TILE);
+  const int nt = lt / nkh, kbh = lt % nkh;
+  __nv_bfloat16* o_re = out + inst * out_is + P.b_sl + (int64_t(nt) * nkb + kbh) * (S * SH::B_TILE);
+  __nv_bfloat16* o_im = out + inst * out_is + P.b_sl + (int64_t(nt) * nkb + nkh + kbh) * (S * SH::B_TILE);
   const cplx* b = B + inst * b_is + P.b_src;
   const int* e = ex + inst * ex_is + P.b_ex;
-  for (int idx = threadIdx.x; idx < SH::BN * KB; idx += blockDim.x) {
-    const int k = idx / SH::BN, r = idx % SH::BN;  // r fastest: consecutive j reads
-    const int gj = nt * (SH::BN / 2) + (r >> 1), c = r & 1;
-    const int gk = kb * KB + k;
-    double x = 0.0;
-    if (gj < P.N && gk < 2 * P.K) {
-      const bool lo = gk < P.K;
-      const cplx v = b[int64_t(lo ? gk : gk - P.K) * P.N + gj];
-      const double val = c == 0 ? (lo ? v.x : -v.y) : (lo ? v.y : v.x);
-      x = ldexp(val, -e[gj]);
+  for (int u = threadIdx.x; u < NJ * (KB / 8); u += blockDim.x) {
+    const int jl = u % NJ, g = u / NJ;
+    const int gj = nt * NJ + jl;
+    const int k0 = kbh * KB + g * 8;
+    double xr[8], xi[8];
+    const int sh = gj < P.N ? -e[gj] : 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      xr[q] = 0.0;
+      xi[q] = 0.0;
+      if (gj < P.N && k0 + q < P.K) {
+        const cplx v = b[int64_t(k0 + q) * P.N + gj];
+        xr[q] = ldexp(v.x, sh);
+        xi[q] = ldexp(v.y, sh);
+      }
     }
-    slice_store<S>(x, o + core_off(r, k), SH::B_TILE);
+    uint4 sr[S], si[S], sin_[S], dummy[S];
+    slice8<S>(xr, sr, false, dummy);
+    slice8<S>(xi, si, true, sin_);
+    const int off0 = core_off(2 * jl, g * 8), off1 = core_off(2 * jl + 1, g * 8);
+#pragma unroll
+    for (int s2 = 0; s2 < S; ++s2) {
+      *reinterpret_cast<uint4*>(o_re + s2 * SH::B_TILE + off0) = sr[s2];    // row 2j, Re half:  Re B
+      *reinterpret_cast<uint4*>(o_im + s2 * SH::B_TILE + off0) = sin_[s2];  // row 2j, Im half: -Im B
+      *reinterpret_cast<uint4*>(o_re + s2 * SH::B_TILE + off1) = si[s2];    // row 2j+1, Re half: Im B
+      *reinterpret_cast<uint4*>(o_im + s2 * SH::B_TILE + off1) = sr[s2];    // row 2j+1, Im half: Re B
+    }
   }
 }
 
@@ -518,10 +570,20 @@ struct EmuPlan {
   int* d_err = nullptr;
   cplx* d_ws = nullptr;
   int64_t ws_is = 0, red_elems = 0;
+  const EmuPlan* b_owner = nullptr;  // another plan that slices the same B (same tensor, layout, S) first
+};
+
+struct BKey {
+  const void* ptr;
+  int64_t is;
+  int S;
+  std::vector<int64_t> probs;  // (b_src, K, N) per problem
+  bool operator==(const BKey& o) const { return ptr == o.ptr && is == o.is && S == o.S && probs == o.probs; }
 };
 
 struct EmuState {
   std::vector<EmuPlan*> plans;
+  std::vector<std::pair<BKey, EmuPlan*>> bowners;
   int* d_err = nullptr;
 };
 
@@ -578,8 +640,7 @@ EmuPlan* emu_plan(Ctx& c, const GemmPlan& g, const Tensor* A, const Tensor* B, b
     e.M = q.M;
     e.N = q.N;
     e.K = q.K;
-    e.Kp = ((2 * q.K + KB - 1) / KB) * KB;
-    if (e.Kp == 0) e.Kp = KB;
+    e.Kp = 2 * std::max((q.K + KB - 1) / KB, 1) * KB;  // [Re | Im], each half padded to KB
     e.tiles_m = (q.M + BM - 1) / BM;
     e.tiles_n = (q.N + BN / 2 - 1) / (BN / 2);
     const int nkb = e.Kp / KB;
@@ -611,16 +672,16 @@ EmuPlan* emu_plan(Ctx& c, const GemmPlan& g, const Tensor* A, const Tensor* B, b
     p->total_cols += q.N;
     p->n_rowexp += q.M * std::max((q.K + ROW_KR - 1) / ROW_KR, 1);
     p->n_colexp += ((q.N + 31) / 32) * std::max((q.K + 255) / 256, 1);
-    e.pad = bt0;  // first split-B tile
-    bt0 += e.tiles_n * nkb;
-    at0 += e.tiles_m * nkb;
+    e.pad = bt0;  // first split-B CTA
+    bt0 += e.tiles_n * (nkb / 2);
+    at0 += e.tiles_m * (nkb / 2);
     p->h.push_back(e);
   }
   // split-A tile indexing reuses tile0 as the first split-A tile of each problem
   std::vector<EmuProb> ha = p->h;
   {
     int t = 0;
-    for (auto& e : ha) { e.tile0 = t; t += e.tiles_m * (e.Kp / KB); }
+    for (auto& e : ha) { e.tile0 = t; t += e.tiles_m * (e.Kp / (2 * KB)); }
   }
   p->n_tiles = tile0;
   p->n_atiles = at0;
@@ -630,9 +691,21 @@ EmuPlan* emu_plan(Ctx& c, const GemmPlan& g, const Tensor* A, const Tensor* B, b
   p->aex_is = std::max<int64_t>(aex, 1);
   p->bex_is = std::max<int64_t>(bex, 1);
   p->asl = (__nv_bfloat16*)c.dalloc(sizeof(__nv_bfloat16) * p->asl_is * c.ninst);
-  p->bsl = (__nv_bfloat16*)c.dalloc(sizeof(__nv_bfloat16) * p->bsl_is * c.ninst);
   p->aex = (int*)c.dalloc(sizeof(int) * p->aex_is * c.ninst);
-  p->bex = (int*)c.dalloc(sizeof(int) * p->bex_is * c.ninst);
+  // B slices: reuse those of an earlier plan that reads the same tensor the same way
+  // (plans run in creation order every iteration, so the owner has sliced it already)
+  BKey key{B ? (const void*)B->d : nullptr, B ? B->is : 0, p->S, {}};
+  for (auto& e : p->h) { key.probs.push_back(e.b_src); key.probs.push_back(e.K); key.probs.push_back(e.N); }
+  for (auto& kv : st->bowners)
+    if (B && kv.first == key) { p->b_owner = kv.second; break; }
+  if (p->b_owner) {
+    p->bsl = p->b_owner->bsl;
+    p->bex = p->b_owner->bex;
+  } else {
+    p->bsl = (__nv_bfloat16*)c.dalloc(sizeof(__nv_bfloat16) * p->bsl_is * c.ninst);
+    p->bex = (int*)c.dalloc(sizeof(int) * p->bex_is * c.ninst);
+    if (B) st->bowners.push_back({key, p});
+  }
   if (ws) {
     p->ws_is = ws;
     p->d_ws = (cplx*)c.dalloc(sizeof(cplx) * ws * c.ninst);
@@ -643,7 +716,6 @@ EmuPlan* emu_plan(Ctx& c, const GemmPlan& g, const Tensor* A, const Tensor* B, b
   p->d = (EmuProb*)c.dalloc(sizeof(EmuProb) * both.size());
   upload(c, p->d, both.data(), sizeof(EmuProb) * both.size());
   (void)A;
-  (void)B;
   return p;
 }
 
@@ -662,13 +734,13 @@ static void run_s(Ctx& c, EmuPlan* p, const cplx* A, const cplx* B, cplx* C, int
     KCHECK(c);
     if (p->a_const) p->a_ready = true;
   }
-  if (!p->b_ready) {
+  if (!p->b_ready && !p->b_owner) {
     k_fill_int<<<dim3(std::max<int64_t>(1, std::min<int64_t>((p->bex_is * c.ninst + 255) / 256, 1024))), 256, 0, c.stream>>>(
         p->bex, p->bex_is * c.ninst, EXP_ZERO);
     KCHECK(c);
     k_col_exp<<<dim3(p->n_colexp, c.ninst), 256, 0, c.stream>>>(p->d, np, B, bis, p->bex, p->bex_is);
     KCHECK(c);
-    k_split_b<S><<<dim3(p->n_btiles, c.ninst), 256, 0, c.stream>>>(p->d, np, B, bis, p->bex, p->bex_is, p->bsl,
+    k_split_b<S><<<dim3(p->n_btiles, c.ninst), 128, 0, c.stream>>>(p->d, np, B, bis, p->bex, p->bex_is, p->bsl,
                                                                    p->bsl_is, 0);
     KCHECK(c);
     if (p->b_const) p->b_ready = true;
@@ -747,7 +819,7 @@ exp_status noalloc_launch(cudaStream_t st, unsigned char* base, int M, int N, in
   e.M = M;
   e.N = N;
   e.K = K;
-  e.Kp = std::max(((2 * K + KB - 1) / KB) * KB, KB);
+  e.Kp = 2 * std::max((K + KB - 1) / KB, 1) * KB;
   e.tiles_m = (M + BM - 1) / BM;
   e.tiles_n = (N + BN / 2 - 1) / (BN / 2);
   const int nkb = e.Kp / KB;
@@ -797,8 +869,8 @@ exp_status noalloc_launch(cudaStream_t st, unsigned char* base, int M, int N, in
   k_fill_int<<<std::max(1, std::min((N + 255) / 256, 1024)), 256, 0, st>>>(bex, N, EXP_ZERO);
   k_row_exp<<<dim3(unsigned(n_rowexp), 1), 256, 0, st>>>(d_probs, 1, A, 0, aex, 0);
   k_col_exp<<<dim3(unsigned(n_colexp), 1), 256, 0, st>>>(d_probs, 1, B, 0, bex, 0);
-  k_split_a<S><<<dim3(e.tiles_m * nkb, 1), 256, 0, st>>>(d_probs + 1, 1, A, 0, aex, 0, asl, 0);
-  k_split_b<S><<<dim3(e.tiles_n * nkb, 1), 256, 0, st>>>(d_probs, 1, B, 0, bex, 0, bsl, 0, 0);
+  k_split_a<S><<<dim3(e.tiles_m * (nkb / 2), 1), 256, 0, st>>>(d_probs + 1, 1, A, 0, aex, 0, asl, 0);
+  k_split_b<S><<<dim3(e.tiles_n * (nkb / 2), 1), 128, 0, st>>>(d_probs, 1, B, 0, bex, 0, bsl, 0, 0);
   if (cudaFuncSetAttribute(k_emu_gemm<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, SH::SMEM) != cudaSuccess) {
     err = "exp_zgemm_emu_noalloc: shared-memory attribute refused";
     return EXP_ECUDA;

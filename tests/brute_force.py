@@ -154,3 +154,34 @@ def sector_spectrum(f, V, o, nel):
     h, eref = core_hamiltonian(f, V, o)
     H = sp.operator(hamiltonian_terms(h, V))
     return np.linalg.eigvalsh(H) - eref.real
+
+
+def ea_eom_matrix(f, V, o, t1, t2):
+    """Electron-attached block of Hbar_N - E_CC on {a+|0>, a+ b+ j|0> (a<b)} by explicit
+    second quantisation in the (o+1)-electron space.  Returns (M, labels)."""
+    n = f.shape[0]
+    nv = n - o
+    h, eref = core_hamiltonian(f, V, o)
+    sp0 = Space(n, o)
+    sp1 = Space(n, o + 1)
+    H0 = sp0.operator(hamiltonian_terms(h, V)) - eref * np.eye(len(sp0))
+    T0 = sp0.operator(cluster_terms(t1, t2, o))
+    Hbar0 = expm_nilpotent(-T0) @ H0 @ expm_nilpotent(T0)
+    ref = (1 << o) - 1
+    phi0 = sp0.vector([], ref)
+    ecc = np.vdot(phi0, Hbar0 @ phi0)
+    H1 = sp1.operator(hamiltonian_terms(h, V)) - eref * np.eye(len(sp1))
+    T1 = sp1.operator(cluster_terms(t1, t2, o))
+    Hbar1 = expm_nilpotent(-T1) @ H1 @ expm_nilpotent(T1)
+    basis, labels = [], []
+    for a in range(nv):
+        basis.append(sp1.vector([(o + a, 1)], ref))
+        labels.append(("p", a))
+    for j in range(o):
+        for a in range(nv):
+            for b in range(a + 1, nv):
+                basis.append(sp1.vector([(o + a, 1), (o + b, 1), (j, 0)], ref))
+                labels.append(("pph", j, a, b))
+    B = np.stack(basis, axis=1)
+    M = B.conj().T @ Hbar1 @ B - ecc * np.eye(B.shape[1])
+    return M, labels

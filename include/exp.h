@@ -77,7 +77,10 @@ typedef struct {
   int max_iter;            /* per exp_ccsd_iterate sequence, counted from the guess */
   int guess;               /* EXP_GUESS_MP2 or EXP_GUESS_USER (amplitudes set by exp_set_amplitudes) */
   double emu_min_macs;     /* with EXP_EMU_BF16: contractions with fewer complex multiply-adds per
-                              instance stay FP64 (0 = default, 2^26) */
+                              instance stay FP64 (0 = default) */
+  int n_active;            /* (0h,1p) sector: number of active (valence) virtual spinors, 0 = none */
+  const int32_t* active_virt; /* [n_active] their indices within the virtual space (config order),
+                                 shared by all instances; NULL when n_active = 0 */
 } exp_config;
 
 /* Create a context: validates the config, builds the symmetry-blocked layouts
@@ -124,6 +127,23 @@ exp_status exp_ccsd_iterate(exp_ctx* ctx, int n_iter, exp_iter_info* info, int* 
 /* Correlation energy of instance `inst` for the current amplitudes (E of the last
  * t_new; the MP2 energy before any iteration), in hartree.  Synchronises. */
 exp_status exp_energy(exp_ctx* ctx, int inst, double* e_re, double* e_im);
+
+/* Steps II-V for the (0h,1p) sector (Eq. (sectors); H_eff = (H Omega)_Cl, Sec. II.A;
+ * flowchart step V, Sec. II.B): with the (0h,0p) amplitudes T converged, solve the
+ * Bloch equation Q Hbar (P + S) = S H_eff, H_eff = P Hbar (P + S), for the
+ * one-valence-particle amplitudes s_x^a, s_xj^ab of the configured active spinors
+ * (the contractions of Eq. (eq:contraction) and its companions, all through the
+ * same grouped permute/GEMM launches), iterating s <- s + (Q Hbar (P+S) - S H_eff)/D
+ * with D_x^a = e_x - e_a, D_xj^ab = e_x + e_j - e_a - e_b and DIIS, then
+ * diagonalise H_eff per irrep block (FP64 shifted QR on the device).  Runs the
+ * iteration for all instances on the first call (conv_tol, max_iter and diis_dim
+ * of the config), then reports instance `inst`: heff (host, n_active^2 (re, im)
+ * pairs, row y = active y, column x; nullable), eig_re / eig_im (host, n_active,
+ * sorted by real part, then imaginary part), *n_iter (nullable).  ESTATE unless
+ * every instance's (0h,0p) iteration has converged and n_active > 0; ENOTCONV if
+ * the Bloch iteration did not converge within max_iter. */
+exp_status exp_fs_sector_0h1p(exp_ctx* ctx, int inst, double* heff, double* eig_re, double* eig_im,
+                              int* n_iter);
 
 /* Copy amplitudes of instance `inst` between the context and caller device
  * buffers, dense layout: t1[i][a] (n_occ x n_virt), t2[i][j][a][b]; complex128,

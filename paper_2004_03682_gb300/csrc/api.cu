@@ -8,6 +8,7 @@
 #include <cstdlib>
 
 #include "ccsd.h"
+#include "fs.h"
 #include "emu.h"
 
 struct exp_ctx {
@@ -53,6 +54,16 @@ static void check_config(const exp_config* cfg) {
     throw ExpError{EXP_EINVAL, "n_slices must be in 3..6"};
   if (cfg->diis_dim < 0 || cfg->diis_dim > EXP_MAX_DIIS) throw ExpError{EXP_EINVAL, "diis_dim must be in 0..8"};
   if (!(cfg->conv_tol > 0)) throw ExpError{EXP_EINVAL, "conv_tol must be > 0"};
+  if (cfg->n_active < 0 || cfg->n_active > cfg->n_virt) throw ExpError{EXP_EINVAL, "n_active out of range"};
+  if (cfg->n_active > 0) {
+    if (!cfg->active_virt) throw ExpError{EXP_EINVAL, "null active_virt"};
+    std::vector<char> seen(cfg->n_virt, 0);
+    for (int k = 0; k < cfg->n_active; ++k) {
+      const int a = cfg->active_virt[k];
+      if (a < 0 || a >= cfg->n_virt || seen[a]) throw ExpError{EXP_EINVAL, "active_virt: bad or repeated index"};
+      seen[a] = 1;
+    }
+  }
   if (cfg->max_iter < 1) throw ExpError{EXP_EINVAL, "max_iter must be >= 1"};
   for (int64_t k = 0; k < int64_t(cfg->n_inst) * cfg->n_occ; ++k)
     if (!std::isfinite(cfg->eps_occ[k])) throw ExpError{EXP_EINVAL, "non-finite eps_occ"};
@@ -72,6 +83,7 @@ extern "C" exp_status exp_create(const exp_config* cfg, const exp_allocator* all
   c.cfg = *cfg;
   c.cfg.irrep_occ = c.cfg.irrep_virt = nullptr;
   c.cfg.eps_occ = c.cfg.eps_virt = nullptr;
+  c.cfg.active_virt = nullptr;
   c.alloc = *alloc;
   c.stream = (cudaStream_t)stream;
   c.G = cfg->n_irrep;
@@ -81,26 +93,71 @@ extern "C" exp_status exp_create(const exp_config* cfg, const exp_allocator* all
   int dev = 0;
   CK(cudaGetDevice(&dev));
   CK(cudaDeviceGetAttribute(&c.sm_count, cudaDevAttrMultiProcessorCount, dev));
+  // Spaces.  With active spinors, every active virtual x gets a ghost occupied
+  // spinor g_x (same irrep, orbital energy 0, no integrals); the (0h,1p) sector's
+  // electron-attached vectors are carried as the ghosts' amplitudes.  Inside each
+  // occupied irrep the real spinors come first, then the ghosts.
+  c.no_real = cfg->n_occ;
+  c.nact = cfg->n_active;
+  c.act.assign(cfg->active_virt, cfg->active_virt + c.nact);
+  std::vector<int> virt_irrep(c.nv);
+  {
+    int a = 0;
+    for (int g = 0; g < c.G; ++g)
+      for (int k = 0; k < cfg->irrep_virt[g]; ++k) virt_irrep[a++] = g;
+  }
+  std::vector<int> ghosts_in(c.G, 0);
+  for (int k = 0; k < c.nact; ++k) ghosts_in[virt_irrep[c.act[k]]]++;
+  c.no = c.no_real + c.nact;
   c.spaces.resize(SP_COUNT);
-  for (int s = 0; s < SP_COUNT; ++s) {
-    Space& sp = c.spaces[s];
-    const int32_t* cnt = s == SP_OCC ? cfg->irrep_occ : cfg->irrep_virt;
-    sp.cnt.assign(cnt, cnt + c.G);
+  for (int s2 = 0; s2 < SP_COUNT; ++s2) {
+    Space& sp = c.spaces[s2];
+    sp.cnt.resize(c.G);
+    for (int g = 0; g < c.G; ++g)
+      sp.cnt[g] = s2 == SP_OCC ? cfg->irrep_occ[g] + ghosts_in[g] : cfg->irrep_virt[g];
     sp.off.resize(c.G);
     int o = 0;
     for (int g = 0; g < c.G; ++g) { sp.off[g] = o; o += sp.cnt[g]; }
     sp.n = o;
-    sp.gbase = s == SP_OCC ? 0 : c.no;
+    sp.gbase = s2 == SP_OCC ? 0 : c.no;
+  }
+  c.occ_real.assign(c.no, -1);
+  c.occ_ghost.assign(c.no, -1);
+  {
+    int real = 0;
+    for (int g = 0; g < c.G; ++g) {
+      int l = c.spaces[SP_OCC].off[g];
+      for (int k = 0; k < cfg->irrep_occ[g]; ++k) c.occ_real[l++] = real++;
+      for (int k = 0; k < c.nact; ++k)
+        if (virt_irrep[c.act[k]] == g) c.occ_ghost[l++] = k;
+    }
   }
   const int n = c.no + c.nv;
-  std::vector<double> eps(size_t(c.ninst) * n);
+  c.n_gen = c.no_real + c.nv;
+  std::vector<double> eps(size_t(c.ninst) * n), eps_fs(size_t(c.ninst) * n);
   for (int k = 0; k < c.ninst; ++k) {
-    std::copy(cfg->eps_occ + size_t(k) * c.no, cfg->eps_occ + size_t(k + 1) * c.no, eps.begin() + size_t(k) * n);
-    std::copy(cfg->eps_virt + size_t(k) * c.nv, cfg->eps_virt + size_t(k + 1) * c.nv,
-              eps.begin() + size_t(k) * n + c.no);
+    for (int l = 0; l < c.no; ++l) {
+      const int r = c.occ_real[l];
+      eps[size_t(k) * n + l] = r >= 0 ? cfg->eps_occ[size_t(k) * c.no_real + r] : 0.0;
+      eps_fs[size_t(k) * n + l] =
+          r >= 0 ? cfg->eps_occ[size_t(k) * c.no_real + r] : cfg->eps_virt[size_t(k) * c.nv + c.act[c.occ_ghost[l]]];
+    }
+    for (int a = 0; a < c.nv; ++a) eps[size_t(k) * n + c.no + a] = eps_fs[size_t(k) * n + c.no + a] =
+        cfg->eps_virt[size_t(k) * c.nv + a];
   }
   c.d_eps = (double*)c.dalloc(eps.size() * sizeof(double));
   upload(c, c.d_eps, eps.data(), eps.size() * sizeof(double));
+  c.d_occreal = (int*)c.dalloc(sizeof(int) * c.no);
+  upload(c, c.d_occreal, c.occ_real.data(), sizeof(int) * c.no);
+  if (c.nact) {
+    c.d_eps_fs = (double*)c.dalloc(eps_fs.size() * sizeof(double));
+    upload(c, c.d_eps_fs, eps_fs.data(), eps_fs.size() * sizeof(double));
+    std::vector<int> gm(n);
+    for (int l = 0; l < c.no; ++l) gm[l] = c.occ_real[l];
+    for (int a = 0; a < c.nv; ++a) gm[c.no + a] = c.no_real + a;
+    c.d_genmap = (int*)c.dalloc(sizeof(int) * n);
+    upload(c, c.d_genmap, gm.data(), sizeof(int) * n);
+  }
   c.d_seed = (uint64_t*)c.dalloc(sizeof(uint64_t) * c.ninst);
   c.d_scale = (double*)c.dalloc(sizeof(double) * c.ninst);
   CK(cudaEventCreate(&c.ev0));
@@ -138,6 +195,7 @@ extern "C" void exp_destroy(exp_ctx* x) {
   if (c.pev0) cudaEventDestroy(c.pev0);
   if (c.pev1) cudaEventDestroy(c.pev1);
   if (c.h_stats) cudaFreeHost(c.h_stats);
+  fs_release(c);
   try { emu_release(c); } catch (...) {}
   ccsd_release(c);
   c.dfree_all();
@@ -271,6 +329,14 @@ extern "C" exp_status exp_energy(exp_ctx* x, int inst, double* e_re, double* e_i
   if (e_re) *e_re = s[1];
   if (e_im) *e_im = s[2];
   return EXP_OK;
+  API_END(x)
+}
+
+extern "C" exp_status exp_fs_sector_0h1p(exp_ctx* x, int inst, double* heff, double* eig_re, double* eig_im,
+                                         int* n_iter) {
+  API_BEGIN
+  if (!x) throw ExpError{EXP_EINVAL, "null context"};
+  return fs_entry(x->c, inst, heff, eig_re, eig_im, n_iter);
   API_END(x)
 }
 

@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <functional>
 
 #include "ccsd.h"
 #include "emu.h"
@@ -401,7 +402,10 @@ void ccsd_setup(Ctx& c) {
       upload(c, dt, tk.data(), tk.size() * sizeof(GenTask));
       upload(c, dc, ch.data(), ch.size() * sizeof(ChunkRef));
       const int sg[2] = {+1, -1};
-      launch_fill_denom(c, c.d_D, na, dt, dc, int(ch.size()), 2, sg);
+      launch_fill_denom(c, c.d_D, na, dt, dc, int(ch.size()), 2, sg, nullptr);
+      s->t1tasks.d_tasks = dt;
+      s->t1tasks.d_chunks = dc;
+      s->t1tasks.n_chunks = int(ch.size());
     }
     tk.clear();
     ch.clear();
@@ -412,7 +416,7 @@ void ccsd_setup(Ctx& c) {
       upload(c, dt, tk.data(), tk.size() * sizeof(GenTask));
       upload(c, dc, ch.data(), ch.size() * sizeof(ChunkRef));
       const int sg[4] = {+1, +1, -1, -1};
-      launch_fill_denom(c, c.d_D + c.n1, na, dt, dc, int(ch.size()), 4, sg);
+      launch_fill_denom(c, c.d_D + c.n1, na, dt, dc, int(ch.size()), 4, sg, nullptr);
       s->t2tasks.d_tasks = dt;
       s->t2tasks.d_chunks = dc;
       s->t2tasks.n_chunks = int(ch.size());
@@ -625,16 +629,14 @@ void copy_newest(Ctx& c, cplx* dst) {
   KCHECK(c);
 }
 
-// One full iteration: RHS, update, residual, energy, DIIS.
-void ccsd_iteration(Ctx& c) {
+// Update + residual + (energy) + DIIS for every instance.  `upd` launches the
+// update kernel that writes t_new and the error into the next DIIS slot and the
+// per-CTA max |error| into part (RED_BLOCKS CTAs per instance).
+void ccsd_update_step(Ctx& c, const std::function<void(double*, int)>& upd, bool energy) {
   CcsdState& s = S(c);
-  ccsd_rhs(c);
   const int dim = c.cfg.diis_dim;
-  const int D = std::max(dim, 1);
   const int nb = RED_BLOCKS;
-  k_update<<<dim3(nb, c.ninst), RED_THREADS, 0, c.stream>>>(c.d_R, c.d_D, c.d_T, c.d_diis_t, c.d_diis_e, c.namp,
-                                                            dim, c.d_diis_state, s.d_part);
-  KCHECK(c);
+  upd(s.d_part, nb);
   k_finalize_update<<<c.ninst, 32, 0, c.stream>>>(s.d_part, nb, c.d_diis_state, c.d_stats, dim, c.cfg.conv_tol);
   KCHECK(c);
   if (dim > 0) {
@@ -643,10 +645,12 @@ void ccsd_iteration(Ctx& c) {
     k_diis_solve<<<c.ninst, 32, 0, c.stream>>>(s.d_part, nb, dim, c.d_diis_state, c.d_diis_B, s.d_coef, c.d_stats);
     KCHECK(c);
   }
-  // energy of t_new: gather the newest t_new of every instance into R (free by
-  // now), then tau + dot
-  copy_newest(c, c.d_R);
-  ccsd_energy_of(c, c.d_R, true);
+  if (energy) {
+    // energy of t_new: gather the newest t_new of every instance into R (free by
+    // now), then tau + dot
+    copy_newest(c, c.d_R);
+    ccsd_energy_of(c, c.d_R, true);
+  }
   k_extrapolate<<<dim3(grid_for(c.namp), c.ninst), 256, 0, c.stream>>>(c.d_T, c.d_diis_t, c.namp, dim, s.d_coef,
                                                                        c.d_diis_state);
   KCHECK(c);
@@ -654,11 +658,35 @@ void ccsd_iteration(Ctx& c) {
   KCHECK(c);
 }
 
+// One full iteration: RHS, update, residual, energy, DIIS.
+void ccsd_iteration(Ctx& c) {
+  ccsd_rhs(c);
+  ccsd_update_step(c, [&](double* part, int nb) {
+    k_update<<<dim3(nb, c.ninst), RED_THREADS, 0, c.stream>>>(c.d_R, c.d_D, c.d_T, c.d_diis_t, c.d_diis_e, c.namp,
+                                                              c.cfg.diis_dim, c.d_diis_state, part);
+    KCHECK(c);
+  }, true);
+}
+
+// Instances frozen as converged (-1 if a NaN/Inf was seen).  Synchronises.
+int ccsd_count_converged(Ctx& c) {
+  std::vector<int> st(4 * c.ninst);
+  CK(cudaMemcpyAsync(st.data(), c.d_diis_state, sizeof(int) * 4 * c.ninst, cudaMemcpyDeviceToHost, c.stream));
+  CK(cudaMemcpyAsync(c.h_stats, c.d_stats, sizeof(double) * 8 * c.ninst, cudaMemcpyDeviceToHost, c.stream));
+  CK(cudaStreamSynchronize(c.stream));
+  int n = 0;
+  for (int k = 0; k < c.ninst; ++k) {
+    if (c.h_stats[k * 8 + 4] != 0.0) return -1;
+    if (st[k * 4 + 2]) ++n;
+  }
+  return n;
+}
+
 
 // Dense <-> blocked amplitude copies: t1[i][a], t2[i][j][a][b].
 __global__ void k_dense_io(cplx* __restrict__ T, int64_t off, int64_t namp, cplx* __restrict__ dense,
                            const GenTask* __restrict__ tasks, const ChunkRef* __restrict__ chunks, int rank,
-                           int no, int nv, int to_dense) {
+                           int no, int nv, int to_dense, const int* __restrict__ occreal, int no_real) {
   const ChunkRef ch = chunks[blockIdx.x];
   const GenTask Tk = tasks[ch.task];
   const int64_t end = min(ch.start + (int64_t)4096, Tk.count);
@@ -672,12 +700,14 @@ __global__ void k_dense_io(cplx* __restrict__ T, int64_t off, int64_t namp, cplx
     const int64_t p = off + Tk.base + i[0] * Tk.st[0] + i[1] * Tk.st[1] + i[2] * Tk.st[2] + i[3] * Tk.st[3];
     int64_t dp;
     if (rank == 2) {  // slots (a, i) in dims 2, 3
-      const int a = Tk.g0[2] + i[2] - no, ii = Tk.g0[3] + i[3];
+      const int a = Tk.g0[2] + i[2] - no, ii = occreal[Tk.g0[3] + i[3]];
+      if (ii < 0) continue;  // ghost spinor: not part of the dense amplitudes
       dp = int64_t(ii) * nv + a;
     } else {  // slots (a, b, i, j)
       const int a = Tk.g0[0] + i[0] - no, b = Tk.g0[1] + i[1] - no;
-      const int ii = Tk.g0[2] + i[2], jj = Tk.g0[3] + i[3];
-      dp = ((int64_t(ii) * no + jj) * nv + a) * nv + b;
+      const int ii = occreal[Tk.g0[2] + i[2]], jj = occreal[Tk.g0[3] + i[3]];
+      if (ii < 0 || jj < 0) continue;
+      dp = ((int64_t(ii) * no_real + jj) * nv + a) * nv + b;
     }
     if (to_dense) dense[dp] = T[p];
     else T[p] = dense[dp];
@@ -686,29 +716,21 @@ __global__ void k_dense_io(cplx* __restrict__ T, int64_t off, int64_t namp, cplx
 
 void ccsd_dense_io(Ctx& c, int inst, cplx* t1d, cplx* t2d, bool to_dense) {
   CcsdState& s = S(c);
-  if (!s.t1tasks.n_chunks && c.n1) {
-    std::vector<GenTask> tk;
-    std::vector<ChunkRef> ch;
-    gen_tasks(c, c.t1.L, tk, ch);
-    s.t1tasks.d_tasks = (GenTask*)c.dalloc(tk.size() * sizeof(GenTask));
-    s.t1tasks.d_chunks = (ChunkRef*)c.dalloc(ch.size() * sizeof(ChunkRef));
-    upload(c, s.t1tasks.d_tasks, tk.data(), tk.size() * sizeof(GenTask));
-    upload(c, s.t1tasks.d_chunks, ch.data(), ch.size() * sizeof(ChunkRef));
-    s.t1tasks.n_chunks = int(ch.size());
-  }
   if (to_dense) {
-    CK(cudaMemsetAsync(t1d, 0, sizeof(cplx) * c.no * c.nv, c.stream));
-    CK(cudaMemsetAsync(t2d, 0, sizeof(cplx) * size_t(c.no) * c.no * c.nv * c.nv, c.stream));
+    CK(cudaMemsetAsync(t1d, 0, sizeof(cplx) * c.no_real * c.nv, c.stream));
+    CK(cudaMemsetAsync(t2d, 0, sizeof(cplx) * size_t(c.no_real) * c.no_real * c.nv * c.nv, c.stream));
   }
   const int64_t off = int64_t(inst) * c.namp;
   if (s.t1tasks.n_chunks) {
     k_dense_io<<<s.t1tasks.n_chunks, 256, 0, c.stream>>>(c.d_T, off, c.namp, t1d, s.t1tasks.d_tasks,
-                                                         s.t1tasks.d_chunks, 2, c.no, c.nv, to_dense);
+                                                         s.t1tasks.d_chunks, 2, c.no, c.nv, to_dense, c.d_occreal,
+                                                         c.no_real);
     KCHECK(c);
   }
   if (s.t2tasks.n_chunks) {
     k_dense_io<<<s.t2tasks.n_chunks, 256, 0, c.stream>>>(c.d_T, off + c.n1, c.namp, t2d, s.t2tasks.d_tasks,
-                                                         s.t2tasks.d_chunks, 4, c.no, c.nv, to_dense);
+                                                         s.t2tasks.d_chunks, 4, c.no, c.nv, to_dense, c.d_occreal,
+                                                         c.no_real);
     KCHECK(c);
   }
 }

@@ -1,5 +1,7 @@
 // CCSD (0h,0p) driver entry points used by the C ABI.
 #pragma once
+#include <functional>
+
 #include "engine.h"
 
 Layout L4(Ctx& c, int s0, int g0, int s1, int g1, int s2, int g2, int s3, int g3, int nrow);
@@ -13,3 +15,5 @@ void ccsd_energy_of(Ctx& c, const cplx* T, bool skip_frozen);
 void ccsd_rhs(Ctx& c);
 void ccsd_iteration(Ctx& c);
 void ccsd_dense_io(Ctx& c, int inst, cplx* t1_dense, cplx* t2_dense, bool to_dense);
+void ccsd_update_step(Ctx& c, const std::function<void(double*, int)>& upd, bool energy);
+int ccsd_count_converged(Ctx& c);

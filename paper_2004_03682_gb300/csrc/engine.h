@@ -163,7 +163,8 @@ void launch_permute(Ctx& c, const PermPlan& p, cplx* dst, const cplx* src, int64
 void launch_generate(Ctx& c, cplx* dst, int64_t inst_stride, const GenTask* d_tasks,
                      const ChunkRef* d_chunks, int n_chunks, const int map[4]);
 void launch_fill_denom(Ctx& c, double* dst, int64_t inst_stride, const GenTask* d_tasks,
-                       const ChunkRef* d_chunks, int n_chunks, int nslots, const int sgn[4]);
+                       const ChunkRef* d_chunks, int n_chunks, int nslots, const int sgn[4],
+                       const double* eps);
 void launch_tau(Ctx& c, cplx* dst, int64_t dst_is, const cplx* t2, const cplx* t1,
                 int64_t t_is, const int32_t* t1_index, const GenTask* d_tasks,
                 const ChunkRef* d_chunks, int n_chunks, double c0, double c1, double c2);
@@ -222,6 +223,16 @@ struct Ctx {
   cudaEvent_t pev0 = nullptr, pev1 = nullptr;
 
   int* d_emu_err = nullptr;  // set by a bounded device wait that gave up
+  // (0h,1p) sector: one non-interacting "ghost" occupied spinor per active virtual
+  int no_real = 0, nact = 0, n_gen = 0;
+  std::vector<int> act;        // active virtual local indices (config order)
+  std::vector<int> occ_real;   // occupied local index -> real occupied index, -1 for a ghost
+  std::vector<int> occ_ghost;  // occupied local index -> active slot, -1 for a real spinor
+  int* d_genmap = nullptr;     // global spinor index -> generator index (-1: ghost), or null
+  int* d_occreal = nullptr;    // device copy of occ_real
+  double* d_eps_fs = nullptr;  // [ninst][n] orbital energies with ghost x <- eps of active x
+  void* fs_state = nullptr;
+
   // emulation and driver state
   void* emu_state = nullptr;
   void* ccsd_state = nullptr;

@@ -115,11 +115,14 @@ struct Map4 {
   int m[4];
 };
 
+// genmap (nullable): global spinor index -> generator index, -1 for a ghost spinor
+// (every integral with a ghost index is zero).  n = number of generator indices.
 __global__ void __launch_bounds__(256) k_generate(cplx* __restrict__ dst, int64_t is,
                                                   const GenTask* __restrict__ tasks,
                                                   const ChunkRef* __restrict__ chunks, Map4 map,
                                                   int n, const uint64_t* __restrict__ seeds,
-                                                  const double* __restrict__ scales) {
+                                                  const double* __restrict__ scales,
+                                                  const int* __restrict__ genmap) {
   const ChunkRef ch = chunks[blockIdx.x];
   const GenTask T = tasks[ch.task];
   const int inst = blockIdx.y;
@@ -135,9 +138,21 @@ __global__ void __launch_bounds__(256) k_generate(cplx* __restrict__ dst, int64_
     i[1] = int(r % T.n[1]);
     i[0] = int(r / T.n[1]);
     uint64_t g[4];
+    bool ghost = false;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) g[k] = uint64_t(T.g0[k] + i[k]);
+    for (int k = 0; k < 4; ++k) {
+      int gi = T.g0[k] + i[k];
+      if (genmap) {
+        gi = genmap[gi];
+        ghost |= gi < 0;
+      }
+      g[k] = uint64_t(gi < 0 ? 0 : gi);
+    }
     const int64_t dp = T.base + i[0] * T.st[0] + i[1] * T.st[1] + i[2] * T.st[2] + i[3] * T.st[3];
+    if (ghost) {
+      dst[dp] = make_double2(0.0, 0.0);
+      continue;
+    }
     const cplx v = v_element(g[map.m[0]], g[map.m[1]], g[map.m[2]], g[map.m[3]], uint64_t(n), seed);
     dst[dp] = make_double2(sc * v.x, sc * v.y);
   }
@@ -150,7 +165,7 @@ void launch_generate(Ctx& c, cplx* dst, int64_t is, const GenTask* d_tasks, cons
   // generator tasks use padded dims: slot k of a rank-4 tensor is dim k
   for (int k = 0; k < 4; ++k) m.m[k] = map[k];
   k_generate<<<dim3(n_chunks, c.ninst), 256, 0, c.stream>>>(dst, is, d_tasks, d_chunks, m,
-                                                            c.no + c.nv, c.d_seed, c.d_scale);
+                                                            c.n_gen, c.d_seed, c.d_scale, c.d_genmap);
   KCHECK(c);
 }
 
@@ -183,14 +198,14 @@ __global__ void k_fill_denom(double* __restrict__ dst, int64_t is, const GenTask
 }
 
 void launch_fill_denom(Ctx& c, double* dst, int64_t is, const GenTask* d_tasks, const ChunkRef* d_chunks,
-                       int n_chunks, int nslots, const int sgn[4]) {
+                       int n_chunks, int nslots, const int sgn[4], const double* eps) {
   if (!n_chunks) return;
   Sgn4 s;
   const int pad = 4 - nslots;
   for (int k = 0; k < 4; ++k) s.s[k] = 0;
   for (int k = 0; k < nslots; ++k) s.s[pad + k] = sgn[k];
   k_fill_denom<<<dim3(n_chunks, c.ninst), 256, 0, c.stream>>>(dst, is, d_tasks, d_chunks, s, c.no + c.nv,
-                                                              c.d_eps);
+                                                              eps ? eps : c.d_eps);
   KCHECK(c);
 }
 

@@ -41,7 +41,8 @@ class Config(C.Structure):
                 ("eps_occ", C.POINTER(C.c_double)), ("eps_virt", C.POINTER(C.c_double)),
                 ("precision", C.c_int), ("n_slices", C.c_int), ("diis_dim", C.c_int),
                 ("conv_tol", C.c_double), ("max_iter", C.c_int), ("guess", C.c_int),
-                ("emu_min_macs", C.c_double)]
+                ("emu_min_macs", C.c_double), ("n_active", C.c_int),
+                ("active_virt", C.POINTER(C.c_int32))]
 
 
 class IterInfo(C.Structure):
@@ -68,6 +69,9 @@ def lib():
     L.exp_ccsd_iterate.argtypes = [P, C.c_int, C.POINTER(IterInfo), C.POINTER(C.c_int)]
     L.exp_energy.argtypes = [P, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]
     L.exp_get_amplitudes.argtypes = [P, C.c_int, P, P]
+    L.exp_fs_sector_0h1p.argtypes = [P, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                     C.POINTER(C.c_double), C.POINTER(C.c_int)]
+    L.exp_fs_sector_0h1p.restype = C.c_int
     L.exp_set_amplitudes.argtypes = [P, C.c_int, P, P]
     L.exp_work_per_iteration.argtypes = [P, C.POINTER(C.c_double)]
     L.exp_work_per_iteration.restype = C.c_int
@@ -126,7 +130,7 @@ class Context:
 
     def __init__(self, n_occ, n_virt, irrep_occ, irrep_virt, eps_occ, eps_virt, n_inst=1,
                  precision=EXP_FP64, n_slices=5, diis_dim=6, conv_tol=1e-9, max_iter=500,
-                 guess=EXP_GUESS_MP2, device=0, emu_min_macs=0.0):
+                 guess=EXP_GUESS_MP2, device=0, emu_min_macs=0.0, active=None):
         import torch
         self._torch = torch
         L = lib()
@@ -142,9 +146,14 @@ class Context:
         eo, peo = _arr(np.asarray(eps_occ, dtype=np.float64).reshape(-1), C.c_double, np.float64)
         ev, pev = _arr(np.asarray(eps_virt, dtype=np.float64).reshape(-1), C.c_double, np.float64)
         self._keep += [io, iv, eo, ev]
+        self.n_active = 0 if active is None else len(active)
+        pa = None
+        if self.n_active:
+            ac, pa = _arr(np.asarray(active, dtype=np.int32), C.c_int32, np.int32)
+            self._keep.append(ac)
         cfg = Config(self.n_inst, self.n_occ, self.n_virt, len(io), pio, piv, peo, pev,
                      int(precision), int(n_slices), int(diis_dim), float(conv_tol), int(max_iter),
-                     int(guess), float(emu_min_macs))
+                     int(guess), float(emu_min_macs), self.n_active, pa)
         h = C.c_void_p()
         st = L.exp_create(C.byref(cfg), C.byref(self.alloc.struct), C.c_void_p(self.stream.cuda_stream),
                           C.byref(h))
@@ -181,6 +190,20 @@ class Context:
             recs.append(dict(e=complex(r.e_re, r.e_im), max_dt=r.max_dt, diis_n=r.diis_n,
                              n_converged=r.n_converged, ms=r.ms))
         return recs, bool(conv.value), st
+
+    def fs_sector_0h1p(self, inst=0):
+        """(H_eff, eigenvalues, n_iter, status) of the (0h,1p) sector for instance `inst`."""
+        na = self.n_active
+        heff = np.zeros(2 * na * na)
+        er, ei = np.zeros(na), np.zeros(na)
+        nit = C.c_int(0)
+        dp = C.POINTER(C.c_double)
+        st = self.L.exp_fs_sector_0h1p(self.h, int(inst), heff.ctypes.data_as(dp), er.ctypes.data_as(dp),
+                                       ei.ctypes.data_as(dp), C.byref(nit))
+        if st not in (0, 4):
+            self._check(st)
+        H = (heff[0::2] + 1j * heff[1::2]).reshape(na, na)
+        return H, er + 1j * ei, nit.value, st
 
     def energy(self, inst=0) -> complex:
         re, im = C.c_double(), C.c_double()

@@ -38,7 +38,7 @@ def test_hbar_on_attached_vectors_equals_brute_force(rng, no, nv):
         vec = np.array([r1[k, l[1]] if l[0] == "p" else r2[k, l[1], l[2], l[3]] for l in labels])
         out = M @ vec
         got = np.array([s1[k, l[1]] if l[0] == "p" else s2[k, l[1], l[2], l[3]] for l in labels])
-        np.testing.assert_allclose(got, out, atol=1e-12, rtol=0)
+        np.testing.assert_allclose(got, out, atol=1e-13 * np.max(np.abs(out)), rtol=0)
 
 
 def test_heff_eigenvalues_in_attached_spectrum_and_one_electron_fci():

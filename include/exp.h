@@ -202,6 +202,38 @@ exp_status exp_zgemm_emu_noalloc(void* stream, int n_slices, int M, int N, int K
                                  void* C, double alpha_re, double alpha_im, int beta);
 const char* exp_noalloc_last_error(void);
 
+/* Learned initial guess for T2 (no counterpart in the paper; a starting point for
+ * the amplitude iteration, which alone decides the converged result).  A 3-layer
+ * MLP of width 128 maps the features (|t_MP2|/0.05, -D_ij^ab/10,
+ * |<ij||ab>|/max|<ij||ab>|) of every doubles amplitude to a complex multiplier:
+ * t2 = (1 + y0 + i y1) <ab||ij>/D_ij^ab (phase covariant, antisymmetric); t1 = 0.
+ * Training: loss = mean |t2 - t2_converged|^2 / 0.05^2 over the unique (a<b, i<j)
+ * amplitudes of converged solves, Adam; forward, backward and update are
+ * hand-written kernels accumulating in FP32 with BF16-rounded weights and
+ * activations (bf16 = 1) or in plain FP32 (bf16 = 0, for gradient checks).  The
+ * untrained model (zero output layer) reproduces the MP2 guess exactly.
+ * Parameters (exp_mlp_num_params() floats): W1[128][3], b1[128], W2[128][128],
+ * b2[128], W3[2][128], b3[2].  Device memory from `alloc`, work on `stream`. */
+typedef struct exp_mlp exp_mlp;
+int exp_mlp_num_params(void);
+exp_status exp_mlp_create(const exp_allocator* alloc, void* stream, uint64_t seed, int bf16, exp_mlp** out);
+void exp_mlp_destroy(exp_mlp* mlp);
+/* Append the unique amplitudes of every converged instance of ctx as training samples. */
+exp_status exp_mlp_add_training_data(exp_mlp* mlp, exp_ctx* ctx);
+/* `epochs` passes over the samples in shuffled mini-batches (shuffle seeded by
+ * `seed`); loss_out (host, nullable) receives each epoch's mean batch loss. */
+exp_status exp_mlp_train(exp_mlp* mlp, int epochs, int batch, double lr, uint64_t seed, double* loss_out);
+/* Initial amplitudes of every instance of ctx from the model (replaces the MP2
+ * guess; resets DIIS and the iteration count).  Requires exp_init_integrals. */
+exp_status exp_mlp_apply(exp_mlp* mlp, exp_ctx* ctx);
+/* Copy parameters out (get, host, nullable) and/or in (set, host, nullable). */
+exp_status exp_mlp_params(exp_mlp* mlp, float* get, const float* set);
+/* Loss and gradient on n host samples: x [n][3] features, tmp2 and target [n][2]
+ * (re, im) first-order and target amplitudes; grad (host, num_params). */
+exp_status exp_mlp_loss_grad(exp_mlp* mlp, int n, const float* x, const double* tmp2, const double* target,
+                             double* loss, float* grad);
+const char* exp_mlp_last_error(const exp_mlp* mlp);
+
 /* Number of kernels this context has launched so far (for launch accounting). */
 int64_t exp_kernel_launches(const exp_ctx* ctx);
 

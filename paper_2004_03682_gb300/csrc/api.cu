@@ -11,10 +11,6 @@
 #include "fs.h"
 #include "emu.h"
 
-struct exp_ctx {
-  Ctx c;
-};
-
 static thread_local std::string g_err;
 
 #define API_BEGIN try {

@@ -734,3 +734,11 @@ void ccsd_dense_io(Ctx& c, int inst, cplx* t1d, cplx* t2d, bool to_dense) {
     KCHECK(c);
   }
 }
+
+const Tensor* ccsd_driver_integral(Ctx& c) { return S(c).Vd; }
+
+void ccsd_mark_guessed(Ctx& c) {
+  ccsd_reset_diis(c);
+  ccsd_energy_of(c, c.d_T, false);
+  c.guessed = true;
+}

@@ -17,3 +17,5 @@ void ccsd_iteration(Ctx& c);
 void ccsd_dense_io(Ctx& c, int inst, cplx* t1_dense, cplx* t2_dense, bool to_dense);
 void ccsd_update_step(Ctx& c, const std::function<void(double*, int)>& upd, bool energy);
 int ccsd_count_converged(Ctx& c);
+const Tensor* ccsd_driver_integral(Ctx& c);
+void ccsd_mark_guessed(Ctx& c);

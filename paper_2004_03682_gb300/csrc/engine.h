@@ -280,3 +280,7 @@ struct ExpError {
     cudaError_t _e = cudaGetLastError();                 \
     if (_e != cudaSuccess) throw CudaError{_e, "launch"}; \
   } while (0)
+
+struct exp_ctx {
+  Ctx c;
+};

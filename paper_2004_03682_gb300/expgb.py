@@ -81,6 +81,22 @@ def lib():
     L.exp_zgemm.argtypes = [C.POINTER(Allocator), P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, P, P, P,
                             C.c_double, C.c_double, C.c_int]
     L.exp_zgemm.restype = C.c_int
+    L.exp_mlp_num_params.argtypes = []
+    L.exp_mlp_num_params.restype = C.c_int
+    L.exp_mlp_create.argtypes = [C.POINTER(Allocator), P, C.c_uint64, C.c_int, C.POINTER(P)]
+    L.exp_mlp_destroy.argtypes = [P]
+    L.exp_mlp_destroy.restype = None
+    L.exp_mlp_add_training_data.argtypes = [P, P]
+    L.exp_mlp_train.argtypes = [P, C.c_int, C.c_int, C.c_double, C.c_uint64, C.POINTER(C.c_double)]
+    L.exp_mlp_apply.argtypes = [P, P]
+    L.exp_mlp_params.argtypes = [P, C.POINTER(C.c_float), C.POINTER(C.c_float)]
+    L.exp_mlp_loss_grad.argtypes = [P, C.c_int, C.POINTER(C.c_float), C.POINTER(C.c_double),
+                                    C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_float)]
+    L.exp_mlp_last_error.argtypes = [P]
+    L.exp_mlp_last_error.restype = C.c_char_p
+    for name in ("exp_mlp_create", "exp_mlp_add_training_data", "exp_mlp_train", "exp_mlp_apply",
+                 "exp_mlp_params", "exp_mlp_loss_grad"):
+        getattr(L, name).restype = C.c_int
     L.exp_kernel_launches.argtypes = [P]
     L.exp_kernel_launches.restype = C.c_int64
     L.exp_last_error.argtypes = [P]
@@ -248,6 +264,73 @@ class Context:
     def close(self):
         if getattr(self, "h", None):
             self.L.exp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Mlp:
+    """The learned T2 guess (exp_mlp_*)."""
+
+    def __init__(self, seed=0, bf16=True, device=0, stream=None):
+        import torch
+        self._torch = torch
+        self.L = lib()
+        torch.cuda.set_device(device)
+        self.stream = stream or torch.cuda.Stream(device=device)
+        self.alloc = TorchAllocator(device, self.stream)
+        h = C.c_void_p()
+        st = self.L.exp_mlp_create(C.byref(self.alloc.struct), C.c_void_p(self.stream.cuda_stream), int(seed),
+                                   int(bool(bf16)), C.byref(h))
+        if st != 0:
+            raise ExpError(st, self.L.exp_mlp_last_error(None).decode())
+        self.h = h
+        self.n_params = self.L.exp_mlp_num_params()
+
+    def _check(self, st):
+        if st != 0:
+            raise ExpError(st, self.L.exp_mlp_last_error(self.h).decode())
+
+    def add_training_data(self, ctx):
+        self._check(self.L.exp_mlp_add_training_data(self.h, ctx.h))
+
+    def train(self, epochs, batch=65536, lr=1e-3, seed=0):
+        out = np.zeros(max(epochs, 1))
+        self._check(self.L.exp_mlp_train(self.h, int(epochs), int(batch), float(lr), int(seed),
+                                         out.ctypes.data_as(C.POINTER(C.c_double))))
+        return out[:epochs]
+
+    def apply(self, ctx):
+        self._check(self.L.exp_mlp_apply(self.h, ctx.h))
+
+    def params(self, set=None):
+        get = np.zeros(self.n_params, np.float32)
+        ps = None
+        if set is not None:
+            s_ = np.ascontiguousarray(set, dtype=np.float32)
+            ps = s_.ctypes.data_as(C.POINTER(C.c_float))
+        self._check(self.L.exp_mlp_params(self.h, get.ctypes.data_as(C.POINTER(C.c_float)), ps))
+        return get
+
+    def loss_grad(self, x, tmp2, target):
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        t = np.ascontiguousarray(np.stack([tmp2.real, tmp2.imag], -1), dtype=np.float64)
+        g_ = np.ascontiguousarray(np.stack([target.real, target.imag], -1), dtype=np.float64)
+        loss = C.c_double()
+        grad = np.zeros(self.n_params, np.float32)
+        self._check(self.L.exp_mlp_loss_grad(self.h, len(x), x.ctypes.data_as(C.POINTER(C.c_float)),
+                                             t.ctypes.data_as(C.POINTER(C.c_double)),
+                                             g_.ctypes.data_as(C.POINTER(C.c_double)), C.byref(loss),
+                                             grad.ctypes.data_as(C.POINTER(C.c_float))))
+        return loss.value, grad
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.exp_mlp_destroy(self.h)
             self.h = None
 
     def __del__(self):

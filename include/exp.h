@@ -118,11 +118,15 @@ typedef struct {
  * T1/T2 diagrams (grouped permute + contraction launches), t_new = RHS/D,
  * residual max|t_new - t|, E(t_new), DIIS extrapolation.  Runs at most n_iter
  * iterations, stopping early when every instance has converged (residual below
- * conv_tol).  info: host array of n_iter records or NULL.  *converged (host,
- * nullable) = 1 when all instances converged.  Returns ENOTCONV once max_iter
- * iterations have run in total without convergence, ENUMERIC on NaN/Inf, ESTATE
- * before exp_init_integrals. */
+ * conv_tol) or failed.  An instance whose amplitudes turn NaN/Inf is frozen as
+ * failed and the others go on; the call then returns ENUMERIC.  info: host array
+ * of n_iter records or NULL.  *converged (host, nullable) = 1 when all instances
+ * converged.  Returns ENOTCONV once max_iter iterations have run in total without
+ * convergence, ESTATE before exp_init_integrals. */
 exp_status exp_ccsd_iterate(exp_ctx* ctx, int n_iter, exp_iter_info* info, int* converged);
+
+/* State of instance `inst`: 0 iterating, 1 converged, 2 failed (NaN/Inf).  Synchronises. */
+exp_status exp_instance_state(exp_ctx* ctx, int inst, int* state);
 
 /* Correlation energy of instance `inst` for the current amplitudes (E of the last
  * t_new; the MP2 energy before any iteration), in hartree.  Synchronises. */
@@ -232,6 +236,11 @@ exp_status exp_mlp_params(exp_mlp* mlp, float* get, const float* set);
  * (re, im) first-order and target amplitudes; grad (host, num_params). */
 exp_status exp_mlp_loss_grad(exp_mlp* mlp, int n, const float* x, const double* tmp2, const double* target,
                              double* loss, float* grad);
+/* Samples held, and the mean loss over all of them for the current parameters. */
+int64_t exp_mlp_num_samples(const exp_mlp* mlp);
+/* Copy samples [first, first+count) to host: x [count][3], tmp2 and target [count][2] (re, im). */
+exp_status exp_mlp_samples(exp_mlp* mlp, int64_t first, int64_t count, float* x, float* tmp2, float* target);
+exp_status exp_mlp_eval(exp_mlp* mlp, double* loss);
 const char* exp_mlp_last_error(const exp_mlp* mlp);
 
 /* Number of kernels this context has launched so far (for launch accounting). */

@@ -284,12 +284,11 @@ extern "C" exp_status exp_ccsd_iterate(exp_ctx* x, int n_iter, exp_iter_info* in
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, c.ev0, c.ev1));
     double mdt = 0.0;
-    int nconv = 0;
-    bool bad = false;
+    int nconv = 0, nfail = 0;
     for (int k = 0; k < c.ninst; ++k) {
-      mdt = std::max(mdt, c.h_stats[k * 8 + 0]);
-      if (c.h_stats[k * 8 + 4] != 0.0) bad = true;
-      if (st[k * 4 + 2]) ++nconv;
+      if (st[k * 4 + 2] == 1) ++nconv;
+      else if (st[k * 4 + 2] == 2) ++nfail;
+      else mdt = std::max(mdt, c.h_stats[k * 8 + 0]);
     }
     if (info) {
       info[it].e_re = c.h_stats[1];
@@ -304,11 +303,25 @@ extern "C" exp_status exp_ccsd_iterate(exp_ctx* x, int n_iter, exp_iter_info* in
       CK(cudaMemcpy(&err, c.d_emu_err, sizeof(int), cudaMemcpyDeviceToHost));
       if (err) throw ExpError{EXP_ETIMEOUT, "emulated GEMM: a bounded device wait gave up"};
     }
-    if (bad) throw ExpError{EXP_ENUMERIC, "NaN/Inf in the amplitudes"};
-    if (nconv == c.ninst) { all_conv = true; break; }
+    c.n_failed = nfail;
+    if (nconv + nfail == c.ninst) { all_conv = nfail == 0; break; }
   }
   if (converged) *converged = all_conv ? 1 : 0;
+  if (c.n_failed) throw ExpError{EXP_ENUMERIC, std::to_string(c.n_failed) + " instance(s) diverged (NaN/Inf)"};
   if (!all_conv && c.iter_done >= c.cfg.max_iter) return EXP_ENOTCONV;
+  return EXP_OK;
+  API_END(x)
+}
+
+extern "C" exp_status exp_instance_state(exp_ctx* x, int inst, int* state) {
+  API_BEGIN
+  if (!x || !state) throw ExpError{EXP_EINVAL, "null argument"};
+  Ctx& c = x->c;
+  if (inst < 0 || inst >= c.ninst) throw ExpError{EXP_EINVAL, "instance out of range"};
+  int st[4];
+  CK(cudaMemcpyAsync(st, c.d_diis_state + 4 * inst, sizeof(st), cudaMemcpyDeviceToHost, c.stream));
+  CK(cudaStreamSynchronize(c.stream));
+  *state = st[2];
   return EXP_OK;
   API_END(x)
 }

@@ -55,7 +55,9 @@ __device__ T block_reduce(T v, Op op, T* sh) {
   }
   return v;
 }
-struct MaxOp { __device__ double operator()(double a, double b) const { return fmax(a, b); } };
+// max that propagates NaN (fmax would drop it and let a diverged instance look converged)
+__device__ __forceinline__ double nanmax(double a, double b) { return (b != b || b > a) ? b : a; }
+struct MaxOp { __device__ double operator()(double a, double b) const { return nanmax(a, b); } };
 struct AddOp { __device__ double operator()(double a, double b) const { return a + b; } };
 
 // t_new = R / D over the whole amplitude vector; e = t_new - t.  Writes t_new and
@@ -80,7 +82,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_update(const cplx* __restrict__
       const cplx e = make_double2(tn.x - t.x, tn.y - t.y);
       Tn[soff + k] = tn;
       En[soff + k] = e;
-      m = fmax(m, hypot(e.x, e.y));
+      m = nanmax(m, hypot(e.x, e.y));
     }
   }
   m = block_reduce(m, MaxOp(), sh);
@@ -100,10 +102,14 @@ __global__ void k_finalize_update(const double* __restrict__ part, int nb, int* 
   for (int b = 0; b < nb; ++b) {
     const double v = part[(inst * nb + b) * 8];
     if (!(v == v) || isinf(v)) bad = true;
-    m = fmax(m, v);
+    m = nanmax(m, v);
   }
   s[0] = bad ? INFINITY : m;
   s[4] = bad ? 1.0 : 0.0;
+  if (bad) {  // this instance failed: freeze it as failed (2), the others go on
+    st[2] = 2;
+    return;
+  }
   if (dim > 0) {
     st[1] = (st[1] + 1) % dim;
     st[0] = min(st[0] + 1, dim);
@@ -282,7 +288,7 @@ __global__ void __launch_bounds__(256) k_extrapolate(cplx* __restrict__ T, const
 // converged instances freeze after their final t_new has been taken
 __global__ void k_freeze(int* __restrict__ state, int ninst) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < ninst && state[i * 4 + 3]) state[i * 4 + 2] = 1;
+  if (i < ninst && state[i * 4 + 3] && state[i * 4 + 2] == 0) state[i * 4 + 2] = 1;
 }
 
 // scale pass: max |V_abij / D_ij^ab| per instance
@@ -294,7 +300,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_maxratio(const cplx* __restrict
   double m = 0.0;
   for (int64_t k = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; k < n; k += int64_t(gridDim.x) * blockDim.x) {
     const cplx v = V[inst * vis + k];
-    m = fmax(m, hypot(v.x, v.y) / fabs(D[inst * dis + off + k]));
+    m = nanmax(m, hypot(v.x, v.y) / fabs(D[inst * dis + off + k]));
   }
   m = block_reduce(m, MaxOp(), sh);
   if (threadIdx.x == 0) part[(inst * gridDim.x + blockIdx.x) * 8] = m;
@@ -668,7 +674,7 @@ void ccsd_iteration(Ctx& c) {
   }, true);
 }
 
-// Instances frozen as converged (-1 if a NaN/Inf was seen).  Synchronises.
+// Instances frozen as converged (-1 if any instance failed with NaN/Inf).  Synchronises.
 int ccsd_count_converged(Ctx& c) {
   std::vector<int> st(4 * c.ninst);
   CK(cudaMemcpyAsync(st.data(), c.d_diis_state, sizeof(int) * 4 * c.ninst, cudaMemcpyDeviceToHost, c.stream));
@@ -676,8 +682,8 @@ int ccsd_count_converged(Ctx& c) {
   CK(cudaStreamSynchronize(c.stream));
   int n = 0;
   for (int k = 0; k < c.ninst; ++k) {
-    if (c.h_stats[k * 8 + 4] != 0.0) return -1;
-    if (st[k * 4 + 2]) ++n;
+    if (st[k * 4 + 2] == 2) return -1;
+    if (st[k * 4 + 2] == 1) ++n;
   }
   return n;
 }

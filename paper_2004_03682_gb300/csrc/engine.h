@@ -202,6 +202,7 @@ struct Ctx {
   double* d_stats = nullptr;       // [ninst][4]: max_dt, e_re, e_im, diis_n
   double* h_stats = nullptr;       // pinned host mirror
   int iter_done = 0;
+  int n_failed = 0;  // instances frozen after NaN/Inf
   bool guessed = false;
 
   // caches

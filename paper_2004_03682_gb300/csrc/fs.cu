@@ -130,18 +130,22 @@ __global__ void __launch_bounds__(256) k_fs_update(const cplx* __restrict__ R, c
         const double rr = r.x - d0 * t.x - x.x, ri = r.y - d0 * t.y - x.y;
         e = make_double2(rr / df, ri / df);
         tn = make_double2(t.x + e.x, t.y + e.y);
-        m = fmax(m, hypot(e.x, e.y));
+        const double ae = hypot(e.x, e.y);
+        m = (ae != ae || ae > m) ? ae : m;  // NaN-propagating max
       }
       Tn[soff + k] = tn;
       En[soff + k] = e;
     }
   }
-  for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  for (int o = 16; o; o >>= 1) {
+    const double v = __shfl_xor_sync(0xffffffffu, m, o);
+    m = (v != v || v > m) ? v : m;
+  }
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   if (l == 0) sh[w] = m;
   __syncthreads();
   if (threadIdx.x == 0) {
-    for (int k = 1; k < (blockDim.x >> 5); ++k) m = fmax(m, sh[k]);
+    for (int k = 1; k < (blockDim.x >> 5); ++k) m = (sh[k] != sh[k] || sh[k] > m) ? sh[k] : m;
     part[(inst * gridDim.x + blockIdx.x) * 8] = m;
   }
 }

@@ -461,7 +461,7 @@ extern "C" exp_status exp_mlp_add_training_data(exp_mlp* m, exp_ctx* x) {
   std::vector<int> st(4 * c.ninst), list;
   CK(cudaMemcpy(st.data(), c.d_diis_state, sizeof(int) * 4 * c.ninst, cudaMemcpyDeviceToHost));
   for (int k = 0; k < c.ninst; ++k)
-    if (st[k * 4 + 2]) list.push_back(k);
+    if (st[k * 4 + 2] == 1) list.push_back(k);  // converged (2 = failed)
   if (list.empty()) return EXP_OK;
   // unique real elements a<b, i<j of the t2 layout
   std::vector<SubBlock> sb;
@@ -534,6 +534,34 @@ extern "C" exp_status exp_mlp_train(exp_mlp* m, int epochs, int batch, double lr
     CK(cudaStreamSynchronize(m->stream));  // the permutation buffer is reused next epoch
     if (loss_out) loss_out[ep] = l / nbat;
   }
+  return EXP_OK;
+  MLP_CATCH(m)
+}
+
+extern "C" int64_t exp_mlp_num_samples(const exp_mlp* m) { return m ? m->n : 0; }
+
+extern "C" exp_status exp_mlp_samples(exp_mlp* m, int64_t first, int64_t count, float* x, float* tmp2, float* target) {
+  MLP_TRY
+  if (!m || first < 0 || count < 0 || first + count > m->n) throw ExpError{EXP_EINVAL, "bad range"};
+  if (x) CK(cudaMemcpyAsync(x, m->X + first * NF, sizeof(float) * NF * count, cudaMemcpyDeviceToHost, m->stream));
+  if (tmp2) CK(cudaMemcpyAsync(tmp2, m->TM + first, sizeof(float2) * count, cudaMemcpyDeviceToHost, m->stream));
+  if (target) CK(cudaMemcpyAsync(target, m->TG + first, sizeof(float2) * count, cudaMemcpyDeviceToHost, m->stream));
+  CK(cudaStreamSynchronize(m->stream));
+  return EXP_OK;
+  MLP_CATCH(m)
+}
+
+extern "C" exp_status exp_mlp_eval(exp_mlp* m, double* loss) {
+  MLP_TRY
+  if (!m || !loss) throw ExpError{EXP_EINVAL, "null argument"};
+  if (m->n == 0) throw ExpError{EXP_ESTATE, "no training data"};
+  std::vector<int> id(m->n);
+  std::iota(id.begin(), id.end(), 0);
+  CK(cudaMemcpyAsync(m->idx, id.data(), sizeof(int) * m->n, cudaMemcpyHostToDevice, m->stream));
+  CK(cudaMemsetAsync(m->d_loss, 0, sizeof(double), m->stream));
+  grad_batch(m, m->X, m->TM, m->TG, m->idx, 0, m->n);
+  CK(cudaMemcpyAsync(loss, m->d_loss, sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+  CK(cudaStreamSynchronize(m->stream));
   return EXP_OK;
   MLP_CATCH(m)
 }

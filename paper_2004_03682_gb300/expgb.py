@@ -68,6 +68,8 @@ def lib():
     L.exp_init_integrals.argtypes = [P, C.POINTER(C.c_uint64), C.POINTER(C.c_double), C.POINTER(C.c_double)]
     L.exp_ccsd_iterate.argtypes = [P, C.c_int, C.POINTER(IterInfo), C.POINTER(C.c_int)]
     L.exp_energy.argtypes = [P, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    L.exp_instance_state.argtypes = [P, C.c_int, C.POINTER(C.c_int)]
+    L.exp_instance_state.restype = C.c_int
     L.exp_get_amplitudes.argtypes = [P, C.c_int, P, P]
     L.exp_fs_sector_0h1p.argtypes = [P, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                      C.POINTER(C.c_double), C.POINTER(C.c_int)]
@@ -92,6 +94,13 @@ def lib():
     L.exp_mlp_params.argtypes = [P, C.POINTER(C.c_float), C.POINTER(C.c_float)]
     L.exp_mlp_loss_grad.argtypes = [P, C.c_int, C.POINTER(C.c_float), C.POINTER(C.c_double),
                                     C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_float)]
+    L.exp_mlp_num_samples.argtypes = [P]
+    L.exp_mlp_num_samples.restype = C.c_int64
+    L.exp_mlp_eval.argtypes = [P, C.POINTER(C.c_double)]
+    L.exp_mlp_samples.argtypes = [P, C.c_int64, C.c_int64, C.POINTER(C.c_float), C.POINTER(C.c_float),
+                                  C.POINTER(C.c_float)]
+    L.exp_mlp_samples.restype = C.c_int
+    L.exp_mlp_eval.restype = C.c_int
     L.exp_mlp_last_error.argtypes = [P]
     L.exp_mlp_last_error.restype = C.c_char_p
     for name in ("exp_mlp_create", "exp_mlp_add_training_data", "exp_mlp_train", "exp_mlp_apply",
@@ -190,13 +199,13 @@ class Context:
         self._check(self.L.exp_init_integrals(self.h, ps, pm, out.ctypes.data_as(C.POINTER(C.c_double))))
         return out
 
-    def iterate(self, n_iter, raise_notconv=False):
+    def iterate(self, n_iter, raise_notconv=False, raise_numeric=True):
         info = (IterInfo * max(n_iter, 1))()
         for k in range(n_iter):
             info[k].ms = -1.0
         conv = C.c_int(0)
         st = self.L.exp_ccsd_iterate(self.h, int(n_iter), info, C.byref(conv))
-        if st not in (0, 4) or (st == 4 and raise_notconv):
+        if (st not in (0, 4, 5)) or (st == 4 and raise_notconv) or (st == 5 and raise_numeric):
             self._check(st)
         recs = []
         for k in range(n_iter):
@@ -220,6 +229,12 @@ class Context:
             self._check(st)
         H = (heff[0::2] + 1j * heff[1::2]).reshape(na, na)
         return H, er + 1j * ei, nit.value, st
+
+    def state(self, inst=0) -> int:
+        """0 iterating, 1 converged, 2 failed."""
+        v = C.c_int()
+        self._check(self.L.exp_instance_state(self.h, int(inst), C.byref(v)))
+        return v.value
 
     def energy(self, inst=0) -> complex:
         re, im = C.c_double(), C.c_double()
@@ -306,6 +321,25 @@ class Mlp:
 
     def apply(self, ctx):
         self._check(self.L.exp_mlp_apply(self.h, ctx.h))
+
+    @property
+    def n_samples(self):
+        return int(self.L.exp_mlp_num_samples(self.h))
+
+    def samples(self, first=0, count=None):
+        n = self.n_samples - first if count is None else count
+        x = np.zeros((n, 3), np.float32)
+        tm = np.zeros((n, 2), np.float32)
+        tg = np.zeros((n, 2), np.float32)
+        fp = C.POINTER(C.c_float)
+        self._check(self.L.exp_mlp_samples(self.h, int(first), int(n), x.ctypes.data_as(fp), tm.ctypes.data_as(fp),
+                                           tg.ctypes.data_as(fp)))
+        return x, tm[:, 0] + 1j * tm[:, 1], tg[:, 0] + 1j * tg[:, 1]
+
+    def eval(self):
+        v = C.c_double()
+        self._check(self.L.exp_mlp_eval(self.h, C.byref(v)))
+        return v.value
 
     def params(self, set=None):
         get = np.zeros(self.n_params, np.float32)

@@ -19,7 +19,7 @@ def _solve(probs, guess_model=None, max_iter=600, conv_tol=1e-9, precision=expgb
     t0 = time.perf_counter()
     if guess_model is not None:
         guess_model.apply(ctx)
-    recs, conv, _ = ctx.iterate(max_iter)
+    recs, conv, _ = ctx.iterate(max_iter, raise_numeric=False)  # diverging members drop out
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     n = len(probs)
@@ -28,7 +28,8 @@ def _solve(probs, guess_model=None, max_iter=600, conv_tol=1e-9, precision=expgb
     for it, r in enumerate(recs, 1):
         conv_at += [it] * (r["n_converged"] - prev)
         prev = r["n_converged"]
-    energies = np.array([ctx.energy(k) for k in range(n)])
+    states = np.array([ctx.state(k) for k in range(n)])
+    energies = np.array([ctx.energy(k) if states[k] == 1 else complex(np.nan, np.nan) for k in range(n)])
     return ctx, dict(conv_at=conv_at, n_conv=prev, n_iter=len(recs), wall_s=wall, energies=energies)
 
 

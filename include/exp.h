@@ -81,6 +81,9 @@ typedef struct {
   int n_active;            /* (0h,1p) sector: number of active (valence) virtual spinors, 0 = none */
   const int32_t* active_virt; /* [n_active] their indices within the virtual space (config order),
                                  shared by all instances; NULL when n_active = 0 */
+  double level_shift;      /* sigma >= 0: (0h,0p) update t <- t + (RHS - D t)/(D - sigma) (the same
+                              fixed point; smaller steps for strongly coupled problems); 0 = the
+                              plain update t <- RHS/D */
 } exp_config;
 
 /* Create a context: validates the config, builds the symmetry-blocked layouts

@@ -50,6 +50,7 @@ static void check_config(const exp_config* cfg) {
     throw ExpError{EXP_EINVAL, "n_slices must be in 3..6"};
   if (cfg->diis_dim < 0 || cfg->diis_dim > EXP_MAX_DIIS) throw ExpError{EXP_EINVAL, "diis_dim must be in 0..8"};
   if (!(cfg->conv_tol > 0)) throw ExpError{EXP_EINVAL, "conv_tol must be > 0"};
+  if (!(cfg->level_shift >= 0) || !std::isfinite(cfg->level_shift)) throw ExpError{EXP_EINVAL, "level_shift must be >= 0"};
   if (cfg->n_active < 0 || cfg->n_active > cfg->n_virt) throw ExpError{EXP_EINVAL, "n_active out of range"};
   if (cfg->n_active > 0) {
     if (!cfg->active_virt) throw ExpError{EXP_EINVAL, "null active_virt"};

@@ -65,7 +65,8 @@ struct AddOp { __device__ double operator()(double a, double b) const { return a
 __global__ void __launch_bounds__(RED_THREADS) k_update(const cplx* __restrict__ R, const double* __restrict__ D,
                                                         const cplx* __restrict__ T, cplx* __restrict__ Tn,
                                                         cplx* __restrict__ En, int64_t namp, int dim,
-                                                        const int* __restrict__ state, double* __restrict__ part) {
+                                                        const int* __restrict__ state, double* __restrict__ part,
+                                                        double shift) {
   __shared__ double sh[32];
   const int inst = blockIdx.y;
   const int* st = state + inst * 4;
@@ -78,7 +79,9 @@ __global__ void __launch_bounds__(RED_THREADS) k_update(const cplx* __restrict__
       const cplx r = R[off + k];
       const double d = D[off + k];
       const cplx t = T[off + k];
-      const cplx tn = make_double2(r.x / d, r.y / d);
+      // t_new = (RHS - sigma t) / (D - sigma); sigma = 0 gives RHS / D
+      const cplx tn = shift == 0.0 ? make_double2(r.x / d, r.y / d)
+                                   : make_double2((r.x - shift * t.x) / (d - shift), (r.y - shift * t.y) / (d - shift));
       const cplx e = make_double2(tn.x - t.x, tn.y - t.y);
       Tn[soff + k] = tn;
       En[soff + k] = e;
@@ -669,7 +672,7 @@ void ccsd_iteration(Ctx& c) {
   ccsd_rhs(c);
   ccsd_update_step(c, [&](double* part, int nb) {
     k_update<<<dim3(nb, c.ninst), RED_THREADS, 0, c.stream>>>(c.d_R, c.d_D, c.d_T, c.d_diis_t, c.d_diis_e, c.namp,
-                                                              c.cfg.diis_dim, c.d_diis_state, part);
+                                                              c.cfg.diis_dim, c.d_diis_state, part, c.cfg.level_shift);
     KCHECK(c);
   }, true);
 }

@@ -48,13 +48,13 @@ def _cfg(expgb, **over):
                        io.ctypes.data_as(C.POINTER(C.c_int32)), iv.ctypes.data_as(C.POINTER(C.c_int32)),
                        eo.ctypes.data_as(C.POINTER(C.c_double)), ev.ctypes.data_as(C.POINTER(C.c_double)),
                        d["precision"], d["n_slices"], d["diis_dim"], d["conv_tol"], d["max_iter"], d["guess"], 0.0,
-                       d.get("n_active", 0), None)
+                       d.get("n_active", 0), None, d.get("level_shift", 0.0))
     return cfg, keep
 
 
 @pytest.mark.parametrize("bad", [dict(n_occ=5), dict(n_irrep=17), dict(diis_dim=9), dict(conv_tol=0.0),
                                  dict(max_iter=0), dict(precision=7), dict(precision=1, n_slices=2),
-                                 dict(n_inst=0), dict(n_active=2)])
+                                 dict(n_inst=0), dict(n_active=2), dict(level_shift=-1.0)])
 def test_create_rejects_bad_config_on_host(lib, bad):
     from paper_2004_03682_gb300 import expgb
     cfg, keep = _cfg(expgb, **bad)

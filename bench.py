@@ -153,8 +153,10 @@ def run_reference(args):
 # Complex MACs of one CCSD iteration as planned by the library (exp_work_per_iteration),
 # for the reference arm, which runs without the library: o=10 v=40 C1 and o=40 v=200 Z8
 # (seed 2001).  The GPU arm measures both live.
-C1_MACS = 4.8e8
-C2_MACS = 3.2e11
+C1_MACS = 5.264e8
+C2_MACS = 8.948e10
+# ladder k_emu_gemm<5> DRAM read + write per launch (see the bench roofline note)
+LADDER_TRAFFIC_BYTES = {"ccsd_z8_o24_v120": 0.742e9, "ccsd_z8_o40_v200": 5.63e9}
 
 
 def main():
@@ -238,8 +240,11 @@ def main():
         # executed BF16 tensor flops: 4 real MACs per complex MAC (real embedding) x slice pairs x 2
         achieved = kmacs * 4 * pairs * 2 / (kms * 1e-3) / 1e12
         eff = kmacs * 8 / (kms * 1e-3) / 1e12
+        # DRAM bytes per ladder launch: ncu capture at o=24 v=120 (0.742 GB = 1.08 x its slice bytes)
+        # scaled by the slice bytes of this workload (profiles/k_emu_gemm_ccsd_z8_o24_v120.md)
+        traffic = LADDER_TRAFFIC_BYTES.get(WORKLOAD["name"]) if args.slices == 5 and site == "R2pp" else None
         roof = {"bound": "tensor", "kernel": f"k_emu_gemm<{args.slices}> ({site})", "achieved": achieved,
-                "peak": pk["bf16"], "unit": "TFLOP/s", "frac": achieved / pk["bf16"], "traffic": None,
+                "peak": pk["bf16"], "unit": "TFLOP/s", "frac": achieved / pk["bf16"], "traffic": traffic,
                 "peak_src": f"{pk['src']} bf16 dense (burst)",
                 "effective_complex_fp64_tflops": eff}
     e_final = ctx.energy(0)

@@ -469,7 +469,11 @@ void einsum(Ctx& c, const std::string& site, cplx alpha, Operand A, Operand B, T
   }
   // execute
   const bool prof = c.profile;
-  if (prof) CK(cudaEventRecord(c.pev0, c.stream));
+  cudaEvent_t pe[4] = {nullptr, nullptr, nullptr, nullptr};
+  if (prof) {
+    for (auto& e : pe) CK(cudaEventCreate(&e));
+    CK(cudaEventRecord(c.pev0, c.stream));
+  }
   if (P->permA) {
     cplx one = make_double2(1, 0);
     launch_permute(c, P->pA, P->A2.d, A.t->d, P->A2.is, A.t->is, &one, false, false);
@@ -481,19 +485,27 @@ void einsum(Ctx& c, const std::string& site, cplx alpha, Operand A, Operand B, T
   Tensor* Cg = P->permC ? &P->C2 : &C;
   P->gemm_out = Cg->d;
   P->gemm_out_is = Cg->is;
+  if (prof) CK(cudaEventRecord(pe[0], c.stream));
   if (P->emulate)
     emu_run(c, P->emu, P->g, P->A->d, P->B->d, Cg->d, P->A->is, P->B->is, Cg->is, alpha,
             P->gemm_beta);
   else
     launch_gemm_fp64(c, P->g, P->A->d, P->B->d, Cg->d, P->A->is, P->B->is, Cg->is, alpha,
                      P->gemm_beta);
+  if (prof) CK(cudaEventRecord(pe[1], c.stream));
   if (P->permC)
     launch_permute(c, P->pC, C.d, P->C2.d, C.is, P->C2.is, P->cterms, accumulate, false);
   if (prof) {
     CK(cudaEventRecord(c.pev1, c.stream));
     CK(cudaEventSynchronize(c.pev1));
-    float ms = 0.f;
+    float ms = 0.f, m_in = 0.f, m_g = 0.f, m_out = 0.f;
     CK(cudaEventElapsedTime(&ms, c.pev0, c.pev1));
+    CK(cudaEventElapsedTime(&m_in, c.pev0, pe[0]));
+    CK(cudaEventElapsedTime(&m_g, pe[0], pe[1]));
+    CK(cudaEventElapsedTime(&m_out, pe[1], c.pev1));
+    for (auto& e : pe)
+      if (e) cudaEventDestroy(e);
+    fprintf(stderr, "[exp_phase] %-8s in %7.3f  gemm %7.3f  out %7.3f ms\n", site.c_str(), m_in, m_g, m_out);
     int64_t M = 0, N = 0, K = 0;
     for (auto& q : P->g.h_probs) { M = std::max<int64_t>(M, q.M); N = std::max<int64_t>(N, q.N); K = std::max<int64_t>(K, q.K); }
     fprintf(stderr, "[exp_profile] %-8s %9.3f ms  %10.3g cMAC  %7.1f GF/s  probs=%d maxM=%lld maxN=%lld maxK=%lld perm=%d%d%d emu=%d\n",

@@ -330,6 +330,18 @@ __global__ void __launch_bounds__(THREADS, 1)
 // max |Re|, |Im| < 2^E (0 for an all-zero row).
 __device__ __forceinline__ int exp_of(double m) { return m > 0.0 ? ilogb(m) + 1 : EXP_ZERO; }
 
+// |x| as an order-preserving unsigned integer (IEEE bits without the sign); the
+// exponent E with |x| < 2^E follows from the biased exponent field of the max.
+__device__ __forceinline__ unsigned long long abits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+}
+__device__ __forceinline__ int exp_of_bits(unsigned long long m) {
+  const int e = int(m >> 52);
+  if (m == 0) return EXP_ZERO;
+  if (e == 0) return exp_of(__longlong_as_double((long long)m));  // subnormal
+  return e - 1022;  // |x| in [2^(e-1023), 2^(e-1022))
+}
+
 // Row exponents: CTA = (one row, a K range of ROW_KR); block max -> atomicMax
 // (max is order-independent, so the result is deterministic).  Exponent arrays
 // start at EXP_ZERO (all-zero row or column).
@@ -337,7 +349,7 @@ __device__ __forceinline__ int exp_of(double m) { return m > 0.0 ? ilogb(m) + 1 
 __global__ void __launch_bounds__(256) k_row_exp(const EmuProb* __restrict__ probs, int nprobs,
                                                  const cplx* __restrict__ A, int64_t a_is, int* __restrict__ ex,
                                                  int64_t ex_is) {
-  __shared__ double sh[8];
+  __shared__ unsigned long long sh[8];
   const int inst = blockIdx.y;
   int t = blockIdx.x, pi = 0;
   // work items: per problem M * ceil(K / ROW_KR)
@@ -352,15 +364,17 @@ __global__ void __launch_bounds__(256) k_row_exp(const EmuProb* __restrict__ pro
   const int r = t / nk, kc = t % nk;
   if (r >= P.M) return;
   const cplx* a = A + inst * a_is + P.a_src + int64_t(r) * P.K;
-  double m = 0.0;
-  for (int k = kc * ROW_KR + threadIdx.x; k < min(P.K, (kc + 1) * ROW_KR); k += 256)
-    m = fmax(m, fmax(fabs(a[k].x), fabs(a[k].y)));
-  for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  unsigned long long m = 0;
+  for (int k = kc * ROW_KR + threadIdx.x; k < min(P.K, (kc + 1) * ROW_KR); k += 256) {
+    const cplx v = a[k];
+    m = max(m, max(abits(v.x), abits(v.y)));
+  }
+  for (int o = 16; o; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
   if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
   __syncthreads();
   if (threadIdx.x == 0) {
-    for (int w = 1; w < 8; ++w) m = fmax(m, sh[w]);
-    atomicMax(&ex[inst * ex_is + P.a_ex + r], exp_of(m));
+    for (int w = 1; w < 8; ++w) m = max(m, sh[w]);
+    atomicMax(&ex[inst * ex_is + P.a_ex + r], exp_of_bits(m));
   }
 }
 
@@ -368,7 +382,7 @@ __global__ void __launch_bounds__(256) k_row_exp(const EmuProb* __restrict__ pro
 __global__ void __launch_bounds__(256) k_col_exp(const EmuProb* __restrict__ probs, int nprobs,
                                                  const cplx* __restrict__ B, int64_t b_is, int* __restrict__ ex,
                                                  int64_t ex_is) {
-  __shared__ double sh[8][33];
+  __shared__ unsigned long long sh[8][33];
   const int inst = blockIdx.y;
   int t = blockIdx.x, pi = 0;
   for (;; ++pi) {
@@ -381,19 +395,19 @@ __global__ void __launch_bounds__(256) k_col_exp(const EmuProb* __restrict__ pro
   const int ct = t / nk, kc = t % nk;
   const int cl = threadIdx.x & 31, rl = threadIdx.x >> 5;
   const int j = ct * 32 + cl;
-  double m = 0.0;
+  unsigned long long m = 0;
   if (j < P.N) {
     const cplx* b = B + inst * b_is + P.b_src + j;
     for (int k = kc * 256 + rl; k < min(P.K, (kc + 1) * 256); k += 8) {
       const cplx v = b[int64_t(k) * P.N];
-      m = fmax(m, fmax(fabs(v.x), fabs(v.y)));
+      m = max(m, max(abits(v.x), abits(v.y)));
     }
   }
   sh[rl][cl] = m;
   __syncthreads();
   if (rl == 0 && j < P.N) {
-    for (int w = 1; w < 8; ++w) m = fmax(m, sh[w][cl]);
-    atomicMax(&ex[inst * ex_is + P.b_ex + j], exp_of(m));
+    for (int w = 1; w < 8; ++w) m = max(m, sh[w][cl]);
+    atomicMax(&ex[inst * ex_is + P.b_ex + j], exp_of_bits(m));
   }
 }
 
@@ -401,31 +415,55 @@ __global__ void k_fill_int(int* __restrict__ p, int64_t n, int v) {
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) p[i] = v;
 }
 
-// Slices of 8 consecutive values, written as one 16-byte vector per slice (a
-// core-matrix row).  x in (-1, 1): a_1 = rint(x 2^B), r <- x 2^B - a_1,
-// a_2 = rint(r 2^B), ...  (exact in FP64; rint is odd, so slices of -x are -slices of x).
 __device__ __forceinline__ uint32_t pack2(__nv_bfloat16 a, __nv_bfloat16 b) {
   return uint32_t(__bfloat16_as_ushort(a)) | (uint32_t(__bfloat16_as_ushort(b)) << 16);
 }
 
+// x 2^sh rounded to the nearest integer (|x 2^sh| < 2^62), from the IEEE bits with
+// integer operations only (GB300's FP64 pipe is the slowest unit on the chip).
+__device__ __forceinline__ long long fixed_of(double x, int sh) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = int((b >> 52) & 0x7FF);
+  if (e == 0) return 0;  // zero or subnormal: below every slice
+  const long long mant = (long long)((b & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull);
+  const int k = e - 1075 + sh;  // x 2^sh = mant 2^k
+  long long X;
+  if (k >= 0) X = mant << k;
+  else if (k > -64) X = (mant + (1ll << (-k - 1))) >> (-k);
+  else X = 0;
+  return (b >> 63) ? -X : X;
+}
+
+// Balanced base-2^BETA digits of X = rint(x 2^(BETA S)), |x| < 1: the lower S-1
+// digits in [-2^(BETA-1), 2^(BETA-1)), the leading one in [-2^BETA, 2^BETA];
+// x = sum_s a_s 2^(-BETA s) + r with |r| <= 2^(-BETA S - 1).  Each digit is exact
+// in BF16 (built from the exact float of a small integer).
+__device__ __forceinline__ uint16_t bf16_of_int(int v) {
+  return uint16_t(__float_as_uint(float(v)) >> 16);  // exact: |v| <= 256 needs 9 bits
+}
 template <int S>
-__device__ __forceinline__ void slice8(const double (&x)[8], uint4 (&out)[S], bool neg_copy, uint4 (&outn)[S]) {
-  double r[8];
+__device__ __forceinline__ void digits(long long X, uint16_t (&h)[S]) {
 #pragma unroll
-  for (int u = 0; u < 8; ++u) r[u] = x[u];
+  for (int s = S - 1; s >= 1; --s) {
+    const int d = int(((X + (1 << (BETA - 1))) & ((1 << BETA) - 1))) - (1 << (BETA - 1));
+    h[s] = bf16_of_int(d);
+    X = (X - d) >> BETA;
+  }
+  h[0] = bf16_of_int(int(X));
+}
+
+template <int S>
+__device__ __forceinline__ void slice8(const double (&x)[8], int sh, uint4 (&out)[S], bool neg_copy,
+                                       uint4 (&outn)[S]) {
+  uint16_t h[8][S];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) digits<S>(fixed_of(x[u], sh + BETA * S), h[u]);
 #pragma unroll
   for (int s = 0; s < S; ++s) {
-    __nv_bfloat16 h[8], hn[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      r[u] *= double(1 << BETA);
-      const double a = rint(r[u]);
-      r[u] -= a;
-      h[u] = __float2bfloat16_rn(float(a));
-      hn[u] = __float2bfloat16_rn(float(-a));
-    }
-    out[s] = make_uint4(pack2(h[0], h[1]), pack2(h[2], h[3]), pack2(h[4], h[5]), pack2(h[6], h[7]));
-    if (neg_copy) outn[s] = make_uint4(pack2(hn[0], hn[1]), pack2(hn[2], hn[3]), pack2(hn[4], hn[5]), pack2(hn[6], hn[7]));
+    out[s] = make_uint4(uint32_t(h[0][s]) | (uint32_t(h[1][s]) << 16), uint32_t(h[2][s]) | (uint32_t(h[3][s]) << 16),
+                        uint32_t(h[4][s]) | (uint32_t(h[5][s]) << 16), uint32_t(h[6][s]) | (uint32_t(h[7][s]) << 16));
+    if (neg_copy) outn[s] = make_uint4(out[s].x ^ 0x80008000u, out[s].y ^ 0x80008000u, out[s].z ^ 0x80008000u,
+                                       out[s].w ^ 0x80008000u);  // -a: flip the BF16 sign bits
   }
 }
 
@@ -460,13 +498,13 @@ __global__ void __launch_bounds__(256) k_split_a(const EmuProb* __restrict__ pro
       xi[q] = 0.0;
       if (gi < P.M && k0 + q < P.K) {
         const cplx v = a[int64_t(gi) * P.K + k0 + q];
-        xr[q] = ldexp(v.x, sh);
-        xi[q] = ldexp(v.y, sh);
+        xr[q] = v.x;
+        xi[q] = v.y;
       }
     }
     uint4 sr[S], si[S], dummy[S];
-    slice8<S>(xr, sr, false, dummy);
-    slice8<S>(xi, si, false, dummy);
+    slice8<S>(xr, sh, sr, false, dummy);
+    slice8<S>(xi, sh, si, false, dummy);
     const int off = core_off(r, g * 8);
 #pragma unroll
     for (int s2 = 0; s2 < S; ++s2) {
@@ -508,13 +546,13 @@ __global__ void __launch_bounds__(128) k_split_b(const EmuProb* __restrict__ pro
       xi[q] = 0.0;
       if (gj < P.N && k0 + q < P.K) {
         const cplx v = b[int64_t(k0 + q) * P.N + gj];
-        xr[q] = ldexp(v.x, sh);
-        xi[q] = ldexp(v.y, sh);
+        xr[q] = v.x;
+        xi[q] = v.y;
       }
     }
     uint4 sr[S], si[S], sin_[S], dummy[S];
-    slice8<S>(xr, sr, false, dummy);
-    slice8<S>(xi, si, true, sin_);
+    slice8<S>(xr, sh, sr, false, dummy);
+    slice8<S>(xi, sh, si, true, sin_);
     const int off0 = core_off(2 * jl, g * 8), off1 = core_off(2 * jl + 1, g * 8);
 #pragma unroll
     for (int s2 = 0; s2 < S; ++s2) {
@@ -590,11 +628,12 @@ struct EmuState {
 bool emu_wanted(Ctx& c, const GemmPlan& g, const std::string&) {
   if (c.cfg.precision != EXP_EMU_BF16) return false;
   if (c.cfg.emu_min_macs > 0) return double(g.flops_mac) >= c.cfg.emu_min_macs;
-  // below ~8e6 complex MACs, or with a contraction length under 128, the split
-  // passes cost more than the FP64 kernel
+  // below ~8e6 complex MACs the slicing passes cost more than the FP64 kernel;
+  // contraction lengths from 64 up are faster on the tensor cores than at GB300's
+  // FP64 rate, shorter ones (K = o/G ~ 14) are not (per-tile overhead dominates)
   int maxK = 0;
   for (auto& p : g.h_probs) maxK = std::max(maxK, p.K);
-  return g.flops_mac >= int64_t(1) << 23 && maxK >= 128;
+  return g.flops_mac >= int64_t(1) << 23 && maxK >= 64;
 }
 
 template <int S>

@@ -258,6 +258,8 @@ static PermPlan make_perm_plan(Ctx& c, const Layout& D, const char* dl, const La
       for (int d = 0; d < 4; ++d) T.src_st[t][d] = 0;
       for (int k = 0; k < r; ++k) T.src_st[t][pad + pos[t][k]] = s.st[k];
     }
+    if (T.count >= (int64_t(1) << 31)) throw ExpError{EXP_EINVAL, "permute sub-block above 2^31 elements"};
+    for (int d = 0; d < 4; ++d) udiv_magic(uint32_t(T.n[d]), T.mg[d], T.ml[d]);
     add_chunks(chunks, int(tasks.size()), T.count);
     tasks.push_back(T);
   }
@@ -349,6 +351,18 @@ GemmPlan make_gemm_plan(Ctx& c, const Layout& A, const Layout& B, const Layout& 
     g.flops_mac += M * N * K;
     g.h_probs.push_back(p);
   }
+  // small products and matrix-vector ones: one warp per output element
+  if (g.flops_mac < (int64_t(1) << 22) || maxN <= 2) {
+    int64_t o = 0;
+    for (auto& p : g.h_probs) { p.ws = o; o += int64_t(p.M) * p.N; }
+    g.dot_outputs = o;
+    g.n_probs = int(g.h_probs.size());
+    if (g.n_probs) {
+      g.d_probs = (GemmProb*)c.dalloc(g.h_probs.size() * sizeof(GemmProb));
+      upload(c, g.d_probs, g.h_probs.data(), g.h_probs.size() * sizeof(GemmProb));
+    }
+    return g;
+  }
   // split K when the output tiles cannot fill the GPU (long-K, small-MN blocks)
   const int64_t want = 8LL * std::max(c.sm_count, 1);
   const int64_t have = tiles_mn * c.ninst;
@@ -408,6 +422,19 @@ static const Tensor* prepare_operand(Ctx& c, const std::string& site, const Oper
   return &scratch;
 }
 
+// product of the full space sizes of an operand's labels in F
+static double free_extent(const Ctx& c, const Operand& op, const std::string& F) {
+  double d = 1.0;
+  for (char x : F) {
+    const char* p = strchr(op.labels, x);
+    if (!p) continue;
+    const int k = int(p - op.labels);
+    const int sp = op.v ? op.v->sp[k] : op.t->L.sp[k];
+    d *= double(c.spaces[sp].n);
+  }
+  return d;
+}
+
 void einsum(Ctx& c, const std::string& site, cplx alpha, Operand A, Operand B, Tensor& C,
             const char* cl, bool accumulate, std::vector<std::pair<double, std::string>> terms) {
   auto it = c.plans.find(site);
@@ -415,15 +442,33 @@ void einsum(Ctx& c, const std::string& site, cplx alpha, Operand A, Operand B, T
   if (it == c.plans.end()) {
     P = new EinsumPlan();
     c.plans[site].reset(P);
-    const std::string al = A.labels, bl = B.labels, clab = cl;
+    const std::string clab = cl;
     std::string K, FA, FB;
-    for (char x : al)
-      if (bl.find(x) != std::string::npos && clab.find(x) == std::string::npos) K += x;
-    for (char x : al)
-      if (K.find(x) == std::string::npos) FA += x;
-    for (char x : bl)
-      if (K.find(x) == std::string::npos) FB += x;
+    auto split_labels = [&]() {
+      const std::string al = A.labels, bl = B.labels;
+      K.clear();
+      FA.clear();
+      FB.clear();
+      for (char x : al)
+        if (bl.find(x) != std::string::npos && clab.find(x) == std::string::npos) K += x;
+      for (char x : al)
+        if (K.find(x) == std::string::npos) FA += x;
+      for (char x : bl)
+        if (K.find(x) == std::string::npos) FB += x;
+    };
+    split_labels();
     if (FA.size() + FB.size() != clab.size()) throw ExpError{EXP_EINVAL, "einsum labels: " + site};
+    // The emulated GEMM slices its A operand into half the bytes of B (B'' holds
+    // every element twice), so when the output goes through a permute anyway the
+    // operand with the larger free extent takes the A role (C^T = B^T A^T).
+    if (c.cfg.precision == EXP_EMU_BF16) {
+      const bool identity0 = terms.empty() && FA + FB == clab && C.L.nrow == int(FA.size());
+      if (!identity0 && free_extent(c, B, FB) > 2.0 * free_extent(c, A, FA)) {
+        std::swap(A, B);
+        split_labels();
+        P->swapped = true;
+      }
+    }
     // contracted labels must meet with opposite signs
     const std::string ordA = FA + K, ordB = K + FB;
     const Tensor* Ap = prepare_operand(c, site, A, ordA, int(FA.size()), P->A2, P->pA, P->permA);
@@ -466,6 +511,7 @@ void einsum(Ctx& c, const std::string& site, cplx alpha, Operand A, Operand B, T
     if (P->emulate) P->emu = emu_plan(c, P->g, P->A, P->B, A.v != nullptr, B.v != nullptr);
   } else {
     P = it->second.get();
+    if (P->swapped) std::swap(A, B);
   }
   // execute
   const bool prof = c.profile;

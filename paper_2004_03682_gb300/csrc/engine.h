@@ -64,8 +64,19 @@ struct PermTask {
   int64_t src[EXP_MAX_TERMS];
   int64_t src_st[EXP_MAX_TERMS][4];
   int32_t n[4];
-  int64_t count;
+  int64_t count;     // elements, < 2^31
+  uint32_t mg[4];    // division by n[d] as a multiply-high: see udiv_magic
+  uint32_t ml[4];
 };
+
+// q = floor(x / d) for 32-bit x as (t + ((x - t) >> 1)) >> (l - 1), t = umulhi(m, x),
+// with l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1 (l = 0: q = x); the
+// round-up method of Granlund and Montgomery (PLDI 1994).
+inline void udiv_magic(uint32_t d, uint32_t& m, uint32_t& l) {
+  l = 0;
+  while ((uint64_t(1) << l) < d) ++l;
+  m = uint32_t(((uint64_t(1) << 32) * ((uint64_t(1) << l) - d)) / d + 1);
+}
 
 struct ChunkRef {
   int32_t task;
@@ -132,6 +143,7 @@ struct GemmPlan {
   int64_t ws_is = 0;
   int64_t red_elems = 0;     // output elements of split problems (per instance)
   int64_t flops_mac = 0;  // complex MACs per instance
+  int64_t dot_outputs = 0;  // > 0: run as one warp per output element (k_gemm_dot), this many outputs
   std::vector<GemmProb> h_probs;
 };
 
@@ -151,6 +163,7 @@ struct EinsumPlan {
   cplx* gemm_out = nullptr;  // GEMM output when it writes the destination directly
   int64_t gemm_out_is = 0;
   bool emulate = false;
+  bool swapped = false;  // operands exchanged at planning (C^T = B^T A^T); every call swaps them too
   EmuPlan* emu = nullptr;
   size_t scratch_bytes = 0;
 };

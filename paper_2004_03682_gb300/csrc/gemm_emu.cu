@@ -24,6 +24,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <string>
 
@@ -36,8 +37,14 @@ constexpr int KB = 32;         // real K per smem k-block (4 core matrices of 8 
 constexpr int BETA = 7;        // bits per slice
 constexpr int KC_BLOCKS = 16;  // k-blocks per exact chunk: KC = 512 real terms
 constexpr int STAGES = 3;
-constexpr int THREADS = 192;   // 6 warps
+constexpr int THREADS = 320;   // 10 warps: producer, MMA issuer, 8 epilogue warps
+constexpr int EPI_WARPS = 8;
 #define EXP_ZERO (-1100)       // exponent of an all-zero row / column (any x 2^-EXP_ZERO stays 0)
+// alpha encodings for the GEMM epilogue: alpha = +2^k -> k + ALPHA_POS_BIAS,
+// alpha = -2^k -> -(k + ALPHA_NEG_BIAS), anything else -> ALPHA_GENERAL
+#define ALPHA_GENERAL 0
+#define ALPHA_POS_BIAS 64
+#define ALPHA_NEG_BIAS 64
 
 template <int S>
 struct Shape {
@@ -59,9 +66,14 @@ struct EmuProb {
   int64_t a_sl, b_sl;           // bf16 offsets of the slice tiles (per instance)
   int64_t a_ex, b_ex;           // offsets of the exponent arrays (per instance)
   int64_t ws;                   // split-K partials offset (complex, per instance)
-  int32_t M, N, K, Kp;          // Kp = 2K padded to KB
-  int32_t tiles_m, tiles_n, tile0, pad;
-  int32_t ksplit, kcb, pad2, pad3;  // K splits and k-blocks per split (multiple of KC_BLOCKS)
+  int32_t M, N, K, Kp;          // Kp = 2 Kh, Kh = K rounded up to 16
+  int32_t tiles_m, tiles_n, tile0, bt0;  // tile0 / at0 / bt0: first GEMM / split-A / split-B item
+  int32_t ksplit, kcb, arows, brows;     // K splits, k-blocks per split (multiple of KC_BLOCKS),
+                                         // rows stored per A / B slice tile (a problem with a
+                                         // single row / column tile keeps only its 8-row groups
+                                         // in use: a prefix of the canonical tile)
+  int32_t at0, pad0;
+  int64_t red0;  // first output of this problem in the split-K reduction order
 };
 
 // ---------------------------------------------------------------------------
@@ -142,6 +154,11 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
         "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
 }
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* r) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+}
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // offset (in elements) of element (r, k) inside a tile of `rows` x KB, core-matrix order
@@ -149,12 +166,65 @@ __device__ __forceinline__ int core_off(int r, int k) { return ((r >> 3) * (KB /
 
 // ---------------------------------------------------------------------------
 // GEMM kernel
+// R 2^e as a double, R rounded to 53 bits (nearest, ties to even) with integer
+// operations; the rare results outside the normal range take the FP64 route.
+// Same value as ldexp(double(R), e).
+__device__ __forceinline__ double scaled_i64(long long R, int e) {
+  if (R == 0) return 0.0;
+  const unsigned long long sgn = R < 0 ? (1ull << 63) : 0ull;
+  unsigned long long m = R < 0 ? 0ull - (unsigned long long)R : (unsigned long long)R;
+  const int lz = __clzll((long long)m);
+  m <<= lz;  // leading one at bit 63
+  unsigned long long mant = m >> 11;
+  const unsigned long long rem = m & 0x7FFull;
+  if (rem > 0x400ull || (rem == 0x400ull && (mant & 1ull))) ++mant;
+  int ex = 63 - lz + e;  // |R| 2^e = (mant / 2^52) 2^ex
+  if (mant >> 53) { mant >>= 1; ++ex; }
+  const int be = ex + 1023;
+  if (be <= 0 || be >= 2047) return ldexp(double(R), e);
+  return __longlong_as_double((long long)(sgn | (unsigned long long)(be) << 52 | (mant & 0xFFFFFFFFFFFFFull)));
+}
+
+// K half of the real embedding (each half padded to 16) and the number of
+// 32-wide k ranges a half spans (the split kernels' CTA count per tile)
+__host__ __device__ __forceinline__ int kh_of(const EmuProb& P) { return P.Kp / 2; }
+__host__ __device__ __forceinline__ int nkh_of(const EmuProb& P) { return (P.Kp / 2 + KB - 1) / KB; }
+
+// One work item of the persistent GEMM: (instance, K split, row tile, column tile).
+struct EmuWork {
+  int pi, inst, ks, mt, nt, kb0, nkb, nkb_all;
+};
+__device__ __forceinline__ EmuWork emu_work(const EmuProb* __restrict__ probs, int nprobs, int n_tiles, int w) {
+  EmuWork W;
+  W.inst = w / n_tiles;
+  const int tile = w - W.inst * n_tiles;
+  int pi = 0;
+  while (pi + 1 < nprobs && probs[pi + 1].tile0 <= tile) ++pi;
+  const EmuProb& P = probs[pi];
+  W.pi = pi;
+  int lt = tile - P.tile0;
+  const int tmn = P.tiles_m * P.tiles_n;
+  W.ks = lt / tmn;
+  lt -= W.ks * tmn;
+  W.mt = lt / P.tiles_n;
+  W.nt = lt % P.tiles_n;
+  W.nkb_all = P.Kp / KB;
+  W.kb0 = W.ks * P.kcb;
+  W.nkb = min(W.nkb_all, W.kb0 + P.kcb) - W.kb0;
+  return W;
+}
+
+// Persistent: each CTA walks the work items blockIdx.x, blockIdx.x + gridDim.x, ...
+// The stage ring and the two TMEM accumulator buffers run on across items, so
+// the epilogue of one tile overlaps the MMAs of the next and the producer
+// prefetches across tile boundaries.
 template <int S>
 __global__ void __launch_bounds__(THREADS, 1)
-    k_emu_gemm(const EmuProb* __restrict__ probs, int nprobs, const __nv_bfloat16* __restrict__ Asl,
-               const __nv_bfloat16* __restrict__ Bsl, const int* __restrict__ Aex, const int* __restrict__ Bex,
-               cplx* __restrict__ C, int64_t asl_is, int64_t bsl_is, int64_t aex_is, int64_t bex_is, int64_t c_is,
-               cplx alpha, int beta, int* __restrict__ gerr, cplx* __restrict__ ws, int64_t ws_is) {
+    k_emu_gemm(const EmuProb* __restrict__ probs, int nprobs, int n_tiles, int n_work,
+               const __nv_bfloat16* __restrict__ Asl, const __nv_bfloat16* __restrict__ Bsl,
+               const int* __restrict__ Aex, const int* __restrict__ Bex, cplx* __restrict__ C, int64_t asl_is,
+               int64_t bsl_is, int64_t aex_is, int64_t bex_is, int64_t c_is, cplx alpha, int alpha_e, int beta,
+               int* __restrict__ gerr, cplx* __restrict__ ws, int64_t ws_is) {
   using SH = Shape<S>;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)((uintptr_t(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -167,23 +237,10 @@ __global__ void __launch_bounds__(THREADS, 1)
   volatile int* abort = (volatile int*)(tslot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int tile = blockIdx.x, inst = blockIdx.y;
-  int pi = 0;
-  while (pi + 1 < nprobs && probs[pi + 1].tile0 <= tile) ++pi;
-  const EmuProb P = probs[pi];
-  int lt = tile - P.tile0;  // tile -> (K split, row tile, column tile)
-  const int tmn = P.tiles_m * P.tiles_n;
-  const int ks = lt / tmn;
-  lt -= ks * tmn;
-  const int mt = lt / P.tiles_n, nt = lt % P.tiles_n;
-  const int nkb_all = P.Kp / KB;
-  const int kb0 = ks * P.kcb;
-  const int nkb = min(nkb_all, kb0 + P.kcb) - kb0;  // k-blocks of this split
-  const int nchunks = (nkb + KC_BLOCKS - 1) / KC_BLOCKS;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
-    for (int b = 0; b < 2; ++b) { mbar_init(&accf[b], 1); mbar_init(&acce[b], 4); }
+    for (int b = 0; b < 2; ++b) { mbar_init(&accf[b], 1); mbar_init(&acce[b], EPI_WARPS); }
     mbar_init(drain, 1);
     *abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -198,25 +255,42 @@ __global__ void __launch_bounds__(THREADS, 1)
   fence_after();
   const uint32_t tmem = *tslot;
 
-  const __nv_bfloat16* Ab = Asl + inst * asl_is + P.a_sl + (int64_t(mt) * nkb_all + kb0) * (S * SH::A_TILE);
-  const __nv_bfloat16* Bb = Bsl + inst * bsl_is + P.b_sl + (int64_t(nt) * nkb_all + kb0) * (S * SH::B_TILE);
-
   if (warp == 0) {
     // ---- producer: 1-D TMA bulk copies of the pre-tiled slice tiles
     if (lane == 0) {
-      int kb = 0;
-      for (; kb < nkb; ++kb) {
-        const int st = kb % STAGES;
-        if (kb >= STAGES && !mbar_wait(&empty[st], ((kb / STAGES) & 1) ^ 1, abort, gerr)) break;
-        uint8_t* sA = smem + st * SH::STAGE;
-        uint8_t* sB = sA + SH::A_STAGE;
-        mbar_expect_tx(&full[st], SH::STAGE);
-        bulk_g2s(sA, Ab + int64_t(kb) * S * SH::A_TILE, SH::A_STAGE, &full[st]);
-        bulk_g2s(sB, Bb + int64_t(kb) * S * SH::B_TILE, SH::B_STAGE, &full[st]);
+      uint32_t g = 0;  // k-blocks issued by this CTA
+      bool stop = false;
+      for (int w = blockIdx.x; w < n_work && !stop; w += gridDim.x) {
+        const EmuWork W = emu_work(probs, nprobs, n_tiles, w);
+        const EmuProb& P = probs[W.pi];
+        const int at = P.arows * KB, bt = P.brows * KB;  // stored slice tile sizes (elements)
+        const __nv_bfloat16* Ab = Asl + W.inst * asl_is + P.a_sl + (int64_t(W.mt) * W.nkb_all + W.kb0) * (S * at);
+        const __nv_bfloat16* Bb = Bsl + W.inst * bsl_is + P.b_sl + (int64_t(W.nt) * W.nkb_all + W.kb0) * (S * bt);
+        for (int kb = 0; kb < W.nkb; ++kb, ++g) {
+          const int st = g % STAGES;
+          if (g >= STAGES && !mbar_wait(&empty[st], ((g / STAGES) & 1) ^ 1, abort, gerr)) { stop = true; break; }
+          uint8_t* sA = smem + st * SH::STAGE;
+          uint8_t* sB = sA + SH::A_STAGE;
+          mbar_expect_tx(&full[st], uint32_t(S * (at + bt) * 2));
+          // rows past the stored prefix keep stale data: they only feed output rows /
+          // columns beyond M / N, which the epilogue never stores
+          if (P.arows == BM) {
+            bulk_g2s(sA, Ab + int64_t(kb) * S * at, SH::A_STAGE, &full[st]);
+          } else {
+            for (int s2 = 0; s2 < S; ++s2)
+              bulk_g2s(sA + s2 * SH::A_TILE * 2, Ab + (int64_t(kb) * S + s2) * at, at * 2, &full[st]);
+          }
+          if (P.brows == SH::BN) {
+            bulk_g2s(sB, Bb + int64_t(kb) * S * bt, SH::B_STAGE, &full[st]);
+          } else {
+            for (int s2 = 0; s2 < S; ++s2)
+              bulk_g2s(sB + s2 * SH::B_TILE * 2, Bb + (int64_t(kb) * S + s2) * bt, bt * 2, &full[st]);
+          }
+        }
       }
       if (*abort) {
         // let the copies already issued land before the CTA exits
-        for (int k = max(0, kb - STAGES); k < kb; ++k) {
+        for (uint32_t k = g > STAGES ? g - STAGES : 0; k < g; ++k) {
           volatile int dummy = 0;
           mbar_wait(&full[k % STAGES], (k / STAGES) & 1, &dummy, gerr);
         }
@@ -225,85 +299,118 @@ __global__ void __launch_bounds__(THREADS, 1)
   } else if (warp == 1) {
     // ---- MMA issuer
     if (lane == 0) {
-      for (int kb = 0; kb < nkb; ++kb) {
-        const int st = kb % STAGES;
-        const int ch = kb / KC_BLOCKS, buf = ch & 1;
-        const bool first = (kb % KC_BLOCKS) == 0;
-        if (first && ch >= 2) {
-          if (!mbar_wait(&acce[buf], ((ch >> 1) - 1) & 1, abort, gerr)) break;
+      uint32_t g = 0, gc = 0;  // k-blocks consumed, accumulator chunks started
+      bool stop = false;
+      for (int w = blockIdx.x; w < n_work && !stop; w += gridDim.x) {
+        const EmuWork W = emu_work(probs, nprobs, n_tiles, w);
+        for (int kb = 0; kb < W.nkb; ++kb, ++g) {
+          const int st = g % STAGES;
+          const bool first = (kb % KC_BLOCKS) == 0;
+          const int buf = gc & 1;
+          if (first && gc >= 2) {
+            if (!mbar_wait(&acce[buf], ((gc >> 1) - 1) & 1, abort, gerr)) { stop = true; break; }
+            fence_after();
+          }
+          if (!mbar_wait(&full[st], (g / STAGES) & 1, abort, gerr)) { stop = true; break; }
           fence_after();
-        }
-        if (!mbar_wait(&full[st], (kb / STAGES) & 1, abort, gerr)) break;
-        fence_after();
-        const uint32_t aA = su32(smem + st * SH::STAGE);
-        const uint32_t aB = aA + SH::A_STAGE;
+          const uint32_t aA = su32(smem + st * SH::STAGE);
+          const uint32_t aB = aA + SH::A_STAGE;
 #pragma unroll
-        for (int s = 0; s < S; ++s) {
-          const uint32_t id = idesc_bf16((S - s) * SH::BN);
-          const uint32_t d = tmem + buf * 256 + s * SH::BN;
+          for (int s = 0; s < S; ++s) {
+            const uint32_t id = idesc_bf16((S - s) * SH::BN);
+            const uint32_t d = tmem + buf * 256 + s * SH::BN;
 #pragma unroll
-          for (int k16 = 0; k16 < 2; ++k16) {
-            const uint64_t ad = sdesc(aA + s * SH::A_TILE * 2 + k16 * 256, 128, 512);
-            const uint64_t bd = sdesc(aB + k16 * 256, 128, 512);
-            mma_bf16(d, ad, bd, id, (first && s == 0 && k16 == 0) ? 0u : 1u);
+            for (int k16 = 0; k16 < 2; ++k16) {
+              const uint64_t ad = sdesc(aA + s * SH::A_TILE * 2 + k16 * 256, 128, 512);
+              const uint64_t bd = sdesc(aB + k16 * 256, 128, 512);
+              mma_bf16(d, ad, bd, id, (first && s == 0 && k16 == 0) ? 0u : 1u);
+            }
+          }
+          mma_commit(&empty[st]);
+          if ((kb % KC_BLOCKS) == KC_BLOCKS - 1 || kb == W.nkb - 1) {
+            mma_commit(&accf[buf]);
+            ++gc;
           }
         }
-        mma_commit(&empty[st]);
-        if ((kb % KC_BLOCKS) == KC_BLOCKS - 1 || kb == nkb - 1) mma_commit(&accf[buf]);
       }
     }
   } else {
-    // ---- epilogue: 4 warps, one TMEM lane (= output row) per thread
-    const int q = warp & 3;  // TMEM lane quarter this warp may access
+    // ---- epilogue: 8 warps, one TMEM lane (= output row) per thread.  A warp may
+    // only read its own lane quarter (warp % 4); the two warps of a quarter take
+    // one half of the BN columns of every diagonal each.
+    constexpr int HW = SH::BN / 2;  // real columns per epilogue warp
+    const int q = warp & 3;
+    const int h = (warp - 2) >> 2;
     const int row = q * 32 + lane;
-    long long R[SH::BN];
-#pragma unroll
-    for (int j = 0; j < SH::BN; ++j) R[j] = 0;
+    uint32_t gc = 0;
     bool ok = true;
-    for (int ch = 0; ch < nchunks && ok; ++ch) {
-      const int buf = ch & 1;
-      if (!mbar_wait(&accf[buf], (ch >> 1) & 1, abort, gerr)) { ok = false; break; }
-      fence_after();
+    for (int w = blockIdx.x; w < n_work && ok; w += gridDim.x) {
+      const EmuWork W = emu_work(probs, nprobs, n_tiles, w);
+      const EmuProb& P = probs[W.pi];
+      const int nchunks = (W.nkb + KC_BLOCKS - 1) / KC_BLOCKS;
+      long long R[HW];
 #pragma unroll
-      for (int dgi = 0; dgi < S; ++dgi) {
-        const int shift = BETA * (S - 1 - dgi);
+      for (int j = 0; j < HW; ++j) R[j] = 0;
+      // 8-column groups of this warp that hold outputs (warp-uniform): none when the
+      // warp's 32 rows are all past M
+      const int ncv = 2 * min(P.N - W.nt * (SH::BN / 2), SH::BN / 2);
+      int nv8 = min(max((ncv - h * HW + 7) / 8, 0), HW / 8);
+      if (W.mt * BM + q * 32 >= P.M) nv8 = 0;
+      for (int ch = 0; ch < nchunks; ++ch, ++gc) {
+        const int buf = gc & 1;
+        if (!mbar_wait(&accf[buf], (gc >> 1) & 1, abort, gerr)) { ok = false; break; }
+        fence_after();
 #pragma unroll
-        for (int j16 = 0; j16 < SH::BN / 16; ++j16) {
-          uint32_t v[16];
-          tmem_ld16(tmem + (uint32_t(q * 32) << 16) + buf * 256 + dgi * SH::BN + j16 * 16, v);
+        for (int dgi = 0; dgi < S; ++dgi) {
+          const int shift = BETA * (S - 1 - dgi);
+          uint32_t v[HW];
+#pragma unroll
+          for (int j8 = 0; j8 < HW / 8; ++j8)
+            if (j8 < nv8)
+              tmem_ld8(tmem + (uint32_t(q * 32) << 16) + buf * 256 + dgi * SH::BN + h * HW + j8 * 8, v + j8 * 8);
           tmem_wait_ld();
 #pragma unroll
-          for (int u = 0; u < 16; ++u)
-            R[j16 * 16 + u] += (long long)__float2int_rn(__uint_as_float(v[u])) << shift;
+          for (int u = 0; u < HW; ++u)
+            if (u < nv8 * 8) R[u] += (long long)__float2int_rn(__uint_as_float(v[u])) << shift;
         }
+        fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&acce[buf]);
       }
-      fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&acce[buf]);
-    }
-    if (ok) {
-      const int gi = mt * BM + row;
-      if (gi < P.M && P.ksplit > 1) {  // scaled partial for the fixed-order reduction
-        const int ei = Aex[inst * aex_is + P.a_ex + gi];
-        cplx* W = ws + inst * ws_is + P.ws + int64_t(ks) * P.M * P.N + int64_t(gi) * P.N;
+      if (!ok) break;
+      const int gi = W.mt * BM + row;
+      if (gi >= P.M) continue;
+      const int ei = Aex[W.inst * aex_is + P.a_ex + gi];
+      const int* bex = Bex + W.inst * bex_is + P.b_ex;
+      const int j0 = W.nt * (SH::BN / 2) + h * (HW / 2);  // first complex column of this warp
+      if (P.ksplit > 1) {  // scaled partial for the fixed-order reduction
+        cplx* Wp = ws + W.inst * ws_is + P.ws + int64_t(W.ks) * P.M * P.N + int64_t(gi) * P.N;
 #pragma unroll
-        for (int jj = 0; jj < SH::BN / 2; ++jj) {
-          const int gj = nt * (SH::BN / 2) + jj;
+        for (int jj = 0; jj < HW / 2; ++jj) {
+          const int gj = j0 + jj;
           if (gj < P.N) {
-            const int e = ei + Bex[inst * bex_is + P.b_ex + gj] - BETA * (S + 1);
-            W[gj] = make_double2(ldexp(double(R[2 * jj]), e), ldexp(double(R[2 * jj + 1]), e));
+            const int e = ei + bex[gj] - BETA * (S + 1);
+            Wp[gj] = make_double2(scaled_i64(R[2 * jj], e), scaled_i64(R[2 * jj + 1], e));
           }
         }
-      } else if (gi < P.M) {
-        const int ei = Aex[inst * aex_is + P.a_ex + gi];
-        cplx* Crow = C + inst * c_is + P.c_off + int64_t(gi) * P.N;
+      } else {
+        cplx* Crow = C + W.inst * c_is + P.c_off + int64_t(gi) * P.N;
 #pragma unroll
-        for (int jj = 0; jj < SH::BN / 2; ++jj) {
-          const int gj = nt * (SH::BN / 2) + jj;
+        for (int jj = 0; jj < HW / 2; ++jj) {
+          const int gj = j0 + jj;
           if (gj < P.N) {
-            const int e = ei + Bex[inst * bex_is + P.b_ex + gj] - BETA * (S + 1);
-            const double re = ldexp(double(R[2 * jj]), e), im = ldexp(double(R[2 * jj + 1]), e);
-            double vr = alpha.x * re - alpha.y * im, vi = alpha.x * im + alpha.y * re;
+            const int e = ei + bex[gj] - BETA * (S + 1);
+            double vr, vi;
+            if (alpha_e != ALPHA_GENERAL) {  // alpha = +-2^k: folded into the exponent and sign
+              const long long rr = alpha_e < 0 ? -R[2 * jj] : R[2 * jj], ri = alpha_e < 0 ? -R[2 * jj + 1] : R[2 * jj + 1];
+              const int k = alpha_e < 0 ? -alpha_e - ALPHA_NEG_BIAS : alpha_e - ALPHA_POS_BIAS;
+              vr = scaled_i64(rr, e + k);
+              vi = scaled_i64(ri, e + k);
+            } else {
+              const double re = scaled_i64(R[2 * jj], e), im = scaled_i64(R[2 * jj + 1], e);
+              vr = alpha.x * re - alpha.y * im;
+              vi = alpha.x * im + alpha.y * re;
+            }
             if (beta) { const cplx o = Crow[gj]; vr += o.x; vi += o.y; }
             Crow[gj] = make_double2(vr, vi);
           }
@@ -342,39 +449,35 @@ __device__ __forceinline__ int exp_of_bits(unsigned long long m) {
   return e - 1022;  // |x| in [2^(e-1023), 2^(e-1022))
 }
 
-// Row exponents: CTA = (one row, a K range of ROW_KR); block max -> atomicMax
-// (max is order-independent, so the result is deterministic).  Exponent arrays
-// start at EXP_ZERO (all-zero row or column).
+// Row exponents: one warp per (row, K range of ROW_KR), grid-stride over all
+// of them; warp max -> atomicMax (max is order-independent, so the result is
+// deterministic).  Exponent arrays start at EXP_ZERO (all-zero row or column).
 #define ROW_KR 8192
 __global__ void __launch_bounds__(256) k_row_exp(const EmuProb* __restrict__ probs, int nprobs,
                                                  const cplx* __restrict__ A, int64_t a_is, int* __restrict__ ex,
-                                                 int64_t ex_is) {
-  __shared__ unsigned long long sh[8];
-  const int inst = blockIdx.y;
-  int t = blockIdx.x, pi = 0;
-  // work items: per problem M * ceil(K / ROW_KR)
-  for (;; ++pi) {
-    const int nk = (probs[pi].K + ROW_KR - 1) / ROW_KR;
-    const int items = probs[pi].M * max(nk, 1);
-    if (t < items || pi + 1 >= nprobs) break;
-    t -= items;
-  }
-  const EmuProb P = probs[pi];
-  const int nk = max((P.K + ROW_KR - 1) / ROW_KR, 1);
-  const int r = t / nk, kc = t % nk;
-  if (r >= P.M) return;
-  const cplx* a = A + inst * a_is + P.a_src + int64_t(r) * P.K;
-  unsigned long long m = 0;
-  for (int k = kc * ROW_KR + threadIdx.x; k < min(P.K, (kc + 1) * ROW_KR); k += 256) {
-    const cplx v = a[k];
-    m = max(m, max(abits(v.x), abits(v.y)));
-  }
-  for (int o = 16; o; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int w = 1; w < 8; ++w) m = max(m, sh[w]);
-    atomicMax(&ex[inst * ex_is + P.a_ex + r], exp_of_bits(m));
+                                                 int64_t ex_is, int64_t n_items) {
+  const int inst = blockIdx.y, lane = threadIdx.x & 31;
+  const int64_t stride = int64_t(gridDim.x) * (blockDim.x >> 5);
+  for (int64_t it = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); it < n_items; it += stride) {
+    int64_t t = it;
+    int pi = 0;
+    for (;; ++pi) {  // work items: per problem M * ceil(K / ROW_KR)
+      const int64_t items = int64_t(probs[pi].M) * max((probs[pi].K + ROW_KR - 1) / ROW_KR, 1);
+      if (t < items || pi + 1 >= nprobs) break;
+      t -= items;
+    }
+    const EmuProb& P = probs[pi];
+    const int nk = max((P.K + ROW_KR - 1) / ROW_KR, 1);
+    const int r = int(t / nk), kc = int(t % nk);
+    if (r >= P.M) continue;
+    const cplx* a = A + inst * a_is + P.a_src + int64_t(r) * P.K;
+    unsigned long long m = 0;
+    for (int k = kc * ROW_KR + lane; k < min(P.K, (kc + 1) * ROW_KR); k += 32) {
+      const cplx v = a[k];
+      m = max(m, max(abits(v.x), abits(v.y)));
+    }
+    for (int o = 16; o; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) atomicMax(&ex[inst * ex_is + P.a_ex + r], exp_of_bits(m));
   }
 }
 
@@ -467,31 +570,35 @@ __device__ __forceinline__ void slice8(const double (&x)[8], int sh, uint4 (&out
   }
 }
 
-// A' = [Re A | Im A], each half padded to Kh = K rounded up to KB.  CTA = (row
-// tile mt, half-k-block kbh): one read of A per element, writes the Re tile
-// (k-block kbh) and the Im tile (k-block Kh/KB + kbh).  Thread unit = (row, 8-group).
-template <int S>
-__global__ void __launch_bounds__(256) k_split_a(const EmuProb* __restrict__ probs, int nprobs, const cplx* __restrict__ A,
-                                                 int64_t a_is, const int* __restrict__ ex, int64_t ex_is,
-                                                 __nv_bfloat16* __restrict__ out, int64_t out_is) {
-  using SH = Shape<S>;
+// A' = [Re A | Im A], each half Kh = K rounded up to 16 (Kp = 2 Kh, a multiple
+// of KB).  Work item = (row tile mt, 32-wide range kbh of the half); unit = (row,
+// 8-group), 4 units per row in adjacent lanes; grid-stride over all units.  One
+// read of A per element, written at positions k (Re) and Kh + k (Im) of the tiled
+// K' axis.  FUSE_EXP (every K <= 32: a row lies inside one item): the row
+// exponent is formed here from the 4 lanes of the row, not by k_row_exp.
+__device__ __forceinline__ int64_t kpos_off(int r, int p, int tile_elems, int S) {
+  return int64_t(p / KB) * S * tile_elems + core_off(r, p % KB);
+}
+template <int S, bool FUSE_EXP>
+__global__ void __launch_bounds__(256) k_split_a(const EmuProb* __restrict__ probs, int nprobs, int n_items,
+                                                 const cplx* __restrict__ A, int64_t a_is, int* __restrict__ ex,
+                                                 int64_t ex_is, __nv_bfloat16* __restrict__ out, int64_t out_is) {
+  constexpr int UA = BM * (KB / 8);
   const int inst = blockIdx.y;
-  int t = blockIdx.x, pi = 0;
-  while (pi + 1 < nprobs && t >= probs[pi].tile0 + probs[pi].tiles_m * (probs[pi].Kp / (2 * KB))) ++pi;
-  const EmuProb P = probs[pi];
-  const int nkb = P.Kp / KB, nkh = nkb / 2;
-  const int lt = t - P.tile0;
-  const int mt = lt / nkh, kbh = lt % nkh;
-  __nv_bfloat16* o_re = out + inst * out_is + P.a_sl + (int64_t(mt) * nkb + kbh) * (S * SH::A_TILE);
-  __nv_bfloat16* o_im = out + inst * out_is + P.a_sl + (int64_t(mt) * nkb + nkh + kbh) * (S * SH::A_TILE);
-  const cplx* a = A + inst * a_is + P.a_src;
-  const int* e = ex + inst * ex_is + P.a_ex;
-  for (int u = threadIdx.x; u < BM * (KB / 8); u += blockDim.x) {
+  const int64_t total = int64_t(n_items) * UA;  // a multiple of 32: lanes of a warp stay together
+  for (int64_t U = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; U < total; U += int64_t(gridDim.x) * blockDim.x) {
+    const int t = int(U / UA), u = int(U - int64_t(t) * UA);
+    int pi = 0;
+    while (pi + 1 < nprobs && t >= probs[pi + 1].at0) ++pi;
+    const EmuProb& P = probs[pi];
+    const int nkb = P.Kp / KB, nkh = nkh_of(P), Kh = kh_of(P);
+    const int lt = t - P.at0;
+    const int mt = lt / nkh, kbh = lt % nkh;
     const int r = u >> 2, g = u & 3;
     const int gi = mt * BM + r;
     const int k0 = kbh * KB + g * 8;
+    const cplx* a = A + inst * a_is + P.a_src;
     double xr[8], xi[8];
-    const int sh = gi < P.M ? -e[gi] : 0;
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       xr[q] = 0.0;
@@ -502,44 +609,63 @@ __global__ void __launch_bounds__(256) k_split_a(const EmuProb* __restrict__ pro
         xi[q] = v.y;
       }
     }
+    int sh;
+    if (FUSE_EXP) {
+      unsigned long long m = 0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) m = max(m, max(abits(xr[q]), abits(xi[q])));
+      m = max(m, __shfl_xor_sync(0xffffffffu, m, 1));
+      m = max(m, __shfl_xor_sync(0xffffffffu, m, 2));
+      const int e = exp_of_bits(m);
+      if (g == 0 && gi < P.M) ex[inst * ex_is + P.a_ex + gi] = e;
+      sh = gi < P.M ? -e : 0;
+    } else {
+      sh = gi < P.M ? -ex[inst * ex_is + P.a_ex + gi] : 0;
+    }
+    if (k0 >= Kh || r >= P.arows) continue;
     uint4 sr[S], si[S], dummy[S];
     slice8<S>(xr, sh, sr, false, dummy);
     slice8<S>(xi, sh, si, false, dummy);
-    const int off = core_off(r, g * 8);
+    const int at = P.arows * KB;
+    __nv_bfloat16* o = out + inst * out_is + P.a_sl + int64_t(mt) * nkb * (S * at);
+    __nv_bfloat16* o_re = o + kpos_off(r, k0, at, S);
+    __nv_bfloat16* o_im = o + kpos_off(r, Kh + k0, at, S);
 #pragma unroll
     for (int s2 = 0; s2 < S; ++s2) {
-      *reinterpret_cast<uint4*>(o_re + s2 * SH::A_TILE + off) = sr[s2];
-      *reinterpret_cast<uint4*>(o_im + s2 * SH::A_TILE + off) = si[s2];
+      *reinterpret_cast<uint4*>(o_re + s2 * at) = sr[s2];
+      *reinterpret_cast<uint4*>(o_im + s2 * at) = si[s2];
     }
   }
 }
 
 // B'' rows n' = 2j + c: c = 0 -> [Re B_j ; -Im B_j], c = 1 -> [Im B_j ; Re B_j] over the
-// two K halves.  CTA = (column tile nt, half-k-block kbh); thread unit = (column j,
-// 8-group); lanes run along j, so the strided column reads coalesce across a warp.
+// two K halves (positions k and Kh + k).  Work item = (column tile nt, 32-wide range
+// kbh of the half); unit = (column j, 8-group), lanes along j so the strided column
+// reads coalesce; grid-stride over all units.
 template <int S>
-__global__ void __launch_bounds__(128) k_split_b(const EmuProb* __restrict__ probs, int nprobs, const cplx* __restrict__ B,
-                                                 int64_t b_is, const int* __restrict__ ex, int64_t ex_is,
-                                                 __nv_bfloat16* __restrict__ out, int64_t out_is, int) {
+__global__ void __launch_bounds__(256) k_split_b(const EmuProb* __restrict__ probs, int nprobs, int n_items,
+                                                 const cplx* __restrict__ B, int64_t b_is, const int* __restrict__ ex,
+                                                 int64_t ex_is, __nv_bfloat16* __restrict__ out, int64_t out_is) {
   using SH = Shape<S>;
   constexpr int NJ = SH::BN / 2;
+  constexpr int UB = NJ * (KB / 8);
   const int inst = blockIdx.y;
-  int t = blockIdx.x, pi = 0;
-  while (pi + 1 < nprobs && t >= probs[pi + 1].pad) ++pi;  // pad = first split-B CTA of the problem
-  const EmuProb P = probs[pi];
-  const int nkb = P.Kp / KB, nkh = nkb / 2;
-  const int lt = t - P.pad;
-  const int nt = lt / nkh, kbh = lt % nkh;
-  __nv_bfloat16* o_re = out + inst * out_is + P.b_sl + (int64_t(nt) * nkb + kbh) * (S * SH::B_TILE);
-  __nv_bfloat16* o_im = out + inst * out_is + P.b_sl + (int64_t(nt) * nkb + nkh + kbh) * (S * SH::B_TILE);
-  const cplx* b = B + inst * b_is + P.b_src;
-  const int* e = ex + inst * ex_is + P.b_ex;
-  for (int u = threadIdx.x; u < NJ * (KB / 8); u += blockDim.x) {
+  const int64_t total = int64_t(n_items) * UB;
+  for (int64_t U = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; U < total; U += int64_t(gridDim.x) * blockDim.x) {
+    const int t = int(U / UB), u = int(U - int64_t(t) * UB);
+    int pi = 0;
+    while (pi + 1 < nprobs && t >= probs[pi + 1].bt0) ++pi;
+    const EmuProb& P = probs[pi];
+    const int nkb = P.Kp / KB, nkh = nkh_of(P), Kh = kh_of(P);
+    const int lt = t - P.bt0;
+    const int nt = lt / nkh, kbh = lt % nkh;
     const int jl = u % NJ, g = u / NJ;
     const int gj = nt * NJ + jl;
     const int k0 = kbh * KB + g * 8;
+    if (k0 >= Kh || 2 * jl >= P.brows) continue;
+    const cplx* b = B + inst * b_is + P.b_src;
     double xr[8], xi[8];
-    const int sh = gj < P.N ? -e[gj] : 0;
+    const int sh = gj < P.N ? -ex[inst * ex_is + P.b_ex + gj] : 0;
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       xr[q] = 0.0;
@@ -553,35 +679,52 @@ __global__ void __launch_bounds__(128) k_split_b(const EmuProb* __restrict__ pro
     uint4 sr[S], si[S], sin_[S], dummy[S];
     slice8<S>(xr, sh, sr, false, dummy);
     slice8<S>(xi, sh, si, true, sin_);
-    const int off0 = core_off(2 * jl, g * 8), off1 = core_off(2 * jl + 1, g * 8);
+    const int bt = P.brows * KB;
+    __nv_bfloat16* o = out + inst * out_is + P.b_sl + int64_t(nt) * nkb * (S * bt);
+    __nv_bfloat16* re0 = o + kpos_off(2 * jl, k0, bt, S);
+    __nv_bfloat16* im0 = o + kpos_off(2 * jl, Kh + k0, bt, S);
+    __nv_bfloat16* re1 = o + kpos_off(2 * jl + 1, k0, bt, S);
+    __nv_bfloat16* im1 = o + kpos_off(2 * jl + 1, Kh + k0, bt, S);
 #pragma unroll
     for (int s2 = 0; s2 < S; ++s2) {
-      *reinterpret_cast<uint4*>(o_re + s2 * SH::B_TILE + off0) = sr[s2];    // row 2j, Re half:  Re B
-      *reinterpret_cast<uint4*>(o_im + s2 * SH::B_TILE + off0) = sin_[s2];  // row 2j, Im half: -Im B
-      *reinterpret_cast<uint4*>(o_re + s2 * SH::B_TILE + off1) = si[s2];    // row 2j+1, Re half: Im B
-      *reinterpret_cast<uint4*>(o_im + s2 * SH::B_TILE + off1) = sr[s2];    // row 2j+1, Im half: Re B
+      *reinterpret_cast<uint4*>(re0 + s2 * bt) = sr[s2];    // row 2j, Re half:  Re B
+      *reinterpret_cast<uint4*>(im0 + s2 * bt) = sin_[s2];  // row 2j, Im half: -Im B
+      *reinterpret_cast<uint4*>(re1 + s2 * bt) = si[s2];    // row 2j+1, Re half: Im B
+      *reinterpret_cast<uint4*>(im1 + s2 * bt) = sr[s2];    // row 2j+1, Im half: Re B
     }
   }
 }
 
-// C = alpha * sum_s partial_s (+ C), splits in index order
+// C = alpha * sum_s partial_s (+ C).  WARP: one warp per output element, lane l
+// sums the splits l, l + 32, ..., then a fixed butterfly (long split lists);
+// otherwise one thread per element in split order.  Either way the same inputs
+// always give the same bits.
+template <bool WARP>
 __global__ void __launch_bounds__(256) k_emu_reduce(const EmuProb* __restrict__ probs, int nprobs,
                                                     const cplx* __restrict__ ws, int64_t ws_is, cplx* __restrict__ C,
-                                                    int64_t c_is, cplx alpha, int beta) {
-  const int inst = blockIdx.y;
-  for (int p = 0; p < nprobs; ++p) {
-    const EmuProb P = probs[p];
-    if (P.ksplit <= 1) continue;
-    const int64_t n = int64_t(P.M) * P.N;
+                                                    int64_t c_is, cplx alpha, int beta, int64_t n_red) {
+  const int inst = blockIdx.y, lane = WARP ? (threadIdx.x & 31) : 0;
+  const int per = WARP ? 32 : 1;
+  const int64_t stride = int64_t(gridDim.x) * (blockDim.x / per);
+  for (int64_t it = int64_t(blockIdx.x) * (blockDim.x / per) + threadIdx.x / per; it < n_red; it += stride) {
+    int pi = 0;
+    while (pi + 1 < nprobs && (probs[pi].ksplit <= 1 || it >= probs[pi].red0 + int64_t(probs[pi].M) * probs[pi].N)) ++pi;
+    const EmuProb& P = probs[pi];
+    const int64_t n = int64_t(P.M) * P.N, e = it - P.red0;
     const cplx* W = ws + inst * ws_is + P.ws;
-    cplx* Cp = C + inst * c_is + P.c_off;
-    for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < n; e += int64_t(gridDim.x) * blockDim.x) {
-      double sr = 0.0, si = 0.0;
-      for (int s = 0; s < P.ksplit; ++s) {
-        const cplx w = W[int64_t(s) * n + e];
-        sr += w.x;
-        si += w.y;
+    double sr = 0.0, si = 0.0;
+    for (int s = lane; s < P.ksplit; s += per) {
+      const cplx w = W[int64_t(s) * n + e];
+      sr += w.x;
+      si += w.y;
+    }
+    if (WARP)
+      for (int o = 16; o; o >>= 1) {
+        sr += __shfl_xor_sync(0xffffffffu, sr, o);
+        si += __shfl_xor_sync(0xffffffffu, si, o);
       }
+    if (lane == 0) {
+      cplx* Cp = C + inst * c_is + P.c_off;
       double vr = alpha.x * sr - alpha.y * si, vi = alpha.x * si + alpha.y * sr;
       if (beta) { const cplx o = Cp[e]; vr += o.x; vi += o.y; }
       Cp[e] = make_double2(vr, vi);
@@ -589,15 +732,47 @@ __global__ void __launch_bounds__(256) k_emu_reduce(const EmuProb* __restrict__ 
   }
 }
 
+static void launch_emu_reduce(const EmuProb* d, int np, int max_ksplit, const cplx* ws, int64_t ws_is, cplx* C,
+                              int64_t c_is, cplx alpha, int beta, int64_t n_red, int ninst, int sms, cudaStream_t st) {
+  const int64_t cap = int64_t(std::max(sms, 1)) * 16;
+  if (max_ksplit >= 64) {
+    const int blocks = int(std::max<int64_t>(1, std::min<int64_t>((n_red + 7) / 8, cap)));
+    k_emu_reduce<true><<<dim3(blocks, ninst), 256, 0, st>>>(d, np, ws, ws_is, C, c_is, alpha, beta, n_red);
+  } else {
+    const int blocks = int(std::max<int64_t>(1, std::min<int64_t>((n_red + 255) / 256, cap)));
+    k_emu_reduce<false><<<dim3(blocks, ninst), 256, 0, st>>>(d, np, ws, ws_is, C, c_is, alpha, beta, n_red);
+  }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
+static int kp_of(int K) { return 2 * ((std::max(K, 1) + 15) / 16) * 16; }
+
+// grid of a warp-per-item kernel (8 warps per CTA) and of a thread-per-unit kernel
+static int row_exp_blocks(int64_t items, int sms) {
+  return int(std::max<int64_t>(1, std::min<int64_t>((items + 7) / 8, int64_t(std::max(sms, 1)) * 16)));
+}
+static int split_blocks(int64_t units, int sms) {
+  return int(std::max<int64_t>(1, std::min<int64_t>((units + 255) / 256, int64_t(std::max(sms, 1)) * 8)));
+}
+
+// epilogue encoding of alpha (see ALPHA_GENERAL)
+static int alpha_code(cplx a) {
+  if (a.y != 0.0 || a.x == 0.0) return ALPHA_GENERAL;
+  int ex = 0;
+  const double m = std::frexp(std::fabs(a.x), &ex);  // |a| = m 2^ex, m in [0.5, 1)
+  if (m != 0.5 || ex - 1 < -60 || ex - 1 > 60) return ALPHA_GENERAL;
+  return a.x > 0 ? (ex - 1) + ALPHA_POS_BIAS : -((ex - 1) + ALPHA_NEG_BIAS);
+}
+
 struct EmuPlan {
   int S = 5;
   std::vector<EmuProb> h;
   EmuProb* d = nullptr;
-  int n_tiles = 0, n_atiles = 0, n_btiles = 0;
+  int n_tiles = 0, n_atiles = 0, n_btiles = 0;  // GEMM work items, split-A / split-B items
   int total_rows = 0, total_cols = 0;
+  bool fuse_a = false;  // every K <= 32: split-A forms the row exponents itself
   int n_rowexp = 0, n_colexp = 0;  // work items of the exponent scans
   __nv_bfloat16* asl = nullptr;
   __nv_bfloat16* bsl = nullptr;
@@ -628,12 +803,9 @@ struct EmuState {
 bool emu_wanted(Ctx& c, const GemmPlan& g, const std::string&) {
   if (c.cfg.precision != EXP_EMU_BF16) return false;
   if (c.cfg.emu_min_macs > 0) return double(g.flops_mac) >= c.cfg.emu_min_macs;
-  // below ~8e6 complex MACs the slicing passes cost more than the FP64 kernel;
-  // contraction lengths from 64 up are faster on the tensor cores than at GB300's
-  // FP64 rate, shorter ones (K = o/G ~ 14) are not (per-tile overhead dominates)
-  int maxK = 0;
-  for (auto& p : g.h_probs) maxK = std::max(maxK, p.K);
-  return g.flops_mac >= int64_t(1) << 23 && maxK >= 64;
+  // below ~4e6 complex MACs the slicing passes cost more than the FP64 dot
+  // kernel; above, GB300's FP64 rate loses to the tensor cores at every K
+  return g.flops_mac >= int64_t(1) << 22;
 }
 
 template <int S>
@@ -671,6 +843,7 @@ EmuPlan* emu_plan(Ctx& c, const GemmPlan& g, const Tensor* A, const Tensor* B, b
   tiles_mn *= c.ninst;
   const int64_t sms = std::max(c.sm_count, 1);
   int64_t ws = 0;
+  p->fuse_a = true;
   for (auto& q : g.h_probs) {
     EmuProb e{};
     e.a_src = q.a;
@@ -679,9 +852,12 @@ EmuPlan* emu_plan(Ctx& c, const GemmPlan& g, const Tensor* A, const Tensor* B, b
     e.M = q.M;
     e.N = q.N;
     e.K = q.K;
-    e.Kp = 2 * std::max((q.K + KB - 1) / KB, 1) * KB;  // [Re | Im], each half padded to KB
+    e.Kp = kp_of(q.K);  // [Re | Im], each half padded to 16
     e.tiles_m = (q.M + BM - 1) / BM;
     e.tiles_n = (q.N + BN / 2 - 1) / (BN / 2);
+    e.arows = e.tiles_m == 1 ? (q.M + 7) / 8 * 8 : BM;
+    e.brows = e.tiles_n == 1 ? (2 * q.N + 7) / 8 * 8 : BN;
+    if (q.K > 32) p->fuse_a = false;
     const int nkb = e.Kp / KB;
     e.ksplit = 1;
     e.kcb = ((nkb + KC_BLOCKS - 1) / KC_BLOCKS) * KC_BLOCKS;
@@ -695,14 +871,15 @@ EmuPlan* emu_plan(Ctx& c, const GemmPlan& g, const Tensor* A, const Tensor* B, b
     if (e.ksplit > 1) {
       e.ws = ws;
       ws += int64_t(e.ksplit) * q.M * q.N;
+      e.red0 = p->red_elems;
       p->red_elems += int64_t(q.M) * q.N;
     }
     e.tile0 = tile0;
     tile0 += e.tiles_m * e.tiles_n * e.ksplit;
     e.a_sl = asl;
     e.b_sl = bsl;
-    asl += int64_t(e.tiles_m) * nkb * p->S * BM * KB;
-    bsl += int64_t(e.tiles_n) * nkb * p->S * BN * KB;
+    asl += int64_t(e.tiles_m) * nkb * p->S * e.arows * KB;
+    bsl += int64_t(e.tiles_n) * nkb * p->S * e.brows * KB;
     e.a_ex = aex;
     e.b_ex = bex;
     aex += q.M;
@@ -711,16 +888,11 @@ EmuPlan* emu_plan(Ctx& c, const GemmPlan& g, const Tensor* A, const Tensor* B, b
     p->total_cols += q.N;
     p->n_rowexp += q.M * std::max((q.K + ROW_KR - 1) / ROW_KR, 1);
     p->n_colexp += ((q.N + 31) / 32) * std::max((q.K + 255) / 256, 1);
-    e.pad = bt0;  // first split-B CTA
-    bt0 += e.tiles_n * (nkb / 2);
-    at0 += e.tiles_m * (nkb / 2);
+    e.at0 = at0;
+    e.bt0 = bt0;
+    at0 += e.tiles_m * nkh_of(e);
+    bt0 += e.tiles_n * nkh_of(e);
     p->h.push_back(e);
-  }
-  // split-A tile indexing reuses tile0 as the first split-A tile of each problem
-  std::vector<EmuProb> ha = p->h;
-  {
-    int t = 0;
-    for (auto& e : ha) { e.tile0 = t; t += e.tiles_m * (e.Kp / (2 * KB)); }
   }
   p->n_tiles = tile0;
   p->n_atiles = at0;
@@ -749,51 +921,95 @@ EmuPlan* emu_plan(Ctx& c, const GemmPlan& g, const Tensor* A, const Tensor* B, b
     p->ws_is = ws;
     p->d_ws = (cplx*)c.dalloc(sizeof(cplx) * ws * c.ninst);
   }
-  // two device copies of the problem list: [0, n) for the GEMM and split-B, [n, 2n) for split-A
-  std::vector<EmuProb> both = p->h;
-  both.insert(both.end(), ha.begin(), ha.end());
-  p->d = (EmuProb*)c.dalloc(sizeof(EmuProb) * both.size());
-  upload(c, p->d, both.data(), sizeof(EmuProb) * both.size());
+  p->d = (EmuProb*)c.dalloc(sizeof(EmuProb) * p->h.size());
+  upload(c, p->d, p->h.data(), sizeof(EmuProb) * p->h.size());
   (void)A;
   return p;
 }
+
+// profiling mode: stage boundaries of one emulated product (A scan + split, B scan
+// + split, GEMM, split-K reduction), reported after the stream drains
+struct EmuStageTimer {
+  bool on;
+  cudaStream_t st;
+  cudaEvent_t ev[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  EmuStageTimer(bool on_, cudaStream_t s) : on(on_), st(s) {
+    if (on)
+      for (auto& e : ev) { CK(cudaEventCreate(&e)); }
+    mark(0);
+  }
+  int last = -1;
+  void mark(int k) {  // a skipped stage gets a zero-length interval
+    if (on)
+      for (; last < k; ++last) CK(cudaEventRecord(ev[last + 1], st));
+  }
+  void report(int64_t tiles) {
+    if (!on) return;
+    CK(cudaEventSynchronize(ev[6]));
+    float t[6];
+    for (int k = 0; k < 6; ++k) CK(cudaEventElapsedTime(&t[k], ev[k], ev[k + 1]));
+    fprintf(stderr,
+            "[exp_emu] exp_a %6.3f split_a %6.3f exp_b %6.3f split_b %6.3f gemm %6.3f reduce %6.3f ms  work items %lld\n",
+            t[0], t[1], t[2], t[3], t[4], t[5], (long long)tiles);
+    for (auto& e : ev) cudaEventDestroy(e);
+  }
+};
 
 template <int S>
 static void run_s(Ctx& c, EmuPlan* p, const cplx* A, const cplx* B, cplx* C, int64_t ais, int64_t bis, int64_t cis,
                   cplx alpha, bool beta) {
   const int np = int(p->h.size());
+  EmuStageTimer tm(c.profile, c.stream);
   if (!p->a_ready) {
-    k_fill_int<<<dim3(std::max<int64_t>(1, std::min<int64_t>((p->aex_is * c.ninst + 255) / 256, 1024))), 256, 0, c.stream>>>(
-        p->aex, p->aex_is * c.ninst, EXP_ZERO);
-    KCHECK(c);
-    k_row_exp<<<dim3(p->n_rowexp, c.ninst), 256, 0, c.stream>>>(p->d, np, A, ais, p->aex, p->aex_is);
-    KCHECK(c);
-    k_split_a<S><<<dim3(p->n_atiles, c.ninst), 256, 0, c.stream>>>(p->d + np, np, A, ais, p->aex, p->aex_is, p->asl,
-                                                                   p->asl_is);
+    const int blocks = split_blocks(int64_t(p->n_atiles) * BM * (KB / 8), c.sm_count);
+    if (p->fuse_a) {
+      tm.mark(1);
+      k_split_a<S, true><<<dim3(blocks, c.ninst), 256, 0, c.stream>>>(p->d, np, p->n_atiles, A, ais, p->aex, p->aex_is,
+                                                                      p->asl, p->asl_is);
+    } else {
+      k_fill_int<<<dim3(std::max<int64_t>(1, std::min<int64_t>((p->aex_is * c.ninst + 255) / 256, 1024))), 256, 0,
+                   c.stream>>>(p->aex, p->aex_is * c.ninst, EXP_ZERO);
+      KCHECK(c);
+      k_row_exp<<<dim3(row_exp_blocks(p->n_rowexp, c.sm_count), c.ninst), 256, 0, c.stream>>>(p->d, np, A, ais, p->aex,
+                                                                                                p->aex_is, p->n_rowexp);
+      KCHECK(c);
+      tm.mark(1);
+      k_split_a<S, false><<<dim3(blocks, c.ninst), 256, 0, c.stream>>>(p->d, np, p->n_atiles, A, ais, p->aex, p->aex_is,
+                                                                       p->asl, p->asl_is);
+    }
     KCHECK(c);
     if (p->a_const) p->a_ready = true;
   }
+  tm.mark(2);
   if (!p->b_ready && !p->b_owner) {
     k_fill_int<<<dim3(std::max<int64_t>(1, std::min<int64_t>((p->bex_is * c.ninst + 255) / 256, 1024))), 256, 0, c.stream>>>(
         p->bex, p->bex_is * c.ninst, EXP_ZERO);
     KCHECK(c);
     k_col_exp<<<dim3(p->n_colexp, c.ninst), 256, 0, c.stream>>>(p->d, np, B, bis, p->bex, p->bex_is);
     KCHECK(c);
-    k_split_b<S><<<dim3(p->n_btiles, c.ninst), 128, 0, c.stream>>>(p->d, np, B, bis, p->bex, p->bex_is, p->bsl,
-                                                                   p->bsl_is, 0);
+    tm.mark(3);
+    k_split_b<S><<<dim3(split_blocks(int64_t(p->n_btiles) * (Shape<S>::BN / 2) * (KB / 8), c.sm_count), c.ninst), 256, 0,
+                   c.stream>>>(p->d, np, p->n_btiles, B, bis, p->bex, p->bex_is, p->bsl, p->bsl_is);
     KCHECK(c);
     if (p->b_const) p->b_ready = true;
   }
+  tm.mark(4);
   set_smem_attr<S>();
-  k_emu_gemm<S><<<dim3(p->n_tiles, c.ninst), THREADS, Shape<S>::SMEM, c.stream>>>(
-      p->d, np, p->asl, p->bsl, p->aex, p->bex, C, p->asl_is, p->bsl_is, p->aex_is, p->bex_is, cis, alpha, beta ? 1 : 0,
-      p->d_err, p->d_ws, p->ws_is);
+  const int n_work = p->n_tiles * c.ninst;
+  k_emu_gemm<S><<<dim3(std::min(n_work, std::max(c.sm_count, 1))), THREADS, Shape<S>::SMEM, c.stream>>>(
+      p->d, np, p->n_tiles, n_work, p->asl, p->bsl, p->aex, p->bex, C, p->asl_is, p->bsl_is, p->aex_is, p->bex_is, cis,
+      alpha, p->red_elems ? ALPHA_GENERAL : alpha_code(alpha), beta ? 1 : 0, p->d_err, p->d_ws, p->ws_is);
   KCHECK(c);
+  tm.mark(5);
   if (p->red_elems) {
-    const int blocks = int(std::min<int64_t>((p->red_elems + 255) / 256, 2LL * std::max(c.sm_count, 1)));
-    k_emu_reduce<<<dim3(blocks, c.ninst), 256, 0, c.stream>>>(p->d, np, p->d_ws, p->ws_is, C, cis, alpha, beta ? 1 : 0);
+    int mks = 1;
+    for (auto& e : p->h) mks = std::max(mks, int(e.ksplit));
+    launch_emu_reduce(p->d, np, mks, p->d_ws, p->ws_is, C, cis, alpha, beta ? 1 : 0, p->red_elems, c.ninst, c.sm_count,
+                      c.stream);
     KCHECK(c);
   }
+  tm.mark(6);
+  tm.report(int64_t(n_work));
 }
 
 void emu_run(Ctx& c, EmuPlan* p, const GemmPlan&, const cplx* A, const cplx* B, cplx* C, int64_t ais, int64_t bis,
@@ -858,7 +1074,7 @@ exp_status noalloc_launch(cudaStream_t st, unsigned char* base, int M, int N, in
   e.M = M;
   e.N = N;
   e.K = K;
-  e.Kp = 2 * std::max((K + KB - 1) / KB, 1) * KB;
+  e.Kp = kp_of(K);
   e.tiles_m = (M + BM - 1) / BM;
   e.tiles_n = (N + BN / 2 - 1) / (BN / 2);
   const int nkb = e.Kp / KB;
@@ -872,24 +1088,25 @@ exp_status noalloc_launch(cudaStream_t st, unsigned char* base, int M, int N, in
     e.kcb = int32_t(((chunks + ks - 1) / ks) * KC_BLOCKS);
     e.ksplit = (nkb + e.kcb - 1) / e.kcb;
   }
-  e.pad = 0;
-  e.tile0 = 0;
+  e.arows = e.tiles_m == 1 ? (M + 7) / 8 * 8 : BM;
+  e.brows = e.tiles_n == 1 ? (2 * N + 7) / 8 * 8 : BN;
+  e.tile0 = e.at0 = e.bt0 = 0;
+  e.red0 = 0;
   // scratch layout
   int64_t off = 0;
-  const int64_t o_probs = carve(off, 2 * sizeof(EmuProb));
+  const int64_t o_probs = carve(off, sizeof(EmuProb));
   const int64_t o_err = carve(off, sizeof(int));
   const int64_t o_aex = carve(off, sizeof(int) * int64_t(M));
   const int64_t o_bex = carve(off, sizeof(int) * int64_t(N));
-  const int64_t o_asl = carve(off, int64_t(2) * e.tiles_m * nkb * S * BM * KB);
-  const int64_t o_bsl = carve(off, int64_t(2) * e.tiles_n * nkb * S * BN * KB);
+  const int64_t o_asl = carve(off, int64_t(2) * e.tiles_m * nkb * S * e.arows * KB);
+  const int64_t o_bsl = carve(off, int64_t(2) * e.tiles_n * nkb * S * e.brows * KB);
   const int64_t o_ws = carve(off, e.ksplit > 1 ? int64_t(sizeof(cplx)) * e.ksplit * M * N : 0);
   if (off > int64_t(EXP_NOALLOC_SCRATCH_BYTES)) {
     err = "exp_zgemm_emu_noalloc: problem needs " + std::to_string(off) + " bytes of scratch, more than the " +
           std::to_string(int64_t(EXP_NOALLOC_SCRATCH_BYTES)) + " bytes available";
     return EXP_EINVAL;
   }
-  EmuProb recs[2] = {e, e};
-  recs[1].tile0 = 0;  // split-A tile numbering starts at 0 as well
+  EmuProb recs[1] = {e};
   EmuProb* d_probs = (EmuProb*)(base + o_probs);
   int* d_err = (int*)(base + o_err);
   int* aex = (int*)(base + o_aex);
@@ -906,19 +1123,23 @@ exp_status noalloc_launch(cudaStream_t st, unsigned char* base, int M, int N, in
   const int64_t n_colexp = int64_t((N + 31) / 32) * std::max((K + 255) / 256, 1);
   k_fill_int<<<std::max(1, std::min((M + 255) / 256, 1024)), 256, 0, st>>>(aex, M, EXP_ZERO);
   k_fill_int<<<std::max(1, std::min((N + 255) / 256, 1024)), 256, 0, st>>>(bex, N, EXP_ZERO);
-  k_row_exp<<<dim3(unsigned(n_rowexp), 1), 256, 0, st>>>(d_probs, 1, A, 0, aex, 0);
+  k_row_exp<<<dim3(row_exp_blocks(n_rowexp, sms), 1), 256, 0, st>>>(d_probs, 1, A, 0, aex, 0, n_rowexp);
   k_col_exp<<<dim3(unsigned(n_colexp), 1), 256, 0, st>>>(d_probs, 1, B, 0, bex, 0);
-  k_split_a<S><<<dim3(e.tiles_m * (nkb / 2), 1), 256, 0, st>>>(d_probs + 1, 1, A, 0, aex, 0, asl, 0);
-  k_split_b<S><<<dim3(e.tiles_n * (nkb / 2), 1), 128, 0, st>>>(d_probs, 1, B, 0, bex, 0, bsl, 0, 0);
+  const int na = e.tiles_m * nkh_of(e), nb = e.tiles_n * nkh_of(e);
+  k_split_a<S, false><<<dim3(split_blocks(int64_t(na) * BM * (KB / 8), sms), 1), 256, 0, st>>>(d_probs, 1, na, A, 0, aex, 0,
+                                                                                              asl, 0);
+  k_split_b<S><<<dim3(split_blocks(int64_t(nb) * (BN / 2) * (KB / 8), sms), 1), 256, 0, st>>>(d_probs, 1, nb, B, 0, bex, 0,
+                                                                                             bsl, 0);
   if (cudaFuncSetAttribute(k_emu_gemm<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, SH::SMEM) != cudaSuccess) {
     err = "exp_zgemm_emu_noalloc: shared-memory attribute refused";
     return EXP_ECUDA;
   }
-  k_emu_gemm<S><<<dim3(unsigned(tiles_mn * e.ksplit), 1), THREADS, SH::SMEM, st>>>(
-      d_probs, 1, asl, bsl, aex, bex, Cout, 0, 0, 0, 0, 0, alpha, beta, d_err, ws, 0);
+  const int n_work = int(tiles_mn * e.ksplit);
+  k_emu_gemm<S><<<dim3(unsigned(std::min(n_work, sms)), 1), THREADS, SH::SMEM, st>>>(
+      d_probs, 1, n_work, n_work, asl, bsl, aex, bex, Cout, 0, 0, 0, 0, 0, alpha,
+      e.ksplit > 1 ? ALPHA_GENERAL : alpha_code(alpha), beta, d_err, ws, 0);
   if (e.ksplit > 1) {
-    const int blocks = int(std::min<int64_t>((int64_t(M) * N + 255) / 256, 2LL * sms));
-    k_emu_reduce<<<dim3(blocks, 1), 256, 0, st>>>(d_probs, 1, ws, 0, Cout, 0, alpha, beta);
+    launch_emu_reduce(d_probs, 1, e.ksplit, ws, 0, Cout, 0, alpha, beta, int64_t(M) * N, 1, sms, st);
   }
   cudaError_t ce = cudaGetLastError();
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);

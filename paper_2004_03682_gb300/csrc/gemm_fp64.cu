@@ -128,8 +128,57 @@ __global__ void __launch_bounds__(256) k_splitk_reduce(const GemmProb* __restric
   }
 }
 
+// Small products (and every matrix-vector one): one warp per output element, the
+// lanes striding over K, then a fixed butterfly.  At GB300's FP64 rate (about two
+// FMAs per clock per SM) a tile kernel leaves most SMs idle on these; here every
+// SM takes a share of the outputs and no padded rows or columns are computed.
+__global__ void __launch_bounds__(256) k_gemm_dot(const GemmProb* __restrict__ probs, int n_probs,
+                                                  const cplx* __restrict__ A, const cplx* __restrict__ B,
+                                                  cplx* __restrict__ C, int64_t ais, int64_t bis, int64_t cis,
+                                                  cplx alpha, int beta, int64_t n_out) {
+  const int lane = threadIdx.x & 31;
+  A += blockIdx.y * ais;
+  B += blockIdx.y * bis;
+  C += blockIdx.y * cis;
+  const int64_t stride = int64_t(gridDim.x) * (blockDim.x >> 5);
+  for (int64_t it = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); it < n_out; it += stride) {
+    int pi = 0;
+    while (pi + 1 < n_probs && it >= probs[pi + 1].ws) ++pi;  // ws = first output of the problem here
+    const GemmProb& P = probs[pi];
+    const int64_t e = it - P.ws;
+    const int m = int(e / P.N), n = int(e - int64_t(m) * P.N);
+    const cplx* a = A + P.a + int64_t(m) * P.K;
+    const cplx* b = B + P.b + n;
+    double sr = 0.0, si = 0.0;
+    for (int k = lane; k < P.K; k += 32) {
+      const cplx x = a[k], y = b[int64_t(k) * P.N];
+      sr = fma(x.x, y.x, sr);
+      sr = fma(-x.y, y.y, sr);
+      si = fma(x.x, y.y, si);
+      si = fma(x.y, y.x, si);
+    }
+    for (int o = 16; o; o >>= 1) {
+      sr += __shfl_xor_sync(0xffffffffu, sr, o);
+      si += __shfl_xor_sync(0xffffffffu, si, o);
+    }
+    if (lane == 0) {
+      double vr = alpha.x * sr - alpha.y * si, vi = alpha.x * si + alpha.y * sr;
+      cplx* dp = C + P.c + e;
+      if (beta) { const cplx o = *dp; vr += o.x; vi += o.y; }
+      *dp = make_double2(vr, vi);
+    }
+  }
+}
+
 void launch_gemm_fp64(Ctx& c, const GemmPlan& g, const cplx* A, const cplx* B, cplx* C, int64_t ais,
                       int64_t bis, int64_t cis, cplx alpha, bool beta) {
+  if (g.dot_outputs) {
+    const int blocks = int(std::max<int64_t>(1, std::min<int64_t>((g.dot_outputs + 7) / 8, 16LL * std::max(c.sm_count, 1))));
+    k_gemm_dot<<<dim3(blocks, c.ninst), 256, 0, c.stream>>>(g.d_probs, g.n_probs, A, B, C, ais, bis, cis, alpha,
+                                                             beta, g.dot_outputs);
+    KCHECK(c);
+    return;
+  }
   if (g.n_tiles == 0) return;
   const dim3 grid(g.n_tiles, c.ninst);
   if (g.tm == 64 && g.tn == 64)

@@ -11,10 +11,18 @@ struct Coefs {
   cplx c[EXP_MAX_TERMS];
 };
 
+__device__ __forceinline__ uint32_t udiv(uint32_t x, uint32_t m, uint32_t l) {
+  const uint32_t t = __umulhi(m, x);
+  return l == 0 ? x : (t + ((x - t) >> 1)) >> (l - 1);
+}
+
 // Each CTA handles one chunk of one sub-block task.  Elements are walked in
 // destination order (dim 3 innermost, stride 1 in dst) so that stores are
-// coalesced; sources are gathered through the task's strides.
-template <int NT>
+// coalesced; sources are gathered through the task's strides.  SIGNS: every
+// coefficient is +1 or -1, applied as a sign-bit flip (GB300 issues FP64
+// arithmetic at a small fraction of its integer rate), so a term costs one
+// FP64 add and a single-term copy none.
+template <int NT, bool SIGNS>
 __global__ void __launch_bounds__(256) k_permute(const PermTask* __restrict__ tasks,
                                                  const ChunkRef* __restrict__ chunks,
                                                  cplx* __restrict__ dst,
@@ -28,16 +36,19 @@ __global__ void __launch_bounds__(256) k_permute(const PermTask* __restrict__ ta
   __syncthreads();
   dst += blockIdx.y * dis;
   src += blockIdx.y * sis;
-  const int64_t end = min(ch.start + (int64_t)EXP_CHUNK, T.count);
-  const int n1 = T.n[1], n2 = T.n[2], n3 = T.n[3];
-  for (int64_t e = ch.start + threadIdx.x; e < end; e += blockDim.x) {
-    int64_t r = e;
-    const int i3 = int(r % n3);
-    r /= n3;
-    const int i2 = int(r % n2);
-    r /= n2;
-    const int i1 = int(r % n1);
-    const int i0 = int(r / n1);
+  const uint32_t end = uint32_t(min(ch.start + (int64_t)EXP_CHUNK, T.count));
+  const uint32_t n1 = T.n[1], n2 = T.n[2], n3 = T.n[3];
+  unsigned long long sgn[NT];
+#pragma unroll
+  for (int t = 0; t < NT; ++t) sgn[t] = co.c[t].x < 0.0 ? 0x8000000000000000ull : 0ull;
+  for (uint32_t e = uint32_t(ch.start) + threadIdx.x; e < end; e += blockDim.x) {
+    const uint32_t q3 = udiv(e, T.mg[3], T.ml[3]);
+    const int i3 = int(e - q3 * n3);
+    const uint32_t q2 = udiv(q3, T.mg[2], T.ml[2]);
+    const int i2 = int(q3 - q2 * n2);
+    const uint32_t q1 = udiv(q2, T.mg[1], T.ml[1]);
+    const int i1 = int(q2 - q1 * n1);
+    const int i0 = int(q1);
     const int64_t dp = T.dst + i0 * T.dst_st[0] + i1 * T.dst_st[1] + i2 * T.dst_st[2] + i3 * T.dst_st[3];
     double vr = 0.0, vi = 0.0;
 #pragma unroll
@@ -45,8 +56,14 @@ __global__ void __launch_bounds__(256) k_permute(const PermTask* __restrict__ ta
       const int64_t sp = T.src[t] + i0 * T.src_st[t][0] + i1 * T.src_st[t][1] +
                          i2 * T.src_st[t][2] + i3 * T.src_st[t][3];
       const cplx x = src[sp];
-      vr += co.c[t].x * x.x - co.c[t].y * x.y;
-      vi += co.c[t].x * x.y + co.c[t].y * x.x;
+      if (SIGNS) {
+        const double xr = __longlong_as_double(__double_as_longlong(x.x) ^ (long long)sgn[t]);
+        const double xi = __longlong_as_double(__double_as_longlong(x.y) ^ (long long)sgn[t]);
+        if (t == 0) { vr = xr; vi = xi; } else { vr += xr; vi += xi; }
+      } else {
+        vr += co.c[t].x * x.x - co.c[t].y * x.y;
+        vi += co.c[t].x * x.y + co.c[t].y * x.x;
+      }
     }
     if (acc) {
       const cplx o = dst[dp];
@@ -57,17 +74,30 @@ __global__ void __launch_bounds__(256) k_permute(const PermTask* __restrict__ ta
   }
 }
 
+template <int NT>
+static void permute_nt(Ctx& c, const PermPlan& p, cplx* dst, const cplx* src, int64_t dst_is, int64_t src_is,
+                       const Coefs& co, bool signs, bool accumulate) {
+  dim3 grid(p.n_chunks, c.ninst);
+  if (signs)
+    k_permute<NT, true><<<grid, 256, 0, c.stream>>>(p.d_tasks, p.d_chunks, dst, src, dst_is, src_is, co, accumulate);
+  else
+    k_permute<NT, false><<<grid, 256, 0, c.stream>>>(p.d_tasks, p.d_chunks, dst, src, dst_is, src_is, co, accumulate);
+}
+
 void launch_permute(Ctx& c, const PermPlan& p, cplx* dst, const cplx* src, int64_t dst_is,
                     int64_t src_is, const cplx* coef, bool accumulate, bool) {
   if (p.n_chunks == 0) return;
   Coefs co;
-  for (int t = 0; t < EXP_MAX_TERMS; ++t) co.c[t] = t < p.n_terms ? coef[t] : make_double2(0, 0);
-  dim3 grid(p.n_chunks, c.ninst);
+  bool signs = true;
+  for (int t = 0; t < EXP_MAX_TERMS; ++t) {
+    co.c[t] = t < p.n_terms ? coef[t] : make_double2(0, 0);
+    if (t < p.n_terms && !(co.c[t].y == 0.0 && (co.c[t].x == 1.0 || co.c[t].x == -1.0))) signs = false;
+  }
   switch (p.n_terms) {
-    case 1: k_permute<1><<<grid, 256, 0, c.stream>>>(p.d_tasks, p.d_chunks, dst, src, dst_is, src_is, co, accumulate); break;
-    case 2: k_permute<2><<<grid, 256, 0, c.stream>>>(p.d_tasks, p.d_chunks, dst, src, dst_is, src_is, co, accumulate); break;
-    case 3: k_permute<3><<<grid, 256, 0, c.stream>>>(p.d_tasks, p.d_chunks, dst, src, dst_is, src_is, co, accumulate); break;
-    default: k_permute<4><<<grid, 256, 0, c.stream>>>(p.d_tasks, p.d_chunks, dst, src, dst_is, src_is, co, accumulate); break;
+    case 1: permute_nt<1>(c, p, dst, src, dst_is, src_is, co, signs, accumulate); break;
+    case 2: permute_nt<2>(c, p, dst, src, dst_is, src_is, co, signs, accumulate); break;
+    case 3: permute_nt<3>(c, p, dst, src, dst_is, src_is, co, signs, accumulate); break;
+    default: permute_nt<4>(c, p, dst, src, dst_is, src_is, co, signs, accumulate); break;
   }
   KCHECK(c);
 }

@@ -84,6 +84,9 @@ typedef struct {
   double level_shift;      /* sigma >= 0: (0h,0p) update t <- t + (RHS - D t)/(D - sigma) (the same
                               fixed point; smaller steps for strongly coupled problems); 0 = the
                               plain update t <- RHS/D */
+  int packed;              /* 1: the particle-particle ladder sum_{c<d} <ab||cd> tau_ij^cd on pair-packed
+                              operands (a<b, c<d, i<j per pair irrep; <ab||cd> stored packed, a
+                              quarter of the full size); 0: full pair compounds */
 } exp_config;
 
 /* Create a context: validates the config, builds the symmetry-blocked layouts

@@ -10,6 +10,7 @@
 #include "ccsd.h"
 #include "fs.h"
 #include "emu.h"
+#include "packed.h"
 
 static thread_local std::string g_err;
 
@@ -51,6 +52,7 @@ static void check_config(const exp_config* cfg) {
   if (cfg->diis_dim < 0 || cfg->diis_dim > EXP_MAX_DIIS) throw ExpError{EXP_EINVAL, "diis_dim must be in 0..8"};
   if (!(cfg->conv_tol > 0)) throw ExpError{EXP_EINVAL, "conv_tol must be > 0"};
   if (!(cfg->level_shift >= 0) || !std::isfinite(cfg->level_shift)) throw ExpError{EXP_EINVAL, "level_shift must be >= 0"};
+  if (cfg->packed != 0 && cfg->packed != 1) throw ExpError{EXP_EINVAL, "packed must be 0 or 1"};
   if (cfg->n_active < 0 || cfg->n_active > cfg->n_virt) throw ExpError{EXP_EINVAL, "n_active out of range"};
   if (cfg->n_active > 0) {
     if (!cfg->active_virt) throw ExpError{EXP_EINVAL, "null active_virt"};
@@ -194,6 +196,7 @@ extern "C" void exp_destroy(exp_ctx* x) {
   if (c.h_stats) cudaFreeHost(c.h_stats);
   fs_release(c);
   try { emu_release(c); } catch (...) {}
+  packed_release(c);
   ccsd_release(c);
   c.dfree_all();
   delete x;

@@ -10,6 +10,7 @@
 
 #include "ccsd.h"
 #include "emu.h"
+#include "packed.h"
 
 static const cplx ONE = {1.0, 0.0};
 static inline cplx C(double x) { return make_double2(x, 0.0); }
@@ -600,7 +601,10 @@ void ccsd_rhs(Ctx& c) {
   // hole-hole ladder: 1/2 sum_mn tau_mn^ab W_mnij
   einsum(c, "R2hh", C(0.5), {&tau, nullptr, "abmn"}, {&Wmnij, nullptr, "mnij"}, r2, "abij", true);
   // particle-particle ladder: 1/2 sum_ef <ab||ef> tau_ij^ef
-  einsum(c, "R2pp", C(0.5), {nullptr, &VVVV, "abef"}, {&tau, nullptr, "efij"}, r2, "abij", true);
+  if (c.cfg.packed)
+    packed_ladder(c, tau, r2);  // the same sum over c<d on pair-packed operands
+  else
+    einsum(c, "R2pp", C(0.5), {nullptr, &VVVV, "abef"}, {&tau, nullptr, "efij"}, r2, "abij", true);
   // W_abef's t1 term: -1/2 P(ab) sum_m t_m^b X_amij,  X_amij = sum_ef <am||ef> tau_ij^ef
   einsum(c, "Xamij", ONE, {nullptr, &VOVV, "amef"}, {&tau, nullptr, "efij"}, X, "amij", false);
   einsum(c, "R2x", C(-0.5), {&X, nullptr, "amij"}, {&t1, nullptr, "bm"}, r2, "abij", true,

@@ -249,6 +249,7 @@ struct Ctx {
 
   // emulation and driver state
   void* emu_state = nullptr;
+  void* packed_state = nullptr;  // packed particle-particle ladder (packed.cu)
   void* ccsd_state = nullptr;
 
   void* dalloc(size_t bytes);

@@ -1,0 +1,299 @@
+// Pair-packed antisymmetric compounds (p<q per pair irrep) and the packed
+// particle-particle ladder.  The blocked layouts of Sec. II.C store t2, tau and
+// <ab||cd> with full pair compounds; antisymmetry makes three quarters of
+// <ab||cd> and half of each tau column redundant, and the ladder of
+// Eq. (amplitudes) needs only
+//     Z_ij^ab = sum_{c<d} <ab||cd> tau_ij^cd,   r2_ij^ab += Z, with Z_ij^ba = -Z_ij^ab.
+// Packed operands are plain per-irrep matrices, so the product is one more
+// grouped GEMM (step 3 of the TTGT list, Sec. II.B) on the same kernels.
+#include <algorithm>
+#include <cstdio>
+
+#include "emu.h"
+#include "packed.h"
+
+static inline int imod(int a, int G) { return ((a % G) + G) % G; }
+
+void build_pair_table(Ctx& c, const Layout& L, bool rows, bool packed, PairTable& T) {
+  const int G = c.G;
+  if (G > PK_MAXG) throw ExpError{EXP_EINVAL, "packed pairs: too many irreps"};
+  const int ns = rows ? L.nrow : L.rank - L.nrow;
+  if (ns != 2) throw ExpError{EXP_EINVAL, "packed pairs: compound must have two slots"};
+  const int s0 = rows ? 0 : L.nrow, s1 = s0 + 1;
+  const Space& S0 = c.spaces[L.sp[s0]];
+  const Space& S1 = c.spaces[L.sp[s1]];
+  const int sg0 = L.sg[s0], sg1 = L.sg[s1];
+  if (packed && (L.sp[s0] != L.sp[s1] || sg0 != sg1))
+    throw ExpError{EXP_EINVAL, "packed pairs: slots of different spaces or signs"};
+  if (S0.gbase + S0.n > 32768 || S1.gbase + S1.n > 32768) throw ExpError{EXP_EINVAL, "packed pairs: too many spinors"};
+  const std::vector<int64_t>& tup = rows ? L.rtup : L.ctup;
+  auto in_block = [&](int g0, int g1) {
+    const int s = sg0 * g0 + sg1 * g1;
+    return (rows ? imod(s, G) : imod(-s, G));
+  };
+  T.G = G;
+  T.n.assign(G, 0);
+  T.off.assign(G, 0);
+  T.fn.assign(G, 0);
+  T.foff.assign(G, 0);
+  T.pair.clear();
+  T.full.clear();
+  T.inv.clear();
+  for (int g = 0; g < G; ++g) {
+    const int64_t fsz = rows ? L.rows[g] : L.cols[g];
+    if (fsz >= (int64_t(1) << 31)) throw ExpError{EXP_EINVAL, "packed pairs: block above 2^31"};
+    T.fn[g] = int32_t(fsz);
+    T.foff[g] = int32_t(T.inv.size());
+    T.off[g] = int32_t(T.pair.size());
+    const size_t inv0 = T.inv.size();
+    T.inv.resize(inv0 + size_t(fsz), 0);
+    auto full_index = [&](int g0, int x0, int g1, int x1) {
+      return int32_t(tup[size_t(g0) * G + g1] + int64_t(x0) * S1.cnt[g1] + x1);
+    };
+    auto code = [&](int g0, int x0, int g1, int x1) {
+      return int32_t(((S0.gbase + S0.off[g0] + x0) << 16) | (S1.gbase + S1.off[g1] + x1));
+    };
+    if (!packed) {  // every tuple, layout order
+      for (int g0 = 0; g0 < G; ++g0)
+        for (int g1 = 0; g1 < G; ++g1) {
+          if (in_block(g0, g1) != g) continue;
+          for (int x0 = 0; x0 < S0.cnt[g0]; ++x0)
+            for (int x1 = 0; x1 < S1.cnt[g1]; ++x1) {
+              const int32_t f = full_index(g0, x0, g1, x1);
+              const int32_t k = int32_t(T.pair.size()) - T.off[g];
+              T.pair.push_back(code(g0, x0, g1, x1));
+              T.full.push_back(f);
+              T.inv[inv0 + f] = k + 1;
+            }
+        }
+    } else {  // canonical p<q: irrep pairs g0 < g1 whole, g0 = g1 strict triangle
+      for (int g0 = 0; g0 < G; ++g0)
+        for (int g1 = g0; g1 < G; ++g1) {
+          if (in_block(g0, g1) != g) continue;
+          for (int x0 = 0; x0 < S0.cnt[g0]; ++x0)
+            for (int x1 = (g0 == g1 ? x0 + 1 : 0); x1 < S1.cnt[g1]; ++x1) {
+              const int32_t k = int32_t(T.pair.size()) - T.off[g];
+              T.pair.push_back(code(g0, x0, g1, x1));
+              T.full.push_back(full_index(g0, x0, g1, x1));
+              T.inv[inv0 + full_index(g0, x0, g1, x1)] = k + 1;
+              T.inv[inv0 + full_index(g1, x1, g0, x0)] = -(k + 1);
+            }
+        }
+    }
+    T.n[g] = int32_t(T.pair.size()) - T.off[g];
+  }
+  auto up = [&](const std::vector<int32_t>& v) {
+    int32_t* d = (int32_t*)c.dalloc(sizeof(int32_t) * std::max<size_t>(v.size(), 1));
+    if (!v.empty()) upload(c, d, v.data(), sizeof(int32_t) * v.size());
+    return d;
+  };
+  T.d_pair = up(T.pair);
+  T.d_full = up(T.full);
+  T.d_inv = up(T.inv);
+}
+
+PackDims pack_dims(const PairTable& R, const PairTable& C) {
+  PackDims D{};
+  D.G = R.G;
+  int64_t o = 0, fo = 0;
+  for (int g = 0; g < R.G; ++g) {
+    D.blk[g] = o;
+    D.fblk[g] = fo;
+    D.nr[g] = R.n[g];
+    D.nc[g] = C.n[g];
+    D.roff[g] = R.off[g];
+    D.coff[g] = C.off[g];
+    D.fnr[g] = R.fn[g];
+    D.fnc[g] = C.fn[g];
+    D.froff[g] = R.foff[g];
+    D.fcoff[g] = C.foff[g];
+    o += int64_t(R.n[g]) * C.n[g];
+    fo += int64_t(R.fn[g]) * C.fn[g];
+  }
+  D.blk[R.G] = o;
+  D.fblk[R.G] = fo;
+  return D;
+}
+
+// block of element e of a matrix with block offsets off[0..G]
+__device__ __forceinline__ int find_block(const int64_t* off, int G, int64_t e) {
+  int g = 0;
+  while (g + 1 < G && e >= off[g + 1]) ++g;
+  return g;
+}
+
+__global__ void __launch_bounds__(256) k_pack_gather(cplx* __restrict__ dst, int64_t dis, const cplx* __restrict__ src,
+                                                     int64_t sis, PackDims D, const int32_t* __restrict__ rfull,
+                                                     const int32_t* __restrict__ cfull) {
+  const int inst = blockIdx.y;
+  dst += inst * dis;
+  src += inst * sis;
+  const int64_t total = D.blk[D.G];
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total; e += int64_t(gridDim.x) * blockDim.x) {
+    const int g = find_block(D.blk, D.G, e);
+    const uint32_t loc = uint32_t(e - D.blk[g]);
+    const uint32_t p = loc / uint32_t(D.nc[g]), q = loc - p * uint32_t(D.nc[g]);
+    dst[e] = src[D.fblk[g] + int64_t(rfull[D.roff[g] + p]) * D.fnc[g] + cfull[D.coff[g] + q]];
+  }
+}
+
+// full element (R, C): entries kr = |inv_r| - 1, kc = |inv_c| - 1, sign = product of
+// the inv signs (times coef); a p = q row or column has no packed entry
+__global__ void __launch_bounds__(256) k_pack_scatter(cplx* __restrict__ dst, int64_t dis, const cplx* __restrict__ src,
+                                                      int64_t sis, PackDims D, const int32_t* __restrict__ rinv,
+                                                      const int32_t* __restrict__ cinv, int neg, int acc) {
+  const int inst = blockIdx.y;
+  dst += inst * dis;
+  src += inst * sis;
+  const int64_t total = D.fblk[D.G];
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total; e += int64_t(gridDim.x) * blockDim.x) {
+    const int g = find_block(D.fblk, D.G, e);
+    const uint32_t loc = uint32_t(e - D.fblk[g]);
+    const uint32_t R = loc / uint32_t(D.fnc[g]), Cc = loc - R * uint32_t(D.fnc[g]);
+    const int ir = rinv[D.froff[g] + R], ic = cinv[D.fcoff[g] + Cc];
+    if (ir == 0 || ic == 0) {
+      if (!acc) dst[e] = make_double2(0.0, 0.0);
+      continue;
+    }
+    const int kr = (ir < 0 ? -ir : ir) - 1, kc = (ic < 0 ? -ic : ic) - 1;
+    const long long sgn = (((ir < 0) ^ (ic < 0) ^ neg) != 0) ? (long long)0x8000000000000000ull : 0ll;
+    const cplx v = src[D.blk[g] + int64_t(kr) * D.nc[g] + kc];
+    const double vr = __longlong_as_double(__double_as_longlong(v.x) ^ sgn);
+    const double vi = __longlong_as_double(__double_as_longlong(v.y) ^ sgn);
+    if (acc) {
+      const cplx o = dst[e];
+      dst[e] = make_double2(o.x + vr, o.y + vi);
+    } else {
+      dst[e] = make_double2(vr, vi);
+    }
+  }
+}
+
+static int pk_blocks(Ctx& c, int64_t n) {
+  return int(std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, int64_t(std::max(c.sm_count, 1)) * 8)));
+}
+
+void launch_pack_gather(Ctx& c, cplx* dst, int64_t dis, const cplx* src, int64_t sis, const PackDims& D,
+                        const PairTable& R, const PairTable& C) {
+  if (D.blk[D.G] == 0) return;
+  k_pack_gather<<<dim3(pk_blocks(c, D.blk[D.G]), c.ninst), 256, 0, c.stream>>>(dst, dis, src, sis, D, R.d_full,
+                                                                              C.d_full);
+  KCHECK(c);
+}
+
+void launch_pack_scatter(Ctx& c, cplx* dst, int64_t dis, const cplx* src, int64_t sis, const PackDims& D,
+                         const PairTable& R, const PairTable& C, double coef, bool accumulate) {
+  if (coef != 1.0 && coef != -1.0) throw ExpError{EXP_EINVAL, "packed scatter: coefficient must be +-1"};
+  if (D.fblk[D.G] == 0) return;
+  k_pack_scatter<<<dim3(pk_blocks(c, D.fblk[D.G]), c.ninst), 256, 0, c.stream>>>(
+      dst, dis, src, sis, D, R.d_inv, C.d_inv, coef < 0 ? 1 : 0, accumulate ? 1 : 0);
+  KCHECK(c);
+}
+
+// ---------------------------------------------------------------------------
+// The packed ladder.  Operands per pair irrep g:
+//   V_P[g]   = <ab||cd>,     rows a<b, cols c<d   (generated once, packed)
+//   T_P[g]   = tau_ij^cd,    rows c<d, cols i<j   (gathered from tau every call)
+//   Z_P[g]   = V_P[g] T_P[g]                      (emulated or FP64 grouped GEMM)
+// then r2_ij^ab += Z with the signs of the pair swaps.
+struct PackedLadder {
+  PairTable vv, oo;
+  PackDims dt{}, dv{};
+  Tensor V, T, Z;
+  EinsumPlan* plan = nullptr;  // owned by c.plans (registered as the "R2pp" contraction)
+};
+
+static Layout packed_layout(const PairTable& R, const PairTable& C) {
+  Layout L;
+  L.rank = 2;
+  L.nrow = 1;
+  L.G = R.G;
+  L.rows.assign(R.G, 0);
+  L.cols.assign(R.G, 0);
+  L.blk_off.assign(R.G, 0);
+  int64_t o = 0;
+  for (int g = 0; g < R.G; ++g) {
+    L.rows[g] = R.n[g];
+    L.cols[g] = C.n[g];
+    L.blk_off[g] = o;
+    o += int64_t(R.n[g]) * C.n[g];
+  }
+  L.size = o;
+  return L;
+}
+
+static PackedLadder* ladder_state(Ctx& c, const Tensor& tau) {
+  if (c.packed_state) return (PackedLadder*)c.packed_state;
+  PackedLadder* s = new PackedLadder();
+  c.packed_state = s;
+  build_pair_table(c, tau.L, true, true, s->vv);   // (c, d) of tau = (a, b) of r2
+  build_pair_table(c, tau.L, false, true, s->oo);  // (i, j)
+  s->dt = pack_dims(s->vv, s->oo);
+  s->dv = pack_dims(s->vv, s->vv);
+  const Layout LV = packed_layout(s->vv, s->vv), LT = packed_layout(s->vv, s->oo);
+  Tensor* v = new_tensor(c, LV, false);
+  Tensor* t = new_tensor(c, LT, false);
+  Tensor* z = new_tensor(c, LT, false);
+  s->V = *v;
+  s->T = *t;
+  s->Z = *z;
+  delete v;
+  delete t;
+  delete z;
+  launch_generate_pairs(c, s->V.d, s->V.is, s->dv, s->vv, s->vv);
+  EinsumPlan* P = new EinsumPlan();
+  c.plans["R2pp"].reset(P);
+  s->plan = P;
+  P->A = &s->V;
+  P->B = &s->T;
+  P->permC = true;
+  P->C2 = s->Z;
+  P->alpha = make_double2(1.0, 0.0);
+  P->gemm_beta = false;
+  P->g = make_gemm_plan(c, LV, LT, LT);
+  P->emulate = emu_wanted(c, P->g, "R2pp");
+  if (P->emulate) P->emu = emu_plan(c, P->g, &s->V, &s->T, true, false);
+  return s;
+}
+
+void packed_ladder(Ctx& c, const Tensor& tau, Tensor& r2) {
+  PackedLadder* s = ladder_state(c, tau);
+  EinsumPlan* P = s->plan;
+  const bool prof = c.profile;
+  cudaEvent_t pe[2] = {nullptr, nullptr};
+  if (prof) {
+    for (auto& e : pe) CK(cudaEventCreate(&e));
+    CK(cudaEventRecord(c.pev0, c.stream));
+  }
+  launch_pack_gather(c, s->T.d, s->T.is, tau.d, tau.is, s->dt, s->vv, s->oo);
+  if (prof) CK(cudaEventRecord(pe[0], c.stream));
+  if (P->emulate)
+    emu_run(c, P->emu, P->g, s->V.d, s->T.d, s->Z.d, s->V.is, s->T.is, s->Z.is, P->alpha, false);
+  else
+    launch_gemm_fp64(c, P->g, s->V.d, s->T.d, s->Z.d, s->V.is, s->T.is, s->Z.is, P->alpha, false);
+  if (prof) CK(cudaEventRecord(pe[1], c.stream));
+  launch_pack_scatter(c, r2.d, r2.is, s->Z.d, s->Z.is, s->dt, s->vv, s->oo, 1.0, true);
+  if (prof) {
+    CK(cudaEventRecord(c.pev1, c.stream));
+    CK(cudaEventSynchronize(c.pev1));
+    float ms = 0.f, m_in = 0.f, m_g = 0.f, m_out = 0.f;
+    CK(cudaEventElapsedTime(&ms, c.pev0, c.pev1));
+    CK(cudaEventElapsedTime(&m_in, c.pev0, pe[0]));
+    CK(cudaEventElapsedTime(&m_g, pe[0], pe[1]));
+    CK(cudaEventElapsedTime(&m_out, pe[1], c.pev1));
+    for (auto& e : pe) cudaEventDestroy(e);
+    int64_t M = 0, N = 0, K = 0;
+    for (auto& q : P->g.h_probs) { M = std::max<int64_t>(M, q.M); N = std::max<int64_t>(N, q.N); K = std::max<int64_t>(K, q.K); }
+    fprintf(stderr, "[exp_phase] %-8s in %7.3f  gemm %7.3f  out %7.3f ms\n", "R2pp", m_in, m_g, m_out);
+    fprintf(stderr,
+            "[exp_profile] %-8s %9.3f ms  %10.3g cMAC  %7.1f GF/s  probs=%d maxM=%lld maxN=%lld maxK=%lld perm=011 emu=%d "
+            "packed\n",
+            "R2pp", ms, double(P->g.flops_mac) * c.ninst, 8.0 * double(P->g.flops_mac) * c.ninst / (ms * 1e6),
+            P->g.n_probs, (long long)M, (long long)N, (long long)K, P->emulate);
+  }
+}
+
+void packed_release(Ctx& c) {
+  delete (PackedLadder*)c.packed_state;  // device memory belongs to the context's allocator
+  c.packed_state = nullptr;
+}

@@ -4,6 +4,9 @@
 // synthetic Hamiltonian of Eq. (ham) straight into blocked layouts), the
 // energy denominators of Eq. (amplitudes), and the tau builders.
 #include "engine.h"
+#include "packed.h"
+
+#include <algorithm>
 
 #define EXP_CHUNK 4096
 
@@ -285,5 +288,51 @@ void launch_tau(Ctx& c, cplx* dst, int64_t dst_is, const cplx* t2, const cplx* t
   if (!n_chunks) return;
   k_tau<<<dim3(n_chunks, c.ninst), 256, 0, c.stream>>>(dst, dst_is, t2, t1, t_is, t1_index, d_tasks,
                                                        d_chunks, c0, c1, c2, c.no, c.no);
+  KCHECK(c);
+}
+
+// ---------------------------------------------------------------------------
+// Integrals straight into a pair-packed matrix: element (p, q; r, s) of block g
+// with the pairs (p, q) from the row table and (r, s) from the column table.
+__global__ void __launch_bounds__(256) k_generate_pairs(cplx* __restrict__ dst, int64_t is, PackDims D,
+                                                        const int32_t* __restrict__ rpair,
+                                                        const int32_t* __restrict__ cpair, int n,
+                                                        const uint64_t* __restrict__ seeds,
+                                                        const double* __restrict__ scales,
+                                                        const int* __restrict__ genmap) {
+  const int inst = blockIdx.y;
+  dst += inst * is;
+  const uint64_t seed = seeds[inst];
+  const double sc = scales[inst];
+  const int64_t total = D.blk[D.G];
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total; e += int64_t(gridDim.x) * blockDim.x) {
+    int g = 0;
+    while (g + 1 < D.G && e >= D.blk[g + 1]) ++g;
+    const uint32_t loc = uint32_t(e - D.blk[g]);
+    const uint32_t p = loc / uint32_t(D.nc[g]), q = loc - p * uint32_t(D.nc[g]);
+    const int32_t rc = rpair[D.roff[g] + p], cc = cpair[D.coff[g] + q];
+    int gi[4] = {rc >> 16, rc & 0xFFFF, cc >> 16, cc & 0xFFFF};
+    bool ghost = false;
+    if (genmap)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        gi[k] = genmap[gi[k]];
+        ghost |= gi[k] < 0;
+      }
+    if (ghost) {
+      dst[e] = make_double2(0.0, 0.0);
+      continue;
+    }
+    const cplx v = v_element(uint64_t(gi[0]), uint64_t(gi[1]), uint64_t(gi[2]), uint64_t(gi[3]), uint64_t(n), seed);
+    dst[e] = make_double2(sc * v.x, sc * v.y);
+  }
+}
+
+void launch_generate_pairs(Ctx& c, cplx* dst, int64_t is, const PackDims& D, const PairTable& R, const PairTable& C) {
+  const int64_t total = D.blk[D.G];
+  if (total == 0) return;
+  const int blocks = int(std::min<int64_t>((total + 255) / 256, int64_t(std::max(c.sm_count, 1)) * 8));
+  k_generate_pairs<<<dim3(blocks, c.ninst), 256, 0, c.stream>>>(dst, is, D, R.d_pair, C.d_pair, c.n_gen, c.d_seed,
+                                                                c.d_scale, c.d_genmap);
   KCHECK(c);
 }

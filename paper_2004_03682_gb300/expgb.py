@@ -42,7 +42,8 @@ class Config(C.Structure):
                 ("precision", C.c_int), ("n_slices", C.c_int), ("diis_dim", C.c_int),
                 ("conv_tol", C.c_double), ("max_iter", C.c_int), ("guess", C.c_int),
                 ("emu_min_macs", C.c_double), ("n_active", C.c_int),
-                ("active_virt", C.POINTER(C.c_int32)), ("level_shift", C.c_double)]
+                ("active_virt", C.POINTER(C.c_int32)), ("level_shift", C.c_double),
+                ("packed", C.c_int)]
 
 
 class IterInfo(C.Structure):
@@ -155,7 +156,8 @@ class Context:
 
     def __init__(self, n_occ, n_virt, irrep_occ, irrep_virt, eps_occ, eps_virt, n_inst=1,
                  precision=EXP_FP64, n_slices=5, diis_dim=6, conv_tol=1e-9, max_iter=500,
-                 guess=EXP_GUESS_MP2, device=0, emu_min_macs=0.0, active=None, level_shift=0.0):
+                 guess=EXP_GUESS_MP2, device=0, emu_min_macs=0.0, active=None, level_shift=0.0,
+                 packed=True):
         import torch
         self._torch = torch
         L = lib()
@@ -178,7 +180,7 @@ class Context:
             self._keep.append(ac)
         cfg = Config(self.n_inst, self.n_occ, self.n_virt, len(io), pio, piv, peo, pev,
                      int(precision), int(n_slices), int(diis_dim), float(conv_tol), int(max_iter),
-                     int(guess), float(emu_min_macs), self.n_active, pa, float(level_shift))
+                     int(guess), float(emu_min_macs), self.n_active, pa, float(level_shift), int(bool(packed)))
         h = C.c_void_p()
         st = L.exp_create(C.byref(cfg), C.byref(self.alloc.struct), C.c_void_p(self.stream.cuda_stream),
                           C.byref(h))

@@ -48,7 +48,7 @@ def _cfg(expgb, **over):
                        io.ctypes.data_as(C.POINTER(C.c_int32)), iv.ctypes.data_as(C.POINTER(C.c_int32)),
                        eo.ctypes.data_as(C.POINTER(C.c_double)), ev.ctypes.data_as(C.POINTER(C.c_double)),
                        d["precision"], d["n_slices"], d["diis_dim"], d["conv_tol"], d["max_iter"], d["guess"], 0.0,
-                       d.get("n_active", 0), None, d.get("level_shift", 0.0))
+                       d.get("n_active", 0), None, d.get("level_shift", 0.0), d.get("packed", 1))
     return cfg, keep
 
 

@@ -61,9 +61,16 @@ __device__ __forceinline__ double nanmax(double a, double b) { return (b != b ||
 struct MaxOp { __device__ double operator()(double a, double b) const { return nanmax(a, b); } };
 struct AddOp { __device__ double operator()(double a, double b) const { return a + b; } };
 
-// t_new = R / D over the whole amplitude vector; e = t_new - t.  Writes t_new and
-// e into the next DIIS slot; per-CTA max |e|.  Frozen (converged) instances skip.
-__global__ void __launch_bounds__(RED_THREADS) k_update(const cplx* __restrict__ R, const double* __restrict__ D,
+// Dinv = 1 / (D - sigma), once per context (the update then needs no FP64 divide)
+__global__ void k_inv_denom(const double* __restrict__ D, double* __restrict__ Dinv, int64_t n, double shift) {
+  for (int64_t k = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; k < n; k += int64_t(gridDim.x) * blockDim.x)
+    Dinv[k] = 1.0 / (D[k] - shift);
+}
+
+// t_new = (R - sigma t) / (D - sigma) over the whole amplitude vector (sigma = 0:
+// R / D); e = t_new - t.  Writes t_new and e into the next DIIS slot and the
+// per-CTA max |e|^2 (k_finalize_update takes the root).  Frozen instances skip.
+__global__ void __launch_bounds__(RED_THREADS) k_update(const cplx* __restrict__ R, const double* __restrict__ Dinv,
                                                         const cplx* __restrict__ T, cplx* __restrict__ Tn,
                                                         cplx* __restrict__ En, int64_t namp, int dim,
                                                         const int* __restrict__ state, double* __restrict__ part,
@@ -78,15 +85,13 @@ __global__ void __launch_bounds__(RED_THREADS) k_update(const cplx* __restrict__
   if (!st[2]) {
     for (int64_t k = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; k < namp; k += int64_t(gridDim.x) * blockDim.x) {
       const cplx r = R[off + k];
-      const double d = D[off + k];
+      const double q = Dinv[off + k];
       const cplx t = T[off + k];
-      // t_new = (RHS - sigma t) / (D - sigma); sigma = 0 gives RHS / D
-      const cplx tn = shift == 0.0 ? make_double2(r.x / d, r.y / d)
-                                   : make_double2((r.x - shift * t.x) / (d - shift), (r.y - shift * t.y) / (d - shift));
+      const cplx tn = make_double2(fma(-shift, t.x, r.x) * q, fma(-shift, t.y, r.y) * q);
       const cplx e = make_double2(tn.x - t.x, tn.y - t.y);
       Tn[soff + k] = tn;
       En[soff + k] = e;
-      m = nanmax(m, hypot(e.x, e.y));
+      m = nanmax(m, fma(e.x, e.x, e.y * e.y));
     }
   }
   m = block_reduce(m, MaxOp(), sh);
@@ -108,6 +113,7 @@ __global__ void k_finalize_update(const double* __restrict__ part, int nb, int* 
     if (!(v == v) || isinf(v)) bad = true;
     m = nanmax(m, v);
   }
+  m = sqrt(m);  // the update kernels reduce |e|^2
   s[0] = bad ? INFINITY : m;
   s[4] = bad ? 1.0 : 0.0;
   if (bad) {  // this instance failed: freeze it as failed (2), the others go on
@@ -364,6 +370,8 @@ struct CcsdState {
   const Tensor* Vd = nullptr;  // <ab||ij> in the t2 layout
   Tensor Tn2;                  // view used for the energy tau (scratch)
   cplx* d_taun = nullptr;      // tau of t_new
+  double* d_Dinv = nullptr;    // 1 / (D - sigma), filled on the first (eager) iteration
+  bool dinv_ready = false;
 };
 
 static CcsdState& S(Ctx& c) { return *reinterpret_cast<CcsdState*>(c.ccsd_state); }
@@ -380,6 +388,7 @@ void ccsd_setup(Ctx& c) {
   c.d_T = (cplx*)c.dalloc(sizeof(cplx) * na * ni);
   c.d_R = (cplx*)c.dalloc(sizeof(cplx) * na * ni);
   c.d_D = (double*)c.dalloc(sizeof(double) * na * ni);
+  s->d_Dinv = (double*)c.dalloc(sizeof(double) * na * ni);
   CK(cudaMemsetAsync(c.d_T, 0, sizeof(cplx) * na * ni, c.stream));
   const int dslots = std::max(c.cfg.diis_dim, 1);
   c.d_diis_t = (cplx*)c.dalloc(sizeof(cplx) * na * ni * dslots);
@@ -508,12 +517,6 @@ void ccsd_energy_of(Ctx& c, const cplx* T, bool skip_frozen) {
 
 // ---------------------------------------------------------------------------
 // The right-hand sides R1, R2 of the T1 and T2 equations at the current T.
-static void tau_build(Ctx& c, Tensor& dst, double c0, double c1, double c2) {
-  CcsdState& s = S(c);
-  launch_tau(c, dst.d, dst.is, c.t2.d, c.t1.d, c.namp, s.d_t1i, s.t2tasks.d_tasks, s.t2tasks.d_chunks,
-             s.t2tasks.n_chunks, c0, c1, c2);
-}
-
 static void copy_int(Ctx& c, Tensor& dst, const Tensor* src) {
   if (src->L.size != dst.L.size) throw ExpError{EXP_EINVAL, "copy between different layouts"};
   CK(cudaMemcpy2DAsync(dst.d, dst.is * sizeof(cplx), src->d, src->is * sizeof(cplx), dst.L.size * sizeof(cplx),
@@ -547,9 +550,12 @@ void ccsd_rhs(Ctx& c) {
   Tensor& Z = *work_tensor(c, "Zmbji", L4(c, O, +1, V, +1, O, -1, O, -1, 3));
   CcsdState& s = S(c);
 
-  tau_build(c, tau, 1.0, 1.0, -1.0);
-  tau_build(c, taut, 1.0, 0.5, -0.5);
-  tau_build(c, zeta, 0.5, 1.0, 0.0);
+  // tau = t2 + t1^t1 (antisymmetrised), taut = t2 + t1^t1 / 2, zeta = t2 / 2 + t_i^a t_j^b
+  launch_tau3(c, tau.d, taut.d, zeta.d, tau.is, c.t2.d, c.t1.d, c.namp, s.d_t1i, s.t2tasks.d_tasks,
+              s.t2tasks.d_chunks, s.t2tasks.n_chunks);
+  // pair-packed operands: tau over c<d, i<j once per iteration for the four products that sum over a tau pair
+  const bool packed = c.cfg.packed != 0;
+  if (packed) packed_tau(c, tau);
 
   // F_ae = sum_mf t_m^f <ma||fe> - 1/2 sum_mnf taut_mn^af <mn||ef>       (f_ov = 0, f diagonal)
   einsum(c, "Fae1", ONE, {nullptr, &OVVV, "mafe"}, {&t1, nullptr, "fm"}, Fae, "ae", false);
@@ -567,7 +573,10 @@ void ccsd_rhs(Ctx& c) {
   }
   einsum(c, "Wmnij1", ONE, {nullptr, &OOOV, "mnie"}, {&t1, nullptr, "ej"}, Wmnij, "mnij", true,
          {{1.0, "mnij"}, {-1.0, "mnji"}});
-  einsum(c, "Wmnij2", C(0.5), {nullptr, &OOVV, "mnef"}, {&tau, nullptr, "efij"}, Wmnij, "mnij", true);
+  if (packed)
+    packed_wmnij(c, Wmnij);
+  else
+    einsum(c, "Wmnij2", C(0.5), {nullptr, &OOVV, "mnef"}, {&tau, nullptr, "efij"}, Wmnij, "mnij", true);
   // W_mbej = <mb||ej> + sum_f t_j^f <mb||ef> - sum_n t_n^b <mn||ej> - sum_nf zeta_jn^fb <mn||ef>
   {
     const int arg[4] = {2, 0, 3, 1};  // storage (e, m, j, b) <- V(m, b, e, j)
@@ -599,14 +608,20 @@ void ccsd_rhs(Ctx& c) {
   einsum(c, "R2b", C(-1.0), {&t2, nullptr, "abim"}, {&Fq, nullptr, "mj"}, r2, "abij", true,
          {{1.0, "abij"}, {-1.0, "abji"}});
   // hole-hole ladder: 1/2 sum_mn tau_mn^ab W_mnij
-  einsum(c, "R2hh", C(0.5), {&tau, nullptr, "abmn"}, {&Wmnij, nullptr, "mnij"}, r2, "abij", true);
+  if (packed)
+    packed_hh(c, Wmnij, r2);
+  else
+    einsum(c, "R2hh", C(0.5), {&tau, nullptr, "abmn"}, {&Wmnij, nullptr, "mnij"}, r2, "abij", true);
   // particle-particle ladder: 1/2 sum_ef <ab||ef> tau_ij^ef
-  if (c.cfg.packed)
-    packed_ladder(c, tau, r2);  // the same sum over c<d on pair-packed operands
+  if (packed)
+    packed_ladder(c, r2);
   else
     einsum(c, "R2pp", C(0.5), {nullptr, &VVVV, "abef"}, {&tau, nullptr, "efij"}, r2, "abij", true);
   // W_abef's t1 term: -1/2 P(ab) sum_m t_m^b X_amij,  X_amij = sum_ef <am||ef> tau_ij^ef
-  einsum(c, "Xamij", ONE, {nullptr, &VOVV, "amef"}, {&tau, nullptr, "efij"}, X, "amij", false);
+  if (packed)
+    packed_xamij(c, X);
+  else
+    einsum(c, "Xamij", ONE, {nullptr, &VOVV, "amef"}, {&tau, nullptr, "efij"}, X, "amij", false);
   einsum(c, "R2x", C(-0.5), {&X, nullptr, "amij"}, {&t1, nullptr, "bm"}, r2, "abij", true,
          {{1.0, "abij"}, {-1.0, "baij"}});
   // ring: P(ij)P(ab) [ sum_me t_im^ae W_mbej - sum_me t_i^e t_m^a <mb||ej> ]
@@ -673,9 +688,16 @@ void ccsd_update_step(Ctx& c, const std::function<void(double*, int)>& upd, bool
 
 // One full iteration: RHS, update, residual, energy, DIIS.
 void ccsd_iteration(Ctx& c) {
+  CcsdState& s = S(c);
+  if (!s.dinv_ready) {  // D and sigma are fixed for the context's life
+    k_inv_denom<<<dim3(grid_for(c.namp * c.ninst)), 256, 0, c.stream>>>(c.d_D, s.d_Dinv, c.namp * c.ninst,
+                                                                        c.cfg.level_shift);
+    KCHECK(c);
+    s.dinv_ready = true;
+  }
   ccsd_rhs(c);
   ccsd_update_step(c, [&](double* part, int nb) {
-    k_update<<<dim3(nb, c.ninst), RED_THREADS, 0, c.stream>>>(c.d_R, c.d_D, c.d_T, c.d_diis_t, c.d_diis_e, c.namp,
+    k_update<<<dim3(nb, c.ninst), RED_THREADS, 0, c.stream>>>(c.d_R, s.d_Dinv, c.d_T, c.d_diis_t, c.d_diis_e, c.namp,
                                                               c.cfg.diis_dim, c.d_diis_state, part, c.cfg.level_shift);
     KCHECK(c);
   }, true);

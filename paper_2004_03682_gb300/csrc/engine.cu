@@ -463,7 +463,12 @@ void einsum(Ctx& c, const std::string& site, cplx alpha, Operand A, Operand B, T
     // operand with the larger free extent takes the A role (C^T = B^T A^T).
     if (c.cfg.precision == EXP_EMU_BF16) {
       const bool identity0 = terms.empty() && FA + FB == clab && C.L.nrow == int(FA.size());
-      if (!identity0 && free_extent(c, B, FB) > 2.0 * free_extent(c, A, FA)) {
+      const double ea = free_extent(c, A, FA), eb = free_extent(c, B, FB);
+      // a small output over a long contraction, integral times amplitudes: the
+      // amplitudes (sliced every iteration) go to A, the integral (sliced once) to B
+      const bool small_out = A.v && B.t && ea <= 64.0 && eb <= 64.0;
+      // (a direct write is given up only for a tiny output, where the permute is free)
+      if ((!identity0 && eb > 2.0 * ea) || (small_out && (!identity0 || C.L.size <= (1 << 16)))) {
         std::swap(A, B);
         split_labels();
         P->swapped = true;

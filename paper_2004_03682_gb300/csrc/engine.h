@@ -181,6 +181,9 @@ void launch_fill_denom(Ctx& c, double* dst, int64_t inst_stride, const GenTask* 
 void launch_tau(Ctx& c, cplx* dst, int64_t dst_is, const cplx* t2, const cplx* t1,
                 int64_t t_is, const int32_t* t1_index, const GenTask* d_tasks,
                 const ChunkRef* d_chunks, int n_chunks, double c0, double c1, double c2);
+void launch_tau3(Ctx& c, cplx* tau, cplx* taut, cplx* zeta, int64_t dst_is, const cplx* t2, const cplx* t1,
+                 int64_t t_is, const int32_t* t1_index, const GenTask* d_tasks, const ChunkRef* d_chunks,
+                 int n_chunks);
 void launch_gemm_fp64(Ctx& c, const GemmPlan& g, const cplx* A, const cplx* B, cplx* C,
                       int64_t a_is, int64_t b_is, int64_t c_is, cplx alpha, bool beta);
 

@@ -128,9 +128,10 @@ __global__ void __launch_bounds__(256) k_fs_update(const cplx* __restrict__ R, c
         const cplx r = R[off + k], x = X[off + k];
         const double d0 = D0[off + k], df = Dfs[off + k];
         const double rr = r.x - d0 * t.x - x.x, ri = r.y - d0 * t.y - x.y;
-        e = make_double2(rr / df, ri / df);
+        const double q = 1.0 / df;
+        e = make_double2(rr * q, ri * q);
         tn = make_double2(t.x + e.x, t.y + e.y);
-        const double ae = hypot(e.x, e.y);
+        const double ae = fma(e.x, e.x, e.y * e.y);  // |e|^2: k_finalize_update takes the root
         m = (ae != ae || ae > m) ? ae : m;  // NaN-propagating max
       }
       Tn[soff + k] = tn;

@@ -36,7 +36,6 @@ constexpr int BM = 128;        // rows per tile (tcgen05 M)
 constexpr int KB = 32;         // real K per smem k-block (4 core matrices of 8 bf16)
 constexpr int BETA = 7;        // bits per slice
 constexpr int KC_BLOCKS = 16;  // k-blocks per exact chunk: KC = 512 real terms
-constexpr int STAGES = 3;
 constexpr int THREADS = 320;   // 10 warps: producer, MMA issuer, 8 epilogue warps
 constexpr int EPI_WARPS = 8;
 #define EXP_ZERO (-1100)       // exponent of an all-zero row / column (any x 2^-EXP_ZERO stays 0)
@@ -55,7 +54,9 @@ struct Shape {
   static constexpr int B_STAGE = S * B_TILE * 2;
   static constexpr int STAGE = A_STAGE + B_STAGE;
   static constexpr int ACC = S * BN;             // TMEM columns per accumulator buffer
+  static constexpr int STAGES = S <= 5 ? 4 : 3;  // as many stages as 227 KB of shared memory holds
   static constexpr int SMEM = STAGES * STAGE + 1024 + 256;
+  static_assert(SMEM <= 232448, "shared memory");
   static_assert(2 * ACC <= 512, "TMEM");
   static_assert(S * BN <= 256, "MMA N");
   static_assert(BN % 16 == 0, "N multiple of 16");
@@ -67,13 +68,13 @@ struct EmuProb {
   int64_t a_ex, b_ex;           // offsets of the exponent arrays (per instance)
   int64_t ws;                   // split-K partials offset (complex, per instance)
   int32_t M, N, K, Kp;          // Kp = 2 Kh, Kh = K rounded up to 16
-  int32_t tiles_m, tiles_n, tile0, bt0;  // tile0 / at0 / bt0: first GEMM / split-A / split-B item
+  int32_t tiles_m, tiles_n, tile0, pad0;  // tile0: first GEMM work item
   int32_t ksplit, kcb, arows, brows;     // K splits, k-blocks per split (multiple of KC_BLOCKS),
                                          // rows stored per A / B slice tile (a problem with a
                                          // single row / column tile keeps only its 8-row groups
                                          // in use: a prefix of the canonical tile)
-  int32_t at0, pad0;
-  int64_t red0;  // first output of this problem in the split-K reduction order
+  int64_t au0, bu0;  // first split-A / split-B unit of this problem (units: 8-groups of one row / column)
+  int64_t red0;      // first output of this problem in the split-K reduction order
 };
 
 // ---------------------------------------------------------------------------
@@ -226,6 +227,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                int64_t bsl_is, int64_t aex_is, int64_t bex_is, int64_t c_is, cplx alpha, int alpha_e, int beta,
                int* __restrict__ gerr, cplx* __restrict__ ws, int64_t ws_is) {
   using SH = Shape<S>;
+  constexpr int STAGES = SH::STAGES;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)((uintptr_t(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* full = (uint64_t*)(smem + STAGES * SH::STAGE);
@@ -580,19 +582,19 @@ __device__ __forceinline__ int64_t kpos_off(int r, int p, int tile_elems, int S)
   return int64_t(p / KB) * S * tile_elems + core_off(r, p % KB);
 }
 template <int S, bool FUSE_EXP>
-__global__ void __launch_bounds__(256) k_split_a(const EmuProb* __restrict__ probs, int nprobs, int n_items,
+__global__ void __launch_bounds__(256) k_split_a(const EmuProb* __restrict__ probs, int nprobs, int64_t total,
                                                  const cplx* __restrict__ A, int64_t a_is, int* __restrict__ ex,
                                                  int64_t ex_is, __nv_bfloat16* __restrict__ out, int64_t out_is) {
-  constexpr int UA = BM * (KB / 8);
   const int inst = blockIdx.y;
-  const int64_t total = int64_t(n_items) * UA;  // a multiple of 32: lanes of a warp stay together
+  // units per item = stored rows x 4, a multiple of 32: the lanes of a warp share a problem
   for (int64_t U = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; U < total; U += int64_t(gridDim.x) * blockDim.x) {
-    const int t = int(U / UA), u = int(U - int64_t(t) * UA);
     int pi = 0;
-    while (pi + 1 < nprobs && t >= probs[pi + 1].at0) ++pi;
+    while (pi + 1 < nprobs && U >= probs[pi + 1].au0) ++pi;
     const EmuProb& P = probs[pi];
+    const int UA = P.arows * (KB / 8);
+    const int64_t lu = U - P.au0;
+    const int lt = int(lu / UA), u = int(lu - int64_t(lt) * UA);
     const int nkb = P.Kp / KB, nkh = nkh_of(P), Kh = kh_of(P);
-    const int lt = t - P.at0;
     const int mt = lt / nkh, kbh = lt % nkh;
     const int r = u >> 2, g = u & 3;
     const int gi = mt * BM + r;
@@ -643,26 +645,26 @@ __global__ void __launch_bounds__(256) k_split_a(const EmuProb* __restrict__ pro
 // kbh of the half); unit = (column j, 8-group), lanes along j so the strided column
 // reads coalesce; grid-stride over all units.
 template <int S>
-__global__ void __launch_bounds__(256) k_split_b(const EmuProb* __restrict__ probs, int nprobs, int n_items,
+__global__ void __launch_bounds__(256) k_split_b(const EmuProb* __restrict__ probs, int nprobs, int64_t total,
                                                  const cplx* __restrict__ B, int64_t b_is, const int* __restrict__ ex,
                                                  int64_t ex_is, __nv_bfloat16* __restrict__ out, int64_t out_is) {
   using SH = Shape<S>;
   constexpr int NJ = SH::BN / 2;
-  constexpr int UB = NJ * (KB / 8);
   const int inst = blockIdx.y;
-  const int64_t total = int64_t(n_items) * UB;
   for (int64_t U = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; U < total; U += int64_t(gridDim.x) * blockDim.x) {
-    const int t = int(U / UB), u = int(U - int64_t(t) * UB);
     int pi = 0;
-    while (pi + 1 < nprobs && t >= probs[pi + 1].bt0) ++pi;
+    while (pi + 1 < nprobs && U >= probs[pi + 1].bu0) ++pi;
     const EmuProb& P = probs[pi];
+    const int nj = P.brows / 2;  // stored columns per tile (NJ unless compact)
+    const int UB = nj * (KB / 8);
+    const int64_t lu = U - P.bu0;
+    const int lt = int(lu / UB), u = int(lu - int64_t(lt) * UB);
     const int nkb = P.Kp / KB, nkh = nkh_of(P), Kh = kh_of(P);
-    const int lt = t - P.bt0;
     const int nt = lt / nkh, kbh = lt % nkh;
-    const int jl = u % NJ, g = u / NJ;
+    const int jl = u % nj, g = u / nj;
     const int gj = nt * NJ + jl;
     const int k0 = kbh * KB + g * 8;
-    if (k0 >= Kh || 2 * jl >= P.brows) continue;
+    if (k0 >= Kh) continue;
     const cplx* b = B + inst * b_is + P.b_src;
     double xr[8], xi[8];
     const int sh = gj < P.N ? -ex[inst * ex_is + P.b_ex + gj] : 0;
@@ -770,7 +772,8 @@ struct EmuPlan {
   int S = 5;
   std::vector<EmuProb> h;
   EmuProb* d = nullptr;
-  int n_tiles = 0, n_atiles = 0, n_btiles = 0;  // GEMM work items, split-A / split-B items
+  int n_tiles = 0;                    // GEMM work items
+  int64_t n_aunits = 0, n_bunits = 0;  // split-A / split-B thread units
   int total_rows = 0, total_cols = 0;
   bool fuse_a = false;  // every K <= 32: split-A forms the row exponents itself
   int n_rowexp = 0, n_colexp = 0;  // work items of the exponent scans
@@ -836,7 +839,8 @@ EmuPlan* emu_plan(Ctx& c, const GemmPlan& g, const Tensor* A, const Tensor* B, b
   p->d_err = st->d_err;
   const int BN = bn_of(p->S);
   int64_t asl = 0, bsl = 0, aex = 0, bex = 0;
-  int tile0 = 0, at0 = 0, bt0 = 0;
+  int tile0 = 0;
+  int64_t au0 = 0, bu0 = 0;
   int64_t tiles_mn = 0;
   for (auto& q : g.h_probs)
     tiles_mn += int64_t((q.M + BM - 1) / BM) * ((q.N + BN / 2 - 1) / (BN / 2));
@@ -888,15 +892,15 @@ EmuPlan* emu_plan(Ctx& c, const GemmPlan& g, const Tensor* A, const Tensor* B, b
     p->total_cols += q.N;
     p->n_rowexp += q.M * std::max((q.K + ROW_KR - 1) / ROW_KR, 1);
     p->n_colexp += ((q.N + 31) / 32) * std::max((q.K + 255) / 256, 1);
-    e.at0 = at0;
-    e.bt0 = bt0;
-    at0 += e.tiles_m * nkh_of(e);
-    bt0 += e.tiles_n * nkh_of(e);
+    e.au0 = au0;
+    e.bu0 = bu0;
+    au0 += int64_t(e.tiles_m) * nkh_of(e) * e.arows * (KB / 8);
+    bu0 += int64_t(e.tiles_n) * nkh_of(e) * (e.brows / 2) * (KB / 8);
     p->h.push_back(e);
   }
   p->n_tiles = tile0;
-  p->n_atiles = at0;
-  p->n_btiles = bt0;
+  p->n_aunits = au0;
+  p->n_bunits = bu0;
   p->asl_is = std::max<int64_t>(asl, 1);
   p->bsl_is = std::max<int64_t>(bsl, 1);
   p->aex_is = std::max<int64_t>(aex, 1);
@@ -961,10 +965,10 @@ static void run_s(Ctx& c, EmuPlan* p, const cplx* A, const cplx* B, cplx* C, int
   const int np = int(p->h.size());
   EmuStageTimer tm(c.profile, c.stream);
   if (!p->a_ready) {
-    const int blocks = split_blocks(int64_t(p->n_atiles) * BM * (KB / 8), c.sm_count);
+    const int blocks = split_blocks(p->n_aunits, c.sm_count);
     if (p->fuse_a) {
       tm.mark(1);
-      k_split_a<S, true><<<dim3(blocks, c.ninst), 256, 0, c.stream>>>(p->d, np, p->n_atiles, A, ais, p->aex, p->aex_is,
+      k_split_a<S, true><<<dim3(blocks, c.ninst), 256, 0, c.stream>>>(p->d, np, p->n_aunits, A, ais, p->aex, p->aex_is,
                                                                       p->asl, p->asl_is);
     } else {
       k_fill_int<<<dim3(std::max<int64_t>(1, std::min<int64_t>((p->aex_is * c.ninst + 255) / 256, 1024))), 256, 0,
@@ -974,7 +978,7 @@ static void run_s(Ctx& c, EmuPlan* p, const cplx* A, const cplx* B, cplx* C, int
                                                                                                 p->aex_is, p->n_rowexp);
       KCHECK(c);
       tm.mark(1);
-      k_split_a<S, false><<<dim3(blocks, c.ninst), 256, 0, c.stream>>>(p->d, np, p->n_atiles, A, ais, p->aex, p->aex_is,
+      k_split_a<S, false><<<dim3(blocks, c.ninst), 256, 0, c.stream>>>(p->d, np, p->n_aunits, A, ais, p->aex, p->aex_is,
                                                                        p->asl, p->asl_is);
     }
     KCHECK(c);
@@ -988,8 +992,8 @@ static void run_s(Ctx& c, EmuPlan* p, const cplx* A, const cplx* B, cplx* C, int
     k_col_exp<<<dim3(p->n_colexp, c.ninst), 256, 0, c.stream>>>(p->d, np, B, bis, p->bex, p->bex_is);
     KCHECK(c);
     tm.mark(3);
-    k_split_b<S><<<dim3(split_blocks(int64_t(p->n_btiles) * (Shape<S>::BN / 2) * (KB / 8), c.sm_count), c.ninst), 256, 0,
-                   c.stream>>>(p->d, np, p->n_btiles, B, bis, p->bex, p->bex_is, p->bsl, p->bsl_is);
+    k_split_b<S><<<dim3(split_blocks(p->n_bunits, c.sm_count), c.ninst), 256, 0, c.stream>>>(
+        p->d, np, p->n_bunits, B, bis, p->bex, p->bex_is, p->bsl, p->bsl_is);
     KCHECK(c);
     if (p->b_const) p->b_ready = true;
   }
@@ -1090,7 +1094,8 @@ exp_status noalloc_launch(cudaStream_t st, unsigned char* base, int M, int N, in
   }
   e.arows = e.tiles_m == 1 ? (M + 7) / 8 * 8 : BM;
   e.brows = e.tiles_n == 1 ? (2 * N + 7) / 8 * 8 : BN;
-  e.tile0 = e.at0 = e.bt0 = 0;
+  e.tile0 = 0;
+  e.au0 = e.bu0 = 0;
   e.red0 = 0;
   // scratch layout
   int64_t off = 0;
@@ -1125,11 +1130,10 @@ exp_status noalloc_launch(cudaStream_t st, unsigned char* base, int M, int N, in
   k_fill_int<<<std::max(1, std::min((N + 255) / 256, 1024)), 256, 0, st>>>(bex, N, EXP_ZERO);
   k_row_exp<<<dim3(row_exp_blocks(n_rowexp, sms), 1), 256, 0, st>>>(d_probs, 1, A, 0, aex, 0, n_rowexp);
   k_col_exp<<<dim3(unsigned(n_colexp), 1), 256, 0, st>>>(d_probs, 1, B, 0, bex, 0);
-  const int na = e.tiles_m * nkh_of(e), nb = e.tiles_n * nkh_of(e);
-  k_split_a<S, false><<<dim3(split_blocks(int64_t(na) * BM * (KB / 8), sms), 1), 256, 0, st>>>(d_probs, 1, na, A, 0, aex, 0,
-                                                                                              asl, 0);
-  k_split_b<S><<<dim3(split_blocks(int64_t(nb) * (BN / 2) * (KB / 8), sms), 1), 256, 0, st>>>(d_probs, 1, nb, B, 0, bex, 0,
-                                                                                             bsl, 0);
+  const int64_t na = int64_t(e.tiles_m) * nkh_of(e) * e.arows * (KB / 8);
+  const int64_t nb = int64_t(e.tiles_n) * nkh_of(e) * (e.brows / 2) * (KB / 8);
+  k_split_a<S, false><<<dim3(split_blocks(na, sms), 1), 256, 0, st>>>(d_probs, 1, na, A, 0, aex, 0, asl, 0);
+  k_split_b<S><<<dim3(split_blocks(nb, sms), 1), 256, 0, st>>>(d_probs, 1, nb, B, 0, bex, 0, bsl, 0);
   if (cudaFuncSetAttribute(k_emu_gemm<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, SH::SMEM) != cudaSuccess) {
     err = "exp_zgemm_emu_noalloc: shared-memory attribute refused";
     return EXP_ECUDA;

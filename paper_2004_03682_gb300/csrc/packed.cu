@@ -8,6 +8,9 @@
 // grouped GEMM (step 3 of the TTGT list, Sec. II.B) on the same kernels.
 #include <algorithm>
 #include <cstdio>
+#include <functional>
+#include <map>
+#include <memory>
 
 #include "emu.h"
 #include "packed.h"
@@ -191,17 +194,47 @@ void launch_pack_scatter(Ctx& c, cplx* dst, int64_t dis, const cplx* src, int64_
 }
 
 // ---------------------------------------------------------------------------
-// The packed ladder.  Operands per pair irrep g:
-//   V_P[g]   = <ab||cd>,     rows a<b, cols c<d   (generated once, packed)
-//   T_P[g]   = tau_ij^cd,    rows c<d, cols i<j   (gathered from tau every call)
-//   Z_P[g]   = V_P[g] T_P[g]                      (emulated or FP64 grouped GEMM)
-// then r2_ij^ab += Z with the signs of the pair swaps.
-struct PackedLadder {
-  PairTable vv, oo;
-  PackDims dt{}, dv{};
-  Tensor V, T, Z;
-  EinsumPlan* plan = nullptr;  // owned by c.plans (registered as the "R2pp" contraction)
+// Packed contractions.  tau is gathered once per iteration into
+//   T_P[g] = tau_ij^cd,  rows c<d, cols i<j,
+// and serves every product that sums over a tau pair index:
+//   R2pp   r2_ij^ab  += sum_{c<d} <ab||cd> T_P            (A = <ab||cd>, a<b, c<d)
+//   Xamij  X_am,ij    = 2 sum_{e<f} <am||ef> T_P          (A = <am||ef>, e<f)
+//   Wmnij2 W_mn,ij   += sum_{e<f} <mn||ef> T_P            (A = <mn||ef>, m<n, e<f)
+//   R2hh   r2_ij^ab  += sum_{m<n} T_P(ab, mn) W_mn,ij      (B = W gathered to m<n)
+// (each a sum over the full pair with factor 1/2 in Eq. (amplitudes) and the
+// Stanton-Gauss intermediates).  Results are scattered into the blocked tensors
+// with the signs of the pair swaps.
+struct PackedOp {
+  std::string site;
+  Tensor A, B, C;             // packed operands (A or B may alias the shared T_P)
+  PackDims dA{}, dB{}, dC{};  // with the full counterparts for generation / gather / scatter
+  const PairTable *Ar = nullptr, *Ac = nullptr, *Br = nullptr, *Bc = nullptr, *Cr = nullptr, *Cc = nullptr;
+  EinsumPlan* plan = nullptr;  // owned by c.plans
 };
+
+struct PackedState {
+  std::map<std::string, std::unique_ptr<PairTable>> tables;
+  Tensor TP;  // packed tau
+  PackDims dT{};
+  const PairTable *vv = nullptr, *oo = nullptr;
+  std::map<std::string, std::unique_ptr<PackedOp>> ops;
+};
+
+static PackedState& PS(Ctx& c) {
+  if (!c.packed_state) c.packed_state = new PackedState();
+  return *(PackedState*)c.packed_state;
+}
+
+static const PairTable& table(Ctx& c, const Layout& L, bool rows, bool packed) {
+  PackedState& s = PS(c);
+  const std::string key = L.key() + (rows ? "|r" : "|c") + (packed ? "p" : "f");
+  auto it = s.tables.find(key);
+  if (it != s.tables.end()) return *it->second;
+  PairTable* t = new PairTable();
+  build_pair_table(c, L, rows, packed, *t);
+  s.tables[key].reset(t);
+  return *t;
+}
 
 static Layout packed_layout(const PairTable& R, const PairTable& C) {
   Layout L;
@@ -222,57 +255,57 @@ static Layout packed_layout(const PairTable& R, const PairTable& C) {
   return L;
 }
 
-static PackedLadder* ladder_state(Ctx& c, const Tensor& tau) {
-  if (c.packed_state) return (PackedLadder*)c.packed_state;
-  PackedLadder* s = new PackedLadder();
-  c.packed_state = s;
-  build_pair_table(c, tau.L, true, true, s->vv);   // (c, d) of tau = (a, b) of r2
-  build_pair_table(c, tau.L, false, true, s->oo);  // (i, j)
-  s->dt = pack_dims(s->vv, s->oo);
-  s->dv = pack_dims(s->vv, s->vv);
-  const Layout LV = packed_layout(s->vv, s->vv), LT = packed_layout(s->vv, s->oo);
-  Tensor* v = new_tensor(c, LV, false);
-  Tensor* t = new_tensor(c, LT, false);
-  Tensor* z = new_tensor(c, LT, false);
-  s->V = *v;
-  s->T = *t;
-  s->Z = *z;
-  delete v;
+static Tensor packed_tensor(Ctx& c, const PairTable& R, const PairTable& C) {
+  Tensor* t = new_tensor(c, packed_layout(R, C), false);
+  Tensor r = *t;
   delete t;
-  delete z;
-  launch_generate_pairs(c, s->V.d, s->V.is, s->dv, s->vv, s->vv);
-  EinsumPlan* P = new EinsumPlan();
-  c.plans["R2pp"].reset(P);
-  s->plan = P;
-  P->A = &s->V;
-  P->B = &s->T;
-  P->permC = true;
-  P->C2 = s->Z;
-  P->alpha = make_double2(1.0, 0.0);
-  P->gemm_beta = false;
-  P->g = make_gemm_plan(c, LV, LT, LT);
-  P->emulate = emu_wanted(c, P->g, "R2pp");
-  if (P->emulate) P->emu = emu_plan(c, P->g, &s->V, &s->T, true, false);
-  return s;
+  return r;
 }
 
-void packed_ladder(Ctx& c, const Tensor& tau, Tensor& r2) {
-  PackedLadder* s = ladder_state(c, tau);
-  EinsumPlan* P = s->plan;
+void packed_tau(Ctx& c, const Tensor& tau) {
+  PackedState& s = PS(c);
+  if (!s.vv) {
+    s.vv = &table(c, tau.L, true, true);   // (c, d), c < d
+    s.oo = &table(c, tau.L, false, true);  // (i, j), i < j
+    s.dT = pack_dims(*s.vv, *s.oo);
+    s.TP = packed_tensor(c, *s.vv, *s.oo);
+  }
+  launch_pack_gather(c, s.TP.d, s.TP.is, tau.d, tau.is, s.dT, *s.vv, *s.oo);
+}
+
+// C_P = A_P B_P through the emulated or FP64 grouped GEMM, registered in c.plans
+// under `site` (so the work accounting and the top-contraction report see it)
+static void finish_op(Ctx& c, PackedOp* op, bool a_const, double alpha = 1.0) {
+  EinsumPlan* P = new EinsumPlan();
+  c.plans[op->site].reset(P);
+  op->plan = P;
+  P->A = &op->A;
+  P->B = &op->B;
+  P->permC = true;
+  P->C2 = op->C;
+  P->alpha = make_double2(alpha, 0.0);
+  P->gemm_beta = false;
+  P->g = make_gemm_plan(c, op->A.L, op->B.L, op->C.L);
+  P->emulate = emu_wanted(c, P->g, op->site);
+  if (P->emulate) P->emu = emu_plan(c, P->g, &op->A, &op->B, a_const, false);
+}
+
+static void run_op(Ctx& c, PackedOp* op, const std::function<void()>& before, const std::function<void()>& after) {
+  EinsumPlan* P = op->plan;
   const bool prof = c.profile;
   cudaEvent_t pe[2] = {nullptr, nullptr};
   if (prof) {
     for (auto& e : pe) CK(cudaEventCreate(&e));
     CK(cudaEventRecord(c.pev0, c.stream));
   }
-  launch_pack_gather(c, s->T.d, s->T.is, tau.d, tau.is, s->dt, s->vv, s->oo);
+  before();
   if (prof) CK(cudaEventRecord(pe[0], c.stream));
   if (P->emulate)
-    emu_run(c, P->emu, P->g, s->V.d, s->T.d, s->Z.d, s->V.is, s->T.is, s->Z.is, P->alpha, false);
+    emu_run(c, P->emu, P->g, op->A.d, op->B.d, op->C.d, op->A.is, op->B.is, op->C.is, P->alpha, false);
   else
-    launch_gemm_fp64(c, P->g, s->V.d, s->T.d, s->Z.d, s->V.is, s->T.is, s->Z.is, P->alpha, false);
+    launch_gemm_fp64(c, P->g, op->A.d, op->B.d, op->C.d, op->A.is, op->B.is, op->C.is, P->alpha, false);
   if (prof) CK(cudaEventRecord(pe[1], c.stream));
-  launch_pack_scatter(c, r2.d, r2.is, s->Z.d, s->Z.is, s->dt, s->vv, s->oo, 1.0, true);
+  after();
   if (prof) {
     CK(cudaEventRecord(c.pev1, c.stream));
     CK(cudaEventSynchronize(c.pev1));
@@ -284,16 +317,86 @@ void packed_ladder(Ctx& c, const Tensor& tau, Tensor& r2) {
     for (auto& e : pe) cudaEventDestroy(e);
     int64_t M = 0, N = 0, K = 0;
     for (auto& q : P->g.h_probs) { M = std::max<int64_t>(M, q.M); N = std::max<int64_t>(N, q.N); K = std::max<int64_t>(K, q.K); }
-    fprintf(stderr, "[exp_phase] %-8s in %7.3f  gemm %7.3f  out %7.3f ms\n", "R2pp", m_in, m_g, m_out);
+    fprintf(stderr, "[exp_phase] %-8s in %7.3f  gemm %7.3f  out %7.3f ms\n", op->site.c_str(), m_in, m_g, m_out);
     fprintf(stderr,
             "[exp_profile] %-8s %9.3f ms  %10.3g cMAC  %7.1f GF/s  probs=%d maxM=%lld maxN=%lld maxK=%lld perm=011 emu=%d "
             "packed\n",
-            "R2pp", ms, double(P->g.flops_mac) * c.ninst, 8.0 * double(P->g.flops_mac) * c.ninst / (ms * 1e6),
+            op->site.c_str(), ms, double(P->g.flops_mac) * c.ninst, 8.0 * double(P->g.flops_mac) * c.ninst / (ms * 1e6),
             P->g.n_probs, (long long)M, (long long)N, (long long)K, P->emulate);
   }
 }
 
+// A = integral <pq||rs> with (p, q) from table R and (r, s) from table K, generated once;
+// B = T_P; C scattered into dst (rows Cr, cols oo) with `coef` (+-1), accumulating or not
+static PackedOp* int_times_tau(Ctx& c, const std::string& site, const PairTable& R, const Tensor& dst, bool rows_packed,
+                               double alpha) {
+  PackedState& s = PS(c);
+  auto it = s.ops.find(site);
+  if (it != s.ops.end()) return it->second.get();
+  PackedOp* op = new PackedOp();
+  s.ops[site].reset(op);
+  op->site = site;
+  op->Ar = &R;
+  op->Ac = s.vv;
+  op->A = packed_tensor(c, R, *s.vv);
+  op->dA = pack_dims(R, *s.vv);
+  op->B = s.TP;
+  op->Cr = &table(c, dst.L, true, rows_packed);
+  op->Cc = &table(c, dst.L, false, true);
+  op->C = packed_tensor(c, R, *s.oo);
+  op->dC = pack_dims(*op->Cr, *op->Cc);
+  launch_generate_pairs(c, op->A.d, op->A.is, op->dA, R, *s.vv);
+  finish_op(c, op, true, alpha);
+  return op;
+}
+
+void packed_ladder(Ctx& c, Tensor& r2) {
+  PackedState& s = PS(c);
+  PackedOp* op = int_times_tau(c, "R2pp", *s.vv, r2, true, 1.0);
+  run_op(c, op, [] {}, [&] { launch_pack_scatter(c, r2.d, r2.is, op->C.d, op->C.is, op->dC, *op->Cr, *op->Cc, 1.0, true); });
+}
+
+void packed_xamij(Ctx& c, Tensor& X) {
+  const PairTable& am = table(c, X.L, true, false);
+  PackedOp* op = int_times_tau(c, "Xamij", am, X, false, 2.0);  // sum_ef = 2 sum_{e<f}
+  run_op(c, op, [] {}, [&] { launch_pack_scatter(c, X.d, X.is, op->C.d, op->C.is, op->dC, *op->Cr, *op->Cc, 1.0, false); });
+}
+
+void packed_wmnij(Ctx& c, Tensor& W) {
+  const PairTable& mn = table(c, W.L, true, true);
+  PackedOp* op = int_times_tau(c, "Wmnij2", mn, W, true, 1.0);
+  run_op(c, op, [] {}, [&] { launch_pack_scatter(c, W.d, W.is, op->C.d, op->C.is, op->dC, *op->Cr, *op->Cc, 1.0, true); });
+}
+
+// r2_ij^ab += sum_{m<n} T_P(ab, mn) W_mn,ij: A = T_P, B = W with rows m<n
+void packed_hh(Ctx& c, const Tensor& W, Tensor& r2) {
+  PackedState& s = PS(c);
+  PackedOp* op;
+  auto it = s.ops.find("R2hh");
+  if (it == s.ops.end()) {
+    op = new PackedOp();
+    s.ops["R2hh"].reset(op);
+    op->site = "R2hh";
+    const PairTable& ijf = table(c, W.L, false, false);
+    op->A = s.TP;
+    op->Br = &table(c, W.L, true, true);  // (m, n), m < n: same enumeration as the tau columns
+    op->Bc = &ijf;
+    op->B = packed_tensor(c, *op->Br, ijf);
+    op->dB = pack_dims(*op->Br, ijf);
+    op->Cr = s.vv;
+    op->Cc = &table(c, r2.L, false, false);
+    op->C = packed_tensor(c, *s.vv, ijf);
+    op->dC = pack_dims(*op->Cr, *op->Cc);
+    finish_op(c, op, false);
+  } else {
+    op = it->second.get();
+  }
+  run_op(
+      c, op, [&] { launch_pack_gather(c, op->B.d, op->B.is, W.d, W.is, op->dB, *op->Br, *op->Bc); },
+      [&] { launch_pack_scatter(c, r2.d, r2.is, op->C.d, op->C.is, op->dC, *op->Cr, *op->Cc, 1.0, true); });
+}
+
 void packed_release(Ctx& c) {
-  delete (PackedLadder*)c.packed_state;  // device memory belongs to the context's allocator
+  delete (PackedState*)c.packed_state;  // device memory belongs to the context's allocator
   c.packed_state = nullptr;
 }

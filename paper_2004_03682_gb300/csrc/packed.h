@@ -52,6 +52,15 @@ void launch_pack_scatter(Ctx& c, cplx* dst, int64_t dis, const cplx* src, int64_
 void launch_generate_pairs(Ctx& c, cplx* dst, int64_t is, const PackDims& D, const PairTable& R,
                            const PairTable& C);
 
-// The packed particle-particle ladder (ccsd.cu): r2 += sum_{c<d} <ab||cd> tau_ij^cd.
-void packed_ladder(Ctx& c, const Tensor& tau, Tensor& r2);
+// Packed contractions over tau pair indices (packed.cu).  packed_tau gathers tau
+// (c<d, i<j) once per iteration; the others then use it:
+//   packed_ladder  r2 += sum_{c<d} <ab||cd> tau_ij^cd
+//   packed_xamij   X_amij = 2 sum_{e<f} <am||ef> tau_ij^ef      (= sum_ef; overwrites X)
+//   packed_wmnij   W_mnij += sum_{e<f} <mn||ef> tau_ij^ef
+//   packed_hh      r2 += sum_{m<n} tau_mn^ab W_mnij             (W complete)
+void packed_tau(Ctx& c, const Tensor& tau);
+void packed_ladder(Ctx& c, Tensor& r2);
+void packed_xamij(Ctx& c, Tensor& X);
+void packed_wmnij(Ctx& c, Tensor& W);
+void packed_hh(Ctx& c, const Tensor& W, Tensor& r2);
 void packed_release(Ctx& c);

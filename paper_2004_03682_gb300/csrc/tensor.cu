@@ -282,6 +282,63 @@ __global__ void k_tau(cplx* __restrict__ dst, int64_t dis, const cplx* __restric
   }
 }
 
+// The three tau-like tensors of one iteration in one pass (the t1 products are
+// formed once): with A = t1_ai t1_bj and B = t1_bi t1_aj,
+//   tau = t2 + A - B,   taut = t2 + (A - B)/2,   zeta = t2/2 + A.
+__global__ void k_tau3(cplx* __restrict__ tau, cplx* __restrict__ taut, cplx* __restrict__ zeta, int64_t dis,
+                       const cplx* __restrict__ t2, const cplx* __restrict__ t1, int64_t tis,
+                       const int32_t* __restrict__ t1i, const GenTask* __restrict__ tasks,
+                       const ChunkRef* __restrict__ chunks, int no, int vbase) {
+  const ChunkRef ch = chunks[blockIdx.x];
+  const GenTask T = tasks[ch.task];
+  tau += blockIdx.y * dis;
+  taut += blockIdx.y * dis;
+  zeta += blockIdx.y * dis;
+  t2 += blockIdx.y * tis;
+  t1 += blockIdx.y * tis;
+  const uint32_t n1 = T.n[1], n2 = T.n[2], n3 = T.n[3];
+  const uint32_t end = uint32_t(min(ch.start + (int64_t)EXP_CHUNK, T.count));
+  for (uint32_t e = uint32_t(ch.start) + threadIdx.x; e < end; e += blockDim.x) {
+    uint32_t r = e;
+    const int i3 = int(r % n3);
+    r /= n3;
+    const int i2 = int(r % n2);
+    r /= n2;
+    const int i1 = int(r % n1);
+    const int i0 = int(r / n1);
+    const int a = T.g0[0] + i0 - vbase, b = T.g0[1] + i1 - vbase;
+    const int ii = T.g0[2] + i2, jj = T.g0[3] + i3;
+    const int64_t p = T.base + i0 * T.st[0] + i1 * T.st[1] + i2 * T.st[2] + i3 * T.st[3];
+    const cplx x = t2[p];
+    double ar = 0.0, ai = 0.0, br = 0.0, bi = 0.0;
+    const int kai = t1i[a * no + ii], kbj = t1i[b * no + jj];
+    if (kai >= 0 && kbj >= 0) {
+      const cplx u = t1[kai], w = t1[kbj];
+      ar = u.x * w.x - u.y * w.y;
+      ai = u.x * w.y + u.y * w.x;
+    }
+    const int kbi = t1i[b * no + ii], kaj = t1i[a * no + jj];
+    if (kbi >= 0 && kaj >= 0) {
+      const cplx u = t1[kbi], w = t1[kaj];
+      br = u.x * w.x - u.y * w.y;
+      bi = u.x * w.y + u.y * w.x;
+    }
+    const double dr = ar - br, di = ai - bi;
+    tau[p] = make_double2(x.x + dr, x.y + di);
+    taut[p] = make_double2(fma(0.5, dr, x.x), fma(0.5, di, x.y));
+    zeta[p] = make_double2(fma(0.5, x.x, ar), fma(0.5, x.y, ai));
+  }
+}
+
+void launch_tau3(Ctx& c, cplx* tau, cplx* taut, cplx* zeta, int64_t dst_is, const cplx* t2, const cplx* t1,
+                 int64_t t_is, const int32_t* t1_index, const GenTask* d_tasks, const ChunkRef* d_chunks,
+                 int n_chunks) {
+  if (!n_chunks) return;
+  k_tau3<<<dim3(n_chunks, c.ninst), 256, 0, c.stream>>>(tau, taut, zeta, dst_is, t2, t1, t_is, t1_index, d_tasks,
+                                                        d_chunks, c.no, c.no);
+  KCHECK(c);
+}
+
 void launch_tau(Ctx& c, cplx* dst, int64_t dst_is, const cplx* t2, const cplx* t1, int64_t t_is,
                 const int32_t* t1_index, const GenTask* d_tasks, const ChunkRef* d_chunks,
                 int n_chunks, double c0, double c1, double c2) {

@@ -413,7 +413,7 @@ extern "C" exp_status exp_profile_top(exp_ctx* x, int reps, char* name, int name
   CK(cudaEventRecord(c.ev0, c.stream));
   for (int r = 0; r < reps; ++r) {
     if (P->emulate)
-      emu_run(c, P->emu, P->g, P->A->d, P->B->d, cd, P->A->is, P->B->is, cis, P->alpha, P->gemm_beta);
+      emu_run(c, P->emu, P->g, P->A->d, P->B->d, cd, P->A->is, P->B->is, cis, P->alpha, P->gemm_beta, true);
     else
       launch_gemm_fp64(c, P->g, P->A->d, P->B->d, cd, P->A->is, P->B->is, cis, P->alpha, P->gemm_beta);
   }

@@ -6,6 +6,8 @@
 bool emu_wanted(Ctx& c, const GemmPlan& g, const std::string& site);
 EmuPlan* emu_plan(Ctx& c, const GemmPlan& g, const Tensor* A, const Tensor* B, bool a_const,
                   bool b_const);
+// gemm_only: launch only the tensor-core kernel on the slices of the previous run
+// (timing); the split-K reduction and the slicing passes are skipped
 void emu_run(Ctx& c, EmuPlan* p, const GemmPlan& g, const cplx* A, const cplx* B, cplx* C,
-             int64_t ais, int64_t bis, int64_t cis, cplx alpha, bool beta);
+             int64_t ais, int64_t bis, int64_t cis, cplx alpha, bool beta, bool gemm_only = false);
 void emu_release(Ctx& c);

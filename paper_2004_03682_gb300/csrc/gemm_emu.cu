@@ -36,6 +36,7 @@ constexpr int BM = 128;        // rows per tile (tcgen05 M)
 constexpr int KB = 32;         // real K per smem k-block (4 core matrices of 8 bf16)
 constexpr int BETA = 7;        // bits per slice
 constexpr int KC_BLOCKS = 16;  // k-blocks per exact chunk: KC = 512 real terms
+constexpr int EMU_GM = 8;      // row tiles per group of the GEMM work order
 constexpr int THREADS = 320;   // 10 warps: producer, MMA issuer, 8 epilogue warps
 constexpr int EPI_WARPS = 8;
 #define EXP_ZERO (-1100)       // exponent of an all-zero row / column (any x 2^-EXP_ZERO stays 0)
@@ -190,6 +191,8 @@ __device__ __forceinline__ double scaled_i64(long long R, int e) {
 // 32-wide k ranges a half spans (the split kernels' CTA count per tile)
 __host__ __device__ __forceinline__ int kh_of(const EmuProb& P) { return P.Kp / 2; }
 __host__ __device__ __forceinline__ int nkh_of(const EmuProb& P) { return (P.Kp / 2 + KB - 1) / KB; }
+// split-A units (8-groups) per row of a work item: 2 when a half is 16 wide, else 4
+__host__ __device__ __forceinline__ int gpr_of(const EmuProb& P) { return P.Kp == 32 ? 2 : 4; }
 
 // One work item of the persistent GEMM: (instance, K split, row tile, column tile).
 struct EmuWork {
@@ -207,8 +210,14 @@ __device__ __forceinline__ EmuWork emu_work(const EmuProb* __restrict__ probs, i
   const int tmn = P.tiles_m * P.tiles_n;
   W.ks = lt / tmn;
   lt -= W.ks * tmn;
-  W.mt = lt / P.tiles_n;
-  W.nt = lt % P.tiles_n;
+  // grouped order: consecutive items (one wave of CTAs) walk EMU_GM row tiles
+  // column by column, so their A and B slice tiles are reused from L2
+  const int grp = lt / (EMU_GM * P.tiles_n);
+  const int m0 = grp * EMU_GM;
+  const int gm = min(EMU_GM, P.tiles_m - m0);
+  const int r = lt - m0 * P.tiles_n;
+  W.mt = m0 + r % gm;
+  W.nt = r / gm;
   W.nkb_all = P.Kp / KB;
   W.kb0 = W.ks * P.kcb;
   W.nkb = min(W.nkb_all, W.kb0 + P.kcb) - W.kb0;
@@ -586,17 +595,22 @@ __global__ void __launch_bounds__(256) k_split_a(const EmuProb* __restrict__ pro
                                                  const cplx* __restrict__ A, int64_t a_is, int* __restrict__ ex,
                                                  int64_t ex_is, __nv_bfloat16* __restrict__ out, int64_t out_is) {
   const int inst = blockIdx.y;
-  // units per item = stored rows x 4, a multiple of 32: the lanes of a warp share a problem
-  for (int64_t U = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; U < total; U += int64_t(gridDim.x) * blockDim.x) {
+  // units per item = stored rows x groups per row; the loop runs to a multiple of 32
+  // so that whole warps take part in the exponent shuffles (lanes past the end idle)
+  const int64_t total32 = (total + 31) & ~int64_t(31);
+  for (int64_t U0 = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; U0 < total32; U0 += int64_t(gridDim.x) * blockDim.x) {
+    const bool live = U0 < total;
+    const int64_t U = live ? U0 : total - 1;
     int pi = 0;
     while (pi + 1 < nprobs && U >= probs[pi + 1].au0) ++pi;
     const EmuProb& P = probs[pi];
-    const int UA = P.arows * (KB / 8);
+    const int gpr = gpr_of(P);
+    const int UA = P.arows * gpr;
     const int64_t lu = U - P.au0;
     const int lt = int(lu / UA), u = int(lu - int64_t(lt) * UA);
     const int nkb = P.Kp / KB, nkh = nkh_of(P), Kh = kh_of(P);
     const int mt = lt / nkh, kbh = lt % nkh;
-    const int r = u >> 2, g = u & 3;
+    const int r = gpr == 4 ? (u >> 2) : (u >> 1), g = gpr == 4 ? (u & 3) : (u & 1);
     const int gi = mt * BM + r;
     const int k0 = kbh * KB + g * 8;
     const cplx* a = A + inst * a_is + P.a_src;
@@ -617,14 +631,15 @@ __global__ void __launch_bounds__(256) k_split_a(const EmuProb* __restrict__ pro
 #pragma unroll
       for (int q = 0; q < 8; ++q) m = max(m, max(abits(xr[q]), abits(xi[q])));
       m = max(m, __shfl_xor_sync(0xffffffffu, m, 1));
-      m = max(m, __shfl_xor_sync(0xffffffffu, m, 2));
+      const unsigned long long m2 = __shfl_xor_sync(0xffffffffu, m, 2);
+      if (gpr == 4) m = max(m, m2);
       const int e = exp_of_bits(m);
-      if (g == 0 && gi < P.M) ex[inst * ex_is + P.a_ex + gi] = e;
+      if (live && g == 0 && gi < P.M) ex[inst * ex_is + P.a_ex + gi] = e;
       sh = gi < P.M ? -e : 0;
     } else {
       sh = gi < P.M ? -ex[inst * ex_is + P.a_ex + gi] : 0;
     }
-    if (k0 >= Kh || r >= P.arows) continue;
+    if (!live || k0 >= Kh || r >= P.arows) continue;
     uint4 sr[S], si[S], dummy[S];
     slice8<S>(xr, sh, sr, false, dummy);
     slice8<S>(xi, sh, si, false, dummy);
@@ -894,7 +909,7 @@ EmuPlan* emu_plan(Ctx& c, const GemmPlan& g, const Tensor* A, const Tensor* B, b
     p->n_colexp += ((q.N + 31) / 32) * std::max((q.K + 255) / 256, 1);
     e.au0 = au0;
     e.bu0 = bu0;
-    au0 += int64_t(e.tiles_m) * nkh_of(e) * e.arows * (KB / 8);
+    au0 += int64_t(e.tiles_m) * nkh_of(e) * e.arows * gpr_of(e);
     bu0 += int64_t(e.tiles_n) * nkh_of(e) * (e.brows / 2) * (KB / 8);
     p->h.push_back(e);
   }
@@ -961,8 +976,17 @@ struct EmuStageTimer {
 
 template <int S>
 static void run_s(Ctx& c, EmuPlan* p, const cplx* A, const cplx* B, cplx* C, int64_t ais, int64_t bis, int64_t cis,
-                  cplx alpha, bool beta) {
+                  cplx alpha, bool beta, bool gemm_only) {
   const int np = int(p->h.size());
+  if (gemm_only) {  // the tensor-core product alone, on the slices already in place
+    set_smem_attr<S>();
+    const int n_work = p->n_tiles * c.ninst;
+    k_emu_gemm<S><<<dim3(std::min(n_work, std::max(c.sm_count, 1))), THREADS, Shape<S>::SMEM, c.stream>>>(
+        p->d, np, p->n_tiles, n_work, p->asl, p->bsl, p->aex, p->bex, C, p->asl_is, p->bsl_is, p->aex_is, p->bex_is,
+        cis, alpha, p->red_elems ? ALPHA_GENERAL : alpha_code(alpha), beta ? 1 : 0, p->d_err, p->d_ws, p->ws_is);
+    KCHECK(c);
+    return;
+  }
   EmuStageTimer tm(c.profile, c.stream);
   if (!p->a_ready) {
     const int blocks = split_blocks(p->n_aunits, c.sm_count);
@@ -1017,13 +1041,13 @@ static void run_s(Ctx& c, EmuPlan* p, const cplx* A, const cplx* B, cplx* C, int
 }
 
 void emu_run(Ctx& c, EmuPlan* p, const GemmPlan&, const cplx* A, const cplx* B, cplx* C, int64_t ais, int64_t bis,
-             int64_t cis, cplx alpha, bool beta) {
+             int64_t cis, cplx alpha, bool beta, bool gemm_only) {
   if (p->n_tiles == 0) return;
   switch (p->S) {
-    case 3: run_s<3>(c, p, A, B, C, ais, bis, cis, alpha, beta); break;
-    case 4: run_s<4>(c, p, A, B, C, ais, bis, cis, alpha, beta); break;
-    case 5: run_s<5>(c, p, A, B, C, ais, bis, cis, alpha, beta); break;
-    default: run_s<6>(c, p, A, B, C, ais, bis, cis, alpha, beta); break;
+    case 3: run_s<3>(c, p, A, B, C, ais, bis, cis, alpha, beta, gemm_only); break;
+    case 4: run_s<4>(c, p, A, B, C, ais, bis, cis, alpha, beta, gemm_only); break;
+    case 5: run_s<5>(c, p, A, B, C, ais, bis, cis, alpha, beta, gemm_only); break;
+    default: run_s<6>(c, p, A, B, C, ais, bis, cis, alpha, beta, gemm_only); break;
   }
 }
 
@@ -1130,7 +1154,7 @@ exp_status noalloc_launch(cudaStream_t st, unsigned char* base, int M, int N, in
   k_fill_int<<<std::max(1, std::min((N + 255) / 256, 1024)), 256, 0, st>>>(bex, N, EXP_ZERO);
   k_row_exp<<<dim3(row_exp_blocks(n_rowexp, sms), 1), 256, 0, st>>>(d_probs, 1, A, 0, aex, 0, n_rowexp);
   k_col_exp<<<dim3(unsigned(n_colexp), 1), 256, 0, st>>>(d_probs, 1, B, 0, bex, 0);
-  const int64_t na = int64_t(e.tiles_m) * nkh_of(e) * e.arows * (KB / 8);
+  const int64_t na = int64_t(e.tiles_m) * nkh_of(e) * e.arows * gpr_of(e);
   const int64_t nb = int64_t(e.tiles_n) * nkh_of(e) * (e.brows / 2) * (KB / 8);
   k_split_a<S, false><<<dim3(split_blocks(na, sms), 1), 256, 0, st>>>(d_probs, 1, na, A, 0, aex, 0, asl, 0);
   k_split_b<S><<<dim3(split_blocks(nb, sms), 1), 256, 0, st>>>(d_probs, 1, nb, B, 0, bex, 0, bsl, 0);

@@ -165,3 +165,27 @@ CCSD_C1_O10_V40 = dict(n_occ=10, n_virt=40, G=1, seed=1001)
 CCSD_Z8_O40_V200 = dict(n_occ=40, n_virt=200, G=8, seed=2001)
 CCSD_Z8_O60_V400 = dict(n_occ=60, n_virt=400, G=8, seed=3001)
 FS_Z16_O80_V480 = dict(n_occ=80, n_virt=480, G=16, seed=5001)
+
+
+def trial_amplitudes(prob: Problem, seed: int, t1_max: float = 0.01, t2_max: float = 0.05):
+    """Seeded amplitudes with the structure of CCSD ones, for residual checks away from
+    the MP2 guess: t1[i, a] nonzero only for equal irreps, t2[i, j, a, b] antisymmetric
+    in (i, j) and in (a, b) and nonzero only when the irreps of i + j and a + b agree
+    (mod G); complex Gaussian entries scaled to the given maxima."""
+    rng = _stream(seed, 7)
+    o, v = prob.n_occ, prob.n_virt
+    irr = prob.irrep_of
+    go, gv = irr[:o], irr[o:]
+    t1 = rng.standard_normal((o, v)) + 1j * rng.standard_normal((o, v))
+    t1 *= (go[:, None] == gv[None, :])
+    m1 = np.max(np.abs(t1))
+    t1 *= (t1_max / m1) if m1 > 0 else 0.0
+    x = rng.standard_normal((o, o, v, v)) + 1j * rng.standard_normal((o, o, v, v))
+    t2 = x - x.transpose(1, 0, 2, 3) - x.transpose(0, 1, 3, 2) + x.transpose(1, 0, 3, 2)
+    del x
+    allowed = ((go[:, None, None, None] + go[None, :, None, None]
+                - gv[None, None, :, None] - gv[None, None, None, :]) % prob.G) == 0
+    t2 *= allowed
+    m2 = np.max(np.abs(t2))
+    t2 *= (t2_max / m2) if m2 > 0 else 0.0
+    return t1, t2

@@ -166,6 +166,14 @@ extern "C" exp_status exp_create(const exp_config* cfg, const exp_allocator* all
   {
     const char* pe = getenv("EXP_PROFILE");
     c.profile = pe && pe[0] == '1';
+    // EXP_AUTOTUNE=0: keep the default work decomposition of the emulated products,
+    // or the one forced by EXP_KSPLIT_MULT (K-split multiplier) / EXP_GROUP_ROWS
+    const char* at = getenv("EXP_AUTOTUNE");
+    if (at && at[0] == '0') {
+      c.autotune = false;
+      if (const char* km = getenv("EXP_KSPLIT_MULT")) c.force_ksplit_mult = std::max(0.0, atof(km));
+      if (const char* gr = getenv("EXP_GROUP_ROWS")) c.force_group_rows = std::max(1, atoi(gr));
+    }
   }
   ccsd_setup(c);
   CK(cudaStreamSynchronize(c.stream));
@@ -444,6 +452,7 @@ extern "C" exp_status exp_zgemm(const exp_allocator* alloc, void* stream, int pr
   c.stream = (cudaStream_t)stream;
   c.cfg.precision = precision;
   c.cfg.n_slices = n_slices;
+  c.autotune = false;  // a one-off product: nothing to amortise a tuning pass over
   c.ninst = 1;
   c.G = 1;
   int dev = 0;

@@ -237,6 +237,9 @@ struct Ctx {
   int64_t graph_kernels = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   bool profile = false;  // EXP_PROFILE=1: eager iterations, per-contraction timing on stderr
+  bool autotune = true;  // time candidate work decompositions of each emulated product once
+  double force_ksplit_mult = -1.0;  // >= 0 with autotune off: this K-split multiplier
+  int force_group_rows = 0;         // > 0 with autotune off: this work-order group size
   cudaEvent_t pev0 = nullptr, pev1 = nullptr;
 
   int* d_emu_err = nullptr;  // set by a bounded device wait that gave up

@@ -36,7 +36,7 @@ constexpr int BM = 128;        // rows per tile (tcgen05 M)
 constexpr int KB = 32;         // real K per smem k-block (4 core matrices of 8 bf16)
 constexpr int BETA = 7;        // bits per slice
 constexpr int KC_BLOCKS = 16;  // k-blocks per exact chunk: KC = 512 real terms
-constexpr int EMU_GM = 8;      // row tiles per group of the GEMM work order
+constexpr int EMU_GM = 8;      // default row tiles per group of the GEMM work order (tuned per plan)
 constexpr int THREADS = 320;   // 10 warps: producer, MMA issuer, 8 epilogue warps
 constexpr int EPI_WARPS = 8;
 #define EXP_ZERO (-1100)       // exponent of an all-zero row / column (any x 2^-EXP_ZERO stays 0)
@@ -198,7 +198,7 @@ __host__ __device__ __forceinline__ int gpr_of(const EmuProb& P) { return P.Kp =
 struct EmuWork {
   int pi, inst, ks, mt, nt, kb0, nkb, nkb_all;
 };
-__device__ __forceinline__ EmuWork emu_work(const EmuProb* __restrict__ probs, int nprobs, int n_tiles, int w) {
+__device__ __forceinline__ EmuWork emu_work(const EmuProb* __restrict__ probs, int nprobs, int n_tiles, int w, int GMr) {
   EmuWork W;
   W.inst = w / n_tiles;
   const int tile = w - W.inst * n_tiles;
@@ -210,11 +210,11 @@ __device__ __forceinline__ EmuWork emu_work(const EmuProb* __restrict__ probs, i
   const int tmn = P.tiles_m * P.tiles_n;
   W.ks = lt / tmn;
   lt -= W.ks * tmn;
-  // grouped order: consecutive items (one wave of CTAs) walk EMU_GM row tiles
+  // grouped order: consecutive items (one wave of CTAs) walk GMr row tiles
   // column by column, so their A and B slice tiles are reused from L2
-  const int grp = lt / (EMU_GM * P.tiles_n);
-  const int m0 = grp * EMU_GM;
-  const int gm = min(EMU_GM, P.tiles_m - m0);
+  const int grp = lt / (GMr * P.tiles_n);
+  const int m0 = grp * GMr;
+  const int gm = min(GMr, P.tiles_m - m0);
   const int r = lt - m0 * P.tiles_n;
   W.mt = m0 + r % gm;
   W.nt = r / gm;
@@ -230,7 +230,7 @@ __device__ __forceinline__ EmuWork emu_work(const EmuProb* __restrict__ probs, i
 // prefetches across tile boundaries.
 template <int S>
 __global__ void __launch_bounds__(THREADS, 1)
-    k_emu_gemm(const EmuProb* __restrict__ probs, int nprobs, int n_tiles, int n_work,
+    k_emu_gemm(const EmuProb* __restrict__ probs, int nprobs, int n_tiles, int n_work, int gm,
                const __nv_bfloat16* __restrict__ Asl, const __nv_bfloat16* __restrict__ Bsl,
                const int* __restrict__ Aex, const int* __restrict__ Bex, cplx* __restrict__ C, int64_t asl_is,
                int64_t bsl_is, int64_t aex_is, int64_t bex_is, int64_t c_is, cplx alpha, int alpha_e, int beta,
@@ -272,7 +272,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       uint32_t g = 0;  // k-blocks issued by this CTA
       bool stop = false;
       for (int w = blockIdx.x; w < n_work && !stop; w += gridDim.x) {
-        const EmuWork W = emu_work(probs, nprobs, n_tiles, w);
+        const EmuWork W = emu_work(probs, nprobs, n_tiles, w, gm);
         const EmuProb& P = probs[W.pi];
         const int at = P.arows * KB, bt = P.brows * KB;  // stored slice tile sizes (elements)
         const __nv_bfloat16* Ab = Asl + W.inst * asl_is + P.a_sl + (int64_t(W.mt) * W.nkb_all + W.kb0) * (S * at);
@@ -313,7 +313,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       uint32_t g = 0, gc = 0;  // k-blocks consumed, accumulator chunks started
       bool stop = false;
       for (int w = blockIdx.x; w < n_work && !stop; w += gridDim.x) {
-        const EmuWork W = emu_work(probs, nprobs, n_tiles, w);
+        const EmuWork W = emu_work(probs, nprobs, n_tiles, w, gm);
         for (int kb = 0; kb < W.nkb; ++kb, ++g) {
           const int st = g % STAGES;
           const bool first = (kb % KC_BLOCKS) == 0;
@@ -356,7 +356,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     uint32_t gc = 0;
     bool ok = true;
     for (int w = blockIdx.x; w < n_work && ok; w += gridDim.x) {
-      const EmuWork W = emu_work(probs, nprobs, n_tiles, w);
+      const EmuWork W = emu_work(probs, nprobs, n_tiles, w, gm);
       const EmuProb& P = probs[W.pi];
       const int nchunks = (W.nkb + KC_BLOCKS - 1) / KC_BLOCKS;
       long long R[HW];
@@ -394,15 +394,13 @@ __global__ void __launch_bounds__(THREADS, 1)
       const int ei = Aex[W.inst * aex_is + P.a_ex + gi];
       const int* bex = Bex + W.inst * bex_is + P.b_ex;
       const int j0 = W.nt * (SH::BN / 2) + h * (HW / 2);  // first complex column of this warp
-      if (P.ksplit > 1) {  // scaled partial for the fixed-order reduction
-        cplx* Wp = ws + W.inst * ws_is + P.ws + int64_t(W.ks) * P.M * P.N + int64_t(gi) * P.N;
+      if (P.ksplit > 1) {  // the exact integer partial; the reduction adds them exactly
+        longlong2* Wp = reinterpret_cast<longlong2*>(ws + W.inst * ws_is + P.ws) + int64_t(W.ks) * P.M * P.N +
+                        int64_t(gi) * P.N;
 #pragma unroll
         for (int jj = 0; jj < HW / 2; ++jj) {
           const int gj = j0 + jj;
-          if (gj < P.N) {
-            const int e = ei + bex[gj] - BETA * (S + 1);
-            Wp[gj] = make_double2(scaled_i64(R[2 * jj], e), scaled_i64(R[2 * jj + 1], e));
-          }
+          if (gj < P.N) Wp[gj] = make_longlong2(R[2 * jj], R[2 * jj + 1]);
         }
       } else {
         cplx* Crow = C + W.inst * c_is + P.c_off + int64_t(gi) * P.N;
@@ -712,14 +710,17 @@ __global__ void __launch_bounds__(256) k_split_b(const EmuProb* __restrict__ pro
   }
 }
 
-// C = alpha * sum_s partial_s (+ C).  WARP: one warp per output element, lane l
-// sums the splits l, l + 32, ..., then a fixed butterfly (long split lists);
-// otherwise one thread per element in split order.  Either way the same inputs
-// always give the same bits.
+// C = alpha * 2^(E_i + F_j - BETA (S + 1)) sum_s R_s (+ C): the split partials are
+// the exact int64 accumulators of their K ranges, so their sum is exact and the
+// result does not depend on how K was split (nor on the order).  WARP: one warp
+// per output element, lane l adding the splits l, l + 32, ... (long split lists);
+// otherwise one thread per element.
 template <bool WARP>
 __global__ void __launch_bounds__(256) k_emu_reduce(const EmuProb* __restrict__ probs, int nprobs,
                                                     const cplx* __restrict__ ws, int64_t ws_is, cplx* __restrict__ C,
-                                                    int64_t c_is, cplx alpha, int beta, int64_t n_red) {
+                                                    int64_t c_is, const int* __restrict__ Aex, int64_t aex_is,
+                                                    const int* __restrict__ Bex, int64_t bex_is, int eshift,
+                                                    cplx alpha, int beta, int64_t n_red) {
   const int inst = blockIdx.y, lane = WARP ? (threadIdx.x & 31) : 0;
   const int per = WARP ? 32 : 1;
   const int64_t stride = int64_t(gridDim.x) * (blockDim.x / per);
@@ -728,10 +729,10 @@ __global__ void __launch_bounds__(256) k_emu_reduce(const EmuProb* __restrict__ 
     while (pi + 1 < nprobs && (probs[pi].ksplit <= 1 || it >= probs[pi].red0 + int64_t(probs[pi].M) * probs[pi].N)) ++pi;
     const EmuProb& P = probs[pi];
     const int64_t n = int64_t(P.M) * P.N, e = it - P.red0;
-    const cplx* W = ws + inst * ws_is + P.ws;
-    double sr = 0.0, si = 0.0;
+    const longlong2* W = reinterpret_cast<const longlong2*>(ws + inst * ws_is + P.ws);
+    long long sr = 0, si = 0;
     for (int s = lane; s < P.ksplit; s += per) {
-      const cplx w = W[int64_t(s) * n + e];
+      const longlong2 w = W[int64_t(s) * n + e];
       sr += w.x;
       si += w.y;
     }
@@ -741,8 +742,11 @@ __global__ void __launch_bounds__(256) k_emu_reduce(const EmuProb* __restrict__ 
         si += __shfl_xor_sync(0xffffffffu, si, o);
       }
     if (lane == 0) {
+      const int gi = int(e / P.N), gj = int(e - int64_t(gi) * P.N);
+      const int ex = Aex[inst * aex_is + P.a_ex + gi] + Bex[inst * bex_is + P.b_ex + gj] - eshift;
+      const double re = scaled_i64(sr, ex), im = scaled_i64(si, ex);
       cplx* Cp = C + inst * c_is + P.c_off;
-      double vr = alpha.x * sr - alpha.y * si, vi = alpha.x * si + alpha.y * sr;
+      double vr = alpha.x * re - alpha.y * im, vi = alpha.x * im + alpha.y * re;
       if (beta) { const cplx o = Cp[e]; vr += o.x; vi += o.y; }
       Cp[e] = make_double2(vr, vi);
     }
@@ -750,14 +754,18 @@ __global__ void __launch_bounds__(256) k_emu_reduce(const EmuProb* __restrict__ 
 }
 
 static void launch_emu_reduce(const EmuProb* d, int np, int max_ksplit, const cplx* ws, int64_t ws_is, cplx* C,
-                              int64_t c_is, cplx alpha, int beta, int64_t n_red, int ninst, int sms, cudaStream_t st) {
+                              int64_t c_is, const int* aex, int64_t aex_is, const int* bex, int64_t bex_is, int S,
+                              cplx alpha, int beta, int64_t n_red, int ninst, int sms, cudaStream_t st) {
   const int64_t cap = int64_t(std::max(sms, 1)) * 16;
+  const int eshift = BETA * (S + 1);
   if (max_ksplit >= 64) {
     const int blocks = int(std::max<int64_t>(1, std::min<int64_t>((n_red + 7) / 8, cap)));
-    k_emu_reduce<true><<<dim3(blocks, ninst), 256, 0, st>>>(d, np, ws, ws_is, C, c_is, alpha, beta, n_red);
+    k_emu_reduce<true><<<dim3(blocks, ninst), 256, 0, st>>>(d, np, ws, ws_is, C, c_is, aex, aex_is, bex, bex_is, eshift,
+                                                            alpha, beta, n_red);
   } else {
     const int blocks = int(std::max<int64_t>(1, std::min<int64_t>((n_red + 255) / 256, cap)));
-    k_emu_reduce<false><<<dim3(blocks, ninst), 256, 0, st>>>(d, np, ws, ws_is, C, c_is, alpha, beta, n_red);
+    k_emu_reduce<false><<<dim3(blocks, ninst), 256, 0, st>>>(d, np, ws, ws_is, C, c_is, aex, aex_is, bex, bex_is,
+                                                             eshift, alpha, beta, n_red);
   }
 }
 
@@ -802,7 +810,48 @@ struct EmuPlan {
   cplx* d_ws = nullptr;
   int64_t ws_is = 0, red_elems = 0;
   const EmuPlan* b_owner = nullptr;  // another plan that slices the same B (same tensor, layout, S) first
+  // work decomposition (autotuned on the first eager run; neither choice changes the result bits)
+  int gm = EMU_GM;        // row tiles per group of the work order
+  double ks_mult = 1.0;   // multiplier of the default K-split count (0 = no split)
+  int64_t tiles_mn = 0;   // output tiles of all problems and instances
+  int64_t ws_cap = 0;     // split-K workspace allocated (elements per instance)
+  bool tuned = false;
+  std::vector<int> chunks;  // exact K chunks per problem
 };
+
+// K splits, work-item numbering and split-K workspace for a split multiplier: the
+// default splits long-K problems whose output tiles cannot fill the GPU into about
+// 4 x SM-count / tiles pieces of whole exact chunks
+static void layout_work(EmuPlan* p, int64_t sms, double mult) {
+  int tile0 = 0;
+  int64_t ws = 0;
+  p->red_elems = 0;
+  for (size_t k = 0; k < p->h.size(); ++k) {
+    EmuProb& e = p->h[k];
+    const int nkb = e.Kp / KB;
+    const int64_t chunks = p->chunks[k];
+    e.ksplit = 1;
+    e.kcb = int32_t(chunks * KC_BLOCKS);
+    if (mult > 0.0 && p->tiles_mn < 2 * sms && nkb >= 2 * KC_BLOCKS) {
+      int64_t ks = std::min<int64_t>(chunks, (4 * sms + p->tiles_mn - 1) / std::max<int64_t>(p->tiles_mn, 1));
+      ks = std::max<int64_t>(1, std::min<int64_t>(int64_t(double(ks) * mult + 0.5), std::min<int64_t>(chunks, 1024)));
+      e.kcb = int32_t(((chunks + ks - 1) / ks) * KC_BLOCKS);
+      e.ksplit = (nkb + e.kcb - 1) / e.kcb;
+    }
+    e.ws = 0;
+    e.red0 = 0;
+    if (e.ksplit > 1) {
+      e.ws = ws;
+      ws += int64_t(e.ksplit) * e.M * e.N;
+      e.red0 = p->red_elems;
+      p->red_elems += int64_t(e.M) * e.N;
+    }
+    e.tile0 = tile0;
+    tile0 += e.tiles_m * e.tiles_n * e.ksplit;
+  }
+  p->n_tiles = tile0;
+  p->ws_is = ws;
+}
 
 struct BKey {
   const void* ptr;
@@ -816,6 +865,8 @@ struct EmuState {
   std::vector<EmuPlan*> plans;
   std::vector<std::pair<BKey, EmuPlan*>> bowners;
   int* d_err = nullptr;
+  cplx* tune_buf = nullptr;  // scratch output for the autotuner's trial launches
+  int64_t tune_cap = 0;
 };
 
 bool emu_wanted(Ctx& c, const GemmPlan& g, const std::string&) {
@@ -854,14 +905,12 @@ EmuPlan* emu_plan(Ctx& c, const GemmPlan& g, const Tensor* A, const Tensor* B, b
   p->d_err = st->d_err;
   const int BN = bn_of(p->S);
   int64_t asl = 0, bsl = 0, aex = 0, bex = 0;
-  int tile0 = 0;
   int64_t au0 = 0, bu0 = 0;
   int64_t tiles_mn = 0;
   for (auto& q : g.h_probs)
     tiles_mn += int64_t((q.M + BM - 1) / BM) * ((q.N + BN / 2 - 1) / (BN / 2));
   tiles_mn *= c.ninst;
   const int64_t sms = std::max(c.sm_count, 1);
-  int64_t ws = 0;
   p->fuse_a = true;
   for (auto& q : g.h_probs) {
     EmuProb e{};
@@ -878,23 +927,7 @@ EmuPlan* emu_plan(Ctx& c, const GemmPlan& g, const Tensor* A, const Tensor* B, b
     e.brows = e.tiles_n == 1 ? (2 * q.N + 7) / 8 * 8 : BN;
     if (q.K > 32) p->fuse_a = false;
     const int nkb = e.Kp / KB;
-    e.ksplit = 1;
-    e.kcb = ((nkb + KC_BLOCKS - 1) / KC_BLOCKS) * KC_BLOCKS;
-    if (tiles_mn < 2 * sms && nkb >= 2 * KC_BLOCKS) {
-      const int64_t chunks = (nkb + KC_BLOCKS - 1) / KC_BLOCKS;
-      int64_t ks = std::min<int64_t>(chunks, (4 * sms + tiles_mn - 1) / std::max<int64_t>(tiles_mn, 1));
-      ks = std::max<int64_t>(1, std::min<int64_t>(ks, 512));
-      e.kcb = int32_t(((chunks + ks - 1) / ks) * KC_BLOCKS);
-      e.ksplit = (nkb + e.kcb - 1) / e.kcb;
-    }
-    if (e.ksplit > 1) {
-      e.ws = ws;
-      ws += int64_t(e.ksplit) * q.M * q.N;
-      e.red0 = p->red_elems;
-      p->red_elems += int64_t(q.M) * q.N;
-    }
-    e.tile0 = tile0;
-    tile0 += e.tiles_m * e.tiles_n * e.ksplit;
+    p->chunks.push_back((nkb + KC_BLOCKS - 1) / KC_BLOCKS);
     e.a_sl = asl;
     e.b_sl = bsl;
     asl += int64_t(e.tiles_m) * nkb * p->S * e.arows * KB;
@@ -913,7 +946,10 @@ EmuPlan* emu_plan(Ctx& c, const GemmPlan& g, const Tensor* A, const Tensor* B, b
     bu0 += int64_t(e.tiles_n) * nkh_of(e) * (e.brows / 2) * (KB / 8);
     p->h.push_back(e);
   }
-  p->n_tiles = tile0;
+  p->tiles_mn = tiles_mn;
+  if (c.force_ksplit_mult >= 0.0) p->ks_mult = std::min(c.force_ksplit_mult, 4.0);
+  if (c.force_group_rows > 0) p->gm = c.force_group_rows;
+  layout_work(p, sms, p->ks_mult);
   p->n_aunits = au0;
   p->n_bunits = bu0;
   p->asl_is = std::max<int64_t>(asl, 1);
@@ -936,9 +972,14 @@ EmuPlan* emu_plan(Ctx& c, const GemmPlan& g, const Tensor* A, const Tensor* B, b
     p->bex = (int*)c.dalloc(sizeof(int) * p->bex_is * c.ninst);
     if (B) st->bowners.push_back({key, p});
   }
-  if (ws) {
-    p->ws_is = ws;
-    p->d_ws = (cplx*)c.dalloc(sizeof(cplx) * ws * c.ninst);
+  // workspace for the largest split the tuner may try (multiplier 4)
+  {
+    const double m0 = p->ks_mult;
+    layout_work(p, sms, 4.0);
+    p->ws_cap = p->ws_is;
+    layout_work(p, sms, m0);
+    p->ws_cap = std::max(p->ws_cap, p->ws_is);
+    if (p->ws_cap) p->d_ws = (cplx*)c.dalloc(sizeof(cplx) * p->ws_cap * c.ninst);
   }
   p->d = (EmuProb*)c.dalloc(sizeof(EmuProb) * p->h.size());
   upload(c, p->d, p->h.data(), sizeof(EmuProb) * p->h.size());
@@ -974,17 +1015,88 @@ struct EmuStageTimer {
   }
 };
 
+// The GEMM launch of a plan (plus its split-K reduction) into C.
+template <int S>
+static void launch_product(Ctx& c, EmuPlan* p, cplx* C, int64_t cis, cplx alpha, bool beta, bool reduce) {
+  const int np = int(p->h.size());
+  set_smem_attr<S>();
+  const int n_work = p->n_tiles * c.ninst;
+  k_emu_gemm<S><<<dim3(std::min(n_work, std::max(c.sm_count, 1))), THREADS, Shape<S>::SMEM, c.stream>>>(
+      p->d, np, p->n_tiles, n_work, p->gm, p->asl, p->bsl, p->aex, p->bex, C, p->asl_is, p->bsl_is, p->aex_is,
+      p->bex_is, cis, alpha, p->red_elems ? ALPHA_GENERAL : alpha_code(alpha), beta ? 1 : 0, p->d_err, p->d_ws, p->ws_is);
+  KCHECK(c);
+  if (reduce && p->red_elems) {
+    int mks = 1;
+    for (auto& e : p->h) mks = std::max(mks, int(e.ksplit));
+    launch_emu_reduce(p->d, np, mks, p->d_ws, p->ws_is, C, cis, p->aex, p->aex_is, p->bex, p->bex_is, S, alpha,
+                      beta ? 1 : 0, p->red_elems, c.ninst, c.sm_count, c.stream);
+    KCHECK(c);
+  }
+}
+
+// Autotuner: on a plan's first eager run (slices in place), time the product for
+// each candidate work decomposition -- K-split multipliers {0, 1/2, 1, 2, 4} when the
+// default splits K, group sizes {4, 8, 16} when there are row and column tiles to
+// group -- and keep the fastest.  Trial launches write a scratch output; split-K
+// partials are exact, so no candidate changes the result.  Skipped while the
+// stream is being captured and for one-off products.
+template <int S>
+static void autotune(Ctx& c, EmuPlan* p, int64_t cis, cplx alpha) {
+  p->tuned = true;
+  if (!c.autotune) return;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  CK(cudaStreamIsCapturing(c.stream, &cs));
+  if (cs != cudaStreamCaptureStatusNone) return;
+  const int64_t sms = std::max(c.sm_count, 1);
+  std::vector<double> mults{p->ks_mult};
+  if (p->red_elems) mults = {0.0, 0.5, 1.0, 2.0, 4.0};
+  std::vector<int> gms{p->gm};
+  for (auto& e : p->h)
+    if (e.tiles_m > 4 && e.tiles_n > 1) { gms = {4, 8, 16}; break; }
+  if (mults.size() * gms.size() <= 1) return;
+  EmuState* st = (EmuState*)c.emu_state;
+  const int64_t need = std::max<int64_t>(cis, 1) * c.ninst;
+  if (need > st->tune_cap) {
+    st->tune_cap = std::max(need, 2 * st->tune_cap);
+    st->tune_buf = (cplx*)c.dalloc(sizeof(cplx) * st->tune_cap);
+  }
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  double best_ms = 1e30, best_m = p->ks_mult;
+  int best_gm = p->gm;
+  for (double m : mults) {
+    layout_work(p, sms, m);
+    upload(c, p->d, p->h.data(), sizeof(EmuProb) * p->h.size());
+    for (int g : gms) {
+      p->gm = g;
+      launch_product<S>(c, p, st->tune_buf, cis, alpha, false, true);  // warm-up
+      CK(cudaEventRecord(e0, c.stream));
+      launch_product<S>(c, p, st->tune_buf, cis, alpha, false, true);
+      CK(cudaEventRecord(e1, c.stream));
+      CK(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best_ms) { best_ms = ms; best_m = m; best_gm = g; }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  p->ks_mult = best_m;
+  p->gm = best_gm;
+  layout_work(p, sms, best_m);
+  upload(c, p->d, p->h.data(), sizeof(EmuProb) * p->h.size());
+  if (c.profile)
+    fprintf(stderr, "[exp_tune] %d candidates: K-split x%.1f, group %d rows, %.3f ms\n", int(mults.size() * gms.size()),
+            best_m, best_gm, best_ms);
+}
+
 template <int S>
 static void run_s(Ctx& c, EmuPlan* p, const cplx* A, const cplx* B, cplx* C, int64_t ais, int64_t bis, int64_t cis,
                   cplx alpha, bool beta, bool gemm_only) {
   const int np = int(p->h.size());
   if (gemm_only) {  // the tensor-core product alone, on the slices already in place
-    set_smem_attr<S>();
-    const int n_work = p->n_tiles * c.ninst;
-    k_emu_gemm<S><<<dim3(std::min(n_work, std::max(c.sm_count, 1))), THREADS, Shape<S>::SMEM, c.stream>>>(
-        p->d, np, p->n_tiles, n_work, p->asl, p->bsl, p->aex, p->bex, C, p->asl_is, p->bsl_is, p->aex_is, p->bex_is,
-        cis, alpha, p->red_elems ? ALPHA_GENERAL : alpha_code(alpha), beta ? 1 : 0, p->d_err, p->d_ws, p->ws_is);
-    KCHECK(c);
+    launch_product<S>(c, p, C, cis, alpha, beta, false);
     return;
   }
   EmuStageTimer tm(c.profile, c.stream);
@@ -1022,22 +1134,18 @@ static void run_s(Ctx& c, EmuPlan* p, const cplx* A, const cplx* B, cplx* C, int
     if (p->b_const) p->b_ready = true;
   }
   tm.mark(4);
-  set_smem_attr<S>();
-  const int n_work = p->n_tiles * c.ninst;
-  k_emu_gemm<S><<<dim3(std::min(n_work, std::max(c.sm_count, 1))), THREADS, Shape<S>::SMEM, c.stream>>>(
-      p->d, np, p->n_tiles, n_work, p->asl, p->bsl, p->aex, p->bex, C, p->asl_is, p->bsl_is, p->aex_is, p->bex_is, cis,
-      alpha, p->red_elems ? ALPHA_GENERAL : alpha_code(alpha), beta ? 1 : 0, p->d_err, p->d_ws, p->ws_is);
-  KCHECK(c);
+  if (!p->tuned) autotune<S>(c, p, cis, alpha);
+  launch_product<S>(c, p, C, cis, alpha, beta, false);
   tm.mark(5);
   if (p->red_elems) {
     int mks = 1;
     for (auto& e : p->h) mks = std::max(mks, int(e.ksplit));
-    launch_emu_reduce(p->d, np, mks, p->d_ws, p->ws_is, C, cis, alpha, beta ? 1 : 0, p->red_elems, c.ninst, c.sm_count,
-                      c.stream);
+    launch_emu_reduce(p->d, np, mks, p->d_ws, p->ws_is, C, cis, p->aex, p->aex_is, p->bex, p->bex_is, S, alpha,
+                      beta ? 1 : 0, p->red_elems, c.ninst, c.sm_count, c.stream);
     KCHECK(c);
   }
   tm.mark(6);
-  tm.report(int64_t(n_work));
+  tm.report(int64_t(p->n_tiles) * c.ninst);
 }
 
 void emu_run(Ctx& c, EmuPlan* p, const GemmPlan&, const cplx* A, const cplx* B, cplx* C, int64_t ais, int64_t bis,
@@ -1164,10 +1272,10 @@ exp_status noalloc_launch(cudaStream_t st, unsigned char* base, int M, int N, in
   }
   const int n_work = int(tiles_mn * e.ksplit);
   k_emu_gemm<S><<<dim3(unsigned(std::min(n_work, sms)), 1), THREADS, SH::SMEM, st>>>(
-      d_probs, 1, n_work, n_work, asl, bsl, aex, bex, Cout, 0, 0, 0, 0, 0, alpha,
+      d_probs, 1, n_work, n_work, EMU_GM, asl, bsl, aex, bex, Cout, 0, 0, 0, 0, 0, alpha,
       e.ksplit > 1 ? ALPHA_GENERAL : alpha_code(alpha), beta, d_err, ws, 0);
   if (e.ksplit > 1) {
-    launch_emu_reduce(d_probs, 1, e.ksplit, ws, 0, Cout, 0, alpha, beta, int64_t(M) * N, 1, sms, st);
+    launch_emu_reduce(d_probs, 1, e.ksplit, ws, 0, Cout, 0, aex, 0, bex, 0, S, alpha, beta, int64_t(M) * N, 1, sms, st);
   }
   cudaError_t ce = cudaGetLastError();
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);

@@ -162,3 +162,31 @@ def test_packed_ladder_matches_full_pairs(expgb, no, nv, G):
     for k, ref in enumerate((t1, t2)):
         np.testing.assert_allclose(runs[1][k], runs[0][k], atol=1e-13, rtol=0)
         np.testing.assert_allclose(runs[1][k], ref, atol=1e-12, rtol=0)
+
+
+def test_emulated_bits_independent_of_work_decomposition(expgb):
+    """The autotuner may pick any K split and work order for the emulated products;
+    split-K partials are exact integers, so the amplitudes come out bit for bit the
+    same for the tuned choice and for forced extreme choices."""
+    prob = syn.make_problem(511, 10, 40, 2)
+    runs = []
+    for env in ({}, {"EXP_AUTOTUNE": "0", "EXP_KSPLIT_MULT": "0", "EXP_GROUP_ROWS": "4"},
+                {"EXP_AUTOTUNE": "0", "EXP_KSPLIT_MULT": "2", "EXP_GROUP_ROWS": "16"}):
+        old = {k: os.environ.get(k) for k in ("EXP_AUTOTUNE", "EXP_KSPLIT_MULT", "EXP_GROUP_ROWS")}
+        os.environ.update(env)
+        try:
+            ctx = expgb.from_problems([prob], precision=expgb.EXP_EMU_BF16, n_slices=5, diis_dim=0,
+                                      emu_min_macs=1.0)
+            ctx.init_integrals([prob.seed])
+            ctx.iterate(2)
+            runs.append([x.cpu().numpy() for x in ctx.get_amplitudes(0)])
+            ctx.close()
+        finally:
+            for k, v in old.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+    for r in runs[1:]:
+        for a, b in zip(runs[0], r):
+            assert np.array_equal(a.view(np.float64), b.view(np.float64))

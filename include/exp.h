@@ -168,9 +168,9 @@ exp_status exp_set_amplitudes(exp_ctx* ctx, int inst, const void* t1_dev, const 
 exp_status exp_work_per_iteration(const exp_ctx* ctx, double* complex_macs);
 
 /* Time the contraction with the most work on its own: `reps` launches of its
- * grouped GEMM kernel on the context stream between CUDA events (emulated: the
- * tensor-core kernel alone, on the operand slices of the last iteration; the
- * slicing passes and a split-K reduction are not included).  Writes the call-site
+ * grouped GEMM kernel on the context stream between CUDA events (emulated: one
+ * full product first to put its operand slices in place, then the tensor-core
+ * kernel alone; the slicing passes and a split-K reduction are not timed).  Writes the call-site
  * name (NUL-terminated, truncated to name_len), the mean milliseconds per launch
  * and its complex multiply-adds per launch.  Overwrites that contraction's
  * output buffer, which the next iteration recomputes. */

@@ -417,6 +417,8 @@ extern "C" exp_status exp_profile_top(exp_ctx* x, int reps, char* name, int name
   cplx* cd = Cg ? Cg->d : (P->gemm_out ? P->gemm_out : nullptr);
   int64_t cis = Cg ? Cg->is : P->gemm_out_is;
   if (!cd) throw ExpError{EXP_ESTATE, "contraction output unknown"};
+  // per-iteration operand slices share one region: make them this product's again
+  if (P->emulate) emu_run(c, P->emu, P->g, P->A->d, P->B->d, cd, P->A->is, P->B->is, cis, P->alpha, P->gemm_beta);
   CK(cudaStreamSynchronize(c.stream));
   CK(cudaEventRecord(c.ev0, c.stream));
   for (int r = 0; r < reps; ++r) {

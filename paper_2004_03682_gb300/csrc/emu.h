@@ -4,8 +4,10 @@
 #include "engine.h"
 
 bool emu_wanted(Ctx& c, const GemmPlan& g, const std::string& site);
+// b_shareable: B is a lasting tensor, so a later product reading the same tensor in
+// the same layout may reuse this plan's B slices
 EmuPlan* emu_plan(Ctx& c, const GemmPlan& g, const Tensor* A, const Tensor* B, bool a_const,
-                  bool b_const);
+                  bool b_const, bool b_shareable = true);
 // gemm_only: launch only the tensor-core kernel on the slices of the previous run
 // (timing); the split-K reduction and the slicing passes are skipped
 void emu_run(Ctx& c, EmuPlan* p, const GemmPlan& g, const cplx* A, const cplx* B, cplx* C,

@@ -120,6 +120,31 @@ void* Ctx::dalloc(size_t bytes) {
   return p;
 }
 
+void Ctx::dfree(void* p) {
+  for (size_t k = 0; k < owned.size(); ++k)
+    if (owned[k].p == p) {
+      alloc.free(p, alloc.user);
+      owned.erase(owned.begin() + k);
+      return;
+    }
+}
+
+void* arena_reserve(Ctx& c, Arena& a, size_t bytes) {
+  if (bytes <= a.bytes) return a.base;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  CK(cudaStreamIsCapturing(c.stream, &cs));
+  if (cs != cudaStreamCaptureStatusNone) throw ExpError{EXP_ESTATE, "scratch arena would grow during stream capture"};
+  if (a.base) {
+    CK(cudaStreamSynchronize(c.stream));  // work queued on the old region must finish first
+    c.dfree(a.base);
+    a.base = nullptr;
+    a.bytes = 0;
+  }
+  a.base = c.dalloc(bytes);
+  a.bytes = bytes;
+  return a.base;
+}
+
 void Ctx::dfree_all() {
   for (auto& b : owned) alloc.free(b.p, alloc.user);
   owned.clear();
@@ -413,9 +438,9 @@ static const Tensor* prepare_operand(Ctx& c, const std::string& site, const Oper
   const Tensor* t = op.t;
   if (order == op.labels && t->L.nrow == nrow) return t;
   Layout L = relayout(c, t->L, op.labels, order, nrow);
-  Tensor* s = new_tensor(c, L, false);
-  scratch = *s;
-  delete s;
+  scratch.L = L;  // storage: the operand arena, placed by the caller
+  scratch.is = std::max<int64_t>(L.size, 1);
+  scratch.d = nullptr;
   std::vector<std::string> ts{order};
   plan = make_perm_plan(c, L, order.c_str(), t->L, op.labels, ts);
   permuted = true;
@@ -501,9 +526,9 @@ void einsum(Ctx& c, const std::string& site, cplx alpha, Operand A, Operand B, T
         sg[FA.size() + k] = P->B->L.sg[K.size() + k];
       }
       Layout LC = make_layout(c.spaces, c.G, int(ordC.size()), sp, sg, int(FA.size()));
-      Tensor* s = new_tensor(c, LC, false);
-      P->C2 = *s;
-      delete s;
+      P->C2.L = LC;  // storage: the operand arena
+      P->C2.is = std::max<int64_t>(LC.size, 1);
+      P->C2.d = nullptr;
       P->permC = true;
       P->gemm_beta = false;
       P->g = make_gemm_plan(c, P->A->L, P->B->L, LC);
@@ -512,8 +537,16 @@ void einsum(Ctx& c, const std::string& site, cplx alpha, Operand A, Operand B, T
     }
     for (size_t k = 0; k < coefs.size(); ++k) P->cterms[k] = make_double2(coefs[k], 0.0);
     P->alpha = alpha;
+    {  // A2 | B2 | C2 side by side in the operand arena
+      int64_t off = 0;
+      if (P->permA) { P->offA2 = off; off += P->A2.is * c.ninst; }
+      if (P->permB) { P->offB2 = off; off += P->B2.is * c.ninst; }
+      if (P->permC) { P->offC2 = off; off += P->C2.is * c.ninst; }
+      arena_reserve(c, c.op_arena, size_t(off) * sizeof(cplx));
+    }
     P->emulate = emu_wanted(c, P->g, site);
-    if (P->emulate) P->emu = emu_plan(c, P->g, P->A, P->B, A.v != nullptr, B.v != nullptr);
+    // a B operand in the arena is not a tensor other contractions could share slices of
+    if (P->emulate) P->emu = emu_plan(c, P->g, P->A, P->B, A.v != nullptr, B.v != nullptr, !P->permB);
   } else {
     P = it->second.get();
     if (P->swapped) std::swap(A, B);
@@ -524,6 +557,12 @@ void einsum(Ctx& c, const std::string& site, cplx alpha, Operand A, Operand B, T
   if (prof) {
     for (auto& e : pe) CK(cudaEventCreate(&e));
     CK(cudaEventRecord(c.pev0, c.stream));
+  }
+  {
+    cplx* ab = (cplx*)c.op_arena.base;
+    if (P->permA) P->A2.d = ab + P->offA2;
+    if (P->permB) P->B2.d = ab + P->offB2;
+    if (P->permC) P->C2.d = ab + P->offC2;
   }
   if (P->permA) {
     cplx one = make_double2(1, 0);

@@ -110,6 +110,14 @@ struct DevBuf {
   size_t bytes = 0;
 };
 
+// Scratch shared by the contractions of an iteration: each contraction's transient
+// buffers (permuted operands, GEMM output, operand slices) live only during its own
+// call, and the calls run in stream order, so they share one region per kind.
+struct Arena {
+  void* base = nullptr;
+  size_t bytes = 0;
+};
+
 struct Tensor {
   Layout L;
   cplx* d = nullptr;  // instance k at d + k * is
@@ -164,6 +172,7 @@ struct EinsumPlan {
   int64_t gemm_out_is = 0;
   bool emulate = false;
   bool swapped = false;  // operands exchanged at planning (C^T = B^T A^T); every call swaps them too
+  int64_t offA2 = 0, offB2 = 0, offC2 = 0;  // element offsets of A2 / B2 / C2 in the operand arena
   EmuPlan* emu = nullptr;
   size_t scratch_bytes = 0;
 };
@@ -258,7 +267,11 @@ struct Ctx {
   void* packed_state = nullptr;  // packed particle-particle ladder (packed.cu)
   void* ccsd_state = nullptr;
 
+  Arena op_arena;     // permuted operands and GEMM outputs of one contraction
+  Arena slice_arena;  // per-iteration operand slices of one emulated product
+
   void* dalloc(size_t bytes);
+  void dfree(void* p);
   void dfree_all();
 };
 
@@ -270,6 +283,9 @@ Layout make_layout(const std::vector<Space>& spaces, int G, int rank, const int*
 void enumerate_blocks(const Layout& L, const std::vector<Space>& spaces,
                       std::vector<SubBlock>& out);
 Tensor* new_tensor(Ctx& c, const Layout& L, bool zero);
+// grow an arena to at least `bytes` (only outside stream capture; synchronises the
+// stream before the old region is released); returns its base
+void* arena_reserve(Ctx& c, Arena& a, size_t bytes);
 Tensor* work_tensor(Ctx& c, const std::string& name, const Layout& L);
 const Tensor* integral(Ctx& c, const IntRef& v, const int perm[4], int nrow);
 void gen_tasks(Ctx& c, const Layout& L, std::vector<GenTask>& tasks,

@@ -187,6 +187,23 @@ __device__ __forceinline__ double scaled_i64(long long R, int e) {
   return __longlong_as_double((long long)(sgn | (unsigned long long)(be) << 52 | (mant & 0xFFFFFFFFFFFFFull)));
 }
 
+// the same for a 128-bit integer: above 63 bits the value is shifted down to 63
+// bits with the dropped bits folded into the lowest (sticky) bit, which leaves the
+// round-to-nearest-even decision of scaled_i64 unchanged
+__device__ __forceinline__ double scaled_i128(__int128 R, int e) {
+  const long long lo = (long long)R;
+  if ((__int128)lo == R) return scaled_i64(lo, e);
+  const bool neg = R < 0;
+  unsigned __int128 m = neg ? (unsigned __int128)(-R) : (unsigned __int128)R;
+  const unsigned long long hi = (unsigned long long)(m >> 64);
+  const int len = 128 - __clzll((long long)hi);  // bit length, > 63
+  const int sft = len - 63;
+  unsigned long long v = (unsigned long long)(m >> sft);
+  if ((m << (128 - sft)) != 0) v |= 1ull;
+  const long long sv = (long long)v;
+  return scaled_i64(neg ? -sv : sv, e + sft);
+}
+
 // K half of the real embedding (each half padded to 16) and the number of
 // 32-wide k ranges a half spans (the split kernels' CTA count per tile)
 __host__ __device__ __forceinline__ int kh_of(const EmuProb& P) { return P.Kp / 2; }
@@ -730,7 +747,7 @@ __global__ void __launch_bounds__(256) k_emu_reduce(const EmuProb* __restrict__ 
     const EmuProb& P = probs[pi];
     const int64_t n = int64_t(P.M) * P.N, e = it - P.red0;
     const longlong2* W = reinterpret_cast<const longlong2*>(ws + inst * ws_is + P.ws);
-    long long sr = 0, si = 0;
+    __int128 sr = 0, si = 0;  // the sum of the partials may exceed 63 bits
     for (int s = lane; s < P.ksplit; s += per) {
       const longlong2 w = W[int64_t(s) * n + e];
       sr += w.x;
@@ -738,13 +755,17 @@ __global__ void __launch_bounds__(256) k_emu_reduce(const EmuProb* __restrict__ 
     }
     if (WARP)
       for (int o = 16; o; o >>= 1) {
-        sr += __shfl_xor_sync(0xffffffffu, sr, o);
-        si += __shfl_xor_sync(0xffffffffu, si, o);
+        const long long rh = __shfl_xor_sync(0xffffffffu, (long long)(sr >> 64), o);
+        const unsigned long long rl = __shfl_xor_sync(0xffffffffu, (unsigned long long)sr, o);
+        const long long ih = __shfl_xor_sync(0xffffffffu, (long long)(si >> 64), o);
+        const unsigned long long il = __shfl_xor_sync(0xffffffffu, (unsigned long long)si, o);
+        sr += ((__int128)rh << 64) | (__int128)rl;
+        si += ((__int128)ih << 64) | (__int128)il;
       }
     if (lane == 0) {
       const int gi = int(e / P.N), gj = int(e - int64_t(gi) * P.N);
       const int ex = Aex[inst * aex_is + P.a_ex + gi] + Bex[inst * bex_is + P.b_ex + gj] - eshift;
-      const double re = scaled_i64(sr, ex), im = scaled_i64(si, ex);
+      const double re = scaled_i128(sr, ex), im = scaled_i128(si, ex);
       cplx* Cp = C + inst * c_is + P.c_off;
       double vr = alpha.x * re - alpha.y * im, vi = alpha.x * im + alpha.y * re;
       if (beta) { const cplx o = Cp[e]; vr += o.x; vi += o.y; }
@@ -817,7 +838,18 @@ struct EmuPlan {
   int64_t ws_cap = 0;     // split-K workspace allocated (elements per instance)
   bool tuned = false;
   std::vector<int> chunks;  // exact K chunks per problem
+  bool asl_arena = false, bsl_arena = false;  // slices placed in the slice arena at each run
+  int64_t bsl_off = 0;                        // element offset of the B slices there
 };
+
+// Largest number of exact chunks one work item may accumulate in int64: the sum over
+// a K range of Kp real terms is bounded by Kp 2^(14 + 7 (S - 1) + 1) (leading digits
+// up to 2^7 each, the lower diagonals adding less than the leading one), which must
+// stay below 2^63.  Longer contractions are split and the partials added in 128 bits.
+static int64_t max_chunks_per_split(int S) {
+  const int bits = 48 - 7 * (S - 1);  // log2 of the largest Kp
+  return std::max<int64_t>(1, (int64_t(1) << std::min(bits, 40)) / (KC_BLOCKS * KB));
+}
 
 // K splits, work-item numbering and split-K workspace for a split multiplier: the
 // default splits long-K problems whose output tiles cannot fill the GPU into about
@@ -826,18 +858,19 @@ static void layout_work(EmuPlan* p, int64_t sms, double mult) {
   int tile0 = 0;
   int64_t ws = 0;
   p->red_elems = 0;
+  const int64_t cmax = max_chunks_per_split(p->S);
   for (size_t k = 0; k < p->h.size(); ++k) {
     EmuProb& e = p->h[k];
     const int nkb = e.Kp / KB;
     const int64_t chunks = p->chunks[k];
-    e.ksplit = 1;
-    e.kcb = int32_t(chunks * KC_BLOCKS);
+    int64_t ks = 1;
     if (mult > 0.0 && p->tiles_mn < 2 * sms && nkb >= 2 * KC_BLOCKS) {
-      int64_t ks = std::min<int64_t>(chunks, (4 * sms + p->tiles_mn - 1) / std::max<int64_t>(p->tiles_mn, 1));
+      ks = std::min<int64_t>(chunks, (4 * sms + p->tiles_mn - 1) / std::max<int64_t>(p->tiles_mn, 1));
       ks = std::max<int64_t>(1, std::min<int64_t>(int64_t(double(ks) * mult + 0.5), std::min<int64_t>(chunks, 1024)));
-      e.kcb = int32_t(((chunks + ks - 1) / ks) * KC_BLOCKS);
-      e.ksplit = (nkb + e.kcb - 1) / e.kcb;
     }
+    ks = std::max<int64_t>(ks, (chunks + cmax - 1) / cmax);  // every split's int64 accumulator fits
+    e.kcb = int32_t(((chunks + ks - 1) / ks) * KC_BLOCKS);
+    e.ksplit = (nkb + e.kcb - 1) / e.kcb;
     e.ws = 0;
     e.red0 = 0;
     if (e.ksplit > 1) {
@@ -888,7 +921,8 @@ static void set_smem_attr() {
 
 static int bn_of(int S) { return S <= 5 ? 48 : 32; }
 
-EmuPlan* emu_plan(Ctx& c, const GemmPlan& g, const Tensor* A, const Tensor* B, bool a_const, bool b_const) {
+EmuPlan* emu_plan(Ctx& c, const GemmPlan& g, const Tensor* A, const Tensor* B, bool a_const, bool b_const,
+                  bool b_shareable) {
   EmuState* st = (EmuState*)c.emu_state;
   if (!st) {
     st = new EmuState();
@@ -956,22 +990,39 @@ EmuPlan* emu_plan(Ctx& c, const GemmPlan& g, const Tensor* A, const Tensor* B, b
   p->bsl_is = std::max<int64_t>(bsl, 1);
   p->aex_is = std::max<int64_t>(aex, 1);
   p->bex_is = std::max<int64_t>(bex, 1);
-  p->asl = (__nv_bfloat16*)c.dalloc(sizeof(__nv_bfloat16) * p->asl_is * c.ninst);
+  // slices of an integral (made once) or of a lasting tensor other products may share
+  // get their own buffers; the per-iteration slices of this product alone live in the
+  // slice arena (A first, then B) and are placed at every run
+  int64_t arena_elems = 0;
+  if (a_const) {
+    p->asl = (__nv_bfloat16*)c.dalloc(sizeof(__nv_bfloat16) * p->asl_is * c.ninst);
+  } else {
+    p->asl_arena = true;
+    arena_elems = p->asl_is * c.ninst;
+  }
   p->aex = (int*)c.dalloc(sizeof(int) * p->aex_is * c.ninst);
   // B slices: reuse those of an earlier plan that reads the same tensor the same way
   // (plans run in creation order every iteration, so the owner has sliced it already)
   BKey key{B ? (const void*)B->d : nullptr, B ? B->is : 0, p->S, {}};
   for (auto& e : p->h) { key.probs.push_back(e.b_src); key.probs.push_back(e.K); key.probs.push_back(e.N); }
-  for (auto& kv : st->bowners)
-    if (B && kv.first == key) { p->b_owner = kv.second; break; }
+  if (B && b_shareable)
+    for (auto& kv : st->bowners)
+      if (kv.first == key) { p->b_owner = kv.second; break; }
   if (p->b_owner) {
     p->bsl = p->b_owner->bsl;
     p->bex = p->b_owner->bex;
   } else {
-    p->bsl = (__nv_bfloat16*)c.dalloc(sizeof(__nv_bfloat16) * p->bsl_is * c.ninst);
+    if (b_const || b_shareable) {
+      p->bsl = (__nv_bfloat16*)c.dalloc(sizeof(__nv_bfloat16) * p->bsl_is * c.ninst);
+    } else {
+      p->bsl_arena = true;
+      p->bsl_off = (arena_elems + 127) / 128 * 128;
+      arena_elems = p->bsl_off + p->bsl_is * c.ninst;
+    }
     p->bex = (int*)c.dalloc(sizeof(int) * p->bex_is * c.ninst);
-    if (B) st->bowners.push_back({key, p});
+    if (B && b_shareable) st->bowners.push_back({key, p});
   }
+  if (arena_elems) arena_reserve(c, c.slice_arena, sizeof(__nv_bfloat16) * size_t(arena_elems));
   // workspace for the largest split the tuner may try (multiplier 4)
   {
     const double m0 = p->ks_mult;
@@ -1095,6 +1146,8 @@ template <int S>
 static void run_s(Ctx& c, EmuPlan* p, const cplx* A, const cplx* B, cplx* C, int64_t ais, int64_t bis, int64_t cis,
                   cplx alpha, bool beta, bool gemm_only) {
   const int np = int(p->h.size());
+  if (p->asl_arena) p->asl = (__nv_bfloat16*)c.slice_arena.base;
+  if (p->bsl_arena) p->bsl = (__nv_bfloat16*)c.slice_arena.base + p->bsl_off;
   if (gemm_only) {  // the tensor-core product alone, on the slices already in place
     launch_product<S>(c, p, C, cis, alpha, beta, false);
     return;
@@ -1215,12 +1268,15 @@ exp_status noalloc_launch(cudaStream_t st, unsigned char* base, int M, int N, in
   e.tiles_n = (N + BN / 2 - 1) / (BN / 2);
   const int nkb = e.Kp / KB;
   const int64_t tiles_mn = int64_t(e.tiles_m) * e.tiles_n;
-  e.ksplit = 1;
-  e.kcb = ((nkb + KC_BLOCKS - 1) / KC_BLOCKS) * KC_BLOCKS;
-  if (tiles_mn < 2LL * sms && nkb >= 2 * KC_BLOCKS) {
+  {
     const int64_t chunks = (nkb + KC_BLOCKS - 1) / KC_BLOCKS;
-    int64_t ks = std::min<int64_t>(chunks, (4LL * sms + tiles_mn - 1) / std::max<int64_t>(tiles_mn, 1));
-    ks = std::max<int64_t>(1, std::min<int64_t>(ks, 512));
+    int64_t ks = 1;
+    if (tiles_mn < 2LL * sms && nkb >= 2 * KC_BLOCKS) {
+      ks = std::min<int64_t>(chunks, (4LL * sms + tiles_mn - 1) / std::max<int64_t>(tiles_mn, 1));
+      ks = std::max<int64_t>(1, std::min<int64_t>(ks, 512));
+    }
+    const int64_t cmax = max_chunks_per_split(S);
+    ks = std::max<int64_t>(ks, (chunks + cmax - 1) / cmax);
     e.kcb = int32_t(((chunks + ks - 1) / ks) * KC_BLOCKS);
     e.ksplit = (nkb + e.kcb - 1) / e.kcb;
   }

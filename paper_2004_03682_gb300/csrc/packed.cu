@@ -207,6 +207,7 @@ void launch_pack_scatter(Ctx& c, cplx* dst, int64_t dis, const cplx* src, int64_
 struct PackedOp {
   std::string site;
   Tensor A, B, C;             // packed operands (A or B may alias the shared T_P)
+  int64_t offB = -1, offC = 0;  // operand-arena element offsets of B (-1: not there) and C
   PackDims dA{}, dB{}, dC{};  // with the full counterparts for generation / gather / scatter
   const PairTable *Ar = nullptr, *Ac = nullptr, *Br = nullptr, *Bc = nullptr, *Cr = nullptr, *Cc = nullptr;
   EinsumPlan* plan = nullptr;  // owned by c.plans
@@ -262,6 +263,15 @@ static Tensor packed_tensor(Ctx& c, const PairTable& R, const PairTable& C) {
   return r;
 }
 
+// a packed matrix placed in the operand arena at run time
+static Tensor arena_tensor(const PairTable& R, const PairTable& C) {
+  Tensor t;
+  t.L = packed_layout(R, C);
+  t.is = std::max<int64_t>(t.L.size, 1);
+  t.d = nullptr;
+  return t;
+}
+
 void packed_tau(Ctx& c, const Tensor& tau) {
   PackedState& s = PS(c);
   if (!s.vv) {
@@ -276,6 +286,13 @@ void packed_tau(Ctx& c, const Tensor& tau) {
 // C_P = A_P B_P through the emulated or FP64 grouped GEMM, registered in c.plans
 // under `site` (so the work accounting and the top-contraction report see it)
 static void finish_op(Ctx& c, PackedOp* op, bool a_const, double alpha = 1.0) {
+  {
+    int64_t off = 0;
+    if (op->offB >= 0) { op->offB = off; off += op->B.is * c.ninst; }
+    op->offC = off;
+    off += op->C.is * c.ninst;
+    arena_reserve(c, c.op_arena, size_t(off) * sizeof(cplx));
+  }
   EinsumPlan* P = new EinsumPlan();
   c.plans[op->site].reset(P);
   op->plan = P;
@@ -287,11 +304,15 @@ static void finish_op(Ctx& c, PackedOp* op, bool a_const, double alpha = 1.0) {
   P->gemm_beta = false;
   P->g = make_gemm_plan(c, op->A.L, op->B.L, op->C.L);
   P->emulate = emu_wanted(c, P->g, op->site);
-  if (P->emulate) P->emu = emu_plan(c, P->g, &op->A, &op->B, a_const, false);
+  if (P->emulate) P->emu = emu_plan(c, P->g, &op->A, &op->B, a_const, false, op->offB < 0);
 }
 
 static void run_op(Ctx& c, PackedOp* op, const std::function<void()>& before, const std::function<void()>& after) {
   EinsumPlan* P = op->plan;
+  cplx* ab = (cplx*)c.op_arena.base;
+  if (op->offB >= 0) op->B.d = ab + op->offB;
+  op->C.d = ab + op->offC;
+  P->C2.d = op->C.d;
   const bool prof = c.profile;
   cudaEvent_t pe[2] = {nullptr, nullptr};
   if (prof) {
@@ -343,7 +364,7 @@ static PackedOp* int_times_tau(Ctx& c, const std::string& site, const PairTable&
   op->B = s.TP;
   op->Cr = &table(c, dst.L, true, rows_packed);
   op->Cc = &table(c, dst.L, false, true);
-  op->C = packed_tensor(c, R, *s.oo);
+  op->C = arena_tensor(R, *s.oo);
   op->dC = pack_dims(*op->Cr, *op->Cc);
   launch_generate_pairs(c, op->A.d, op->A.is, op->dA, R, *s.vv);
   finish_op(c, op, true, alpha);
@@ -381,11 +402,12 @@ void packed_hh(Ctx& c, const Tensor& W, Tensor& r2) {
     op->A = s.TP;
     op->Br = &table(c, W.L, true, true);  // (m, n), m < n: same enumeration as the tau columns
     op->Bc = &ijf;
-    op->B = packed_tensor(c, *op->Br, ijf);
+    op->B = arena_tensor(*op->Br, ijf);
+    op->offB = 0;
     op->dB = pack_dims(*op->Br, ijf);
     op->Cr = s.vv;
     op->Cc = &table(c, r2.L, false, false);
-    op->C = packed_tensor(c, *s.vv, ijf);
+    op->C = arena_tensor(*s.vv, ijf);
     op->dC = pack_dims(*op->Cr, *op->Cc);
     finish_op(c, op, false);
   } else {

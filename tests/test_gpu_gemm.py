@@ -46,10 +46,25 @@ def test_fp64_kernel_matches_numpy(env, M, N, K):
 @pytest.mark.parametrize("S", [3, 4, 5, 6])
 @pytest.mark.parametrize("M,N,K", SHAPES + [(14, 14, 40000), (81, 14, 30000)])
 def test_emulated_exact_on_integer_inputs(env, S, M, N, K):
-    """(the two long-K shapes run split over K: partial sums in FP64, fixed order)"""
+    """(the two long-K shapes run split over K: exact integer partials, added exactly)"""
     torch, expgb = env
     rng = np.random.default_rng(S * 100 + M + N + K)
     A, B = _c(rng, (M, K), integer=True), _c(rng, (K, N), integer=True)
+    dA, dB = torch.tensor(A, device="cuda"), torch.tensor(B, device="cuda")
+    out = expgb.zgemm(dA, dB, precision=expgb.EXP_EMU_BF16, n_slices=S).cpu().numpy()
+    np.testing.assert_array_equal(out, A @ B)
+
+
+@pytest.mark.parametrize("S", [5, 6])
+def test_emulated_long_k_equal_magnitudes_exact(env, S):
+    """Every element at its row's / column's maximum makes every leading slice
+    digit as large as it gets: the exact integer accumulator then grows fastest.
+    K' = 2K = 100000 real terms is past what one int64 accumulator holds with six
+    slices, so this pins the forced K splits and the 128-bit sum of the partials."""
+    torch, expgb = env
+    M, N, K = 8, 8, 50000
+    A = np.full((M, K), 8 + 8j)
+    B = np.full((K, N), 8 - 8j)
     dA, dB = torch.tensor(A, device="cuda"), torch.tensor(B, device="cuda")
     out = expgb.zgemm(dA, dB, precision=expgb.EXP_EMU_BF16, n_slices=S).cpu().numpy()
     np.testing.assert_array_equal(out, A @ B)

@@ -83,7 +83,8 @@ typedef struct {
                                  shared by all instances; NULL when n_active = 0 */
   double level_shift;      /* sigma >= 0: (0h,0p) update t <- t + (RHS - D t)/(D - sigma) (the same
                               fixed point; smaller steps for strongly coupled problems); 0 = the
-                              plain update t <- RHS/D */
+                              plain update t <- RHS/D.  The (0h,1p) Bloch update divides by
+                              D + sigma sign(D) the same way. */
   int packed;              /* 1: the particle-particle ladder sum_{c<d} <ab||cd> tau_ij^cd on pair-packed
                               operands (a<b, c<d, i<j per pair irrep; <ab||cd> stored packed, a
                               quarter of the full size); 0: full pair compounds */

@@ -112,7 +112,8 @@ __global__ void __launch_bounds__(256) k_fs_update(const cplx* __restrict__ R, c
                                                    const double* __restrict__ Dfs, const cplx* __restrict__ X,
                                                    const int8_t* __restrict__ role, const cplx* __restrict__ T,
                                                    cplx* __restrict__ Tn, cplx* __restrict__ En, int64_t namp, int dim,
-                                                   const int* __restrict__ state, double* __restrict__ part) {
+                                                   const int* __restrict__ state, double* __restrict__ part,
+                                                   double shift) {
   __shared__ double sh[32];
   const int inst = blockIdx.y;
   const int* st = state + inst * 4;
@@ -128,7 +129,9 @@ __global__ void __launch_bounds__(256) k_fs_update(const cplx* __restrict__ R, c
         const cplx r = R[off + k], x = X[off + k];
         const double d0 = D0[off + k], df = Dfs[off + k];
         const double rr = r.x - d0 * t.x - x.x, ri = r.y - d0 * t.y - x.y;
-        const double q = 1.0 / df;
+        // level shift away from zero in the denominator's sign: |D| grows by sigma,
+        // the step shrinks, the fixed point (zero residual) stays
+        const double q = 1.0 / (df < 0.0 ? df - shift : df + shift);
         e = make_double2(rr * q, ri * q);
         tn = make_double2(t.x + e.x, t.y + e.y);
         const double ae = fma(e.x, e.x, e.y * e.y);  // |e|^2: k_finalize_update takes the root
@@ -413,7 +416,8 @@ exp_status fs_entry(Ctx& c, int inst, double* heff, double* eig_re, double* eig_
 void fs_step(Ctx& c, const double* Dfs, const int8_t* role, const cplx* XV) {
   ccsd_update_step(c, [&](double* part, int nb) {
     k_fs_update<<<dim3(nb, c.ninst), 256, 0, c.stream>>>(c.d_R, c.d_D, Dfs, XV, role, c.d_T, c.d_diis_t, c.d_diis_e,
-                                                         c.namp, c.cfg.diis_dim, c.d_diis_state, part);
+                                                         c.namp, c.cfg.diis_dim, c.d_diis_state, part,
+                                                         c.cfg.level_shift);
     KCHECK(c);
   }, false);
 }

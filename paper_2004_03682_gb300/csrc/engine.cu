@@ -198,6 +198,21 @@ void gen_tasks(Ctx& c, const Layout& L, std::vector<GenTask>& tasks, std::vector
 
 // Integral tensors: V(p,q,r,s) generated directly in the requested storage
 // order (slot k holds V argument arg[k]) and row/column split; cached.
+static PermPlan make_perm_plan(Ctx& c, const Layout& D, const char* dl, const Layout& S, const char* sl,
+                               const std::vector<std::string>& terms, bool check_signs);
+
+// The exact symmetries of the integrals (the recipe antisymmetrises both pairs and
+// Hermitises): V(x0 x1 x2 x3) = coef [conj] V(y) with y[pi[k]] = x_k.
+struct VSym {
+  int pi[4];
+  double coef;
+  bool conj;
+};
+static const VSym kVSym[8] = {
+    {{0, 1, 2, 3}, 1.0, false},  {{1, 0, 2, 3}, -1.0, false}, {{0, 1, 3, 2}, -1.0, false},
+    {{1, 0, 3, 2}, 1.0, false},  {{2, 3, 0, 1}, 1.0, true},   {{3, 2, 0, 1}, -1.0, true},
+    {{2, 3, 1, 0}, -1.0, true},  {{3, 2, 1, 0}, 1.0, true}};
+
 const Tensor* integral(Ctx& c, const IntRef& v, const int arg[4], int nrow) {
   std::ostringstream key;
   key << v.sp[0] << v.sp[1] << v.sp[2] << v.sp[3] << "|" << arg[0] << arg[1] << arg[2] << arg[3]
@@ -212,6 +227,29 @@ const Tensor* integral(Ctx& c, const IntRef& v, const int arg[4], int nrow) {
     map[arg[k]] = k;
   }
   Layout L = make_layout(c.spaces, c.G, 4, sp, sg, nrow);
+  // a cached layout related by a symmetry of V: one permute instead of generating
+  // (the generator draws eight Gaussians per element; the values are the same)
+  for (const auto& m : c.int_list) {
+    for (const VSym& y : kVSym) {
+      bool ok = true;
+      for (int k = 0; k < 4; ++k) ok = ok && v.sp[k] == m.vsp[y.pi[k]];
+      if (!ok) continue;
+      const char* lab = "abcd";  // labels of the new V arguments
+      char dl[5] = {0}, sl[5] = {0};
+      for (int s2 = 0; s2 < 4; ++s2) {
+        dl[s2] = lab[arg[s2]];
+        for (int k = 0; k < 4; ++k)
+          if (y.pi[k] == m.arg[s2]) sl[s2] = lab[k];
+      }
+      Tensor* t = new_tensor(c, L, false);
+      PermPlan pp = make_perm_plan(c, L, dl, m.t->L, sl, {std::string(dl)}, !y.conj);
+      const cplx coef = make_double2(y.coef, 0.0);
+      launch_permute(c, pp, t->d, m.t->d, t->is, m.t->is, &coef, false, y.conj);
+      c.int_cache[key.str()].reset(t);
+      c.int_list.push_back({{v.sp[0], v.sp[1], v.sp[2], v.sp[3]}, {arg[0], arg[1], arg[2], arg[3]}, t});
+      return t;
+    }
+  }
   Tensor* t = new_tensor(c, L, true);
   std::vector<GenTask> tasks;
   std::vector<ChunkRef> chunks;
@@ -224,6 +262,7 @@ const Tensor* integral(Ctx& c, const IntRef& v, const int arg[4], int nrow) {
     launch_generate(c, t->d, t->is, dt, dc, int(chunks.size()), map);
   }
   c.int_cache[key.str()].reset(t);
+  c.int_list.push_back({{v.sp[0], v.sp[1], v.sp[2], v.sp[3]}, {arg[0], arg[1], arg[2], arg[3]}, t});
   return t;
 }
 
@@ -232,7 +271,7 @@ const Tensor* integral(Ctx& c, const IntRef& v, const int arg[4], int nrow) {
 // relabelling string ts (a permutation of dl): the src slot labelled l takes
 // the value of the dst slot labelled sigma_t(l), sigma_t(dl[k]) = ts[k].
 static PermPlan make_perm_plan(Ctx& c, const Layout& D, const char* dl, const Layout& S,
-                               const char* sl, const std::vector<std::string>& terms) {
+                               const char* sl, const std::vector<std::string>& terms, bool check_signs = true) {
   const int r = D.rank;
   if (S.rank != r) throw ExpError{EXP_EINVAL, "permute rank mismatch"};
   std::vector<SubBlock> db, sb;
@@ -258,7 +297,7 @@ static PermPlan make_perm_plan(Ctx& c, const Layout& D, const char* dl, const La
       const char* pd = strchr(dl, target);
       if (!pd) throw ExpError{EXP_EINVAL, "bad permute term"};
       pos[t][k] = int(pd - dl);
-      if (S.sg[k] != D.sg[pos[t][k]] || S.sp[k] != D.sp[pos[t][k]])
+      if ((check_signs && S.sg[k] != D.sg[pos[t][k]]) || S.sp[k] != D.sp[pos[t][k]])
         throw ExpError{EXP_EINVAL, "permute space/sign mismatch"};
     }
   }

@@ -232,6 +232,11 @@ struct Ctx {
 
   // caches
   std::map<std::string, std::unique_ptr<Tensor>> int_cache;   // integral layouts
+  struct IntMeta {
+    int vsp[4], arg[4];  // spaces of the V arguments; storage slot k holds V argument arg[k]
+    const Tensor* t;
+  };
+  std::vector<IntMeta> int_list;  // the cached layouts, for deriving related ones
   std::map<std::string, PermPlan> perm_cache;
   std::map<std::string, std::unique_ptr<EinsumPlan>> plans;   // by call-site key
   std::vector<DevBuf> owned;

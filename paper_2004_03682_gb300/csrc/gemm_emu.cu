@@ -56,7 +56,7 @@ struct Shape {
   static constexpr int STAGE = A_STAGE + B_STAGE;
   static constexpr int ACC = S * BN;             // TMEM columns per accumulator buffer
   static constexpr int STAGES = S <= 5 ? 4 : 3;  // as many stages as 227 KB of shared memory holds
-  static constexpr int SMEM = STAGES * STAGE + 1024 + 256;
+  static constexpr int SMEM = STAGES * STAGE + 1024 + 256 + 4096;  // + barriers + a copy of the problem list
   static_assert(SMEM <= 232448, "shared memory");
   static_assert(2 * ACC <= 512, "TMEM");
   static_assert(S * BN <= 256, "MMA N");
@@ -215,7 +215,7 @@ __host__ __device__ __forceinline__ int gpr_of(const EmuProb& P) { return P.Kp =
 struct EmuWork {
   int pi, inst, ks, mt, nt, kb0, nkb, nkb_all;
 };
-__device__ __forceinline__ EmuWork emu_work(const EmuProb* __restrict__ probs, int nprobs, int n_tiles, int w, int GMr) {
+__device__ __forceinline__ EmuWork emu_work(const EmuProb* probs, int nprobs, int n_tiles, int w, int GMr) {
   EmuWork W;
   W.inst = w / n_tiles;
   const int tile = w - W.inst * n_tiles;
@@ -247,7 +247,7 @@ __device__ __forceinline__ EmuWork emu_work(const EmuProb* __restrict__ probs, i
 // prefetches across tile boundaries.
 template <int S>
 __global__ void __launch_bounds__(THREADS, 1)
-    k_emu_gemm(const EmuProb* __restrict__ probs, int nprobs, int n_tiles, int n_work, int gm,
+    k_emu_gemm(const EmuProb* probs, int nprobs, int n_tiles, int n_work, int gm,
                const __nv_bfloat16* __restrict__ Asl, const __nv_bfloat16* __restrict__ Bsl,
                const int* __restrict__ Aex, const int* __restrict__ Bex, cplx* __restrict__ C, int64_t asl_is,
                int64_t bsl_is, int64_t aex_is, int64_t bex_is, int64_t c_is, cplx alpha, int alpha_e, int beta,
@@ -263,8 +263,17 @@ __global__ void __launch_bounds__(THREADS, 1)
   uint64_t* drain = acce + 2;
   uint32_t* tslot = (uint32_t*)(drain + 1);
   volatile int* abort = (volatile int*)(tslot + 1);
+  // the problem list, read by every role for every work item, kept in shared memory
+  EmuProb* sprobs = (EmuProb*)(smem + STAGES * SH::STAGE + 256);
+  constexpr int MAXP = 4096 / int(sizeof(EmuProb));
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (nprobs <= MAXP) {
+    const long long* src = reinterpret_cast<const long long*>(probs);
+    long long* dst = reinterpret_cast<long long*>(sprobs);
+    for (int i = threadIdx.x; i < nprobs * int(sizeof(EmuProb) / 8); i += blockDim.x) dst[i] = src[i];
+    probs = sprobs;
+  }
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
@@ -384,6 +393,14 @@ __global__ void __launch_bounds__(THREADS, 1)
       const int ncv = 2 * min(P.N - W.nt * (SH::BN / 2), SH::BN / 2);
       int nv8 = min(max((ncv - h * HW + 7) / 8, 0), HW / 8);
       if (W.mt * BM + q * 32 >= P.M) nv8 = 0;
+      // the tile's row / column exponents, loaded before the accumulators are ready
+      const int gi = W.mt * BM + row;
+      const int j0 = W.nt * (SH::BN / 2) + h * (HW / 2);  // first complex column of this warp
+      const int ei = gi < P.M ? Aex[W.inst * aex_is + P.a_ex + gi] : 0;
+      int fj[HW / 2];
+#pragma unroll
+      for (int jj = 0; jj < HW / 2; ++jj)
+        fj[jj] = (gi < P.M && j0 + jj < P.N) ? Bex[W.inst * bex_is + P.b_ex + j0 + jj] : 0;
       for (int ch = 0; ch < nchunks; ++ch, ++gc) {
         const int buf = gc & 1;
         if (!mbar_wait(&accf[buf], (gc >> 1) & 1, abort, gerr)) { ok = false; break; }
@@ -406,11 +423,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (lane == 0) mbar_arrive(&acce[buf]);
       }
       if (!ok) break;
-      const int gi = W.mt * BM + row;
       if (gi >= P.M) continue;
-      const int ei = Aex[W.inst * aex_is + P.a_ex + gi];
-      const int* bex = Bex + W.inst * bex_is + P.b_ex;
-      const int j0 = W.nt * (SH::BN / 2) + h * (HW / 2);  // first complex column of this warp
       if (P.ksplit > 1) {  // the exact integer partial; the reduction adds them exactly
         longlong2* Wp = reinterpret_cast<longlong2*>(ws + W.inst * ws_is + P.ws) + int64_t(W.ks) * P.M * P.N +
                         int64_t(gi) * P.N;
@@ -425,7 +438,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         for (int jj = 0; jj < HW / 2; ++jj) {
           const int gj = j0 + jj;
           if (gj < P.N) {
-            const int e = ei + bex[gj] - BETA * (S + 1);
+            const int e = ei + fj[jj] - BETA * (S + 1);
             double vr, vi;
             if (alpha_e != ALPHA_GENERAL) {  // alpha = +-2^k: folded into the exponent and sign
               const long long rr = alpha_e < 0 ? -R[2 * jj] : R[2 * jj], ri = alpha_e < 0 ? -R[2 * jj + 1] : R[2 * jj + 1];
@@ -1116,12 +1129,14 @@ static void autotune(Ctx& c, EmuPlan* p, int64_t cis, cplx alpha) {
   CK(cudaEventCreate(&e1));
   double best_ms = 1e30, best_m = p->ks_mult;
   int best_gm = p->gm;
+  bool warm = false;
   for (double m : mults) {
     layout_work(p, sms, m);
     upload(c, p->d, p->h.data(), sizeof(EmuProb) * p->h.size());
     for (int g : gms) {
       p->gm = g;
-      launch_product<S>(c, p, st->tune_buf, cis, alpha, false, true);  // warm-up
+      if (!warm) launch_product<S>(c, p, st->tune_buf, cis, alpha, false, true);  // one warm-up
+      warm = true;
       CK(cudaEventRecord(e0, c.stream));
       launch_product<S>(c, p, st->tune_buf, cis, alpha, false, true);
       CK(cudaEventRecord(e1, c.stream));

@@ -30,7 +30,7 @@ __global__ void __launch_bounds__(256) k_permute(const PermTask* __restrict__ ta
                                                  const ChunkRef* __restrict__ chunks,
                                                  cplx* __restrict__ dst,
                                                  const cplx* __restrict__ src, int64_t dis,
-                                                 int64_t sis, Coefs co, int acc) {
+                                                 int64_t sis, Coefs co, int acc, int conj) {
   __shared__ PermTask T;
   const ChunkRef ch = chunks[blockIdx.x];
   if (threadIdx.x < sizeof(PermTask) / 8)
@@ -58,7 +58,8 @@ __global__ void __launch_bounds__(256) k_permute(const PermTask* __restrict__ ta
     for (int t = 0; t < NT; ++t) {
       const int64_t sp = T.src[t] + i0 * T.src_st[t][0] + i1 * T.src_st[t][1] +
                          i2 * T.src_st[t][2] + i3 * T.src_st[t][3];
-      const cplx x = src[sp];
+      cplx x = src[sp];
+      if (conj) x.y = -x.y;
       if (SIGNS) {
         const double xr = __longlong_as_double(__double_as_longlong(x.x) ^ (long long)sgn[t]);
         const double xi = __longlong_as_double(__double_as_longlong(x.y) ^ (long long)sgn[t]);
@@ -79,16 +80,18 @@ __global__ void __launch_bounds__(256) k_permute(const PermTask* __restrict__ ta
 
 template <int NT>
 static void permute_nt(Ctx& c, const PermPlan& p, cplx* dst, const cplx* src, int64_t dst_is, int64_t src_is,
-                       const Coefs& co, bool signs, bool accumulate) {
+                       const Coefs& co, bool signs, bool accumulate, bool conj) {
   dim3 grid(p.n_chunks, c.ninst);
   if (signs)
-    k_permute<NT, true><<<grid, 256, 0, c.stream>>>(p.d_tasks, p.d_chunks, dst, src, dst_is, src_is, co, accumulate);
+    k_permute<NT, true><<<grid, 256, 0, c.stream>>>(p.d_tasks, p.d_chunks, dst, src, dst_is, src_is, co, accumulate,
+                                                    conj);
   else
-    k_permute<NT, false><<<grid, 256, 0, c.stream>>>(p.d_tasks, p.d_chunks, dst, src, dst_is, src_is, co, accumulate);
+    k_permute<NT, false><<<grid, 256, 0, c.stream>>>(p.d_tasks, p.d_chunks, dst, src, dst_is, src_is, co, accumulate,
+                                                     conj);
 }
 
 void launch_permute(Ctx& c, const PermPlan& p, cplx* dst, const cplx* src, int64_t dst_is,
-                    int64_t src_is, const cplx* coef, bool accumulate, bool) {
+                    int64_t src_is, const cplx* coef, bool accumulate, bool conj_src) {
   if (p.n_chunks == 0) return;
   Coefs co;
   bool signs = true;
@@ -97,10 +100,10 @@ void launch_permute(Ctx& c, const PermPlan& p, cplx* dst, const cplx* src, int64
     if (t < p.n_terms && !(co.c[t].y == 0.0 && (co.c[t].x == 1.0 || co.c[t].x == -1.0))) signs = false;
   }
   switch (p.n_terms) {
-    case 1: permute_nt<1>(c, p, dst, src, dst_is, src_is, co, signs, accumulate); break;
-    case 2: permute_nt<2>(c, p, dst, src, dst_is, src_is, co, signs, accumulate); break;
-    case 3: permute_nt<3>(c, p, dst, src, dst_is, src_is, co, signs, accumulate); break;
-    default: permute_nt<4>(c, p, dst, src, dst_is, src_is, co, signs, accumulate); break;
+    case 1: permute_nt<1>(c, p, dst, src, dst_is, src_is, co, signs, accumulate, conj_src); break;
+    case 2: permute_nt<2>(c, p, dst, src, dst_is, src_is, co, signs, accumulate, conj_src); break;
+    case 3: permute_nt<3>(c, p, dst, src, dst_is, src_is, co, signs, accumulate, conj_src); break;
+    default: permute_nt<4>(c, p, dst, src, dst_is, src_is, co, signs, accumulate, conj_src); break;
   }
   KCHECK(c);
 }
@@ -356,7 +359,7 @@ __global__ void __launch_bounds__(256) k_generate_pairs(cplx* __restrict__ dst, 
                                                         const int32_t* __restrict__ cpair, int n,
                                                         const uint64_t* __restrict__ seeds,
                                                         const double* __restrict__ scales,
-                                                        const int* __restrict__ genmap) {
+                                                        const int* __restrict__ genmap, int herm) {
   const int inst = blockIdx.y;
   dst += inst * is;
   const uint64_t seed = seeds[inst];
@@ -367,6 +370,9 @@ __global__ void __launch_bounds__(256) k_generate_pairs(cplx* __restrict__ dst, 
     while (g + 1 < D.G && e >= D.blk[g + 1]) ++g;
     const uint32_t loc = uint32_t(e - D.blk[g]);
     const uint32_t p = loc / uint32_t(D.nc[g]), q = loc - p * uint32_t(D.nc[g]);
+    // herm (rows and columns from one table): element (q, p) is conj of (p, q) -- the
+    // recipe's Hermitisation adds the same two terms -- so only p <= q is drawn
+    if (herm && q < p) continue;
     const int32_t rc = rpair[D.roff[g] + p], cc = cpair[D.coff[g] + q];
     int gi[4] = {rc >> 16, rc & 0xFFFF, cc >> 16, cc & 0xFFFF};
     bool ghost = false;
@@ -376,12 +382,13 @@ __global__ void __launch_bounds__(256) k_generate_pairs(cplx* __restrict__ dst, 
         gi[k] = genmap[gi[k]];
         ghost |= gi[k] < 0;
       }
-    if (ghost) {
-      dst[e] = make_double2(0.0, 0.0);
-      continue;
+    cplx v = make_double2(0.0, 0.0);
+    if (!ghost) {
+      const cplx w = v_element(uint64_t(gi[0]), uint64_t(gi[1]), uint64_t(gi[2]), uint64_t(gi[3]), uint64_t(n), seed);
+      v = make_double2(sc * w.x, sc * w.y);
     }
-    const cplx v = v_element(uint64_t(gi[0]), uint64_t(gi[1]), uint64_t(gi[2]), uint64_t(gi[3]), uint64_t(n), seed);
-    dst[e] = make_double2(sc * v.x, sc * v.y);
+    dst[e] = v;
+    if (herm && q > p) dst[D.blk[g] + int64_t(q) * D.nc[g] + p] = make_double2(v.x, -v.y);
   }
 }
 
@@ -390,6 +397,6 @@ void launch_generate_pairs(Ctx& c, cplx* dst, int64_t is, const PackDims& D, con
   if (total == 0) return;
   const int blocks = int(std::min<int64_t>((total + 255) / 256, int64_t(std::max(c.sm_count, 1)) * 8));
   k_generate_pairs<<<dim3(blocks, c.ninst), 256, 0, c.stream>>>(dst, is, D, R.d_pair, C.d_pair, c.n_gen, c.d_seed,
-                                                                c.d_scale, c.d_genmap);
+                                                                c.d_scale, c.d_genmap, &R == &C ? 1 : 0);
   KCHECK(c);
 }

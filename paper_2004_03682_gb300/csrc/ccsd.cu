@@ -485,6 +485,7 @@ void ccsd_init_integrals(Ctx& c, const double* h_mult) {
   c.h_scale.resize(c.ninst);
   CK(cudaMemcpyAsync(c.h_scale.data(), c.d_scale, sizeof(double) * c.ninst, cudaMemcpyDeviceToHost, c.stream));
   CK(cudaStreamSynchronize(c.stream));
+  c.integrals_scaled = true;
 }
 
 void ccsd_guess(Ctx& c) {

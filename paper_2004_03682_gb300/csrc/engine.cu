@@ -8,6 +8,7 @@
 
 #include "engine.h"
 #include "emu.h"
+#include "packed.h"
 
 static int64_t ipow(int G, int k) {
   int64_t r = 1;
@@ -213,22 +214,10 @@ static const VSym kVSym[8] = {
     {{1, 0, 3, 2}, 1.0, false},  {{2, 3, 0, 1}, 1.0, true},   {{3, 2, 0, 1}, -1.0, true},
     {{2, 3, 1, 0}, -1.0, true},  {{3, 2, 1, 0}, 1.0, true}};
 
-const Tensor* integral(Ctx& c, const IntRef& v, const int arg[4], int nrow) {
-  std::ostringstream key;
-  key << v.sp[0] << v.sp[1] << v.sp[2] << v.sp[3] << "|" << arg[0] << arg[1] << arg[2] << arg[3]
-      << "|" << nrow;
-  auto it = c.int_cache.find(key.str());
-  if (it != c.int_cache.end()) return it->second.get();
-  if (!c.have_integrals) throw ExpError{EXP_ESTATE, "integrals requested before exp_init_integrals"};
-  int sp[4], sg[4], map[4];
-  for (int k = 0; k < 4; ++k) {
-    sp[k] = v.sp[arg[k]];
-    sg[k] = arg[k] < 2 ? 1 : -1;
-    map[arg[k]] = k;
-  }
-  Layout L = make_layout(c.spaces, c.G, 4, sp, sg, nrow);
-  // a cached layout related by a symmetry of V: one permute instead of generating
-  // (the generator draws eight Gaussians per element; the values are the same)
+// A cached layout related by a symmetry of V: one permute instead of generating (the
+// generator draws eight Gaussians per element; the values are the same).  nullptr when
+// no member of the family is cached.
+static Tensor* derive_integral(Ctx& c, const IntRef& v, const int arg[4], const Layout& L) {
   for (const auto& m : c.int_list) {
     for (const VSym& y : kVSym) {
       bool ok = true;
@@ -245,10 +234,104 @@ const Tensor* integral(Ctx& c, const IntRef& v, const int arg[4], int nrow) {
       PermPlan pp = make_perm_plan(c, L, dl, m.t->L, sl, {std::string(dl)}, !y.conj);
       const cplx coef = make_double2(y.coef, 0.0);
       launch_permute(c, pp, t->d, m.t->d, t->is, m.t->is, &coef, false, y.conj);
-      c.int_cache[key.str()].reset(t);
-      c.int_list.push_back({{v.sp[0], v.sp[1], v.sp[2], v.sp[3]}, {arg[0], arg[1], arg[2], arg[3]}, t});
       return t;
     }
+  }
+  return nullptr;
+}
+
+Tensor* integral_uncached(Ctx& c, const IntRef& v, const int arg[4], int nrow) {
+  int sp[4], sg[4];
+  for (int k = 0; k < 4; ++k) {
+    sp[k] = v.sp[arg[k]];
+    sg[k] = arg[k] < 2 ? 1 : -1;
+  }
+  Layout L = make_layout(c.spaces, c.G, 4, sp, sg, nrow);
+  return derive_integral(c, v, arg, L);
+}
+
+// V(p q | r s) in argument order with nrow 2, drawn with each same-space pair of one
+// compound packed (p<q or r<s: the other half follows by antisymmetry) and scattered
+// into the full layout with the swap signs
+static Tensor* generate_packed_pairs(Ctx& c, const int cs[4]) {
+  const int sg[4] = {1, 1, -1, -1};
+  Layout L = make_layout(c.spaces, c.G, 4, cs, sg, 2);
+  PairTable R, C;
+  build_pair_table(c, L, true, cs[0] == cs[1], R);
+  build_pair_table(c, L, false, cs[2] == cs[3], C);
+  const PackDims D = pack_dims(R, C);
+  const int64_t n = std::max<int64_t>(D.blk[D.G], 1);
+  cplx* P = (cplx*)c.dalloc(sizeof(cplx) * n * c.ninst);
+  launch_generate_pairs(c, P, n, D, R, C);
+  Tensor* t = new_tensor(c, L, false);
+  launch_pack_scatter(c, t->d, t->is, P, n, D, R, C, 1.0, false);
+  CK(cudaStreamSynchronize(c.stream));  // the temporaries are released below
+  c.dfree(P);
+  for (PairTable* T : {&R, &C}) {
+    c.dfree(T->d_pair);
+    c.dfree(T->d_full);
+    c.dfree(T->d_inv);
+  }
+  return t;
+}
+
+static std::string int_key(const int sp[4], const int arg[4], int nrow) {
+  std::ostringstream key;
+  key << sp[0] << sp[1] << sp[2] << sp[3] << "|" << arg[0] << arg[1] << arg[2] << arg[3] << "|" << nrow;
+  return key.str();
+}
+
+const Tensor* integral(Ctx& c, const IntRef& v, const int arg[4], int nrow) {
+  std::ostringstream key;
+  key << int_key(v.sp, arg, nrow);
+  auto it = c.int_cache.find(key.str());
+  if (it != c.int_cache.end()) return it->second.get();
+  if (!c.have_integrals) throw ExpError{EXP_ESTATE, "integrals requested before exp_init_integrals"};
+  // the first layout of a symmetry family: when an orientation V(p q | r s) of the
+  // family has a same-space pair in one compound, draw that one packed and derive
+  // the requested layout from it (below).  Before the scale is final only a request
+  // that is itself that orientation is drawn this way (it gets rescaled in place).
+  {
+    bool family = false;
+    for (const auto& m : c.int_list)
+      for (const VSym& y : kVSym) {
+        bool ok = true;
+        for (int k = 0; k < 4; ++k) ok = ok && v.sp[k] == m.vsp[y.pi[k]];
+        family = family || ok;
+      }
+    if (!family) {
+      int best = -1, best_score = 0, cs[4] = {0, 0, 0, 0};
+      for (int y = 0; y < 8; ++y) {
+        int img[4];
+        for (int k = 0; k < 4; ++k) img[kVSym[y].pi[k]] = v.sp[k];
+        const int score = (img[0] == img[1]) + (img[2] == img[3]);
+        if (score > best_score) {
+          best_score = score;
+          best = y;
+          for (int k = 0; k < 4; ++k) cs[k] = img[k];
+        }
+      }
+      const int ident[4] = {0, 1, 2, 3};
+      const bool is_canon = best == 0 && nrow == 2 && arg[0] == 0 && arg[1] == 1 && arg[2] == 2 && arg[3] == 3;
+      if (best >= 0 && (c.integrals_scaled || is_canon)) {
+        Tensor* t = generate_packed_pairs(c, cs);
+        c.int_cache[int_key(cs, ident, 2)].reset(t);
+        c.int_list.push_back({{cs[0], cs[1], cs[2], cs[3]}, {0, 1, 2, 3}, t});
+        if (is_canon) return t;
+      }
+    }
+  }
+  int sp[4], sg[4], map[4];
+  for (int k = 0; k < 4; ++k) {
+    sp[k] = v.sp[arg[k]];
+    sg[k] = arg[k] < 2 ? 1 : -1;
+    map[arg[k]] = k;
+  }
+  Layout L = make_layout(c.spaces, c.G, 4, sp, sg, nrow);
+  if (Tensor* t = derive_integral(c, v, arg, L)) {
+    c.int_cache[key.str()].reset(t);
+    c.int_list.push_back({{v.sp[0], v.sp[1], v.sp[2], v.sp[3]}, {arg[0], arg[1], arg[2], arg[3]}, t});
+    return t;
   }
   Tensor* t = new_tensor(c, L, true);
   std::vector<GenTask> tasks;

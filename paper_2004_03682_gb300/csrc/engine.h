@@ -237,6 +237,7 @@ struct Ctx {
     const Tensor* t;
   };
   std::vector<IntMeta> int_list;  // the cached layouts, for deriving related ones
+  bool integrals_scaled = false;  // the MP2 scale is final (set by exp_init_integrals)
   std::map<std::string, PermPlan> perm_cache;
   std::map<std::string, std::unique_ptr<EinsumPlan>> plans;   // by call-site key
   std::vector<DevBuf> owned;
@@ -293,6 +294,9 @@ Tensor* new_tensor(Ctx& c, const Layout& L, bool zero);
 void* arena_reserve(Ctx& c, Arena& a, size_t bytes);
 Tensor* work_tensor(Ctx& c, const std::string& name, const Layout& L);
 const Tensor* integral(Ctx& c, const IntRef& v, const int perm[4], int nrow);
+// the same layout derived from a cached member of its symmetry family, not cached:
+// the caller releases it (c.dfree(t->d); delete t); nullptr when no member is cached
+Tensor* integral_uncached(Ctx& c, const IntRef& v, const int perm[4], int nrow);
 void gen_tasks(Ctx& c, const Layout& L, std::vector<GenTask>& tasks,
                std::vector<ChunkRef>& chunks);
 void einsum(Ctx& c, const std::string& site, cplx alpha, Operand A, Operand B, Tensor& C,

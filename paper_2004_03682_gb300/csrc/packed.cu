@@ -347,10 +347,12 @@ static void run_op(Ctx& c, PackedOp* op, const std::function<void()>& before, co
   }
 }
 
-// A = integral <pq||rs> with (p, q) from table R and (r, s) from table K, generated once;
-// B = T_P; C scattered into dst (rows Cr, cols oo) with `coef` (+-1), accumulating or not
+// A = integral <pq||rs> with (p, q) from table R and (r, s) from table K, made once:
+// gathered from the full layout V(p q | r s) when it can be derived from a cached
+// member of its family (src: the argument spaces; keep: cache that layout), drawn
+// otherwise; B = T_P; C scattered into dst (rows Cr, cols oo)
 static PackedOp* int_times_tau(Ctx& c, const std::string& site, const PairTable& R, const Tensor& dst, bool rows_packed,
-                               double alpha) {
+                               double alpha, const IntRef* src = nullptr, bool keep = false) {
   PackedState& s = PS(c);
   auto it = s.ops.find(site);
   if (it != s.ops.end()) return it->second.get();
@@ -366,7 +368,26 @@ static PackedOp* int_times_tau(Ctx& c, const std::string& site, const PairTable&
   op->Cc = &table(c, dst.L, false, true);
   op->C = arena_tensor(R, *s.oo);
   op->dC = pack_dims(*op->Cr, *op->Cc);
-  launch_generate_pairs(c, op->A.d, op->A.is, op->dA, R, *s.vv);
+  bool made = false;
+  if (src && &R != s.vv) {
+    const int ident[4] = {0, 1, 2, 3};
+    const Tensor* full = nullptr;
+    Tensor* tmp = nullptr;
+    if (keep) full = integral(c, *src, ident, 2);
+    else full = tmp = integral_uncached(c, *src, ident, 2);
+    if (full) {
+      const PairTable& fr = table(c, full->L, true, rows_packed);
+      const PairTable& fc = table(c, full->L, false, true);
+      launch_pack_gather(c, op->A.d, op->A.is, full->d, full->is, pack_dims(fr, fc), fr, fc);
+      made = true;
+    }
+    if (tmp) {
+      CK(cudaStreamSynchronize(c.stream));
+      c.dfree(tmp->d);
+      delete tmp;
+    }
+  }
+  if (!made) launch_generate_pairs(c, op->A.d, op->A.is, op->dA, R, *s.vv);
   finish_op(c, op, true, alpha);
   return op;
 }
@@ -379,13 +400,15 @@ void packed_ladder(Ctx& c, Tensor& r2) {
 
 void packed_xamij(Ctx& c, Tensor& X) {
   const PairTable& am = table(c, X.L, true, false);
-  PackedOp* op = int_times_tau(c, "Xamij", am, X, false, 2.0);  // sum_ef = 2 sum_{e<f}
+  static const IntRef VOVV{{SP_VIRT, SP_OCC, SP_VIRT, SP_VIRT}};
+  PackedOp* op = int_times_tau(c, "Xamij", am, X, false, 2.0, &VOVV, false);  // sum_ef = 2 sum_{e<f}
   run_op(c, op, [] {}, [&] { launch_pack_scatter(c, X.d, X.is, op->C.d, op->C.is, op->dC, *op->Cr, *op->Cc, 1.0, false); });
 }
 
 void packed_wmnij(Ctx& c, Tensor& W) {
   const PairTable& mn = table(c, W.L, true, true);
-  PackedOp* op = int_times_tau(c, "Wmnij2", mn, W, true, 1.0);
+  static const IntRef OOVV{{SP_OCC, SP_OCC, SP_VIRT, SP_VIRT}};
+  PackedOp* op = int_times_tau(c, "Wmnij2", mn, W, true, 1.0, &OOVV, true);
   run_op(c, op, [] {}, [&] { launch_pack_scatter(c, W.d, W.is, op->C.d, op->C.is, op->dC, *op->Cr, *op->Cc, 1.0, true); });
 }
 

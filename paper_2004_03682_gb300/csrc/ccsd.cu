@@ -70,18 +70,27 @@ __global__ void k_inv_denom(const double* __restrict__ D, double* __restrict__ D
 // t_new = (R - sigma t) / (D - sigma) over the whole amplitude vector (sigma = 0:
 // R / D); e = t_new - t.  Writes t_new and e into the next DIIS slot and the
 // per-CTA max |e|^2 (k_finalize_update takes the root).  Frozen instances skip.
+//
+// dpart != nullptr: also the DIIS inner products Re<e, e_j> of the new error vector with
+// itself (j = 0) and with the stored ones of the window (j = 1..count, newest first),
+// per CTA into dpart (the partials k_diis_solve sums) -- the same grid and element
+// order as k_diis_dots, so the same bits, without reading e back.
 __global__ void __launch_bounds__(RED_THREADS) k_update(const cplx* __restrict__ R, const double* __restrict__ Dinv,
                                                         const cplx* __restrict__ T, cplx* __restrict__ Tn,
                                                         cplx* __restrict__ En, int64_t namp, int dim,
                                                         const int* __restrict__ state, double* __restrict__ part,
-                                                        double shift) {
+                                                        double shift, double* __restrict__ dpart) {
   __shared__ double sh[32];
   const int inst = blockIdx.y;
   const int* st = state + inst * 4;
   const int slot = dim > 0 ? (st[1] + 1) % dim : 0;
+  const int nd = (dpart && dim > 0) ? min(st[0] + 1, dim) : 0;  // dots after this push
   const int64_t off = int64_t(inst) * namp;
   const int64_t soff = (int64_t(inst) * (dim > 0 ? dim : 1) + slot) * namp;
   double m = 0.0;
+  double acc[EXP_MAX_DIIS];
+#pragma unroll
+  for (int j = 0; j < EXP_MAX_DIIS; ++j) acc[j] = 0.0;
   if (!st[2]) {
     for (int64_t k = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; k < namp; k += int64_t(gridDim.x) * blockDim.x) {
       const cplx r = R[off + k];
@@ -92,10 +101,24 @@ __global__ void __launch_bounds__(RED_THREADS) k_update(const cplx* __restrict__
       Tn[soff + k] = tn;
       En[soff + k] = e;
       m = nanmax(m, fma(e.x, e.x, e.y * e.y));
+      if (nd) {
+        acc[0] += e.x * e.x + e.y * e.y;
+#pragma unroll
+        for (int j = 1; j < EXP_MAX_DIIS; ++j)
+          if (j < nd) {
+            const cplx b = En[(int64_t(inst) * dim + (slot - j + dim) % dim) * namp + k];
+            acc[j] += e.x * b.x + e.y * b.y;
+          }
+      }
     }
   }
   m = block_reduce(m, MaxOp(), sh);
   if (threadIdx.x == 0) part[(inst * gridDim.x + blockIdx.x) * 8] = m;
+  if (dpart && dim > 0)
+    for (int j = 0; j < dim; ++j) {
+      const double a = block_reduce(acc[j], AddOp(), sh);
+      if (threadIdx.x == 0) dpart[(inst * gridDim.x + blockIdx.x) * EXP_MAX_DIIS + j] = a;
+    }
 }
 
 // per instance: residual, NaN check, convergence, DIIS push.
@@ -127,21 +150,57 @@ __global__ void k_finalize_update(const double* __restrict__ part, int nb, int* 
   if (m < tol && !bad) st[3] = 1;  // converged this iteration (freeze after extrapolation)
 }
 
-// energy partial sums: E = 1/4 sum conj(<ab||ij>) tau_ij^ab  (<ij||ab> = conj <ab||ij>)
-__global__ void __launch_bounds__(RED_THREADS) k_energy_part(const cplx* __restrict__ Vd, int64_t vis,
-                                                             const cplx* __restrict__ tau, int64_t tis,
-                                                             int64_t n2, const int* __restrict__ state,
-                                                             double* __restrict__ part, int skip_frozen) {
+// Energy partial sums E = 1/4 sum conj(<ab||ij>) tau_ij^ab (<ij||ab> = conj <ab||ij>), with
+// tau formed on the fly from the amplitude vector T = [t1 | t2]
+// (tau_ij^ab = t2 + t1_ai t1_bj - t1_bi t1_aj): CTA b walks the t2 sub-block chunks
+// b, b + gridDim.x, ... in a fixed order, so the result is reproducible.
+__global__ void __launch_bounds__(RED_THREADS) k_energy_tau(const cplx* __restrict__ Vd, int64_t vis,
+                                                            const cplx* __restrict__ T, int64_t tis, int64_t n1,
+                                                            const int32_t* __restrict__ t1i,
+                                                            const GenTask* __restrict__ tasks,
+                                                            const ChunkRef* __restrict__ chunks, int n_chunks, int no,
+                                                            int vbase, const int* __restrict__ state,
+                                                            double* __restrict__ part, int skip_frozen) {
   __shared__ double sh[32];
   const int inst = blockIdx.y;
   double er = 0.0, ei = 0.0;
   if (!(skip_frozen && state[inst * 4 + 2])) {
     const cplx* v = Vd + inst * vis;
-    const cplx* t = tau + inst * tis;
-    for (int64_t k = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; k < n2; k += int64_t(gridDim.x) * blockDim.x) {
-      const cplx a = v[k], b = t[k];
-      er += a.x * b.x + a.y * b.y;
-      ei += a.x * b.y - a.y * b.x;
+    const cplx* t1 = T + inst * tis;
+    const cplx* t2 = t1 + n1;
+    for (int cidx = blockIdx.x; cidx < n_chunks; cidx += gridDim.x) {
+      const ChunkRef ch = chunks[cidx];
+      const GenTask Tk = tasks[ch.task];
+      const uint32_t n1_ = Tk.n[1], n2_ = Tk.n[2], n3_ = Tk.n[3];
+      const uint32_t end = uint32_t(min(ch.start + (int64_t)EXP_CHUNK, Tk.count));
+      for (uint32_t e = uint32_t(ch.start) + threadIdx.x; e < end; e += blockDim.x) {
+        uint32_t r = e;
+        const int i3 = int(r % n3_);
+        r /= n3_;
+        const int i2 = int(r % n2_);
+        r /= n2_;
+        const int i1 = int(r % n1_);
+        const int i0 = int(r / n1_);
+        const int a = Tk.g0[0] + i0 - vbase, b = Tk.g0[1] + i1 - vbase;
+        const int ii = Tk.g0[2] + i2, jj = Tk.g0[3] + i3;
+        const int64_t p = Tk.base + i0 * Tk.st[0] + i1 * Tk.st[1] + i2 * Tk.st[2] + i3 * Tk.st[3];
+        cplx x = t2[p];
+        const int kai = t1i[a * no + ii], kbj = t1i[b * no + jj];
+        if (kai >= 0 && kbj >= 0) {
+          const cplx u = t1[kai], w = t1[kbj];
+          x.x += u.x * w.x - u.y * w.y;
+          x.y += u.x * w.y + u.y * w.x;
+        }
+        const int kbi = t1i[b * no + ii], kaj = t1i[a * no + jj];
+        if (kbi >= 0 && kaj >= 0) {
+          const cplx u = t1[kbi], w = t1[kaj];
+          x.x -= u.x * w.x - u.y * w.y;
+          x.y -= u.x * w.y + u.y * w.x;
+        }
+        const cplx va = v[p];
+        er += va.x * x.x + va.y * x.y;
+        ei += va.x * x.y - va.y * x.x;
+      }
     }
   }
   er = block_reduce(er, AddOp(), sh);
@@ -366,10 +425,9 @@ struct CcsdState {
   TauTasks t1tasks;
   int32_t* d_t1i = nullptr;
   double* d_part = nullptr;
+  double* d_dots = nullptr;  // DIIS inner-product partials formed in the update kernel
   double* d_coef = nullptr;
   const Tensor* Vd = nullptr;  // <ab||ij> in the t2 layout
-  Tensor Tn2;                  // view used for the energy tau (scratch)
-  cplx* d_taun = nullptr;      // tau of t_new
   double* d_Dinv = nullptr;    // 1 / (D - sigma), filled on the first (eager) iteration
   bool dinv_ready = false;
 };
@@ -401,6 +459,7 @@ void ccsd_setup(Ctx& c) {
   CK(cudaMemsetAsync(c.d_diis_B, 0, sizeof(double) * EXP_MAX_DIIS * EXP_MAX_DIIS * ni, c.stream));
   CK(cudaMallocHost(&c.h_stats, sizeof(double) * 8 * ni));
   s->d_part = (double*)c.dalloc(sizeof(double) * 8 * RED_BLOCKS * ni * EXP_MAX_DIIS);
+  s->d_dots = (double*)c.dalloc(sizeof(double) * RED_BLOCKS * ni * EXP_MAX_DIIS);
   s->d_coef = (double*)c.dalloc(sizeof(double) * EXP_MAX_DIIS * ni);
   c.t1.d = c.d_T;
   c.t1.is = na;
@@ -454,7 +513,6 @@ void ccsd_setup(Ctx& c) {
     s->d_t1i = (int32_t*)c.dalloc(idx.size() * sizeof(int32_t));
     upload(c, s->d_t1i, idx.data(), idx.size() * sizeof(int32_t));
   }
-  s->d_taun = (cplx*)c.dalloc(sizeof(cplx) * std::max<int64_t>(c.n2, 1) * ni);
 }
 
 void ccsd_release(Ctx& c) {
@@ -506,11 +564,11 @@ void ccsd_reset_diis(Ctx& c) {
 // E of the amplitude vector at `T` (per instance) into stats[1..2].
 void ccsd_energy_of(Ctx& c, const cplx* T, bool skip_frozen) {
   CcsdState& s = S(c);
-  launch_tau(c, s.d_taun, c.n2, T + c.n1, T, c.namp, s.d_t1i, s.t2tasks.d_tasks, s.t2tasks.d_chunks,
-             s.t2tasks.n_chunks, 1.0, 1.0, -1.0);
   const int nb = RED_BLOCKS;
-  k_energy_part<<<dim3(nb, c.ninst), RED_THREADS, 0, c.stream>>>(s.Vd->d, s.Vd->is, s.d_taun, c.n2, c.n2,
-                                                                 c.d_diis_state, s.d_part, skip_frozen);
+  k_energy_tau<<<dim3(nb, c.ninst), RED_THREADS, 0, c.stream>>>(s.Vd->d, s.Vd->is, T, c.namp, c.n1, s.d_t1i,
+                                                                s.t2tasks.d_tasks, s.t2tasks.d_chunks,
+                                                                s.t2tasks.n_chunks, c.no, c.no, c.d_diis_state,
+                                                                s.d_part, skip_frozen);
   KCHECK(c);
   k_finalize_energy<<<c.ninst, 32, 0, c.stream>>>(s.d_part, nb, c.d_diis_state, c.d_stats, skip_frozen);
   KCHECK(c);
@@ -661,7 +719,7 @@ void copy_newest(Ctx& c, cplx* dst) {
 // Update + residual + (energy) + DIIS for every instance.  `upd` launches the
 // update kernel that writes t_new and the error into the next DIIS slot and the
 // per-CTA max |error| into part (RED_BLOCKS CTAs per instance).
-void ccsd_update_step(Ctx& c, const std::function<void(double*, int)>& upd, bool energy) {
+void ccsd_update_step(Ctx& c, const std::function<void(double*, int)>& upd, bool energy, bool dots_done) {
   CcsdState& s = S(c);
   const int dim = c.cfg.diis_dim;
   const int nb = RED_BLOCKS;
@@ -669,9 +727,11 @@ void ccsd_update_step(Ctx& c, const std::function<void(double*, int)>& upd, bool
   k_finalize_update<<<c.ninst, 32, 0, c.stream>>>(s.d_part, nb, c.d_diis_state, c.d_stats, dim, c.cfg.conv_tol);
   KCHECK(c);
   if (dim > 0) {
-    k_diis_dots<<<dim3(nb, c.ninst), RED_THREADS, 0, c.stream>>>(c.d_diis_e, c.namp, dim, c.d_diis_state, s.d_part);
-    KCHECK(c);
-    k_diis_solve<<<c.ninst, 32, 0, c.stream>>>(s.d_part, nb, dim, c.d_diis_state, c.d_diis_B, s.d_coef, c.d_stats);
+    if (!dots_done) {
+      k_diis_dots<<<dim3(nb, c.ninst), RED_THREADS, 0, c.stream>>>(c.d_diis_e, c.namp, dim, c.d_diis_state, s.d_dots);
+      KCHECK(c);
+    }
+    k_diis_solve<<<c.ninst, 32, 0, c.stream>>>(s.d_dots, nb, dim, c.d_diis_state, c.d_diis_B, s.d_coef, c.d_stats);
     KCHECK(c);
   }
   if (energy) {
@@ -699,9 +759,10 @@ void ccsd_iteration(Ctx& c) {
   ccsd_rhs(c);
   ccsd_update_step(c, [&](double* part, int nb) {
     k_update<<<dim3(nb, c.ninst), RED_THREADS, 0, c.stream>>>(c.d_R, s.d_Dinv, c.d_T, c.d_diis_t, c.d_diis_e, c.namp,
-                                                              c.cfg.diis_dim, c.d_diis_state, part, c.cfg.level_shift);
+                                                              c.cfg.diis_dim, c.d_diis_state, part, c.cfg.level_shift,
+                                                              s.d_dots);
     KCHECK(c);
-  }, true);
+  }, true, true);
 }
 
 // Instances frozen as converged (-1 if any instance failed with NaN/Inf).  Synchronises.

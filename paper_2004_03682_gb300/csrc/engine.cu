@@ -107,7 +107,7 @@ void enumerate_blocks(const Layout& L, const std::vector<Space>& S, std::vector<
   }
 }
 
-static const int64_t kChunk = 4096;
+static const int64_t kChunk = EXP_CHUNK;
 
 static void add_chunks(std::vector<ChunkRef>& chunks, int task, int64_t count) {
   for (int64_t s = 0; s < count; s += kChunk) chunks.push_back(ChunkRef{task, 0, s});

@@ -18,6 +18,7 @@ typedef double2 cplx;  // (re, im)
 #define EXP_MAX_TERMS 4
 #define EXP_MAX_G 16
 #define EXP_MAX_DIIS 8
+#define EXP_CHUNK 4096  // elements per work chunk of a sub-block task (generators, permutes, tau)
 
 // Spinor spaces.  Global spinor index: occupied 0..o-1, virtual o..o+v-1.
 enum SpaceId { SP_OCC = 0, SP_VIRT = 1, SP_COUNT = 2 };

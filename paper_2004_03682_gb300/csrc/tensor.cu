@@ -8,7 +8,6 @@
 
 #include <algorithm>
 
-#define EXP_CHUNK 4096
 
 struct Coefs {
   cplx c[EXP_MAX_TERMS];

@@ -384,8 +384,7 @@ extern "C" exp_status exp_set_amplitudes(exp_ctx* x, int inst, const void* t1, c
     c.guessed = true;
   }
   ccsd_dense_io(c, inst, (cplx*)t1, (cplx*)t2, false);
-  ccsd_reset_diis(c);
-  ccsd_energy_of(c, c.d_T, false);
+  ccsd_mark_guessed(c);
   CK(cudaStreamSynchronize(c.stream));
   return EXP_OK;
   API_END(x)

@@ -115,10 +115,12 @@ __global__ void __launch_bounds__(RED_THREADS) k_update(const cplx* __restrict__
   m = block_reduce(m, MaxOp(), sh);
   if (threadIdx.x == 0) part[(inst * gridDim.x + blockIdx.x) * 8] = m;
   if (dpart && dim > 0)
-    for (int j = 0; j < dim; ++j) {
-      const double a = block_reduce(acc[j], AddOp(), sh);
-      if (threadIdx.x == 0) dpart[(inst * gridDim.x + blockIdx.x) * EXP_MAX_DIIS + j] = a;
-    }
+#pragma unroll
+    for (int j = 0; j < EXP_MAX_DIIS; ++j)
+      if (j < dim) {  // dim is uniform over the block (the reduction synchronises)
+        const double a = block_reduce(acc[j], AddOp(), sh);
+        if (threadIdx.x == 0) dpart[(inst * gridDim.x + blockIdx.x) * EXP_MAX_DIIS + j] = a;
+      }
 }
 
 // per instance: residual, NaN check, convergence, DIIS push.
@@ -212,7 +214,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_energy_tau(const cplx* __restri
 }
 
 __global__ void k_finalize_energy(const double* __restrict__ part, int nb, const int* __restrict__ state,
-                                  double* __restrict__ stats, int skip_frozen) {
+                                  double* __restrict__ stats, int skip_frozen, double scale) {
   const int inst = blockIdx.x;
   if (threadIdx.x) return;
   if (skip_frozen && state[inst * 4 + 2]) return;
@@ -221,8 +223,8 @@ __global__ void k_finalize_energy(const double* __restrict__ part, int nb, const
     er += part[(inst * nb + b) * 8 + 1];
     ei += part[(inst * nb + b) * 8 + 2];
   }
-  stats[inst * 8 + 1] = 0.25 * er;
-  stats[inst * 8 + 2] = 0.25 * ei;
+  stats[inst * 8 + 1] = scale * er;
+  stats[inst * 8 + 2] = scale * ei;
 }
 
 // DIIS: dots of the newest error vector with every stored one (Re <e_new, e_k>).
@@ -360,6 +362,208 @@ __global__ void k_freeze(int* __restrict__ state, int ninst) {
   if (i < ninst && state[i * 4 + 3] && state[i * 4 + 2] == 0) state[i * 4 + 2] = 1;
 }
 
+// ---------------------------------------------------------------------------
+// The pair-packed amplitude vector: t1, then the entries a<b, i<j of t2 (rows and
+// columns of the doubles layout as pair-packed tables).  t2 is antisymmetric in
+// (a, b) and in (i, j), so these entries determine it; the update, the DIIS vectors,
+// the extrapolation and the energy act on them alone (a quarter of the FP64 work
+// and of the DIIS storage), and the extrapolation writes the four signed copies.
+#define PK_THREADS 1024
+
+// offset in one instance's full t2 of packed t2 entry e
+__device__ __forceinline__ int64_t pk_full(const PackDims& D, const int32_t* __restrict__ rfull,
+                                           const int32_t* __restrict__ cfull, int64_t e) {
+  const int g = find_block(D.blk, D.G, e);
+  const uint32_t loc = uint32_t(e - D.blk[g]);
+  const uint32_t p = loc / uint32_t(D.nc[g]), q = loc - p * uint32_t(D.nc[g]);
+  return D.fblk[g] + int64_t(rfull[D.roff[g] + p]) * D.fnc[g] + cfull[D.coff[g] + q];
+}
+
+// Dinv = 1 / (D - sigma) on the packed vector
+__global__ void k_inv_denom_pk(const double* __restrict__ Dn, double* __restrict__ Dinv, int64_t namp, int64_t npk,
+                               int64_t n1, PackDims D, const int32_t* __restrict__ rfull,
+                               const int32_t* __restrict__ cfull, double shift) {
+  const int inst = blockIdx.y;
+  for (int64_t k = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; k < npk; k += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t f = k < n1 ? k : n1 + pk_full(D, rfull, cfull, k - n1);
+    Dinv[inst * npk + k] = 1.0 / (Dn[inst * namp + f] - shift);
+  }
+}
+
+// k_update on the packed vector: R and T are read at each entry's full offset,
+// t_new and e go packed into the DIIS slot.  A stored t2 error is doubled: it
+// stands for the four entries +-e of the full vector, so inner products of stored
+// errors equal those of the full error vectors (the weight of t2 against t1 in
+// the DIIS matrix is unchanged).
+__global__ void __launch_bounds__(PK_THREADS) k_update_pk(const cplx* __restrict__ R, const double* __restrict__ Dinv,
+                                                          const cplx* __restrict__ T, cplx* __restrict__ Tn,
+                                                          cplx* __restrict__ En, int64_t namp, int64_t npk, int64_t n1,
+                                                          PackDims D, const int32_t* __restrict__ rfull,
+                                                          const int32_t* __restrict__ cfull, int dim,
+                                                          const int* __restrict__ state, double* __restrict__ part,
+                                                          double shift, double* __restrict__ dpart) {
+  __shared__ double sh[32];
+  const int inst = blockIdx.y;
+  const int* st = state + inst * 4;
+  const int slot = dim > 0 ? (st[1] + 1) % dim : 0;
+  const int nd = dim > 0 ? min(st[0] + 1, dim) : 0;
+  const int64_t off = int64_t(inst) * namp;
+  const int64_t soff = (int64_t(inst) * (dim > 0 ? dim : 1) + slot) * npk;
+  double m = 0.0;
+  double acc[EXP_MAX_DIIS];
+#pragma unroll
+  for (int j = 0; j < EXP_MAX_DIIS; ++j) acc[j] = 0.0;
+  if (!st[2]) {
+    for (int64_t k = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; k < npk; k += int64_t(gridDim.x) * blockDim.x) {
+      const int64_t f = k < n1 ? k : n1 + pk_full(D, rfull, cfull, k - n1);
+      const cplx r = R[off + f];
+      const double q = Dinv[int64_t(inst) * npk + k];
+      const cplx t = T[off + f];
+      const cplx tn = make_double2(fma(-shift, t.x, r.x) * q, fma(-shift, t.y, r.y) * q);
+      const cplx e = make_double2(tn.x - t.x, tn.y - t.y);
+      Tn[soff + k] = tn;
+      m = nanmax(m, fma(e.x, e.x, e.y * e.y));
+      const cplx ew = k < n1 ? e : make_double2(e.x + e.x, e.y + e.y);
+      En[soff + k] = ew;
+      if (nd) {
+        acc[0] += ew.x * ew.x + ew.y * ew.y;
+#pragma unroll
+        for (int j = 1; j < EXP_MAX_DIIS; ++j)
+          if (j < nd) {
+            const cplx b = En[(int64_t(inst) * dim + (slot - j + dim) % dim) * npk + k];
+            acc[j] += ew.x * b.x + ew.y * b.y;
+          }
+      }
+    }
+  }
+  m = block_reduce(m, MaxOp(), sh);
+  if (threadIdx.x == 0) part[(inst * gridDim.x + blockIdx.x) * 8] = m;
+  if (dim > 0)
+#pragma unroll
+    for (int j = 0; j < EXP_MAX_DIIS; ++j)
+      if (j < dim) {  // dim is uniform over the block (the reduction synchronises)
+        const double a = block_reduce(acc[j], AddOp(), sh);
+        if (threadIdx.x == 0) dpart[(inst * gridDim.x + blockIdx.x) * EXP_MAX_DIIS + j] = a;
+      }
+}
+
+// T = sum_k c_k t_new_k on the packed vector, written to the full amplitude vector:
+// t1 as is, each t2 entry to (a,b,i,j) and (b,a,j,i), its negative to (b,a,i,j)
+// and (a,b,j,i).  The entries a = b or i = j are never written (they stay zero).
+__global__ void __launch_bounds__(256) k_extrapolate_pk(cplx* __restrict__ T, const cplx* __restrict__ Tn,
+                                                        int64_t namp, int64_t npk, int64_t n1, PackDims D,
+                                                        const int32_t* __restrict__ rfull,
+                                                        const int32_t* __restrict__ rswp,
+                                                        const int32_t* __restrict__ cfull,
+                                                        const int32_t* __restrict__ cswp, int dim,
+                                                        const double* __restrict__ coef,
+                                                        const int* __restrict__ state) {
+  const int inst = blockIdx.y;
+  const int* st = state + inst * 4;
+  if (st[2]) return;
+  const int Dm = dim > 0 ? dim : 1;
+  const double* cf = coef + inst * EXP_MAX_DIIS;
+  const bool plain = dim == 0 || st[3];
+  const int head = dim > 0 ? st[1] : 0;
+  cplx* t = T + int64_t(inst) * namp;
+  for (int64_t k = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; k < npk; k += int64_t(gridDim.x) * blockDim.x) {
+    double vr = 0.0, vi = 0.0;
+    if (plain) {
+      const cplx x = Tn[(int64_t(inst) * Dm + head) * npk + k];
+      vr = x.x; vi = x.y;
+    } else {
+      for (int s = 0; s < Dm; ++s) {
+        const double c = cf[s];
+        if (c != 0.0) {
+          const cplx x = Tn[(int64_t(inst) * Dm + s) * npk + k];
+          vr += c * x.x;
+          vi += c * x.y;
+        }
+      }
+    }
+    if (k < n1) {
+      t[k] = make_double2(vr, vi);
+      continue;
+    }
+    const int64_t e = k - n1;
+    const int g = find_block(D.blk, D.G, e);
+    const uint32_t loc = uint32_t(e - D.blk[g]);
+    const uint32_t p = loc / uint32_t(D.nc[g]), q = loc - p * uint32_t(D.nc[g]);
+    const int64_t nc = D.fnc[g];
+    const int64_t r0 = int64_t(rfull[D.roff[g] + p]) * nc, r1 = int64_t(rswp[D.roff[g] + p]) * nc;
+    const int64_t c0 = cfull[D.coff[g] + q], c1 = cswp[D.coff[g] + q];
+    cplx* b = t + n1 + D.fblk[g];
+    b[r0 + c0] = make_double2(vr, vi);
+    b[r1 + c1] = make_double2(vr, vi);
+    b[r1 + c0] = make_double2(-vr, -vi);
+    b[r0 + c1] = make_double2(-vr, -vi);
+  }
+}
+
+// E = sum over a<b, i<j of conj(<ab||ij>) tau_ij^ab (the 1/4 sum over every entry of
+// the two antisymmetric tensors), tau from the newest packed t_new of each active
+// instance; partials as k_energy_tau writes them.
+__global__ void __launch_bounds__(PK_THREADS) k_energy_pk(const cplx* __restrict__ Vp, const cplx* __restrict__ Tn,
+                                                          int64_t npk, int64_t n1, int dim, PackDims D,
+                                                          const int32_t* __restrict__ rpair,
+                                                          const int32_t* __restrict__ cpair,
+                                                          const int32_t* __restrict__ t1i, int no,
+                                                          const int* __restrict__ state, double* __restrict__ part) {
+  __shared__ double sh[32];
+  const int inst = blockIdx.y;
+  const int* st = state + inst * 4;
+  double er = 0.0, ei = 0.0;
+  if (!st[2]) {
+    const int head = dim > 0 ? st[1] : 0;
+    const cplx* t1 = Tn + (int64_t(inst) * (dim > 0 ? dim : 1) + head) * npk;
+    const cplx* t2 = t1 + n1;
+    const cplx* v = Vp + int64_t(inst) * (npk - n1);
+    for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < npk - n1;
+         e += int64_t(gridDim.x) * blockDim.x) {
+      const int g = find_block(D.blk, D.G, e);
+      const uint32_t loc = uint32_t(e - D.blk[g]);
+      const uint32_t p = loc / uint32_t(D.nc[g]), q = loc - p * uint32_t(D.nc[g]);
+      const int32_t pr = rpair[D.roff[g] + p], pc = cpair[D.coff[g] + q];
+      const int a = (pr >> 16) - no, b = (pr & 0xffff) - no, ii = pc >> 16, jj = pc & 0xffff;
+      cplx x = t2[e];
+      const int kai = t1i[a * no + ii], kbj = t1i[b * no + jj];
+      if (kai >= 0 && kbj >= 0) {
+        const cplx u = t1[kai], w = t1[kbj];
+        x.x += u.x * w.x - u.y * w.y;
+        x.y += u.x * w.y + u.y * w.x;
+      }
+      const int kbi = t1i[b * no + ii], kaj = t1i[a * no + jj];
+      if (kbi >= 0 && kaj >= 0) {
+        const cplx u = t1[kbi], w = t1[kaj];
+        x.x -= u.x * w.x - u.y * w.y;
+        x.y -= u.x * w.y + u.y * w.x;
+      }
+      const cplx va = v[e];
+      er += va.x * x.x + va.y * x.y;
+      ei += va.x * x.y - va.y * x.x;
+    }
+  }
+  er = block_reduce(er, AddOp(), sh);
+  ei = block_reduce(ei, AddOp(), sh);
+  if (threadIdx.x == 0) {
+    part[(inst * gridDim.x + blockIdx.x) * 8 + 1] = er;
+    part[(inst * gridDim.x + blockIdx.x) * 8 + 2] = ei;
+  }
+}
+
+// the entries a = b or i = j of t2 set to zero (the packed update never writes them)
+__global__ void k_zero_pair_diag(cplx* __restrict__ T2, int64_t namp, PackDims D, const int32_t* __restrict__ rinv,
+                                 const int32_t* __restrict__ cinv) {
+  const int inst = blockIdx.y;
+  const int64_t total = D.fblk[D.G];
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total; e += int64_t(gridDim.x) * blockDim.x) {
+    const int g = find_block(D.fblk, D.G, e);
+    const uint32_t loc = uint32_t(e - D.fblk[g]);
+    const uint32_t r = loc / uint32_t(D.fnc[g]), cc = loc - r * uint32_t(D.fnc[g]);
+    if (rinv[D.froff[g] + r] == 0 || cinv[D.fcoff[g] + cc] == 0) T2[inst * namp + e] = make_double2(0.0, 0.0);
+  }
+}
+
 // scale pass: max |V_abij / D_ij^ab| per instance
 __global__ void __launch_bounds__(RED_THREADS) k_maxratio(const cplx* __restrict__ V, int64_t vis,
                                                           const double* __restrict__ D, int64_t dis, int64_t off,
@@ -430,6 +634,15 @@ struct CcsdState {
   const Tensor* Vd = nullptr;  // <ab||ij> in the t2 layout
   double* d_Dinv = nullptr;    // 1 / (D - sigma), filled on the first (eager) iteration
   bool dinv_ready = false;
+  // the pair-packed amplitude vector (packed contexts): t1, then t2 over a<b, i<j
+  struct {
+    bool on = false;
+    PackDims D{};
+    const PairTable *vv = nullptr, *oo = nullptr;
+    int64_t n = 0;             // n1 + packed t2 entries
+    double* d_Dinv = nullptr;  // [ninst][n]
+    cplx* d_V = nullptr;       // [ninst][n - n1] <ab||ij> on the packed entries
+  } pk;
 };
 
 static CcsdState& S(Ctx& c) { return *reinterpret_cast<CcsdState*>(c.ccsd_state); }
@@ -446,7 +659,15 @@ void ccsd_setup(Ctx& c) {
   c.d_T = (cplx*)c.dalloc(sizeof(cplx) * na * ni);
   c.d_R = (cplx*)c.dalloc(sizeof(cplx) * na * ni);
   c.d_D = (double*)c.dalloc(sizeof(double) * na * ni);
-  s->d_Dinv = (double*)c.dalloc(sizeof(double) * na * ni);
+  if (c.cfg.packed) {
+    s->pk.D = packed_t2_space(c, c.t2.L, &s->pk.vv, &s->pk.oo);
+    s->pk.n = c.n1 + s->pk.D.blk[s->pk.D.G];
+    s->pk.d_Dinv = (double*)c.dalloc(sizeof(double) * s->pk.n * ni);
+    s->pk.d_V = (cplx*)c.dalloc(sizeof(cplx) * std::max<int64_t>(s->pk.n - c.n1, 1) * ni);
+    s->pk.on = true;
+  } else {
+    s->d_Dinv = (double*)c.dalloc(sizeof(double) * na * ni);
+  }
   CK(cudaMemsetAsync(c.d_T, 0, sizeof(cplx) * na * ni, c.stream));
   const int dslots = std::max(c.cfg.diis_dim, 1);
   c.d_diis_t = (cplx*)c.dalloc(sizeof(cplx) * na * ni * dslots);
@@ -540,18 +761,30 @@ void ccsd_init_integrals(Ctx& c, const double* h_mult) {
   KCHECK(c);
   k_rescale<<<dim3(grid_for(c.n2), c.ninst), 256, 0, c.stream>>>(const_cast<cplx*>(Vd->d), Vd->is, c.n2, c.d_scale);
   KCHECK(c);
+  if (s.pk.on)  // <ab||ij> on the packed entries, for the packed energy
+    launch_pack_gather(c, s.pk.d_V, s.pk.n - c.n1, Vd->d, Vd->is, s.pk.D, *s.pk.vv, *s.pk.oo);
   c.h_scale.resize(c.ninst);
   CK(cudaMemcpyAsync(c.h_scale.data(), c.d_scale, sizeof(double) * c.ninst, cudaMemcpyDeviceToHost, c.stream));
   CK(cudaStreamSynchronize(c.stream));
   c.integrals_scaled = true;
 }
 
+// Packed contexts: the pair-diagonal entries of a freshly set t2 made zero (the
+// packed update writes only a<b, i<j and their signed copies).
+static void zero_pair_diag(Ctx& c) {
+  CcsdState& s = S(c);
+  const int64_t nf = s.pk.on ? s.pk.D.fblk[s.pk.D.G] : 0;
+  if (!nf) return;
+  k_zero_pair_diag<<<dim3(grid_for(nf), c.ninst), 256, 0, c.stream>>>(c.d_T + c.n1, c.namp, s.pk.D, s.pk.vv->d_inv,
+                                                                     s.pk.oo->d_inv);
+  KCHECK(c);
+}
+
 void ccsd_guess(Ctx& c) {
   CcsdState& s = S(c);
   k_mp2_guess<<<dim3(grid_for(c.namp), c.ninst), 256, 0, c.stream>>>(c.d_T, c.d_D, s.Vd->d, s.Vd->is, c.n1, c.namp);
   KCHECK(c);
-  ccsd_reset_diis(c);
-  ccsd_energy_of(c, c.d_T, false);
+  ccsd_mark_guessed(c);
 }
 
 void ccsd_reset_diis(Ctx& c) {
@@ -570,7 +803,7 @@ void ccsd_energy_of(Ctx& c, const cplx* T, bool skip_frozen) {
                                                                 s.t2tasks.n_chunks, c.no, c.no, c.d_diis_state,
                                                                 s.d_part, skip_frozen);
   KCHECK(c);
-  k_finalize_energy<<<c.ninst, 32, 0, c.stream>>>(s.d_part, nb, c.d_diis_state, c.d_stats, skip_frozen);
+  k_finalize_energy<<<c.ninst, 32, 0, c.stream>>>(s.d_part, nb, c.d_diis_state, c.d_stats, skip_frozen, 0.25);
   KCHECK(c);
 }
 
@@ -719,29 +952,44 @@ void copy_newest(Ctx& c, cplx* dst) {
 // Update + residual + (energy) + DIIS for every instance.  `upd` launches the
 // update kernel that writes t_new and the error into the next DIIS slot and the
 // per-CTA max |error| into part (RED_BLOCKS CTAs per instance).
-void ccsd_update_step(Ctx& c, const std::function<void(double*, int)>& upd, bool energy, bool dots_done) {
+void ccsd_update_step(Ctx& c, const std::function<void(double*, int)>& upd, bool energy, bool dots_done,
+                      bool packed) {
   CcsdState& s = S(c);
   const int dim = c.cfg.diis_dim;
   const int nb = RED_BLOCKS;
+  const int64_t nvec = packed ? s.pk.n : c.namp;  // length of the DIIS vectors
   upd(s.d_part, nb);
   k_finalize_update<<<c.ninst, 32, 0, c.stream>>>(s.d_part, nb, c.d_diis_state, c.d_stats, dim, c.cfg.conv_tol);
   KCHECK(c);
   if (dim > 0) {
     if (!dots_done) {
-      k_diis_dots<<<dim3(nb, c.ninst), RED_THREADS, 0, c.stream>>>(c.d_diis_e, c.namp, dim, c.d_diis_state, s.d_dots);
+      k_diis_dots<<<dim3(nb, c.ninst), RED_THREADS, 0, c.stream>>>(c.d_diis_e, nvec, dim, c.d_diis_state, s.d_dots);
       KCHECK(c);
     }
     k_diis_solve<<<c.ninst, 32, 0, c.stream>>>(s.d_dots, nb, dim, c.d_diis_state, c.d_diis_B, s.d_coef, c.d_stats);
     KCHECK(c);
   }
-  if (energy) {
+  if (energy && packed) {  // energy of the newest packed t_new, read in place
+    k_energy_pk<<<dim3(nb, c.ninst), PK_THREADS, 0, c.stream>>>(s.pk.d_V, c.d_diis_t, s.pk.n, c.n1, dim, s.pk.D,
+                                                               s.pk.vv->d_pair, s.pk.oo->d_pair, s.d_t1i, c.no,
+                                                               c.d_diis_state, s.d_part);
+    KCHECK(c);
+    k_finalize_energy<<<c.ninst, 32, 0, c.stream>>>(s.d_part, nb, c.d_diis_state, c.d_stats, 1, 1.0);
+    KCHECK(c);
+  } else if (energy) {
     // energy of t_new: gather the newest t_new of every instance into R (free by
     // now), then tau + dot
     copy_newest(c, c.d_R);
     ccsd_energy_of(c, c.d_R, true);
   }
-  k_extrapolate<<<dim3(grid_for(c.namp), c.ninst), 256, 0, c.stream>>>(c.d_T, c.d_diis_t, c.namp, dim, s.d_coef,
-                                                                       c.d_diis_state);
+  if (packed) {
+    k_extrapolate_pk<<<dim3(grid_for(s.pk.n), c.ninst), 256, 0, c.stream>>>(
+        c.d_T, c.d_diis_t, c.namp, s.pk.n, c.n1, s.pk.D, s.pk.vv->d_full, s.pk.vv->d_swp, s.pk.oo->d_full,
+        s.pk.oo->d_swp, dim, s.d_coef, c.d_diis_state);
+  } else {
+    k_extrapolate<<<dim3(grid_for(c.namp), c.ninst), 256, 0, c.stream>>>(c.d_T, c.d_diis_t, c.namp, dim, s.d_coef,
+                                                                         c.d_diis_state);
+  }
   KCHECK(c);
   k_freeze<<<(c.ninst + 127) / 128, 128, 0, c.stream>>>(c.d_diis_state, c.ninst);
   KCHECK(c);
@@ -751,12 +999,25 @@ void ccsd_update_step(Ctx& c, const std::function<void(double*, int)>& upd, bool
 void ccsd_iteration(Ctx& c) {
   CcsdState& s = S(c);
   if (!s.dinv_ready) {  // D and sigma are fixed for the context's life
-    k_inv_denom<<<dim3(grid_for(c.namp * c.ninst)), 256, 0, c.stream>>>(c.d_D, s.d_Dinv, c.namp * c.ninst,
-                                                                        c.cfg.level_shift);
+    if (s.pk.on)
+      k_inv_denom_pk<<<dim3(grid_for(s.pk.n), c.ninst), 256, 0, c.stream>>>(
+          c.d_D, s.pk.d_Dinv, c.namp, s.pk.n, c.n1, s.pk.D, s.pk.vv->d_full, s.pk.oo->d_full, c.cfg.level_shift);
+    else
+      k_inv_denom<<<dim3(grid_for(c.namp * c.ninst)), 256, 0, c.stream>>>(c.d_D, s.d_Dinv, c.namp * c.ninst,
+                                                                          c.cfg.level_shift);
     KCHECK(c);
     s.dinv_ready = true;
   }
   ccsd_rhs(c);
+  if (s.pk.on) {
+    ccsd_update_step(c, [&](double* part, int nb) {
+      k_update_pk<<<dim3(nb, c.ninst), PK_THREADS, 0, c.stream>>>(
+          c.d_R, s.pk.d_Dinv, c.d_T, c.d_diis_t, c.d_diis_e, c.namp, s.pk.n, c.n1, s.pk.D, s.pk.vv->d_full,
+          s.pk.oo->d_full, c.cfg.diis_dim, c.d_diis_state, part, c.cfg.level_shift, s.d_dots);
+      KCHECK(c);
+    }, true, true, true);
+    return;
+  }
   ccsd_update_step(c, [&](double* part, int nb) {
     k_update<<<dim3(nb, c.ninst), RED_THREADS, 0, c.stream>>>(c.d_R, s.d_Dinv, c.d_T, c.d_diis_t, c.d_diis_e, c.namp,
                                                               c.cfg.diis_dim, c.d_diis_state, part, c.cfg.level_shift,
@@ -835,6 +1096,7 @@ void ccsd_dense_io(Ctx& c, int inst, cplx* t1d, cplx* t2d, bool to_dense) {
 const Tensor* ccsd_driver_integral(Ctx& c) { return S(c).Vd; }
 
 void ccsd_mark_guessed(Ctx& c) {
+  zero_pair_diag(c);
   ccsd_reset_diis(c);
   ccsd_energy_of(c, c.d_T, false);
   c.guessed = true;

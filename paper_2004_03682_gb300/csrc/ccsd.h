@@ -15,8 +15,10 @@ void ccsd_energy_of(Ctx& c, const cplx* T, bool skip_frozen);
 void ccsd_rhs(Ctx& c);
 void ccsd_iteration(Ctx& c);
 void ccsd_dense_io(Ctx& c, int inst, cplx* t1_dense, cplx* t2_dense, bool to_dense);
-// dots_done: `upd` also formed the DIIS inner products of the new error vector
-void ccsd_update_step(Ctx& c, const std::function<void(double*, int)>& upd, bool energy, bool dots_done = false);
+// dots_done: `upd` also formed the DIIS inner products of the new error vector;
+// packed: the DIIS vectors are the pair-packed amplitude vector (t1, t2 over a<b, i<j)
+void ccsd_update_step(Ctx& c, const std::function<void(double*, int)>& upd, bool energy, bool dots_done = false,
+                      bool packed = false);
 int ccsd_count_converged(Ctx& c);
 const Tensor* ccsd_driver_integral(Ctx& c);
 void ccsd_mark_guessed(Ctx& c);

@@ -42,6 +42,7 @@ void build_pair_table(Ctx& c, const Layout& L, bool rows, bool packed, PairTable
   T.pair.clear();
   T.full.clear();
   T.inv.clear();
+  T.swp.clear();
   for (int g = 0; g < G; ++g) {
     const int64_t fsz = rows ? L.rows[g] : L.cols[g];
     if (fsz >= (int64_t(1) << 31)) throw ExpError{EXP_EINVAL, "packed pairs: block above 2^31"};
@@ -66,6 +67,7 @@ void build_pair_table(Ctx& c, const Layout& L, bool rows, bool packed, PairTable
               const int32_t k = int32_t(T.pair.size()) - T.off[g];
               T.pair.push_back(code(g0, x0, g1, x1));
               T.full.push_back(f);
+              T.swp.push_back(f);
               T.inv[inv0 + f] = k + 1;
             }
         }
@@ -78,6 +80,7 @@ void build_pair_table(Ctx& c, const Layout& L, bool rows, bool packed, PairTable
               const int32_t k = int32_t(T.pair.size()) - T.off[g];
               T.pair.push_back(code(g0, x0, g1, x1));
               T.full.push_back(full_index(g0, x0, g1, x1));
+              T.swp.push_back(full_index(g1, x1, g0, x0));
               T.inv[inv0 + full_index(g0, x0, g1, x1)] = k + 1;
               T.inv[inv0 + full_index(g1, x1, g0, x0)] = -(k + 1);
             }
@@ -93,6 +96,7 @@ void build_pair_table(Ctx& c, const Layout& L, bool rows, bool packed, PairTable
   T.d_pair = up(T.pair);
   T.d_full = up(T.full);
   T.d_inv = up(T.inv);
+  T.d_swp = up(T.swp);
 }
 
 PackDims pack_dims(const PairTable& R, const PairTable& C) {
@@ -118,12 +122,6 @@ PackDims pack_dims(const PairTable& R, const PairTable& C) {
   return D;
 }
 
-// block of element e of a matrix with block offsets off[0..G]
-__device__ __forceinline__ int find_block(const int64_t* off, int G, int64_t e) {
-  int g = 0;
-  while (g + 1 < G && e >= off[g + 1]) ++g;
-  return g;
-}
 
 __global__ void __launch_bounds__(256) k_pack_gather(cplx* __restrict__ dst, int64_t dis, const cplx* __restrict__ src,
                                                      int64_t sis, PackDims D, const int32_t* __restrict__ rfull,
@@ -272,14 +270,22 @@ static Tensor arena_tensor(const PairTable& R, const PairTable& C) {
   return t;
 }
 
-void packed_tau(Ctx& c, const Tensor& tau) {
+const PackDims& packed_t2_space(Ctx& c, const Layout& L, const PairTable** vv, const PairTable** oo) {
   PackedState& s = PS(c);
   if (!s.vv) {
-    s.vv = &table(c, tau.L, true, true);   // (c, d), c < d
-    s.oo = &table(c, tau.L, false, true);  // (i, j), i < j
+    s.vv = &table(c, L, true, true);   // (c, d), c < d
+    s.oo = &table(c, L, false, true);  // (i, j), i < j
     s.dT = pack_dims(*s.vv, *s.oo);
     s.TP = packed_tensor(c, *s.vv, *s.oo);
   }
+  if (vv) *vv = s.vv;
+  if (oo) *oo = s.oo;
+  return s.dT;
+}
+
+void packed_tau(Ctx& c, const Tensor& tau) {
+  PackedState& s = PS(c);
+  packed_t2_space(c, tau.L, nullptr, nullptr);
   launch_pack_gather(c, s.TP.d, s.TP.is, tau.d, tau.is, s.dT, *s.vv, *s.oo);
 }
 

@@ -19,9 +19,12 @@ struct PairTable {
   std::vector<int32_t> full;      // full compound index (within its block) per entry
   std::vector<int32_t> inv;       // per full compound index: +(k+1) entry k as is,
                                   // -(k+1) entry k with the pair swapped, 0 for p = q
+  std::vector<int32_t> swp;       // full compound index of the swapped pair (q, p) per entry
+                                  // (= full when not packed)
   int32_t* d_pair = nullptr;
   int32_t* d_full = nullptr;
   int32_t* d_inv = nullptr;
+  int32_t* d_swp = nullptr;
 };
 
 // Shapes passed by value to the pack / unpack / generate kernels: a packed matrix
@@ -36,6 +39,13 @@ struct PackDims {
   int32_t fnr[PK_MAXG], fnc[PK_MAXG];
   int32_t froff[PK_MAXG], fcoff[PK_MAXG];
 };
+
+// block of element e of a matrix with block offsets off[0..G]
+__device__ __forceinline__ int find_block(const int64_t* off, int G, int64_t e) {
+  int g = 0;
+  while (g + 1 < G && e >= off[g + 1]) ++g;
+  return g;
+}
 
 // rows = the first two slots of L (nrow must be 2), else the last two
 void build_pair_table(Ctx& c, const Layout& L, bool rows, bool packed, PairTable& T);
@@ -58,6 +68,10 @@ void launch_generate_pairs(Ctx& c, cplx* dst, int64_t is, const PackDims& D, con
 //   packed_xamij   X_amij = 2 sum_{e<f} <am||ef> tau_ij^ef      (= sum_ef; overwrites X)
 //   packed_wmnij   W_mnij += sum_{e<f} <mn||ef> tau_ij^ef
 //   packed_hh      r2 += sum_{m<n} tau_mn^ab W_mnij             (W complete)
+// The pair-packed space of the doubles layout L (rows a<b, cols i<j): its tables and
+// dims, built once per context (the update / DIIS / energy of the amplitude vector
+// act on these unique entries of the antisymmetric t2).
+const PackDims& packed_t2_space(Ctx& c, const Layout& L, const PairTable** vv, const PairTable** oo);
 void packed_tau(Ctx& c, const Tensor& tau);
 void packed_ladder(Ctx& c, Tensor& r2);
 void packed_xamij(Ctx& c, Tensor& X);

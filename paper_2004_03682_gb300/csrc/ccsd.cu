@@ -123,21 +123,38 @@ __global__ void __launch_bounds__(RED_THREADS) k_update(const cplx* __restrict__
       }
 }
 
-// per instance: residual, NaN check, convergence, DIIS push.
+// sum of the nb per-CTA partials part[(inst * nb + b) * stride + j] over one warp:
+// lane l adds b = l, l + 32, ... in order, then a fixed shuffle tree (reproducible)
+__device__ __forceinline__ double warp_sum_partials(const double* __restrict__ part, int inst, int nb, int stride,
+                                                    int j) {
+  const int l = threadIdx.x & 31;
+  double s = 0.0;
+  for (int b = l; b < nb; b += 32) s += part[(int64_t(inst) * nb + b) * stride + j];
+  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
+}
+
+// per instance (one warp): residual, NaN check, convergence, DIIS push.
 __global__ void k_finalize_update(const double* __restrict__ part, int nb, int* __restrict__ state,
                                   double* __restrict__ stats, int dim, double tol) {
   const int inst = blockIdx.x;
-  if (threadIdx.x) return;
+  if (threadIdx.x >= 32) return;
   int* st = state + inst * 4;
   double* s = stats + inst * 8;
-  if (st[2]) { s[0] = 0.0; return; }
+  if (st[2]) {
+    if (threadIdx.x == 0) s[0] = 0.0;
+    return;
+  }
   double m = 0.0;
   bool bad = false;
-  for (int b = 0; b < nb; ++b) {
+  for (int b = threadIdx.x; b < nb; b += 32) {
     const double v = part[(inst * nb + b) * 8];
     if (!(v == v) || isinf(v)) bad = true;
     m = nanmax(m, v);
   }
+  for (int o = 16; o; o >>= 1) m = nanmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  bad = __any_sync(0xffffffffu, bad);
+  if (threadIdx.x) return;
   m = sqrt(m);  // the update kernels reduce |e|^2
   s[0] = bad ? INFINITY : m;
   s[4] = bad ? 1.0 : 0.0;
@@ -216,13 +233,11 @@ __global__ void __launch_bounds__(RED_THREADS) k_energy_tau(const cplx* __restri
 __global__ void k_finalize_energy(const double* __restrict__ part, int nb, const int* __restrict__ state,
                                   double* __restrict__ stats, int skip_frozen, double scale) {
   const int inst = blockIdx.x;
-  if (threadIdx.x) return;
+  if (threadIdx.x >= 32) return;
   if (skip_frozen && state[inst * 4 + 2]) return;
-  double er = 0.0, ei = 0.0;
-  for (int b = 0; b < nb; ++b) {
-    er += part[(inst * nb + b) * 8 + 1];
-    ei += part[(inst * nb + b) * 8 + 2];
-  }
+  const double er = warp_sum_partials(part, inst, nb, 8, 1);
+  const double ei = warp_sum_partials(part, inst, nb, 8, 2);
+  if (threadIdx.x) return;
   stats[inst * 8 + 1] = scale * er;
   stats[inst * 8 + 2] = scale * ei;
 }
@@ -258,21 +273,26 @@ __global__ void __launch_bounds__(RED_THREADS) k_diis_dots(const cplx* __restric
 __global__ void k_diis_solve(const double* __restrict__ part, int nb, int dim, int* __restrict__ state,
                              double* __restrict__ Bm, double* __restrict__ coef, double* __restrict__ stats) {
   const int inst = blockIdx.x;
-  if (threadIdx.x) return;
+  if (threadIdx.x >= 32) return;
   int* st = state + inst * 4;
   double* cf = coef + inst * EXP_MAX_DIIS;
-  for (int k = 0; k < EXP_MAX_DIIS; ++k) cf[k] = 0.0;
-  if (st[2]) return;
-  const int head = st[1];
-  double* B = Bm + inst * EXP_MAX_DIIS * EXP_MAX_DIIS;  // B[slot][slot]
-  // new row / column from the dots
-  for (int j = 0; j < st[0]; ++j) {
-    double s = 0.0;
-    for (int b = 0; b < nb; ++b) s += part[((inst * nb + b) * EXP_MAX_DIIS + j)];
-    const int slot = (head - j + dim) % dim;
-    B[head * EXP_MAX_DIIS + slot] = s;
-    B[slot * EXP_MAX_DIIS + head] = s;
+  if (st[2]) {
+    if (threadIdx.x < EXP_MAX_DIIS) cf[threadIdx.x] = 0.0;
+    return;
   }
+  const int head = st[1], cnt0 = st[0];
+  double* B = Bm + inst * EXP_MAX_DIIS * EXP_MAX_DIIS;  // B[slot][slot]
+  // new row / column from the dots (partials summed over the warp)
+  for (int j = 0; j < cnt0; ++j) {
+    const double s = warp_sum_partials(part, inst, nb, EXP_MAX_DIIS, j);
+    if (threadIdx.x == 0) {
+      const int slot = (head - j + dim) % dim;
+      B[head * EXP_MAX_DIIS + slot] = s;
+      B[slot * EXP_MAX_DIIS + head] = s;
+    }
+  }
+  if (threadIdx.x) return;
+  for (int k = 0; k < EXP_MAX_DIIS; ++k) cf[k] = 0.0;
   int cnt = st[0];
   while (cnt >= 2) {
     // order by age: index 0 = oldest

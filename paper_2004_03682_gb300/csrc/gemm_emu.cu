@@ -491,7 +491,7 @@ __device__ __forceinline__ int exp_of_bits(unsigned long long m) {
 // Row exponents: one warp per (row, K range of ROW_KR), grid-stride over all
 // of them; warp max -> atomicMax (max is order-independent, so the result is
 // deterministic).  Exponent arrays start at EXP_ZERO (all-zero row or column).
-#define ROW_KR 8192
+#define ROW_KR 1024
 __global__ void __launch_bounds__(256) k_row_exp(const EmuProb* __restrict__ probs, int nprobs,
                                                  const cplx* __restrict__ A, int64_t a_is, int* __restrict__ ex,
                                                  int64_t ex_is, int64_t n_items) {
@@ -581,7 +581,11 @@ __device__ __forceinline__ long long fixed_of(double x, int sh) {
 // x = sum_s a_s 2^(-BETA s) + r with |r| <= 2^(-BETA S - 1).  Each digit is exact
 // in BF16 (built from the exact float of a small integer).
 __device__ __forceinline__ uint16_t bf16_of_int(int v) {
-  return uint16_t(__float_as_uint(float(v)) >> 16);  // exact: |v| <= 256 needs 9 bits
+  // float(v) without the int-to-float conversion unit: for |v| < 2^22 the float with
+  // bits 0x4B400000 + v is 1.5 * 2^23 + v exactly (unit spacing in [2^23, 2^24)), and
+  // subtracting 1.5 * 2^23 leaves v exactly; |v| <= 256 then needs 9 bits of BF16
+  const float f = __int_as_float(0x4B400000 + v) - 12582912.0f;
+  return uint16_t(__float_as_uint(f) >> 16);
 }
 template <int S>
 __device__ __forceinline__ void digits(long long X, uint16_t (&h)[S]) {

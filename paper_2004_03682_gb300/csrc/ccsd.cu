@@ -710,6 +710,7 @@ void ccsd_setup(Ctx& c) {
   c.r1.d = c.d_R;
   c.r2 = c.t2;
   c.r2.d = c.d_R + c.n1;
+  c.r2.pair_canon = c.cfg.packed != 0;  // the packed update reads R2 at a<b, i<j only
   // denominators
   {
     std::vector<GenTask> tk;
@@ -908,7 +909,10 @@ void ccsd_rhs(Ctx& c) {
   einsum(c, "R1f", C(-0.5), {&t2, nullptr, "aemn"}, {nullptr, &OOVO, "nmei"}, r1, "ai", true);
 
   // ---- T2 equation
-  copy_int(c, r2, s.Vd);
+  if (r2.pair_canon && c.canon_pairs)
+    permute_into(c, "R2V", r2, "abij", *s.Vd, "abij", false);  // canonical entries only
+  else
+    copy_int(c, r2, s.Vd);
   // F'_be = F_be - 1/2 sum_m t_m^b F_me ;  + P(ab) sum_e t_ij^ae F'_be
   copy_t(c, Fp, Fae);
   einsum(c, "Fp", C(-0.5), {&t1, nullptr, "bm"}, {&Fme, nullptr, "me"}, Fp, "be", true);
@@ -1028,8 +1032,16 @@ void ccsd_iteration(Ctx& c) {
     KCHECK(c);
     s.dinv_ready = true;
   }
-  ccsd_rhs(c);
   if (s.pk.on) {
+    // R2 is needed at the canonical entries a<b, i<j only: every write into it skips the rest
+    c.canon_pairs = true;
+    try {
+      ccsd_rhs(c);
+    } catch (...) {
+      c.canon_pairs = false;
+      throw;
+    }
+    c.canon_pairs = false;
     ccsd_update_step(c, [&](double* part, int nb) {
       k_update_pk<<<dim3(nb, c.ninst), PK_THREADS, 0, c.stream>>>(
           c.d_R, s.pk.d_Dinv, c.d_T, c.d_diis_t, c.d_diis_e, c.namp, s.pk.n, c.n1, s.pk.D, s.pk.vv->d_full,
@@ -1038,6 +1050,7 @@ void ccsd_iteration(Ctx& c) {
     }, true, true, true);
     return;
   }
+  ccsd_rhs(c);
   ccsd_update_step(c, [&](double* part, int nb) {
     k_update<<<dim3(nb, c.ninst), RED_THREADS, 0, c.stream>>>(c.d_R, s.d_Dinv, c.d_T, c.d_diis_t, c.d_diis_e, c.namp,
                                                               c.cfg.diis_dim, c.d_diis_state, part, c.cfg.level_shift,

@@ -200,7 +200,8 @@ void gen_tasks(Ctx& c, const Layout& L, std::vector<GenTask>& tasks, std::vector
 // Integral tensors: V(p,q,r,s) generated directly in the requested storage
 // order (slot k holds V argument arg[k]) and row/column split; cached.
 static PermPlan make_perm_plan(Ctx& c, const Layout& D, const char* dl, const Layout& S, const char* sl,
-                               const std::vector<std::string>& terms, bool check_signs);
+                               const std::vector<std::string>& terms, bool check_signs = true,
+                               bool canon = false);
 
 // The exact symmetries of the integrals (the recipe antisymmetrises both pairs and
 // Hermitises): V(x0 x1 x2 x3) = coef [conj] V(y) with y[pi[k]] = x_k.
@@ -353,10 +354,16 @@ const Tensor* integral(Ctx& c, const IntRef& v, const int arg[4], int nrow) {
 // Permute plans.  dst[dl] (+)= sum_t coef_t * src[sigma_t], where term t is a
 // relabelling string ts (a permutation of dl): the src slot labelled l takes
 // the value of the dst slot labelled sigma_t(l), sigma_t(dl[k]) = ts[k].
+// canon: the destination is antisymmetric in slots (0, 1) and (2, 3) and only its
+// canonical entries are written -- sub-blocks with irreps g0 <= g1 and g2 <= g3, and
+// inside a block with g0 = g1 (g2 = g3) the elements with local index i0 < i1 (i2 < i3)
 static PermPlan make_perm_plan(Ctx& c, const Layout& D, const char* dl, const Layout& S,
-                               const char* sl, const std::vector<std::string>& terms, bool check_signs = true) {
+                               const char* sl, const std::vector<std::string>& terms, bool check_signs,
+                               bool canon) {
   const int r = D.rank;
   if (S.rank != r) throw ExpError{EXP_EINVAL, "permute rank mismatch"};
+  if (canon && (r != 4 || D.sp[0] != D.sp[1] || D.sg[0] != D.sg[1] || D.sp[2] != D.sp[3] || D.sg[2] != D.sg[3]))
+    throw ExpError{EXP_EINVAL, "canonical-pairs permute: destination without two same-space pairs"};
   std::vector<SubBlock> db, sb;
   enumerate_blocks(D, c.spaces, db);
   enumerate_blocks(S, c.spaces, sb);
@@ -389,10 +396,12 @@ static PermPlan make_perm_plan(Ctx& c, const Layout& D, const char* dl, const La
   std::vector<ChunkRef> chunks;
   for (auto& b : db) {
     if (b.count == 0) continue;
+    if (canon && (b.irr[0] > b.irr[1] || b.irr[2] > b.irr[3])) continue;
     PermTask T;
     memset(&T, 0, sizeof(T));
     T.dst = b.base;
     T.count = b.count;
+    if (canon) T.tri = (b.irr[0] == b.irr[1] ? 1 : 0) | (b.irr[2] == b.irr[3] ? 2 : 0);
     for (int d = 0; d < 4; ++d) { T.n[d] = 1; T.dst_st[d] = 0; }
     for (int k = 0; k < r; ++k) { T.n[pad + k] = b.n[k]; T.dst_st[pad + k] = b.st[k]; }
     for (int t = 0; t < nt; ++t) {
@@ -450,12 +459,13 @@ static std::vector<std::string> term_strings(const char* dl,
 
 void permute_into(Ctx& c, const std::string& site, Tensor& dst, const char* dl, const Tensor& src,
                   const char* sl, bool accumulate, std::vector<std::pair<double, std::string>> terms) {
-  const std::string key = "P:" + site;
+  const bool canon = dst.pair_canon && c.canon_pairs;
+  const std::string key = "P:" + site + (canon ? "|canon" : "");
   auto it = c.perm_cache.find(key);
   std::vector<double> coefs;
   auto ts = term_strings(dl, terms, coefs);
   if (it == c.perm_cache.end()) {
-    PermPlan p = make_perm_plan(c, dst.L, dl, src.L, sl, ts);
+    PermPlan p = make_perm_plan(c, dst.L, dl, src.L, sl, ts, true, canon);
     it = c.perm_cache.emplace(key, p).first;
   }
   cplx co[EXP_MAX_TERMS];
@@ -656,6 +666,7 @@ void einsum(Ctx& c, const std::string& site, cplx alpha, Operand A, Operand B, T
       P->g = make_gemm_plan(c, P->A->L, P->B->L, LC);
       // output permute: C[cl] (+)= sum coef * C'[ordC relabelled]
       P->pC = make_perm_plan(c, C.L, cl, LC, ordC.c_str(), ts);
+      if (C.pair_canon) P->pCc = make_perm_plan(c, C.L, cl, LC, ordC.c_str(), ts, true, true);
     }
     for (size_t k = 0; k < coefs.size(); ++k) P->cterms[k] = make_double2(coefs[k], 0.0);
     P->alpha = alpha;
@@ -706,7 +717,8 @@ void einsum(Ctx& c, const std::string& site, cplx alpha, Operand A, Operand B, T
                      P->gemm_beta);
   if (prof) CK(cudaEventRecord(pe[1], c.stream));
   if (P->permC)
-    launch_permute(c, P->pC, C.d, P->C2.d, C.is, P->C2.is, P->cterms, accumulate, false);
+    launch_permute(c, (C.pair_canon && c.canon_pairs) ? P->pCc : P->pC, C.d, P->C2.d, C.is, P->C2.is, P->cterms,
+                   accumulate, false);
   if (prof) {
     CK(cudaEventRecord(c.pev1, c.stream));
     CK(cudaEventSynchronize(c.pev1));

@@ -68,6 +68,8 @@ struct PermTask {
   int64_t count;     // elements, < 2^31
   uint32_t mg[4];    // division by n[d] as a multiply-high: see udiv_magic
   uint32_t ml[4];
+  int32_t tri;       // bit 0: only elements i0 < i1, bit 1: only i2 < i3 (diagonal blocks
+  int32_t pad_;      // of a canonical-pairs destination)
 };
 
 // q = floor(x / d) for 32-bit x as (t + ((x - t) >> 1)) >> (l - 1), t = umulhi(m, x),
@@ -123,6 +125,9 @@ struct Tensor {
   Layout L;
   cplx* d = nullptr;  // instance k at d + k * is
   int64_t is = 0;     // instance stride in elements (>= L.size)
+  // antisymmetric in slots (0, 1) and in (2, 3): while Ctx::canon_pairs is set, writes
+  // into this tensor cover only the canonical entries (p < q in both pairs)
+  bool pair_canon = false;
 };
 
 // Integral reference: V(p,q,r,s) with the spaces of its four arguments.
@@ -165,6 +170,7 @@ struct EinsumPlan {
   const Tensor* A = nullptr;
   const Tensor* B = nullptr;
   PermPlan pA, pB, pC;
+  PermPlan pCc;  // pC restricted to the canonical entries (destination marked pair_canon)
   GemmPlan g;
   cplx alpha;
   cplx cterms[EXP_MAX_TERMS];
@@ -239,6 +245,7 @@ struct Ctx {
   };
   std::vector<IntMeta> int_list;  // the cached layouts, for deriving related ones
   bool integrals_scaled = false;  // the MP2 scale is final (set by exp_init_integrals)
+  bool canon_pairs = false;       // writes into pair_canon tensors: canonical entries only
   std::map<std::string, PermPlan> perm_cache;
   std::map<std::string, std::unique_ptr<EinsumPlan>> plans;   // by call-site key
   std::vector<DevBuf> owned;

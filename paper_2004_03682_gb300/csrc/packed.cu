@@ -170,6 +170,33 @@ __global__ void __launch_bounds__(256) k_pack_scatter(cplx* __restrict__ dst, in
   }
 }
 
+// dst[full] += sign * src[packed] at the canonical full positions only: entries whose
+// row and column pairs are both p < q (a packed table's entries all are; an unpacked
+// table's others are skipped), each written once, at its own position
+__global__ void __launch_bounds__(256) k_pack_put_canon(cplx* __restrict__ dst, int64_t dis,
+                                                        const cplx* __restrict__ src, int64_t sis, PackDims D,
+                                                        const int32_t* __restrict__ rfull,
+                                                        const int32_t* __restrict__ cfull,
+                                                        const int32_t* __restrict__ rpair,
+                                                        const int32_t* __restrict__ cpair, int neg) {
+  const int inst = blockIdx.y;
+  dst += inst * dis;
+  src += inst * sis;
+  const int64_t total = D.blk[D.G];
+  const long long sgn = neg ? (long long)0x8000000000000000ull : 0ll;
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total; e += int64_t(gridDim.x) * blockDim.x) {
+    const int g = find_block(D.blk, D.G, e);
+    const uint32_t loc = uint32_t(e - D.blk[g]);
+    const uint32_t p = loc / uint32_t(D.nc[g]), q = loc - p * uint32_t(D.nc[g]);
+    const int32_t pr = rpair[D.roff[g] + p], pc = cpair[D.coff[g] + q];
+    if ((pr >> 16) >= (pr & 0xffff) || (pc >> 16) >= (pc & 0xffff)) continue;
+    const cplx v = src[e];
+    cplx& o = dst[D.fblk[g] + int64_t(rfull[D.roff[g] + p]) * D.fnc[g] + cfull[D.coff[g] + q]];
+    o = make_double2(o.x + __longlong_as_double(__double_as_longlong(v.x) ^ sgn),
+                     o.y + __longlong_as_double(__double_as_longlong(v.y) ^ sgn));
+  }
+}
+
 static int pk_blocks(Ctx& c, int64_t n) {
   return int(std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, int64_t(std::max(c.sm_count, 1)) * 8)));
 }
@@ -179,6 +206,19 @@ void launch_pack_gather(Ctx& c, cplx* dst, int64_t dis, const cplx* src, int64_t
   if (D.blk[D.G] == 0) return;
   k_pack_gather<<<dim3(pk_blocks(c, D.blk[D.G]), c.ninst), 256, 0, c.stream>>>(dst, dis, src, sis, D, R.d_full,
                                                                               C.d_full);
+  KCHECK(c);
+}
+
+// into a pair_canon destination while Ctx::canon_pairs is set: canonical entries only
+static void scatter_into(Ctx& c, Tensor& dst, const cplx* src, int64_t sis, const PackDims& D, const PairTable& R,
+                         const PairTable& C) {
+  if (!(dst.pair_canon && c.canon_pairs)) {
+    launch_pack_scatter(c, dst.d, dst.is, src, sis, D, R, C, 1.0, true);
+    return;
+  }
+  if (D.blk[D.G] == 0) return;
+  k_pack_put_canon<<<dim3(pk_blocks(c, D.blk[D.G]), c.ninst), 256, 0, c.stream>>>(
+      dst.d, dst.is, src, sis, D, R.d_full, C.d_full, R.d_pair, C.d_pair, 0);
   KCHECK(c);
 }
 
@@ -401,7 +441,7 @@ static PackedOp* int_times_tau(Ctx& c, const std::string& site, const PairTable&
 void packed_ladder(Ctx& c, Tensor& r2) {
   PackedState& s = PS(c);
   PackedOp* op = int_times_tau(c, "R2pp", *s.vv, r2, true, 1.0);
-  run_op(c, op, [] {}, [&] { launch_pack_scatter(c, r2.d, r2.is, op->C.d, op->C.is, op->dC, *op->Cr, *op->Cc, 1.0, true); });
+  run_op(c, op, [] {}, [&] { scatter_into(c, r2, op->C.d, op->C.is, op->dC, *op->Cr, *op->Cc); });
 }
 
 void packed_xamij(Ctx& c, Tensor& X) {
@@ -444,7 +484,7 @@ void packed_hh(Ctx& c, const Tensor& W, Tensor& r2) {
   }
   run_op(
       c, op, [&] { launch_pack_gather(c, op->B.d, op->B.is, W.d, W.is, op->dB, *op->Br, *op->Bc); },
-      [&] { launch_pack_scatter(c, r2.d, r2.is, op->C.d, op->C.is, op->dC, *op->Cr, *op->Cc, 1.0, true); });
+      [&] { scatter_into(c, r2, op->C.d, op->C.is, op->dC, *op->Cr, *op->Cc); });
 }
 
 void packed_release(Ctx& c) {

@@ -51,6 +51,7 @@ __global__ void __launch_bounds__(256) k_permute(const PermTask* __restrict__ ta
     const uint32_t q1 = udiv(q2, T.mg[1], T.ml[1]);
     const int i1 = int(q2 - q1 * n1);
     const int i0 = int(q1);
+    if (((T.tri & 1) && i0 >= i1) || ((T.tri & 2) && i2 >= i3)) continue;
     const int64_t dp = T.dst + i0 * T.dst_st[0] + i1 * T.dst_st[1] + i2 * T.dst_st[2] + i3 * T.dst_st[3];
     double vr = 0.0, vi = 0.0;
 #pragma unroll

@@ -1,0 +1,55 @@
+"""Profiling entry point: one workload, a few warm iterations, then the part to be
+captured inside an NVTX range, so that a profiler can select it with
+``--nvtx --nvtx-include "<range>/"``.
+
+    python -m paper_2004_03682_gb300.profile_run --occ 40 --virt 200 --irreps 8            # range "iter3"
+    python -m paper_2004_03682_gb300.profile_run --occ 40 --virt 200 --irreps 8 --top      # range "top"
+
+Without --top the range holds one whole CCSD iteration (the CUDA graph the bench
+replays); with --top it holds one launch of the contraction with the most complex
+multiply-adds per iteration (``Context.profile_top``).  Prints the iteration
+times (or the top contraction's site, time and work) as one line.
+"""
+from __future__ import annotations
+
+import argparse
+
+from . import expgb
+from . import synthetic as syn
+
+
+def main():
+    import torch
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--occ", type=int, default=40)
+    ap.add_argument("--virt", type=int, default=200)
+    ap.add_argument("--irreps", type=int, default=8)
+    ap.add_argument("--seed", type=int, default=2001)
+    ap.add_argument("--slices", type=int, default=5)
+    ap.add_argument("--fp64", action="store_true", help="plain FP64 contractions instead of the emulation")
+    ap.add_argument("--top", action="store_true", help="capture the top contraction instead of an iteration")
+    a = ap.parse_args()
+    prob = syn.make_problem(a.seed, a.occ, a.virt, a.irreps)
+    prec = expgb.EXP_FP64 if a.fp64 else expgb.EXP_EMU_BF16
+    ctx = expgb.from_problems([prob], conv_tol=1e-30, max_iter=50, precision=prec, n_slices=a.slices,
+                              level_shift=8.0)
+    ctx.init_integrals([prob.seed])
+    recs, _, _ = ctx.iterate(2)
+    torch.cuda.synchronize()
+    if a.top:
+        torch.cuda.nvtx.range_push("top")
+        site, ms, macs = ctx.profile_top(reps=1)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        print(f"top {site} {ms:.4f} ms {macs:.4e} complex MACs")
+    else:
+        torch.cuda.nvtx.range_push("iter3")
+        recs3, _, _ = ctx.iterate(1)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        print("iteration ms", [round(r["ms"], 3) for r in recs + recs3])
+    ctx.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -153,10 +153,11 @@ def run_reference(args):
     print(json.dumps(line))
 
 
-# Complex MACs of one CCSD iteration with full pair compounds (the oracle's work:
-# it sums over every c, d, e, f, m, n), from exp_work_per_iteration of a packed=0
-# context: o=10 v=40 C1 (the oracle sample) and the bench workloads.  The oracle
-# baseline is converted between them; the GPU arm's own count is the packed one.
+# Complex MACs of one CCSD iteration as the oracle evaluates it: every product of its
+# equation list (R1's <ma||ef> t_im^ef term included) over full pair compounds (it
+# sums over every c, d, e, f, m, n), counted by the blocked planner on o=10 v=40 C1
+# (the oracle sample) and the bench workloads.  The oracle baseline is converted
+# between them; the GPU arm's own count is that of its packed products.
 C1_MACS = 5.264e8
 ORACLE_MACS = {"ccsd_z8_o40_v200": 8.948e10, "ccsd_z8_o24_v120": None, "ccsd_c1_o10_v40": C1_MACS}
 # k_emu_gemm<5> DRAM read + write per launch of the top contraction, from ncu
@@ -276,12 +277,7 @@ def main():
         return
     cpu = None
     if ws == 1:
-        c1p = syn.make_problem(1001, 10, 40, 1)
-        c1 = expgb.from_problems([c1p], conv_tol=1e-30, max_iter=10, device=local, packed=False)
-        c1.init_integrals([c1p.seed])
-        c1.iterate(1)
-        c1_macs = c1.work_per_iteration()
-        c1.close()
+        c1_macs = C1_MACS
         omacs = ORACLE_MACS.get(WORKLOAD["name"]) or macs
         rate, n, dt, cores = cpu_baseline_leg(15.0)
         v = rate * c1_macs / omacs

@@ -842,6 +842,25 @@ static void copy_t(Ctx& c, Tensor& dst, const Tensor& src) {
                        c.ninst, cudaMemcpyDeviceToDevice, c.stream));
 }
 
+// delta_mj on the occupied space, layout (O, -1 | O, +1): a contraction with it over
+// (m, j) is the trace over m = j
+static const Tensor& delta_oo(Ctx& c) {
+  auto it = c.work.find("delta_oo");
+  if (it != c.work.end()) return *it->second;
+  const Layout L = L2(c, SP_OCC, -1, SP_OCC, +1);
+  Tensor* t = work_tensor(c, "delta_oo", L);
+  std::vector<SubBlock> sb;
+  enumerate_blocks(L, c.spaces, sb);
+  std::vector<cplx> h(size_t(t->is) * c.ninst, make_double2(0.0, 0.0));
+  for (const SubBlock& b : sb) {
+    if (b.irr[0] != b.irr[1]) continue;  // the block rule allows no other
+    for (int inst = 0; inst < c.ninst; ++inst)
+      for (int x = 0; x < b.n[0]; ++x) h[size_t(inst) * t->is + b.base + x * b.st[0] + x * b.st[1]] = make_double2(1.0, 0.0);
+  }
+  upload(c, t->d, h.data(), h.size() * sizeof(cplx));
+  return *t;
+}
+
 void ccsd_rhs(Ctx& c) {
   const int V = SP_VIRT, O = SP_OCC;
   Tensor& t1 = c.t1;
@@ -870,8 +889,10 @@ void ccsd_rhs(Ctx& c) {
   const bool packed = c.cfg.packed != 0;
   if (packed) packed_tau(c, tau);
 
-  // F_ae = sum_mf t_m^f <ma||fe> - 1/2 sum_mnf taut_mn^af <mn||ef>       (f_ov = 0, f diagonal)
-  einsum(c, "Fae1", ONE, {nullptr, &OVVV, "mafe"}, {&t1, nullptr, "fm"}, Fae, "ae", false);
+  // F_ae = Y_ae - 1/2 sum_mnf taut_mn^af <mn||ef>,  Y_ae = sum_mf t_m^f <ma||fe>   (f_ov = 0, f diagonal)
+  Tensor& Y = *work_tensor(c, "Yae", L2(c, V, +1, V, -1));
+  einsum(c, "Fae1", ONE, {nullptr, &OVVV, "mafe"}, {&t1, nullptr, "fm"}, Y, "ae", false);
+  copy_t(c, Fae, Y);
   einsum(c, "Fae2", C(-0.5), {&taut, nullptr, "afmn"}, {nullptr, &OOVV, "mnef"}, Fae, "ae", true);
   // F_mi = sum_ne t_n^e <mn||ie> + 1/2 sum_nef taut_in^ef <mn||ef>
   einsum(c, "Fmi1", ONE, {nullptr, &OOOV, "mnie"}, {&t1, nullptr, "en"}, Fmi, "mi", false);
@@ -905,7 +926,12 @@ void ccsd_rhs(Ctx& c) {
   einsum(c, "R1b", C(-1.0), {&t1, nullptr, "am"}, {&Fmi, nullptr, "mi"}, r1, "ai", true);
   einsum(c, "R1c", ONE, {&t2, nullptr, "aeim"}, {&Fme, nullptr, "me"}, r1, "ai", true);
   einsum(c, "R1d", C(-1.0), {nullptr, &OVOV, "naif"}, {&t1, nullptr, "fn"}, r1, "ai", true);
-  einsum(c, "R1e", C(-0.5), {nullptr, &OVVV, "maef"}, {&t2, nullptr, "efim"}, r1, "ai", true);
+  // -1/2 sum_mef <ma||ef> t_im^ef = 1/2 sum_m X_am,im - sum_e Y_ae t_i^e, with
+  // X_amij = sum_ef <am||ef> tau_ij^ef (the W_abef t1 intermediate below): tau - t2 =
+  // t_i^e t_m^f - t_i^f t_m^e and <am||ef> = -<am||fe> = -<ma||ef> = <ma||fe> leave
+  // sum_mef <am||ef> (tau - t2)_im^ef = 2 sum_e t_i^e Y_ae.  No product over the
+  // o v^3 integral; the X trace is added once X is formed.
+  einsum(c, "R1ey", C(-1.0), {&Y, nullptr, "ae"}, {&t1, nullptr, "ei"}, r1, "ai", true);
   einsum(c, "R1f", C(-0.5), {&t2, nullptr, "aemn"}, {nullptr, &OOVO, "nmei"}, r1, "ai", true);
 
   // ---- T2 equation
@@ -940,6 +966,8 @@ void ccsd_rhs(Ctx& c) {
     einsum(c, "Xamij", ONE, {nullptr, &VOVV, "amef"}, {&tau, nullptr, "efij"}, X, "amij", false);
   einsum(c, "R2x", C(-0.5), {&X, nullptr, "amij"}, {&t1, nullptr, "bm"}, r2, "abij", true,
          {{1.0, "abij"}, {-1.0, "baij"}});
+  // the X trace of the T1 equation (see R1ey): + 1/2 sum_m X_am,im
+  einsum(c, "R1ex", C(0.5), {&X, nullptr, "amij"}, {&delta_oo(c), nullptr, "mj"}, r1, "ai", true);
   // ring: P(ij)P(ab) [ sum_me t_im^ae W_mbej - sum_me t_i^e t_m^a <mb||ej> ]
   einsum(c, "Qring", ONE, {&t2, nullptr, "aeim"}, {&Wmbej, nullptr, "emjb"}, Q, "aijb", false);
   einsum(c, "Zmbji", ONE, {nullptr, &OVVO, "mbej"}, {&t1, nullptr, "ei"}, Z, "mbji", false);

@@ -57,7 +57,9 @@ typedef struct {
   void* user;
 } exp_allocator;
 
-enum { EXP_FP64 = 0, EXP_EMU_BF16 = 1 };
+/* EXP_EMU_DS (exp_zgemm only): double-single FP32 SIMT product, K <= 16 -- what the
+ * EXP_EMU_BF16 contractions use when every block has K <= 16 (Sec. II.B step 3). */
+enum { EXP_FP64 = 0, EXP_EMU_BF16 = 1, EXP_EMU_DS = 2 };
 enum { EXP_GUESS_MP2 = 0, EXP_GUESS_USER = 1 };
 
 typedef struct {
@@ -70,7 +72,8 @@ typedef struct {
   const double* eps_virt;     /* [n_inst * n_virt] */
   int precision;           /* EXP_FP64: all contractions in FP64.  EXP_EMU_BF16: the large
                               contractions as split-precision emulation of complex FP64 on
-                              the BF16 tensor cores (update, DIIS, energy stay FP64). */
+                              the BF16 tensor cores, those with every K <= 16 in double-single
+                              FP32 arithmetic (update, DIIS, energy stay FP64). */
   int n_slices;            /* BF16 slices per FP64 operand in emulation (3..6) */
   int diis_dim;            /* Pulay DIIS subspace (0 = off, <= 8) */
   double conv_tol;         /* converged when max |t_new - t| < conv_tol */
@@ -168,19 +171,22 @@ exp_status exp_set_amplitudes(exp_ctx* ctx, int inst, const void* t1_dev, const 
  * grouped GEMMs execute).  Valid after the first iteration has been planned. */
 exp_status exp_work_per_iteration(const exp_ctx* ctx, double* complex_macs);
 
-/* Time the contraction with the most work on its own: `reps` launches of its
- * grouped GEMM kernel on the context stream between CUDA events (emulated: one
- * full product first to put its operand slices in place, then the tensor-core
- * kernel alone; the slicing passes and a split-K reduction are not timed).  Writes the call-site
- * name (NUL-terminated, truncated to name_len), the mean milliseconds per launch
- * and its complex multiply-adds per launch.  Overwrites that contraction's
- * output buffer, which the next iteration recomputes. */
+/* Time one contraction on its own: `reps` launches of its grouped GEMM kernel on
+ * the context stream between CUDA events (emulated: one full product first to put
+ * its operand slices in place, then the tensor-core kernel alone; the slicing
+ * passes and a split-K reduction are not timed).  `name` is in-out: on entry a
+ * call-site name selects the contraction (EINVAL if there is none of that name), an
+ * empty string selects the one with the most work; on return it holds the site
+ * profiled (NUL-terminated, truncated to name_len).  Writes the mean milliseconds
+ * per launch and its complex multiply-adds per launch.  Overwrites that
+ * contraction's output buffer, which the next iteration recomputes. */
 exp_status exp_profile_top(exp_ctx* ctx, int reps, char* name, int name_len, double* ms_per_launch,
                            double* complex_macs_per_launch);
 
 /* One complex GEMM C = alpha A B (+ C if beta) on caller device buffers, with the
  * same kernels the contractions use (step 3 of the TTGT list, Sec. II.B):
- * precision EXP_FP64 (SIMT FP64) or EXP_EMU_BF16 (n_slices BF16 slices on the
+ * precision EXP_FP64 (SIMT FP64), EXP_EMU_DS (double-single FP32 SIMT, K <= 16)
+ * or EXP_EMU_BF16 (n_slices BF16 slices on the
  * tcgen05 tensor cores).  A: M x K, B: K x N, C: M x N, row-major complex128
  * (re, im doubles), 16-byte aligned.  Scratch (slices, exponents, split-K
  * partials) comes from `alloc` and is released before return.  Ordered on

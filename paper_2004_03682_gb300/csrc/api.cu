@@ -408,10 +408,18 @@ extern "C" exp_status exp_profile_top(exp_ctx* x, int reps, char* name, int name
   if (!x || reps < 1) throw ExpError{EXP_EINVAL, "bad argument"};
   Ctx& c = x->c;
   if (c.plans.empty()) throw ExpError{EXP_ESTATE, "no iteration planned yet"};
+  const std::string want = (name && name_len > 0) ? std::string(name, strnlen(name, size_t(name_len))) : "";
   const std::string* best = nullptr;
   EinsumPlan* P = nullptr;
-  for (auto& kv : c.plans)
-    if (!P || kv.second->g.flops_mac > P->g.flops_mac) { P = kv.second.get(); best = &kv.first; }
+  for (auto& kv : c.plans) {
+    if (!want.empty()) {
+      if (kv.first == want) { P = kv.second.get(); best = &kv.first; }
+    } else if (!P || kv.second->g.flops_mac > P->g.flops_mac) {
+      P = kv.second.get();
+      best = &kv.first;
+    }
+  }
+  if (!P) throw ExpError{EXP_EINVAL, "no contraction named " + want};
   Tensor* Cg = P->permC ? &P->C2 : nullptr;
   cplx* cd = Cg ? Cg->d : (P->gemm_out ? P->gemm_out : nullptr);
   int64_t cis = Cg ? Cg->is : P->gemm_out_is;
@@ -423,6 +431,8 @@ extern "C" exp_status exp_profile_top(exp_ctx* x, int reps, char* name, int name
   for (int r = 0; r < reps; ++r) {
     if (P->emulate)
       emu_run(c, P->emu, P->g, P->A->d, P->B->d, cd, P->A->is, P->B->is, cis, P->alpha, P->gemm_beta, true);
+    else if (P->ds)
+      launch_gemm_ds(c, P->g, P->A->d, P->B->d, cd, P->A->is, P->B->is, cis, P->alpha, P->gemm_beta);
     else
       launch_gemm_fp64(c, P->g, P->A->d, P->B->d, cd, P->A->is, P->B->is, cis, P->alpha, P->gemm_beta);
   }
@@ -447,11 +457,13 @@ extern "C" exp_status exp_zgemm(const exp_allocator* alloc, void* stream, int pr
   API_BEGIN
   if (!alloc || !alloc->alloc || !alloc->free || !A || !B || !C) throw ExpError{EXP_EINVAL, "null argument"};
   if (M < 1 || N < 1 || K < 0) throw ExpError{EXP_EINVAL, "bad GEMM shape"};
-  if (precision != EXP_FP64 && precision != EXP_EMU_BF16) throw ExpError{EXP_EINVAL, "bad precision"};
+  if (precision != EXP_FP64 && precision != EXP_EMU_BF16 && precision != EXP_EMU_DS)
+    throw ExpError{EXP_EINVAL, "bad precision"};
   if (precision == EXP_EMU_BF16 && (n_slices < 3 || n_slices > 6)) throw ExpError{EXP_EINVAL, "n_slices must be in 3..6"};
+  if (precision == EXP_EMU_DS && K > 16) throw ExpError{EXP_EINVAL, "double-single product: K above 16"};
   c.alloc = *alloc;
   c.stream = (cudaStream_t)stream;
-  c.cfg.precision = precision;
+  c.cfg.precision = precision == EXP_EMU_DS ? EXP_EMU_BF16 : precision;
   c.cfg.n_slices = n_slices;
   c.autotune = false;  // a one-off product: nothing to amortise a tuning pass over
   c.ninst = 1;
@@ -467,7 +479,10 @@ extern "C" exp_status exp_zgemm(const exp_allocator* alloc, void* stream, int pr
   LC.rows = {M}; LC.cols = {N}; LC.blk_off = {0}; LC.size = int64_t(M) * N;
   GemmPlan g = make_gemm_plan(c, LA, LB, LC);
   const cplx alpha = make_double2(are, aim);
-  if (precision == EXP_EMU_BF16 && K > 0) {
+  if (precision == EXP_EMU_DS && K > 0) {
+    ds_prepare(c, g);
+    launch_gemm_ds(c, g, (const cplx*)A, (const cplx*)B, (cplx*)C, LA.size, LB.size, LC.size, alpha, beta != 0);
+  } else if (precision == EXP_EMU_BF16 && K > 0) {
     Tensor TA, TB;
     TA.L = LA; TA.d = (cplx*)A; TA.is = LA.size;
     TB.L = LB; TB.d = (cplx*)B; TB.is = LB.size;

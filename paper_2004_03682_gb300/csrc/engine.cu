@@ -678,6 +678,11 @@ void einsum(Ctx& c, const std::string& site, cplx alpha, Operand A, Operand B, T
       arena_reserve(c, c.op_arena, size_t(off) * sizeof(cplx));
     }
     P->emulate = emu_wanted(c, P->g, site);
+    if (P->emulate && ds_wanted(c, P->g)) {  // short K: double-single SIMT instead of slices
+      P->emulate = false;
+      P->ds = true;
+      ds_prepare(c, P->g);
+    }
     // a B operand in the arena is not a tensor other contractions could share slices of
     if (P->emulate) P->emu = emu_plan(c, P->g, P->A, P->B, A.v != nullptr, B.v != nullptr, !P->permB);
   } else {
@@ -712,6 +717,8 @@ void einsum(Ctx& c, const std::string& site, cplx alpha, Operand A, Operand B, T
   if (P->emulate)
     emu_run(c, P->emu, P->g, P->A->d, P->B->d, Cg->d, P->A->is, P->B->is, Cg->is, alpha,
             P->gemm_beta);
+  else if (P->ds)
+    launch_gemm_ds(c, P->g, P->A->d, P->B->d, Cg->d, P->A->is, P->B->is, Cg->is, alpha, P->gemm_beta);
   else
     launch_gemm_fp64(c, P->g, P->A->d, P->B->d, Cg->d, P->A->is, P->B->is, Cg->is, alpha,
                      P->gemm_beta);
@@ -732,9 +739,9 @@ void einsum(Ctx& c, const std::string& site, cplx alpha, Operand A, Operand B, T
     fprintf(stderr, "[exp_phase] %-8s in %7.3f  gemm %7.3f  out %7.3f ms\n", site.c_str(), m_in, m_g, m_out);
     int64_t M = 0, N = 0, K = 0;
     for (auto& q : P->g.h_probs) { M = std::max<int64_t>(M, q.M); N = std::max<int64_t>(N, q.N); K = std::max<int64_t>(K, q.K); }
-    fprintf(stderr, "[exp_profile] %-8s %9.3f ms  %10.3g cMAC  %7.1f GF/s  probs=%d maxM=%lld maxN=%lld maxK=%lld perm=%d%d%d emu=%d\n",
+    fprintf(stderr, "[exp_profile] %-8s %9.3f ms  %10.3g cMAC  %7.1f GF/s  probs=%d maxM=%lld maxN=%lld maxK=%lld perm=%d%d%d emu=%d%s\n",
             site.c_str(), ms, double(P->g.flops_mac) * c.ninst,
             8.0 * double(P->g.flops_mac) * c.ninst / (ms * 1e6), P->g.n_probs, (long long)M, (long long)N,
-            (long long)K, P->permA, P->permB, P->permC, P->emulate);
+            (long long)K, P->permA, P->permB, P->permC, P->emulate, P->ds ? " ds" : "");
   }
 }

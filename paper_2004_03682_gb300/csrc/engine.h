@@ -159,6 +159,8 @@ struct GemmPlan {
   int64_t flops_mac = 0;  // complex MACs per instance
   int64_t dot_outputs = 0;  // > 0: run as one warp per output element (k_gemm_dot), this many outputs
   std::vector<GemmProb> h_probs;
+  GemmProb* d_ds = nullptr;  // double-single SIMT tiles (k_gemm_ds), set by ds_prepare
+  int ds_tiles = 0;
 };
 
 struct EmuPlan;  // emulated-GEMM plan (gemm_emu.cu)
@@ -178,6 +180,7 @@ struct EinsumPlan {
   cplx* gemm_out = nullptr;  // GEMM output when it writes the destination directly
   int64_t gemm_out_is = 0;
   bool emulate = false;
+  bool ds = false;  // short K under the emulated precision: double-single SIMT product
   bool swapped = false;  // operands exchanged at planning (C^T = B^T A^T); every call swaps them too
   int64_t offA2 = 0, offB2 = 0, offC2 = 0;  // element offsets of A2 / B2 / C2 in the operand arena
   EmuPlan* emu = nullptr;
@@ -202,6 +205,12 @@ void launch_tau3(Ctx& c, cplx* tau, cplx* taut, cplx* zeta, int64_t dst_is, cons
                  int n_chunks);
 void launch_gemm_fp64(Ctx& c, const GemmPlan& g, const cplx* A, const cplx* B, cplx* C,
                       int64_t a_is, int64_t b_is, int64_t c_is, cplx alpha, bool beta);
+// double-single SIMT product for short contractions (every K <= 16) under the
+// emulated precision: ds_wanted decides, ds_prepare builds its tile list once
+bool ds_wanted(Ctx& c, const GemmPlan& g);
+void ds_prepare(Ctx& c, GemmPlan& g);
+void launch_gemm_ds(Ctx& c, const GemmPlan& g, const cplx* A, const cplx* B, cplx* C, int64_t a_is,
+                    int64_t b_is, int64_t c_is, cplx alpha, bool beta);
 
 // Context -------------------------------------------------------------------
 struct Ctx {

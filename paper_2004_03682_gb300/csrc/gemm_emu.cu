@@ -29,6 +29,7 @@
 #include <string>
 
 #include "emu.h"
+#include "fpbits.h"
 
 namespace {
 
@@ -168,25 +169,6 @@ __device__ __forceinline__ int core_off(int r, int k) { return ((r >> 3) * (KB /
 
 // ---------------------------------------------------------------------------
 // GEMM kernel
-// R 2^e as a double, R rounded to 53 bits (nearest, ties to even) with integer
-// operations; the rare results outside the normal range take the FP64 route.
-// Same value as ldexp(double(R), e).
-__device__ __forceinline__ double scaled_i64(long long R, int e) {
-  if (R == 0) return 0.0;
-  const unsigned long long sgn = R < 0 ? (1ull << 63) : 0ull;
-  unsigned long long m = R < 0 ? 0ull - (unsigned long long)R : (unsigned long long)R;
-  const int lz = __clzll((long long)m);
-  m <<= lz;  // leading one at bit 63
-  unsigned long long mant = m >> 11;
-  const unsigned long long rem = m & 0x7FFull;
-  if (rem > 0x400ull || (rem == 0x400ull && (mant & 1ull))) ++mant;
-  int ex = 63 - lz + e;  // |R| 2^e = (mant / 2^52) 2^ex
-  if (mant >> 53) { mant >>= 1; ++ex; }
-  const int be = ex + 1023;
-  if (be <= 0 || be >= 2047) return ldexp(double(R), e);
-  return __longlong_as_double((long long)(sgn | (unsigned long long)(be) << 52 | (mant & 0xFFFFFFFFFFFFFull)));
-}
-
 // the same for a 128-bit integer: above 63 bits the value is shifted down to 63
 // bits with the dropped bits folded into the lowest (sticky) bit, which leaves the
 // round-to-nearest-even decision of scaled_i64 unchanged

@@ -4,8 +4,10 @@
 // C[MxN] = alpha A[MxK] B[KxN] (+ C).  SIMT FP64 FMA: GB300's FP64 rate is the
 // roofline for this path.
 #include <algorithm>
+#include <cmath>
 
 #include "engine.h"
+#include "fpbits.h"
 
 #define GT_K 8
 
@@ -196,4 +198,132 @@ void launch_gemm_fp64(Ctx& c, const GemmPlan& g, const cplx* A, const cplx* B, c
                                                                  alpha, beta);
     KCHECK(c);
   }
+}
+
+// ---------------------------------------------------------------------------
+// Short contractions (K <= DS_KMAX) under the emulated precision: complex
+// products in double-single arithmetic on the FP32 pipe (about 64x GB300's FP64
+// rate), every operand split into h + l (48 bits), products and sums carried with
+// error-free transformations and the result rounded once to FP64 -- a relative
+// error near K 2^-47 of sum |a||b|, below that of the BF16-sliced emulation.  For
+// short K that emulation pays for slicing and padding each K half to 16 and for a
+// tile pipeline with one k-block per tile; here a product is one pass over A.
+// CTA = DS_ROWS rows x DS_NC columns of one problem (the column chunks of a row
+// block are adjacent CTAs, so its A block is read from HBM about once): the A
+// block (rows contiguous, K each) is read coalesced and split into shared memory,
+// the chunk of alpha B staged as double-single pairs; every thread (one row)
+// forms its DS_NC outputs.
+#define DS_KMAX 16
+#define DS_NC 16
+#define DS_NG 4  // columns per accumulator group
+#define DS_ROWS 128
+#define DS_AST (DS_KMAX + 1)  // A row stride in float4: odd, so the row reads of a warp spread over the banks
+
+__global__ void __launch_bounds__(DS_ROWS) k_gemm_ds(const GemmProb* __restrict__ probs, int n_probs,
+                                                     const cplx* __restrict__ A, const cplx* __restrict__ B,
+                                                     cplx* __restrict__ C, int64_t ais, int64_t bis, int64_t cis,
+                                                     cplx alpha, float ascale, int general, int beta) {
+  __shared__ float4 As[DS_ROWS * DS_AST];  // (Re h, Re l, Im h, Im l) of A[r0 + r][k]
+  __shared__ float4 Bs[DS_KMAX * DS_NC];   // the same for alpha B[k][j0 + jj]
+  const int tile = blockIdx.x;
+  int pi = 0;
+  while (pi + 1 < n_probs && probs[pi + 1].tile0 <= tile) ++pi;
+  const GemmProb P = probs[pi];
+  const int lt = tile - P.tile0;
+  const int rb = lt / P.tiles_n;
+  const int r0 = rb * DS_ROWS, j0 = (lt - rb * P.tiles_n) * DS_NC;
+  const int nr = min(DS_ROWS, P.M - r0), nc = min(DS_NC, P.N - j0);
+  A += blockIdx.y * ais + P.a + int64_t(r0) * P.K;
+  B += blockIdx.y * bis + P.b;
+  C += blockIdx.y * cis + P.c + int64_t(r0) * P.N;
+  for (int e = threadIdx.x; e < nr * P.K; e += blockDim.x) {
+    const cplx x = A[e];
+    const int r = e / P.K, k = e - r * P.K;
+    const float2 xr = ds_split(x.x), xi = ds_split(x.y);
+    As[r * DS_AST + k] = make_float4(xr.x, xr.y, xi.x, xi.y);
+  }
+  const int row = threadIdx.x;
+  for (int t = threadIdx.x; t < P.K * DS_NC; t += blockDim.x) {
+    const int k = t / DS_NC, jj = t - k * DS_NC;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (jj < nc) {
+      cplx b = B[int64_t(k) * P.N + j0 + jj];
+      if (general) b = make_double2(alpha.x * b.x - alpha.y * b.y, alpha.x * b.y + alpha.y * b.x);
+      const float2 br = ds_split(b.x), bq = ds_split(b.y);
+      // ascale = +-2^k (exact in FP32) or 1
+      v = make_float4(br.x * ascale, br.y * ascale, bq.x * ascale, bq.y * ascale);
+    }
+    Bs[t] = v;
+  }
+  __syncthreads();
+  if (row >= nr) return;
+  // columns in groups of DS_NG (accumulators of a group in registers; a small loop
+  // body, 2 DS_NG independent accumulation chains)
+  cplx* crow = C + int64_t(row) * P.N + j0;
+  for (int g0 = 0; g0 < nc; g0 += DS_NG) {
+    float sr[DS_NG], cr[DS_NG], si[DS_NG], ci[DS_NG];
+#pragma unroll
+    for (int u = 0; u < DS_NG; ++u) sr[u] = cr[u] = si[u] = ci[u] = 0.f;
+    for (int k = 0; k < P.K; ++k) {
+      const float4 a = As[row * DS_AST + k];
+#pragma unroll
+      for (int u = 0; u < DS_NG; ++u) {
+        const float4 b = Bs[k * DS_NC + g0 + u];  // zero past nc
+        ds_mac(sr[u], cr[u], a.x, a.y, b.x, b.y);    // Re += Re a Re b
+        ds_mac(sr[u], cr[u], -a.z, -a.w, b.z, b.w);  //     - Im a Im b
+        ds_mac(si[u], ci[u], a.x, a.y, b.z, b.w);    // Im += Re a Im b
+        ds_mac(si[u], ci[u], a.z, a.w, b.x, b.y);    //     + Im a Re b
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < DS_NG; ++u) {
+      if (g0 + u < nc) {
+        double vr = ds_to_double(sr[u], cr[u]), vi = ds_to_double(si[u], ci[u]);
+        if (beta) {
+          const cplx o = crow[g0 + u];
+          vr += o.x;
+          vi += o.y;
+        }
+        crow[g0 + u] = make_double2(vr, vi);
+      }
+    }
+  }
+}
+
+bool ds_wanted(Ctx& c, const GemmPlan& g) {
+  if (c.cfg.precision != EXP_EMU_BF16 || g.dot_outputs || g.h_probs.empty()) return false;
+  int kmax = 0;
+  for (const GemmProb& p : g.h_probs) kmax = std::max(kmax, p.K);
+  return kmax >= 1 && kmax <= DS_KMAX;
+}
+
+void ds_prepare(Ctx& c, GemmPlan& g) {
+  if (g.d_ds) return;
+  for (const GemmProb& p : g.h_probs)
+    if (p.K > DS_KMAX) throw ExpError{EXP_EINVAL, "double-single GEMM: K above 16"};
+  std::vector<GemmProb> v = g.h_probs;
+  int tiles = 0;
+  for (GemmProb& p : v) {  // CTAs: DS_ROWS rows x DS_NC columns, column chunks adjacent
+    p.tiles_m = (p.M + DS_ROWS - 1) / DS_ROWS;
+    p.tiles_n = (p.N + DS_NC - 1) / DS_NC;
+    p.tile0 = tiles;
+    tiles += p.tiles_m * p.tiles_n;
+  }
+  g.ds_tiles = tiles;
+  g.d_ds = (GemmProb*)c.dalloc(sizeof(GemmProb) * std::max<size_t>(v.size(), 1));
+  upload(c, g.d_ds, v.data(), sizeof(GemmProb) * v.size());
+}
+
+void launch_gemm_ds(Ctx& c, const GemmPlan& g, const cplx* A, const cplx* B, cplx* C, int64_t ais, int64_t bis,
+                    int64_t cis, cplx alpha, bool beta) {
+  if (!g.d_ds) throw ExpError{EXP_ESTATE, "double-single GEMM not prepared"};
+  if (g.ds_tiles == 0) return;
+  // alpha = +-2^k folds into the FP32 parts exactly; any other alpha multiplies B in FP64
+  int ex = 0;
+  const double fr = std::frexp(std::fabs(alpha.x), &ex);
+  const bool pow2 = alpha.y == 0.0 && fr == 0.5 && ex > -100 && ex < 100;
+  k_gemm_ds<<<dim3(g.ds_tiles, c.ninst), DS_ROWS, 0, c.stream>>>(g.d_ds, g.n_probs, A, B, C, ais, bis, cis, alpha,
+                                                                 pow2 ? float(alpha.x) : 1.0f, pow2 ? 0 : 1,
+                                                                 beta ? 1 : 0);
+  KCHECK(c);
 }

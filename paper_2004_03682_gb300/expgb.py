@@ -15,7 +15,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libexpgb.so")
 
-EXP_FP64, EXP_EMU_BF16 = 0, 1
+EXP_FP64, EXP_EMU_BF16, EXP_EMU_DS = 0, 1, 2
 EXP_GUESS_MP2, EXP_GUESS_USER = 0, 1
 STATUS = {0: "EXP_OK", 1: "EXP_EINVAL", 2: "EXP_ENOMEM", 3: "EXP_ECUDA", 4: "EXP_ENOTCONV",
           5: "EXP_ENUMERIC", 6: "EXP_ETIMEOUT", 7: "EXP_ESTATE"}
@@ -267,9 +267,10 @@ class Context:
         self._check(self.L.exp_work_per_iteration(self.h, C.byref(m)))
         return m.value
 
-    def profile_top(self, reps=5):
-        """(site, ms per launch, complex MACs per launch) of the largest contraction."""
-        buf = C.create_string_buffer(64)
+    def profile_top(self, reps=5, site=None):
+        """(site, ms per launch, complex MACs per launch) of the largest contraction, or
+        of the contraction at call site `site`."""
+        buf = C.create_string_buffer((site or "").encode(), 64)
         ms, macs = C.c_double(), C.c_double()
         self._check(self.L.exp_profile_top(self.h, int(reps), buf, 64, C.byref(ms), C.byref(macs)))
         return buf.value.decode(), ms.value, macs.value

@@ -4,10 +4,12 @@ captured inside an NVTX range, so that a profiler can select it with
 
     python -m paper_2004_03682_gb300.profile_run --occ 40 --virt 200 --irreps 8            # range "iter3"
     python -m paper_2004_03682_gb300.profile_run --occ 40 --virt 200 --irreps 8 --top      # range "top"
+    python -m paper_2004_03682_gb300.profile_run --occ 24 --virt 120 --irreps 8 --top --site R2b
 
 Without --top the range holds one whole CCSD iteration (the CUDA graph the bench
-replays); with --top it holds one launch of the contraction with the most complex
-multiply-adds per iteration (``Context.profile_top``).  Prints the iteration
+replays); with --top it holds the contraction with the most complex multiply-adds per
+iteration, or the one at call site --site (``Context.profile_top``): one full product
+(slicing passes and GEMM) and one more launch of its GEMM kernel.  Prints the iteration
 times (or the top contraction's site, time and work) as one line.
 """
 from __future__ import annotations
@@ -28,6 +30,7 @@ def main():
     ap.add_argument("--slices", type=int, default=5)
     ap.add_argument("--fp64", action="store_true", help="plain FP64 contractions instead of the emulation")
     ap.add_argument("--top", action="store_true", help="capture the top contraction instead of an iteration")
+    ap.add_argument("--site", default=None, help="with --top: this call site instead of the largest")
     a = ap.parse_args()
     prob = syn.make_problem(a.seed, a.occ, a.virt, a.irreps)
     prec = expgb.EXP_FP64 if a.fp64 else expgb.EXP_EMU_BF16
@@ -38,7 +41,7 @@ def main():
     torch.cuda.synchronize()
     if a.top:
         torch.cuda.nvtx.range_push("top")
-        site, ms, macs = ctx.profile_top(reps=1)
+        site, ms, macs = ctx.profile_top(reps=1, site=a.site)
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
         print(f"top {site} {ms:.4f} ms {macs:.4e} complex MACs")

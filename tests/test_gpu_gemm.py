@@ -98,3 +98,46 @@ def test_emulated_alpha_beta_and_zero_rows(env):
     dA, dB, dC = (torch.tensor(x, device="cuda") for x in (A, B, C0))
     out = expgb.zgemm(dA, dB, dC, alpha=2 - 1j, beta=True, precision=expgb.EXP_EMU_BF16, n_slices=4).cpu().numpy()
     np.testing.assert_allclose(out, (2 - 1j) * (A @ B) + C0, atol=1e-12, rtol=0)
+
+
+DS_SHAPES = [(1, 1, 1), (7, 3, 5), (128, 16, 16), (300, 37, 9), (129, 81, 14), (1000, 5, 1)]
+
+
+@pytest.mark.parametrize("M,N,K", DS_SHAPES)
+@pytest.mark.parametrize("alpha,beta", [(1.0, False), (-0.5, True), (0.3 + 0.2j, True)])
+def test_double_single_within_bound(env, M, N, K, alpha, beta):
+    """The double-single product (FP32 h + l per operand, error-free products and sums,
+    one rounding to FP64) against numpy: each element within 2^-44 of sum_k |a||b|
+    (48-bit operands, K <= 16 terms), on rows and columns spanning 2^-60 .. 2^20,
+    exact zeros, and a ragged last row / column tile."""
+    torch, expgb = env
+    rng = np.random.default_rng(M + 3 * N + 7 * K)
+    A = _c(rng, (M, K)) * np.exp2(rng.integers(-60, 20, (M, 1)))
+    B = _c(rng, (K, N)) * np.exp2(rng.integers(-10, 10, (1, N)))
+    A[0, 0] = 0.0
+    C0 = _c(rng, (M, N))
+    dA, dB, dC = (torch.tensor(x, device="cuda") for x in (A, B, C0))
+    out = expgb.zgemm(dA, dB, dC, alpha=alpha, beta=beta, precision=expgb.EXP_EMU_DS).cpu().numpy()
+    ref = alpha * (A @ B) + (C0 if beta else 0)
+    bound = 2.0 ** -44 * abs(alpha) * 2 * (np.abs(A) @ np.abs(B)) + (1e-15 * np.abs(C0) if beta else 0) + 1e-300
+    assert np.all(np.abs(out - ref) <= bound)
+
+
+def test_double_single_exact_on_integer_inputs(env):
+    """Integer inputs below 2^11: every product and partial sum is exact in h + l,
+    so the result is bit-exact."""
+    torch, expgb = env
+    rng = np.random.default_rng(9)
+    A = (rng.integers(-1000, 1001, (333, 16)) + 1j * rng.integers(-1000, 1001, (333, 16))).astype(np.complex128)
+    B = (rng.integers(-1000, 1001, (16, 45)) + 1j * rng.integers(-1000, 1001, (16, 45))).astype(np.complex128)
+    dA, dB = torch.tensor(A, device="cuda"), torch.tensor(B, device="cuda")
+    out = expgb.zgemm(dA, dB, precision=expgb.EXP_EMU_DS).cpu().numpy()
+    np.testing.assert_array_equal(out, A @ B)
+
+
+def test_double_single_refuses_long_k(env):
+    torch, expgb = env
+    dA = torch.zeros((4, 17), dtype=torch.complex128, device="cuda")
+    dB = torch.zeros((17, 4), dtype=torch.complex128, device="cuda")
+    with pytest.raises(expgb.ExpError):
+        expgb.zgemm(dA, dB, precision=expgb.EXP_EMU_DS)

@@ -894,23 +894,32 @@ void ccsd_rhs(Ctx& c) {
   einsum(c, "Fae1", ONE, {nullptr, &OVVV, "mafe"}, {&t1, nullptr, "fm"}, Y, "ae", false);
   copy_t(c, Fae, Y);
   einsum(c, "Fae2", C(-0.5), {&taut, nullptr, "afmn"}, {nullptr, &OOVV, "mnef"}, Fae, "ae", true);
-  // F_mi = sum_ne t_n^e <mn||ie> + 1/2 sum_nef taut_in^ef <mn||ef>
-  einsum(c, "Fmi1", ONE, {nullptr, &OOOV, "mnie"}, {&t1, nullptr, "en"}, Fmi, "mi", false);
-  einsum(c, "Fmi2", C(0.5), {nullptr, &OOVV, "mnef"}, {&taut, nullptr, "efin"}, Fmi, "mi", true);
   // F_me = sum_nf t_n^f <mn||ef>
   einsum(c, "Fme", ONE, {nullptr, &OOVV, "mnef"}, {&t1, nullptr, "fn"}, Fme, "me", false);
-  // W_mnij = <mn||ij> + P(ij) sum_e t_j^e <mn||ie> + 1/2 sum_ef tau_ij^ef <mn||ef>
-  // (factor 1/2 instead of 1/4: it carries the (1/4) tau <mn||ef> part of W_abef too)
+  // X2_mnij = 1/2 sum_ef tau_ij^ef <mn||ef>, the tau part of W_mnij (factor 1/2 instead
+  // of 1/4: it carries the (1/4) tau <mn||ef> part of W_abef too)
+  Tensor& X2 = *work_tensor(c, "X2mnij", Wmnij.L);
+  if (packed) {
+    CK(cudaMemset2DAsync(X2.d, X2.is * sizeof(cplx), 0, X2.L.size * sizeof(cplx), c.ninst, c.stream));
+    packed_wmnij(c, X2);
+  } else {
+    einsum(c, "Wmnij2", C(0.5), {nullptr, &OOVV, "mnef"}, {&tau, nullptr, "efij"}, X2, "mnij", false);
+  }
+  // F_mi = sum_ne t_n^e <mn||ie> + 1/2 sum_nef taut_in^ef <mn||ef>, the second term as
+  // sum_n X2_mn,in - 1/2 sum_e t_i^e F_me: taut = tau - 1/2 (t_i^e t_n^f - t_i^f t_n^e)
+  // and <mn||ef> = -<mn||fe> leave 1/4 sum_nef <mn||ef> (t_i^e t_n^f - t_i^f t_n^e) =
+  // 1/2 sum_e t_i^e F_me.  No product over a t2-sized operand.
+  einsum(c, "Fmi1", ONE, {nullptr, &OOOV, "mnie"}, {&t1, nullptr, "en"}, Fmi, "mi", false);
+  einsum(c, "Fmi2x", ONE, {&X2, nullptr, "mnij"}, {&delta_oo(c), nullptr, "nj"}, Fmi, "mi", true);
+  einsum(c, "Fmi2t", C(-0.5), {&Fme, nullptr, "me"}, {&t1, nullptr, "ei"}, Fmi, "mi", true);
+  // W_mnij = <mn||ij> + P(ij) sum_e t_j^e <mn||ie> + X2_mnij
   {
     const int arg[4] = {0, 1, 2, 3};
     copy_int(c, Wmnij, integral(c, OOOO, arg, 2));
   }
   einsum(c, "Wmnij1", ONE, {nullptr, &OOOV, "mnie"}, {&t1, nullptr, "ej"}, Wmnij, "mnij", true,
          {{1.0, "mnij"}, {-1.0, "mnji"}});
-  if (packed)
-    packed_wmnij(c, Wmnij);
-  else
-    einsum(c, "Wmnij2", C(0.5), {nullptr, &OOVV, "mnef"}, {&tau, nullptr, "efij"}, Wmnij, "mnij", true);
+  permute_into(c, "WmnijX2", Wmnij, "mnij", X2, "mnij", true);
   // W_mbej = <mb||ej> + sum_f t_j^f <mb||ef> - sum_n t_n^b <mn||ej> - sum_nf zeta_jn^fb <mn||ef>
   {
     const int arg[4] = {2, 0, 3, 1};  // storage (e, m, j, b) <- V(m, b, e, j)

@@ -612,6 +612,28 @@ void einsum(Ctx& c, const std::string& site, cplx alpha, Operand A, Operand B, T
         if (K.find(x) == std::string::npos) FA += x;
       for (char x : bl)
         if (K.find(x) == std::string::npos) FB += x;
+      // when each operand holds exactly one side of the output compound, take its free
+      // labels in the output's order: the GEMM then writes the destination directly.
+      // Only where that adds no operand permute: an integral is generated in any
+      // layout, a tensor only if it is permuted anyway.
+      auto same_set = [](std::string a, std::string b) {
+        std::sort(a.begin(), a.end());
+        std::sort(b.begin(), b.end());
+        return a == b;
+      };
+      auto in_place = [](const Operand& op, const std::string& ord, int nrow) {
+        return op.t && std::string(op.labels) == ord && op.t->L.nrow == nrow;
+      };
+      if (terms.empty() && FA.size() + FB.size() == clab.size() && C.L.nrow == int(FA.size()) &&
+          same_set(FA, clab.substr(0, FA.size())) && same_set(FB, clab.substr(FA.size()))) {
+        const std::string FA2 = clab.substr(0, FA.size()), FB2 = clab.substr(FA.size());
+        const bool okA = FA2 == FA || A.v || !in_place(A, FA + K, int(FA.size()));
+        const bool okB = FB2 == FB || B.v || !in_place(B, K + FB, int(K.size()));
+        if (okA && okB) {
+          FA = FA2;
+          FB = FB2;
+        }
+      }
     };
     split_labels();
     if (FA.size() + FB.size() != clab.size()) throw ExpError{EXP_EINVAL, "einsum labels: " + site};

@@ -933,7 +933,11 @@ void ccsd_rhs(Ctx& c) {
   CK(cudaMemset2DAsync(r1.d, r1.is * sizeof(cplx), 0, r1.L.size * sizeof(cplx), c.ninst, c.stream));
   einsum(c, "R1a", ONE, {&Fae, nullptr, "ae"}, {&t1, nullptr, "ei"}, r1, "ai", true);
   einsum(c, "R1b", C(-1.0), {&t1, nullptr, "am"}, {&Fmi, nullptr, "mi"}, r1, "ai", true);
-  einsum(c, "R1c", ONE, {&t2, nullptr, "aeim"}, {&Fme, nullptr, "me"}, r1, "ai", true);
+  // t2 in the (ai | em) order of the ring product's A operand, permuted once for both
+  // products that read it that way (R1's t_im^ae F_me term and the ring product)
+  Tensor& t2x = *work_tensor(c, "t2aiem", L4(c, V, +1, O, -1, V, +1, O, -1, 2));
+  permute_into(c, "T2aiem", t2x, "aiem", t2, "aeim", false);
+  einsum(c, "R1c", ONE, {&t2x, nullptr, "aiem"}, {&Fme, nullptr, "me"}, r1, "ai", true);
   einsum(c, "R1d", C(-1.0), {nullptr, &OVOV, "naif"}, {&t1, nullptr, "fn"}, r1, "ai", true);
   // -1/2 sum_mef <ma||ef> t_im^ef = 1/2 sum_m X_am,im - sum_e Y_ae t_i^e, with
   // X_amij = sum_ef <am||ef> tau_ij^ef (the W_abef t1 intermediate below): tau - t2 =
@@ -978,7 +982,7 @@ void ccsd_rhs(Ctx& c) {
   // the X trace of the T1 equation (see R1ey): + 1/2 sum_m X_am,im
   einsum(c, "R1ex", C(0.5), {&X, nullptr, "amij"}, {&delta_oo(c), nullptr, "mj"}, r1, "ai", true);
   // ring: P(ij)P(ab) [ sum_me t_im^ae W_mbej - sum_me t_i^e t_m^a <mb||ej> ]
-  einsum(c, "Qring", ONE, {&t2, nullptr, "aeim"}, {&Wmbej, nullptr, "emjb"}, Q, "aijb", false);
+  einsum(c, "Qring", ONE, {&t2x, nullptr, "aiem"}, {&Wmbej, nullptr, "emjb"}, Q, "aijb", false);
   einsum(c, "Zmbji", ONE, {nullptr, &OVVO, "mbej"}, {&t1, nullptr, "ei"}, Z, "mbji", false);
   einsum(c, "Qt1t1", C(-1.0), {&t1, nullptr, "am"}, {&Z, nullptr, "mbji"}, Q, "aijb", true);
   permute_into(c, "R2ring", r2, "abij", Q, "aijb", true,

@@ -43,38 +43,59 @@ __global__ void __launch_bounds__(256) k_permute(const PermTask* __restrict__ ta
   unsigned long long sgn[NT];
 #pragma unroll
   for (int t = 0; t < NT; ++t) sgn[t] = co.c[t].x < 0.0 ? 0x8000000000000000ull : 0ull;
-  for (uint32_t e = uint32_t(ch.start) + threadIdx.x; e < end; e += blockDim.x) {
-    const uint32_t q3 = udiv(e, T.mg[3], T.ml[3]);
-    const int i3 = int(e - q3 * n3);
-    const uint32_t q2 = udiv(q3, T.mg[2], T.ml[2]);
-    const int i2 = int(q3 - q2 * n2);
-    const uint32_t q1 = udiv(q2, T.mg[1], T.ml[1]);
-    const int i1 = int(q2 - q1 * n1);
-    const int i0 = int(q1);
-    if (((T.tri & 1) && i0 >= i1) || ((T.tri & 2) && i2 >= i3)) continue;
-    const int64_t dp = T.dst + i0 * T.dst_st[0] + i1 * T.dst_st[1] + i2 * T.dst_st[2] + i3 * T.dst_st[3];
-    double vr = 0.0, vi = 0.0;
+  // U elements per step (blockDim apart, so every store instruction stays coalesced):
+  // their gathers are all issued before the first store, for U x NT loads in flight
+  constexpr int U = NT <= 2 ? 4 : 2;
+  for (uint32_t e0 = uint32_t(ch.start) + threadIdx.x; e0 < end; e0 += U * blockDim.x) {
+    int64_t dp[U];
+    bool live[U];
+    double vr[U], vi[U];
 #pragma unroll
-    for (int t = 0; t < NT; ++t) {
-      const int64_t sp = T.src[t] + i0 * T.src_st[t][0] + i1 * T.src_st[t][1] +
-                         i2 * T.src_st[t][2] + i3 * T.src_st[t][3];
-      cplx x = src[sp];
-      if (conj) x.y = -x.y;
-      if (SIGNS) {
-        const double xr = __longlong_as_double(__double_as_longlong(x.x) ^ (long long)sgn[t]);
-        const double xi = __longlong_as_double(__double_as_longlong(x.y) ^ (long long)sgn[t]);
-        if (t == 0) { vr = xr; vi = xi; } else { vr += xr; vi += xi; }
-      } else {
-        vr += co.c[t].x * x.x - co.c[t].y * x.y;
-        vi += co.c[t].x * x.y + co.c[t].y * x.x;
+    for (int u = 0; u < U; ++u) {
+      const uint32_t e = e0 + u * blockDim.x;
+      const uint32_t q3 = udiv(e, T.mg[3], T.ml[3]);
+      const int i3 = int(e - q3 * n3);
+      const uint32_t q2 = udiv(q3, T.mg[2], T.ml[2]);
+      const int i2 = int(q3 - q2 * n2);
+      const uint32_t q1 = udiv(q2, T.mg[1], T.ml[1]);
+      const int i1 = int(q2 - q1 * n1);
+      const int i0 = int(q1);
+      live[u] = e < end && !(((T.tri & 1) && i0 >= i1) || ((T.tri & 2) && i2 >= i3));
+      dp[u] = T.dst + i0 * T.dst_st[0] + i1 * T.dst_st[1] + i2 * T.dst_st[2] + i3 * T.dst_st[3];
+      vr[u] = 0.0;
+      vi[u] = 0.0;
+      // loads not under a branch (a dead element reads its task's first source element,
+      // always in bounds), so the U x NT gathers issue back to back
+#pragma unroll
+      for (int t = 0; t < NT; ++t) {
+        const int64_t sp = live[u] ? T.src[t] + i0 * T.src_st[t][0] + i1 * T.src_st[t][1] + i2 * T.src_st[t][2] +
+                                         i3 * T.src_st[t][3]
+                                   : T.src[t];
+        cplx x = src[sp];
+        if (conj) x.y = -x.y;
+        if (SIGNS) {
+          const double xr = __longlong_as_double(__double_as_longlong(x.x) ^ (long long)sgn[t]);
+          const double xi = __longlong_as_double(__double_as_longlong(x.y) ^ (long long)sgn[t]);
+          if (t == 0) { vr[u] = xr; vi[u] = xi; } else { vr[u] += xr; vi[u] += xi; }
+        } else {
+          vr[u] += co.c[t].x * x.x - co.c[t].y * x.y;
+          vi[u] += co.c[t].x * x.y + co.c[t].y * x.x;
+        }
       }
     }
     if (acc) {
-      const cplx o = dst[dp];
-      vr += o.x;
-      vi += o.y;
+      cplx o[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) o[u] = dst[live[u] ? dp[u] : T.dst];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        vr[u] += o[u].x;
+        vi[u] += o[u].y;
+      }
     }
-    dst[dp] = make_double2(vr, vi);
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (live[u]) dst[dp[u]] = make_double2(vr[u], vi[u]);
   }
 }
 

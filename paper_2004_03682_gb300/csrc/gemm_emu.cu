@@ -904,9 +904,10 @@ struct EmuState {
 bool emu_wanted(Ctx& c, const GemmPlan& g, const std::string&) {
   if (c.cfg.precision != EXP_EMU_BF16) return false;
   if (c.cfg.emu_min_macs > 0) return double(g.flops_mac) >= c.cfg.emu_min_macs;
-  // below ~4e6 complex MACs the slicing passes cost more than the FP64 dot
-  // kernel; above, GB300's FP64 rate loses to the tensor cores at every K
-  return g.flops_mac >= int64_t(1) << 22;
+  // below ~4e6 complex MACs per launch (all instances) the slicing passes cost more
+  // than the FP64 kernels; above, GB300's FP64 rate loses to the tensor cores (or, for
+  // K <= 16, to the double-single FP32 product) at every K
+  return g.flops_mac * c.ninst >= int64_t(1) << 22;
 }
 
 template <int S>

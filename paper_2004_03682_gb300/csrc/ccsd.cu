@@ -1021,8 +1021,11 @@ void ccsd_update_step(Ctx& c, const std::function<void(double*, int)>& upd, bool
                       bool packed) {
   CcsdState& s = S(c);
   const int dim = c.cfg.diis_dim;
-  const int nb = RED_BLOCKS;
   const int64_t nvec = packed ? s.pk.n : c.namp;  // length of the DIIS vectors
+  // packed kernels (PK_THREADS per CTA): no more CTAs per instance than the vector fills,
+  // so a batch of small instances does not launch mostly idle blocks
+  const int nb = packed ? int(std::max<int64_t>(1, std::min<int64_t>(RED_BLOCKS, (nvec + PK_THREADS - 1) / PK_THREADS)))
+                        : RED_BLOCKS;
   upd(s.d_part, nb);
   k_finalize_update<<<c.ninst, 32, 0, c.stream>>>(s.d_part, nb, c.d_diis_state, c.d_stats, dim, c.cfg.conv_tol);
   KCHECK(c);

@@ -508,12 +508,16 @@ GemmPlan make_gemm_plan(Ctx& c, const Layout& A, const Layout& B, const Layout& 
     g.flops_mac += M * N * K;
     g.h_probs.push_back(p);
   }
-  // matrix-vector products, and small ones over a K long enough for the warp's lanes
-  // to share: one warp per output element (a short K leaves most lanes idle, and a
-  // batch of instances multiplies the outputs, so those take the tiled kernels)
-  int64_t maxK = 0;
-  for (const GemmProb& p : g.h_probs) maxK = std::max<int64_t>(maxK, p.K);
-  if (maxN <= 2 || (g.flops_mac * c.ninst < (int64_t(1) << 22) && maxK >= 32)) {
+  // matrix-vector products, and small ones whose K is long enough for the warp's lanes
+  // to share or whose outputs are few: one warp per output element (a short K leaves
+  // most lanes idle, which a batch of instances multiplies: those take the tiles)
+  int64_t maxK = 0, outs = 0;
+  for (const GemmProb& p : g.h_probs) {
+    maxK = std::max<int64_t>(maxK, p.K);
+    outs += int64_t(p.M) * p.N;
+  }
+  if (maxN <= 2 ||
+      (g.flops_mac * c.ninst < (int64_t(1) << 22) && (maxK >= 32 || outs * c.ninst <= (int64_t(1) << 18)))) {
     int64_t o = 0;
     for (auto& p : g.h_probs) { p.ws = o; o += int64_t(p.M) * p.N; }
     g.dot_outputs = o;

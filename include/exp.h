@@ -58,7 +58,9 @@ typedef struct {
 } exp_allocator;
 
 /* EXP_EMU_DS (exp_zgemm only): double-single FP32 SIMT product, K <= 16 -- what the
- * EXP_EMU_BF16 contractions use when every block has K <= 16 (Sec. II.B step 3). */
+ * EXP_EMU_BF16 contractions use when every block has K <= 16 (Sec. II.B step 3).
+ * Each operand is carried as two FP32 numbers (48 bits); |x| < 2^-126 counts as 0 and
+ * |x| >= 2^128 as infinite; error within about K 2^-47 of sum |a||b| per element. */
 enum { EXP_FP64 = 0, EXP_EMU_BF16 = 1, EXP_EMU_DS = 2 };
 enum { EXP_GUESS_MP2 = 0, EXP_GUESS_USER = 1 };
 
@@ -88,9 +90,12 @@ typedef struct {
                               fixed point; smaller steps for strongly coupled problems); 0 = the
                               plain update t <- RHS/D.  The (0h,1p) Bloch update divides by
                               D + sigma sign(D) the same way. */
-  int packed;              /* 1: the particle-particle ladder sum_{c<d} <ab||cd> tau_ij^cd on pair-packed
-                              operands (a<b, c<d, i<j per pair irrep; <ab||cd> stored packed, a
-                              quarter of the full size); 0: full pair compounds */
+  int packed;              /* 1: the particle-particle ladder sum_{c<d} <ab||cd> tau_ij^cd and the other
+                              products over a tau pair on pair-packed operands (a<b, c<d, i<j per
+                              pair irrep; <ab||cd> stored packed, a quarter of the full size), and
+                              the update, DIIS vectors and energy on t1 plus the a<b, i<j entries of
+                              t2 (same fixed point and DIIS matrix as full vectors); 0: full pair
+                              compounds everywhere */
 } exp_config;
 
 /* Create a context: validates the config, builds the symmetry-blocked layouts

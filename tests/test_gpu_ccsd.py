@@ -190,3 +190,47 @@ def test_emulated_bits_independent_of_work_decomposition(expgb):
     for r in runs[1:]:
         for a, b in zip(runs[0], r):
             assert np.array_equal(a.view(np.float64), b.view(np.float64))
+
+
+def test_packed_context_zeroes_pair_diagonal_of_set_amplitudes(expgb):
+    """A packed context updates only the a<b, i<j entries of t2 and writes their signed
+    copies, so entries with a = b or i = j set by the caller are cleared when they are set;
+    the next iterate is then the oracle's step from the antisymmetric amplitudes."""
+    import torch
+    prob = syn.make_problem(611, 4, 12, 2)
+    b = _oracle(prob)
+    t1, t2 = syn.trial_amplitudes(prob, 5)
+    no, nv = prob.n_occ, prob.n_virt
+    bad = t2.copy()
+    for i in range(no):
+        t2[i, i] = 0.0  # the trial draw leaves rounding-level values there
+        bad[i, i] = 0.3 + 0.1j
+    for a in range(nv):
+        t2[:, :, a, a] = 0.0
+        bad[:, :, a, a] = -0.2 + 0.05j
+    ctx = expgb.from_problems([prob], diis_dim=0, packed=True)
+    ctx.init_integrals([prob.seed])
+    ctx.set_amplitudes(0, torch.from_numpy(t1), torch.from_numpy(bad))
+    g1, g2 = (x.cpu().numpy() for x in ctx.get_amplitudes(0))
+    np.testing.assert_array_equal(g2, t2)
+    np.testing.assert_array_equal(g1, t1)
+    ctx.iterate(1)
+    r1, r2 = ccsd.rhs(t1, t2, b)
+    D1, D2 = ccsd.denominators(b)
+    g1, g2 = (x.cpu().numpy() for x in ctx.get_amplitudes(0))
+    scale = np.max(np.abs(r2 / D2))
+    np.testing.assert_allclose(g2, r2 / D2, atol=1e-12 * scale, rtol=0)
+    np.testing.assert_allclose(g1, r1 / D1, atol=1e-12 * scale, rtol=0)
+
+
+def test_profile_top_selects_a_contraction_by_name(expgb):
+    prob = syn.make_problem(612, 6, 20, 4)
+    ctx = expgb.from_problems([prob], precision=expgb.EXP_EMU_BF16, n_slices=5, emu_min_macs=1e3)
+    ctx.init_integrals([prob.seed])
+    ctx.iterate(2)
+    top, ms, macs = ctx.profile_top(reps=2)
+    assert top and ms > 0 and macs > 0
+    site, ms2, macs2 = ctx.profile_top(reps=1, site="R2a")
+    assert site == "R2a" and ms2 > 0 and 0 < macs2 <= macs
+    with pytest.raises(expgb.ExpError):
+        ctx.profile_top(reps=1, site="no_such_site")

@@ -109,6 +109,22 @@ def dist_env():
     return ws, rank, local
 
 
+def aggregate_over_ranks(ms, n_it, dist=None, device="cpu"):
+    """(max over ranks of the timed milliseconds, sum over ranks of the iterations): every
+    rank times its own instance, and the job's throughput is all ranks' iterations over
+    the slowest rank's time.  `dist` is torch.distributed after init_process_group (any
+    backend; None for one process); `device` holds the reduction tensors (the GPU for
+    NCCL, the host for gloo)."""
+    if not dist:
+        return float(ms), int(n_it)
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    n = torch.tensor([float(n_it)], dtype=torch.float64, device=device)
+    dist.all_reduce(n)
+    return t.item(), int(round(n.item()))
+
+
 def cpu_baseline_leg(seconds=15.0):
     """The oracle as it stands (dense complex128 numpy/BLAS CCSD) on the host cores.
 
@@ -220,15 +236,7 @@ def main():
     launches = ctx.launches - l0
     ms = e0.elapsed_time(e1)
     n_it = len(recs)
-    t = torch.tensor([ms], dtype=torch.float64, device=f"cuda:{local}")
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot = torch.tensor([float(n_it)], dtype=torch.float64, device=f"cuda:{local}")
-        dist.all_reduce(tot)
-        n_all = tot.item()
-    else:
-        n_all = n_it
-    ms_max = t.item()
+    ms_max, n_all = aggregate_over_ranks(ms, n_it, dist, f"cuda:{local}")
     value = n_all / (ms_max / 1e3)
     macs = ctx.work_per_iteration()
     ctflops = n_all * macs * 8 / (ms_max * 1e-3) / 1e12  # complex flops credited (8 per complex MAC)

@@ -72,3 +72,26 @@ def test_null_arguments_rejected(lib):
     assert lib.exp_ccsd_iterate(None, 1, None, None) == 1
     assert lib.exp_energy(None, 0, None, None) == 1
     lib.exp_destroy(None)
+
+
+def test_zgemm_rejects_bad_arguments_on_host(lib):
+    """exp_zgemm validates shape, precision, slice count and the double-single K limit
+    before any device work (the operand pointers are never touched here)."""
+    from paper_2004_03682_gb300 import expgb
+    a = expgb.Allocator(expgb.ALLOC_FN(lambda n, u: None), expgb.FREE_FN(lambda p, u: None), None)
+    fake = C.c_void_p(256)
+
+    def call(prec, slices, M, N, K):
+        return lib.exp_zgemm(C.byref(a), None, prec, slices, M, N, K, fake, fake, fake, 1.0, 0.0, 0)
+
+    assert call(expgb.EXP_EMU_DS, 5, 4, 4, 17) == 1
+    assert b"16" in lib.exp_last_error(None)
+    assert call(7, 5, 4, 4, 4) == 1
+    assert call(expgb.EXP_EMU_BF16, 2, 4, 4, 4) == 1
+    assert call(expgb.EXP_FP64, 5, 0, 4, 4) == 1
+    assert lib.exp_zgemm(None, None, expgb.EXP_FP64, 5, 4, 4, 4, fake, fake, fake, 1.0, 0.0, 0) == 1
+
+
+def test_profile_top_rejects_null_context(lib):
+    ms, macs = C.c_double(), C.c_double()
+    assert lib.exp_profile_top(None, 1, None, 0, C.byref(ms), C.byref(macs)) == 1

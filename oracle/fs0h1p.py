@@ -9,21 +9,29 @@ sectors solved one after another, T fixed):
 
     Q Hbar (P + S) P = S H_eff,      H_eff = P Hbar (P + S) P,
 
-Hbar = e^-T (H - E_ref) e^T - E_CC on the electron-attached space
-{a+|0>, a+ b+ j|0>}; the eigenvalues of H_eff are the attachment energies of the
-states with active character.  The iteration takes the method's fixed-point form
+Hbar = e^-T H_N e^T - E_CC on the electron-attached space {a+|0>, a+ b+ j|0>};
+the eigenvalues of H_eff are the attachment energies of the states with active
+character.  The iteration takes the method's fixed-point form
 s <- s + D^-1 (Q Hbar (P+S) - S H_eff), with D_x^a = e_x - e_a and
 D_xj^ab = e_x + e_j - e_a - e_b.
 
-Hbar acting on an electron-attached vector r is evaluated as the CCSD residual
-(oracle/ccsd.residual, itself pinned by brute force) of an augmented system in
-which one extra occupied spinor g (orbital energy 0, every integral with g
-zero) carries r as its amplitudes: t_g^a = r_a, t_gj^ab = r_j^ab.  The residual
-is linear in those amplitudes and its g-projections are exactly
-(Hbar_N - E_CC) r; one ghost per active spinor gives all H_eff columns at once.
-Parity: pinned by tests/test_oracle_fs.py against the electron-attached block of
-an explicit second-quantised Hbar, full CI for one-electron vacua, and the
-containment of the H_eff eigenvalues in that block's spectrum.
+Hbar acting on an electron-attached vector r = sum_a r_a a+ + 1/2 sum_jab r_j^ab a+ b+ j
+is written out term by term as the EA-EOM-CCSD sigma equations (Nooijen and
+Bartlett, J. Chem. Phys. 102, 3629 (1995)); FS-CCSD in the (0h,1p) sector and
+EA-EOM-CCSD share that operator.  The one- and two-body elements of Hbar it needs
+(F_ae, F_me, F_mi, W_amef, W_mbej, W_abef, W_abej), with every T1 and T2
+contribution, plus the one three-body piece (<mn||ef> t_mj^ab contracted with
+r_n^ef):
+
+    sigma_a     = F_ae r_e + F_me r_m^ae + 1/2 W_amef r_m^ef
+    sigma_j^ab  = W_abej r_e + P(ab) F_be r_j^ae - F_mj r_m^ab + P(ab) W_mbej r_m^ae
+                  + 1/2 W_abef r_j^ef - 1/2 t_mj^ab <mn||ef> r_n^ef
+
+(sums over repeated indices, P(ab) X = X - X(a<->b)).  Parity: pinned by
+tests/test_oracle_fs.py against the electron-attached block of an explicit
+second-quantised Hbar (brute force on a determinant basis, C1 and Z4 cases), full
+CI for one-electron vacua, and the containment of the H_eff eigenvalues in that
+block's spectrum.
 """
 from __future__ import annotations
 
@@ -32,34 +40,51 @@ import numpy as np
 from oracle import ccsd
 
 
-def augment(V, f, o, n_ghost):
-    """Insert n_ghost non-interacting occupied spinors after the real occupied ones."""
-    n = V.shape[0]
-    keep = np.r_[0:o, o + n_ghost:n + n_ghost]
-    Va = np.zeros((n + n_ghost,) * 4, dtype=np.complex128)
-    Va[np.ix_(keep, keep, keep, keep)] = V
-    fa = np.zeros((n + n_ghost,) * 2, dtype=np.complex128)
-    fa[np.ix_(keep, keep)] = f
-    return Va, fa
+def es(spec, *ops):
+    return np.einsum(spec, *ops, optimize=True)
 
 
-def hbar_ea(b_aug: ccsd.Blocks, t1, t2, o, r1, r2):
-    """(Hbar_N - E_CC) applied to electron-attached vectors r1[k, a], r2[k, j, a, b]
-    (k = ghost slot).  t1, t2: converged (0h,0p) amplitudes of the real system."""
-    ng, nv = r1.shape
-    oa = o + ng
-    T1 = np.zeros((oa, nv), dtype=np.complex128)
-    T2 = np.zeros((oa, oa, nv, nv), dtype=np.complex128)
-    T1[:o] = t1
-    T2[:o, :o] = t2
-    for k in range(ng):
-        T1[o + k] = r1[k]
-        T2[o + k, :o] = r2[k]
-        T2[:o, o + k] = -r2[k]
-    R1, R2 = ccsd.residual(T1, T2, b_aug)
-    s1 = np.stack([R1[o + k] for k in range(ng)])
-    s2 = np.stack([R2[o + k, :o] for k in range(ng)])
-    return s1, s2
+class HbarEA:
+    """The elements of Hbar that act on the electron-attached space, at amplitudes t1, t2."""
+
+    def __init__(self, b: ccsd.Blocks, t1, t2):
+        v = b.v
+        fov, foo, fvv = b.fb("ov"), b.fb("oo"), b.fb("vv")
+        tau = ccsd.tau(t1, t2)
+        self.t2 = t2
+        self.oovv = v("oovv")
+        # one-body elements
+        self.Fme = fov + es("nf,mnef->me", t1, v("oovv"))
+        self.Fmi = (foo + es("ie,me->mi", t1, self.Fme) + es("ne,mnie->mi", t1, v("ooov"))
+                    + 0.5 * es("inef,mnef->mi", t2, v("oovv")))
+        self.Fae = (fvv - es("ma,me->ae", t1, self.Fme) + es("mf,amef->ae", t1, v("vovv"))
+                    - 0.5 * es("mnaf,mnef->ae", t2, v("oovv")))
+        # two-body elements
+        self.Wamef = v("vovv") - es("na,nmef->amef", t1, v("oovv"))
+        self.Wmbej = (v("ovvo") + es("jf,mbef->mbej", t1, v("ovvv")) - es("nb,mnej->mbej", t1, v("oovo"))
+                      - es("jnfb,mnef->mbej", t2 + es("jf,nb->jnfb", t1, t1), v("oovv")))
+        P01 = lambda x: x - x.swapaxes(0, 1)
+        self.Wabef = (v("vvvv") - P01(es("mb,amef->abef", t1, v("vovv")))
+                      + 0.5 * es("mnab,mnef->abef", tau, v("oovv")))
+        # W_abej = <ab||ej> - F_me t_mj^ab + t_j^f W_abef + 1/2 <mn||ej> tau_mn^ab
+        #          - P(ab) <mb||ef> t_mj^af - P(ab) t_m^a (<mb||ej> - t_nj^bf <mn||ef>)
+        x = es("mbef,mjaf->abej", v("ovvv"), t2)
+        y = es("ma,mbej->abej", t1, v("ovvo") - es("njbf,mnef->mbej", t2, v("oovv")))
+        self.Wabej = (v("vvvo") - es("me,mjab->abej", self.Fme, t2) + es("jf,abef->abej", t1, self.Wabef)
+                      + 0.5 * es("mnej,mnab->abej", v("oovo"), tau)
+                      - P01(x) - P01(y))
+
+    def sigma(self, r1, r2):
+        """(Hbar_N - E_CC) on vectors r1[k, a], r2[k, j, a, b] (r2 antisymmetric in a, b)."""
+        s1 = (es("ae,ke->ka", self.Fae, r1) + es("me,kmae->ka", self.Fme, r2)
+              + 0.5 * es("amef,kmef->ka", self.Wamef, r2))
+        x = es("be,kjae->kjab", self.Fae, r2) + es("mbej,kmae->kjab", self.Wmbej, r2)
+        chi = es("mnef,knef->km", self.oovv, r2)
+        s2 = (es("abej,ke->kjab", self.Wabej, r1) + (x - x.swapaxes(2, 3))
+              - es("mj,kmab->kjab", self.Fmi, r2)
+              + 0.5 * es("abef,kjef->kjab", self.Wabef, r2)
+              - 0.5 * es("km,mjab->kjab", chi, self.t2))
+        return s1, s2
 
 
 def solve(V, f, o, t1, t2, act, tol=1e-10, max_iter=300, diis_dim=6):
@@ -71,8 +96,8 @@ def solve(V, f, o, t1, t2, act, tol=1e-10, max_iter=300, diis_dim=6):
     nv = t1.shape[1]
     na = len(act)
     act = np.asarray(act)
-    Va, fa = augment(V, f, o, na)
-    b_aug = ccsd.Blocks(Va, fa, o + na)
+    b = ccsd.Blocks(V, f, o)
+    H = HbarEA(b, t1, t2)
     eps = np.real(np.diag(f))
     eo, ev = eps[:o], eps[o:]
     ex = ev[act]
@@ -90,7 +115,7 @@ def solve(V, f, o, t1, t2, act, tol=1e-10, max_iter=300, diis_dim=6):
     for it in range(1, max_iter + 1):
         r1 = s1.copy()
         r1[np.arange(na), act] = 1.0           # P + S
-        sig1, sig2 = hbar_ea(b_aug, t1, t2, o, r1, s2)
+        sig1, sig2 = H.sigma(r1, s2)
         Heff = sig1[:, act].T                  # Heff[y, x] = (Hbar (P+S))_x at active y
         rho1 = sig1 - np.einsum("ya,yx->xa", s1, Heff)
         rho2 = sig2 - np.einsum("yjab,yx->xjab", s2, Heff)

@@ -200,6 +200,18 @@ exp_status exp_profile_top(exp_ctx* ctx, int reps, char* name, int name_len, dou
 exp_status exp_zgemm(const exp_allocator* alloc, void* stream, int precision, int n_slices, int M, int N, int K,
                      const void* A, const void* B, void* C, double alpha_re, double alpha_im, int beta);
 
+/* Test hook of the bounded device waits (no counterpart in the paper; for tests of
+ * the timeout path only).  Every wait inside the emulated tensor-core GEMM gives up
+ * after a limit (2 s) and sets an error flag that the host reads (EXP_ETIMEOUT); the
+ * kernel then waits, with the same limit, for its own copies in flight, releases its
+ * tensor memory and returns, so the context stays usable.  exp_test_emu_wait sets that
+ * limit to wait_ms (0 < wait_ms <= 2000) and, with skip_kblock >= 0, makes CTA 0 of
+ * every later GEMM launch leave the slice copies of its k-block number skip_kblock
+ * unissued, so the wait on that stage runs out with nothing in flight for it.
+ * exp_test_emu_wait(-1, 2000) restores the normal behaviour.  Process-wide, for the
+ * launches that follow on any thread.  EINVAL on arguments out of range. */
+exp_status exp_test_emu_wait(int skip_kblock, double wait_ms);
+
 /* Allocation-free complex GEMM (no counterpart in the paper: a library service).
  *
  * For callers that cannot allocate device memory when they need the product -
@@ -214,13 +226,17 @@ exp_status exp_zgemm(const exp_allocator* alloc, void* stream, int precision, in
  * EXP_NOALLOC_SCRATCH_BYTES, which every GPU that loads the library holds until
  * the process exits.  A problem whose scratch need exceeds it is rejected with
  * EXP_EINVAL before anything is launched (square problems fit up to about
- * M = N = K = 600 with n_slices = 5 or 6).
- * The first call on a device looks the array's address up (with that device
- * current); make it before any stream capture.  Every call shares the array and
- * re-initialises what must start at a known value; calls whose GPU work can
+ * M = N = K = 600 with n_slices = 5 or 6; K above 2^26 is refused before any size
+ * is derived from it).
+ * The first call on a device (and again after a new context replaces the device's
+ * old one, e.g. after cudaDeviceReset) looks the array's address up with that
+ * device current; make it before any stream capture.  Every call shares the array
+ * and re-initialises what must start at a known value; calls whose GPU work can
  * overlap (different streams without ordering) race on it.  Synchronises
- * `stream`.  Errors: EINVAL, ECUDA, ETIMEOUT; message in
- * exp_noalloc_last_error(). */
+ * `stream`.  Errors: EINVAL, ECUDA (also when a CUDA error was already pending on
+ * the calling thread; nothing is launched then), ETIMEOUT; message in
+ * exp_noalloc_last_error().  On ECUDA or ETIMEOUT the contents of C are
+ * unspecified. */
 #define EXP_NOALLOC_SCRATCH_BYTES (48u << 20)
 exp_status exp_zgemm_emu_noalloc(void* stream, int n_slices, int M, int N, int K, const void* A, const void* B,
                                  void* C, double alpha_re, double alpha_im, int beta);

@@ -461,6 +461,7 @@ extern "C" exp_status exp_zgemm(const exp_allocator* alloc, void* stream, int pr
     throw ExpError{EXP_EINVAL, "bad precision"};
   if (precision == EXP_EMU_BF16 && (n_slices < 3 || n_slices > 6)) throw ExpError{EXP_EINVAL, "n_slices must be in 3..6"};
   if (precision == EXP_EMU_DS && K > 16) throw ExpError{EXP_EINVAL, "double-single product: K above 16"};
+  if (precision == EXP_EMU_BF16 && K > EMU_MAX_K) throw ExpError{EXP_EINVAL, "emulated GEMM: K above 2^26"};
   c.alloc = *alloc;
   c.stream = (cudaStream_t)stream;
   c.cfg.precision = precision == EXP_EMU_DS ? EXP_EMU_BF16 : precision;

@@ -3,6 +3,9 @@
 #pragma once
 #include "engine.h"
 
+// largest K of an emulated product (K' = 2K padded and every slice offset stay in range)
+#define EMU_MAX_K (1 << 26)
+
 bool emu_wanted(Ctx& c, const GemmPlan& g, const std::string& site);
 // b_shareable: B is a lasting tensor, so a later product reading the same tensor in
 // the same layout may reuse this plan's B slices

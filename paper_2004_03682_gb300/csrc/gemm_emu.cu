@@ -21,11 +21,14 @@
 // canonical no-swizzle K-major UMMA layout), warp 1 issues tcgen05.mma (one
 // MMA per A slice s covers all diagonals s+1..S+1 by stacking the B slices
 // along N), warps 2-5 drain the double-buffered TMEM accumulators.
+#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
+#include <mutex>
 #include <string>
 
 #include "emu.h"
@@ -79,6 +82,14 @@ struct EmuProb {
   int64_t red0;      // first output of this problem in the split-K reduction order
 };
 
+// Limit of every bounded wait inside k_emu_gemm, and the timeout test hook (see
+// exp_test_emu_wait in the header): normally 2 s and off.
+struct EmuWaitTest {
+  unsigned long long wait_ns;
+  int skip_kblock;
+  int pad_;
+};
+
 // ---------------------------------------------------------------------------
 // PTX helpers
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -107,16 +118,17 @@ __device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait: gives up after ~2 s (or when another role already gave up),
-// recording the failure; never spins forever.
-__device__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort, int* gerr) {
+// Bounded wait: gives up after wait_ns (2 s unless a test shortens it) or when
+// another role already gave up, recording the failure; never spins forever.
+__device__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort, int* gerr,
+                          unsigned long long wait_ns) {
   if (mbar_try(b, parity)) return true;
   const uint64_t t0 = gtimer();
   for (uint32_t it = 1;; ++it) {
     if (mbar_try(b, parity)) return true;
     if ((it & 255) == 0) {
       if (*abort) return false;
-      if (gtimer() - t0 > 2000000000ull) {
+      if (gtimer() - t0 > wait_ns) {
         *abort = 1;
         atomicExch(gerr, 1);
         return false;
@@ -233,9 +245,13 @@ __global__ void __launch_bounds__(THREADS, 1)
                const __nv_bfloat16* __restrict__ Asl, const __nv_bfloat16* __restrict__ Bsl,
                const int* __restrict__ Aex, const int* __restrict__ Bex, cplx* __restrict__ C, int64_t asl_is,
                int64_t bsl_is, int64_t aex_is, int64_t bex_is, int64_t c_is, cplx alpha, int alpha_e, int beta,
-               int* __restrict__ gerr, cplx* __restrict__ ws, int64_t ws_is) {
+               int* __restrict__ gerr, cplx* __restrict__ ws, int64_t ws_is, EmuWaitTest wt) {
   using SH = Shape<S>;
   constexpr int STAGES = SH::STAGES;
+  const unsigned long long wns = wt.wait_ns;
+  // test hook (-1 = off): CTA 0 never issues the copies of its k-block skip_g, so the
+  // MMA issuer's wait on that stage runs out; nothing is in flight for that stage
+  const int skip_g = blockIdx.x == 0 ? wt.skip_kblock : -1;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)((uintptr_t(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* full = (uint64_t*)(smem + STAGES * SH::STAGE);
@@ -287,7 +303,8 @@ __global__ void __launch_bounds__(THREADS, 1)
         const __nv_bfloat16* Bb = Bsl + W.inst * bsl_is + P.b_sl + (int64_t(W.nt) * W.nkb_all + W.kb0) * (S * bt);
         for (int kb = 0; kb < W.nkb; ++kb, ++g) {
           const int st = g % STAGES;
-          if (g >= STAGES && !mbar_wait(&empty[st], ((g / STAGES) & 1) ^ 1, abort, gerr)) { stop = true; break; }
+          if (g >= STAGES && !mbar_wait(&empty[st], ((g / STAGES) & 1) ^ 1, abort, gerr, wns)) { stop = true; break; }
+          if (int(g) == skip_g) continue;
           uint8_t* sA = smem + st * SH::STAGE;
           uint8_t* sB = sA + SH::A_STAGE;
           mbar_expect_tx(&full[st], uint32_t(S * (at + bt) * 2));
@@ -310,8 +327,9 @@ __global__ void __launch_bounds__(THREADS, 1)
       if (*abort) {
         // let the copies already issued land before the CTA exits
         for (uint32_t k = g > STAGES ? g - STAGES : 0; k < g; ++k) {
+          if (int(k) == skip_g) continue;  // never issued
           volatile int dummy = 0;
-          mbar_wait(&full[k % STAGES], (k / STAGES) & 1, &dummy, gerr);
+          mbar_wait(&full[k % STAGES], (k / STAGES) & 1, &dummy, gerr, wns);
         }
       }
     }
@@ -327,10 +345,10 @@ __global__ void __launch_bounds__(THREADS, 1)
           const bool first = (kb % KC_BLOCKS) == 0;
           const int buf = gc & 1;
           if (first && gc >= 2) {
-            if (!mbar_wait(&acce[buf], ((gc >> 1) - 1) & 1, abort, gerr)) { stop = true; break; }
+            if (!mbar_wait(&acce[buf], ((gc >> 1) - 1) & 1, abort, gerr, wns)) { stop = true; break; }
             fence_after();
           }
-          if (!mbar_wait(&full[st], (g / STAGES) & 1, abort, gerr)) { stop = true; break; }
+          if (!mbar_wait(&full[st], (g / STAGES) & 1, abort, gerr, wns)) { stop = true; break; }
           fence_after();
           const uint32_t aA = su32(smem + st * SH::STAGE);
           const uint32_t aB = aA + SH::A_STAGE;
@@ -385,7 +403,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         fj[jj] = (gi < P.M && j0 + jj < P.N) ? Bex[W.inst * bex_is + P.b_ex + j0 + jj] : 0;
       for (int ch = 0; ch < nchunks; ++ch, ++gc) {
         const int buf = gc & 1;
-        if (!mbar_wait(&accf[buf], (gc >> 1) & 1, abort, gerr)) { ok = false; break; }
+        if (!mbar_wait(&accf[buf], (gc >> 1) & 1, abort, gerr, wns)) { ok = false; break; }
         fence_after();
 #pragma unroll
         for (int dgi = 0; dgi < S; ++dgi) {
@@ -444,7 +462,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     // wait (bounded) for MMAs still in flight before TMEM is released
     mma_commit(drain);
     volatile int dummy = 0;
-    mbar_wait(drain, 0, &dummy, gerr);
+    mbar_wait(drain, 0, &dummy, gerr, wns);
   }
   __syncthreads();
   if (warp == 0) {
@@ -792,6 +810,8 @@ static void launch_emu_reduce(const EmuProb* d, int np, int max_ksplit, const cp
 }  // namespace
 
 // ---------------------------------------------------------------------------
+// K' = 2K with each half padded to 16; callers keep K <= EMU_MAX_K, so this stays far
+// inside int (the slice and split-K offsets derived from it are int64)
 static int kp_of(int K) { return 2 * ((std::max(K, 1) + 15) / 16) * 16; }
 
 // grid of a warp-per-item kernel (8 warps per CTA) and of a thread-per-unit kernel
@@ -954,6 +974,7 @@ EmuPlan* emu_plan(Ctx& c, const GemmPlan& g, const Tensor* A, const Tensor* B, b
     e.M = q.M;
     e.N = q.N;
     e.K = q.K;
+    if (q.K > EMU_MAX_K) throw ExpError{EXP_EINVAL, "emulated GEMM: K above 2^26"};
     e.Kp = kp_of(q.K);  // [Re | Im], each half padded to 16
     e.tiles_m = (q.M + BM - 1) / BM;
     e.tiles_n = (q.N + BN / 2 - 1) / (BN / 2);
@@ -1066,6 +1087,19 @@ struct EmuStageTimer {
   }
 };
 
+// Timeout test hook (exp_test_emu_wait): the wait limit and the k-block that CTA 0
+// skips, for the launches that follow on any thread until it is reset.
+static std::atomic<unsigned long long> g_wait_ns{2000000000ull};
+static std::atomic<int> g_skip_kblock{-1};
+static EmuWaitTest emu_wait_test() { return EmuWaitTest{g_wait_ns.load(), g_skip_kblock.load(), 0}; }
+
+extern "C" exp_status exp_test_emu_wait(int skip_kblock, double wait_ms) {
+  if (skip_kblock < -1 || !(wait_ms > 0.0) || wait_ms > 2000.0) return EXP_EINVAL;
+  g_wait_ns.store((unsigned long long)(wait_ms * 1e6));
+  g_skip_kblock.store(skip_kblock);
+  return EXP_OK;
+}
+
 // The GEMM launch of a plan (plus its split-K reduction) into C.
 template <int S>
 static void launch_product(Ctx& c, EmuPlan* p, cplx* C, int64_t cis, cplx alpha, bool beta, bool reduce) {
@@ -1074,7 +1108,8 @@ static void launch_product(Ctx& c, EmuPlan* p, cplx* C, int64_t cis, cplx alpha,
   const int n_work = p->n_tiles * c.ninst;
   k_emu_gemm<S><<<dim3(std::min(n_work, std::max(c.sm_count, 1))), THREADS, Shape<S>::SMEM, c.stream>>>(
       p->d, np, p->n_tiles, n_work, p->gm, p->asl, p->bsl, p->aex, p->bex, C, p->asl_is, p->bsl_is, p->aex_is,
-      p->bex_is, cis, alpha, p->red_elems ? ALPHA_GENERAL : alpha_code(alpha), beta ? 1 : 0, p->d_err, p->d_ws, p->ws_is);
+      p->bex_is, cis, alpha, p->red_elems ? ALPHA_GENERAL : alpha_code(alpha), beta ? 1 : 0, p->d_err, p->d_ws, p->ws_is,
+      emu_wait_test());
   KCHECK(c);
   if (reduce && p->red_elems) {
     int mks = 1;
@@ -1235,10 +1270,11 @@ void emu_release(Ctx& c) {
 //
 // The array is a file-scope __device__ variable: every GPU that loads this
 // library holds EXP_NOALLOC_SCRATCH_BYTES of it until the process exits.  Its
-// device address is looked up once per device (cudaGetSymbolAddress, with that
-// device current) on the first call on that device; make that first call
-// before any stream capture.  All calls share the one array: the parts that
-// must start at a known value (exponents, the error flag) are re-initialised
+// device address is looked up on the first call on a device (cudaGetSymbolAddress,
+// with that device current) and kept for that device's current context; a new
+// context on the device (after cudaDeviceReset) gets a fresh lookup.  Make that
+// first call before any stream capture.  All calls share the one array: the parts
+// that must start at a known value (exponents, the error flag) are re-initialised
 // on the stream by every call, and two calls whose work overlaps on the GPU
 // (different streams, no ordering between them) race on it.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[EXP_NOALLOC_SCRATCH_BYTES];
@@ -1246,9 +1282,30 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[EXP_NOALLOC_SCR
 namespace {
 struct NoallocDev {
   unsigned char* base = nullptr;
+  unsigned long long ctx_id = 0;  // unique id of the context the address belongs to
   bool ready = false;
 };
 NoallocDev g_noalloc_dev[64];
+std::mutex g_noalloc_mu;  // guards g_noalloc_dev (first calls from several host threads)
+
+// cuCtxGetId through the runtime's driver entry-point query (no link against the
+// driver library): the id of the current context, unique for the process's life
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+CtxGetIdFn ctx_get_id() {
+  static CtxGetIdFn fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    return (CtxGetIdFn)f;
+  }();
+  return fn;
+}
+bool current_ctx_id(unsigned long long& id) {
+  const CtxGetIdFn f = ctx_get_id();
+  return f && f(nullptr, &id) == CUDA_SUCCESS;
+}
 
 int64_t carve(int64_t& off, int64_t bytes) {
   const int64_t at = (off + 255) & ~int64_t(255);
@@ -1314,16 +1371,30 @@ exp_status noalloc_launch(cudaStream_t st, unsigned char* base, int M, int N, in
     err = "exp_zgemm_emu_noalloc: copy to scratch failed";
     return EXP_ECUDA;
   }
+  // every launch is checked before the next one is issued: on a failed launch
+  // nothing after it runs (C is then unspecified, see the header)
+  auto launched = [&](const char* what) {
+    const cudaError_t le = cudaGetLastError();
+    if (le == cudaSuccess) return true;
+    err = std::string("exp_zgemm_emu_noalloc: launch of ") + what + " failed: " + cudaGetErrorString(le);
+    return false;
+  };
   const int64_t n_rowexp = int64_t(M) * std::max((K + ROW_KR - 1) / ROW_KR, 1);
   const int64_t n_colexp = int64_t((N + 31) / 32) * std::max((K + 255) / 256, 1);
   k_fill_int<<<std::max(1, std::min((M + 255) / 256, 1024)), 256, 0, st>>>(aex, M, EXP_ZERO);
+  if (!launched("k_fill_int")) return EXP_ECUDA;
   k_fill_int<<<std::max(1, std::min((N + 255) / 256, 1024)), 256, 0, st>>>(bex, N, EXP_ZERO);
+  if (!launched("k_fill_int")) return EXP_ECUDA;
   k_row_exp<<<dim3(row_exp_blocks(n_rowexp, sms), 1), 256, 0, st>>>(d_probs, 1, A, 0, aex, 0, n_rowexp);
+  if (!launched("k_row_exp")) return EXP_ECUDA;
   k_col_exp<<<dim3(unsigned(n_colexp), 1), 256, 0, st>>>(d_probs, 1, B, 0, bex, 0);
+  if (!launched("k_col_exp")) return EXP_ECUDA;
   const int64_t na = int64_t(e.tiles_m) * nkh_of(e) * e.arows * gpr_of(e);
   const int64_t nb = int64_t(e.tiles_n) * nkh_of(e) * (e.brows / 2) * (KB / 8);
   k_split_a<S, false><<<dim3(split_blocks(na, sms), 1), 256, 0, st>>>(d_probs, 1, na, A, 0, aex, 0, asl, 0);
+  if (!launched("k_split_a")) return EXP_ECUDA;
   k_split_b<S><<<dim3(split_blocks(nb, sms), 1), 256, 0, st>>>(d_probs, 1, nb, B, 0, bex, 0, bsl, 0);
+  if (!launched("k_split_b")) return EXP_ECUDA;
   if (cudaFuncSetAttribute(k_emu_gemm<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, SH::SMEM) != cudaSuccess) {
     err = "exp_zgemm_emu_noalloc: shared-memory attribute refused";
     return EXP_ECUDA;
@@ -1331,12 +1402,13 @@ exp_status noalloc_launch(cudaStream_t st, unsigned char* base, int M, int N, in
   const int n_work = int(tiles_mn * e.ksplit);
   k_emu_gemm<S><<<dim3(unsigned(std::min(n_work, sms)), 1), THREADS, SH::SMEM, st>>>(
       d_probs, 1, n_work, n_work, EMU_GM, asl, bsl, aex, bex, Cout, 0, 0, 0, 0, 0, alpha,
-      e.ksplit > 1 ? ALPHA_GENERAL : alpha_code(alpha), beta, d_err, ws, 0);
+      e.ksplit > 1 ? ALPHA_GENERAL : alpha_code(alpha), beta, d_err, ws, 0, EmuWaitTest{2000000000ull, -1, 0});
+  if (!launched("k_emu_gemm")) return EXP_ECUDA;
   if (e.ksplit > 1) {
     launch_emu_reduce(d_probs, 1, e.ksplit, ws, 0, Cout, 0, aex, 0, bex, 0, S, alpha, beta, int64_t(M) * N, 1, sms, st);
+    if (!launched("the split-K reduction")) return EXP_ECUDA;
   }
-  cudaError_t ce = cudaGetLastError();
-  if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+  const cudaError_t ce = cudaStreamSynchronize(st);
   if (ce != cudaSuccess) {
     err = std::string("exp_zgemm_emu_noalloc: ") + cudaGetErrorString(ce);
     return EXP_ECUDA;
@@ -1365,23 +1437,48 @@ extern "C" exp_status exp_zgemm_emu_noalloc(void* stream, int n_slices, int M, i
     g_noalloc_err = "exp_zgemm_emu_noalloc: null pointer, M, N, K < 1 or n_slices outside 3..6";
     return EXP_EINVAL;
   }
+  // before any layout arithmetic: K' = 2K padded must stay far inside int (a larger K
+  // could not fit the scratch array anyway)
+  if (K > EMU_MAX_K) {
+    g_noalloc_err = "exp_zgemm_emu_noalloc: K above 2^26 (the scratch array cannot hold its slices)";
+    return EXP_EINVAL;
+  }
+  {
+    // an error left pending by earlier work of the caller is reported as such, not
+    // as a failure of this call's launches
+    const cudaError_t pe = cudaPeekAtLastError();
+    if (pe != cudaSuccess) {
+      g_noalloc_err = std::string("exp_zgemm_emu_noalloc: a CUDA error was pending before the call: ") +
+                      cudaGetErrorString(pe);
+      return EXP_ECUDA;
+    }
+  }
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
     g_noalloc_err = "exp_zgemm_emu_noalloc: no current CUDA device";
     return EXP_ECUDA;
   }
-  NoallocDev& nd = g_noalloc_dev[dev];
-  if (!nd.ready) {
-    // one-time set-up on this device: the host-side name of the array is not a
-    // device address; ask the runtime for the real one
-    void* p = nullptr;
-    const cudaError_t ce = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (ce != cudaSuccess || !p) {
-      g_noalloc_err = std::string("exp_zgemm_emu_noalloc: cudaGetSymbolAddress failed: ") + cudaGetErrorString(ce);
-      return EXP_ECUDA;
+  unsigned char* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    NoallocDev& nd = g_noalloc_dev[dev];
+    unsigned long long id = 0;
+    const bool have_id = current_ctx_id(id);
+    if (!nd.ready || !have_id || nd.ctx_id != id) {
+      // set-up on this device (and context): the host-side name of the array is not
+      // a device address; ask the runtime for the real one
+      void* p = nullptr;
+      const cudaError_t ce = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      if (ce != cudaSuccess || !p) {
+        nd.ready = false;
+        g_noalloc_err = std::string("exp_zgemm_emu_noalloc: cudaGetSymbolAddress failed: ") + cudaGetErrorString(ce);
+        return EXP_ECUDA;
+      }
+      nd.base = (unsigned char*)p;
+      // the lookup made the device's context current if it was not: key the address by it
+      nd.ready = current_ctx_id(nd.ctx_id);
     }
-    nd.base = (unsigned char*)p;
-    nd.ready = true;
+    base = nd.base;
   }
   int sms = 1;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1391,9 +1488,9 @@ extern "C" exp_status exp_zgemm_emu_noalloc(void* stream, int n_slices, int M, i
   const cplx* b = (const cplx*)B;
   cplx* c = (cplx*)C;
   switch (n_slices) {
-    case 3: return noalloc_launch<3>(st, nd.base, M, N, K, a, b, c, alpha, beta != 0, sms, g_noalloc_err);
-    case 4: return noalloc_launch<4>(st, nd.base, M, N, K, a, b, c, alpha, beta != 0, sms, g_noalloc_err);
-    case 5: return noalloc_launch<5>(st, nd.base, M, N, K, a, b, c, alpha, beta != 0, sms, g_noalloc_err);
-    default: return noalloc_launch<6>(st, nd.base, M, N, K, a, b, c, alpha, beta != 0, sms, g_noalloc_err);
+    case 3: return noalloc_launch<3>(st, base, M, N, K, a, b, c, alpha, beta != 0, sms, g_noalloc_err);
+    case 4: return noalloc_launch<4>(st, base, M, N, K, a, b, c, alpha, beta != 0, sms, g_noalloc_err);
+    case 5: return noalloc_launch<5>(st, base, M, N, K, a, b, c, alpha, beta != 0, sms, g_noalloc_err);
+    default: return noalloc_launch<6>(st, base, M, N, K, a, b, c, alpha, beta != 0, sms, g_noalloc_err);
   }
 }

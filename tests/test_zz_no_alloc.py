@@ -45,11 +45,19 @@ def _noalloc(torch, L, A, B, C0, alpha, beta, S):
     return out
 
 
-@pytest.mark.parametrize("S", [4, 5])
-def test_noalloc_matches_allocating_gemm_twice(env, S):
+# the second shape is split over K; the reversed order runs a larger split-K problem
+# first, so stale partials or exponents it leaves in the shared array would show up
+# in the smaller split-K problem after it
+ORDERS = {"small_then_split": [(200, 37, 333), (81, 14, 8000)],
+          "split_then_smaller_split": [(96, 20, 9000), (40, 9, 4100)]}
+
+
+@pytest.mark.parametrize("order", sorted(ORDERS))
+@pytest.mark.parametrize("S", [3, 4, 5, 6])
+def test_noalloc_matches_allocating_gemm_twice(env, S, order):
     torch, expgb, L = env
     rng = np.random.default_rng(S)
-    shapes = [(200, 37, 333), (81, 14, 8000)]  # the second one is split over K
+    shapes = ORDERS[order]
     for M, N, K in shapes:  # two calls in a row on the shared scratch
         A = torch.tensor(_rand(rng, (M, K)), device="cuda")
         B = torch.tensor(_rand(rng, (K, N)), device="cuda")
@@ -72,3 +80,15 @@ def test_noalloc_refuses_oversized_problem(env):
                                  1.0, 0.0, 0)
     assert st == 1
     assert b"scratch" in L.exp_noalloc_last_error()
+
+
+def test_noalloc_refuses_huge_k_before_layout_arithmetic(env):
+    # K near 2^30 would overflow the padded K' = 2K in int; it is refused on the host
+    # before any size is derived from it (nothing is launched, no pointer is read)
+    torch, expgb, L = env
+    A = torch.zeros((1, 1), dtype=torch.complex128, device="cuda")
+    st = L.exp_zgemm_emu_noalloc(C.c_void_p(torch.cuda.current_stream().cuda_stream), 5, 1, 1, (1 << 30) - 8,
+                                 C.c_void_p(A.data_ptr()), C.c_void_p(A.data_ptr()), C.c_void_p(A.data_ptr()),
+                                 1.0, 0.0, 0)
+    assert st == 1
+    assert b"2^26" in L.exp_noalloc_last_error()

@@ -107,6 +107,8 @@ def lib():
     for name in ("exp_mlp_create", "exp_mlp_add_training_data", "exp_mlp_train", "exp_mlp_apply",
                  "exp_mlp_params", "exp_mlp_loss_grad"):
         getattr(L, name).restype = C.c_int
+    L.exp_test_emu_wait.argtypes = [C.c_int, C.c_double]
+    L.exp_test_emu_wait.restype = C.c_int
     L.exp_kernel_launches.argtypes = [P]
     L.exp_kernel_launches.restype = C.c_int64
     L.exp_last_error.argtypes = [P]
@@ -157,7 +159,7 @@ class Context:
     def __init__(self, n_occ, n_virt, irrep_occ, irrep_virt, eps_occ, eps_virt, n_inst=1,
                  precision=EXP_FP64, n_slices=5, diis_dim=6, conv_tol=1e-9, max_iter=500,
                  guess=EXP_GUESS_MP2, device=0, emu_min_macs=0.0, active=None, level_shift=0.0,
-                 packed=True):
+                 packed=True, allocator=None):
         import torch
         self._torch = torch
         L = lib()
@@ -166,7 +168,8 @@ class Context:
         self.n_occ, self.n_virt, self.n_inst = int(n_occ), int(n_virt), int(n_inst)
         torch.cuda.set_device(device)
         self.stream = torch.cuda.Stream(device=device)
-        self.alloc = TorchAllocator(device, self.stream)
+        # allocator: a factory (device, stream) -> object with a .struct exp_allocator
+        self.alloc = (allocator or TorchAllocator)(device, self.stream)
         self._keep = []
         io, pio = _arr(irrep_occ, C.c_int32, np.int32)
         iv, piv = _arr(irrep_virt, C.c_int32, np.int32)

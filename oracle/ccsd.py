@@ -252,15 +252,17 @@ class IterRecord:
 
 
 def solve(b: Blocks, tol: float = 1e-9, max_iter: int = 200, diis_dim: int = 6,
-          t_init=None, history: bool = False):
+          t_init=None, history: bool = False, D=None):
     """CCSD fixed point from the MP2 (or a given) guess with DIIS.
 
     Iteration 0 reports E(t_guess) (= E_MP2 for the MP2 guess).  Each iteration
     k >= 1 computes t_new = RHS(t)/D, residual max|t_new - t| and E(t_new);
     it stops when the residual is below `tol`, else extrapolates with DIIS.
+    D: (D1, D2) in place of the denominators of b (the shifted equations of
+    oracle/intruder.py); None = the plain ones.
     Returns (t1, t2, E, n_iter, converged, records).
     """
-    D1, D2 = denominators(b)
+    D1, D2 = denominators(b) if D is None else D
     no, nv = D1.shape
     t1, t2 = mp2_guess(b) if t_init is None else (t_init[0].copy(), t_init[1].copy())
     recs = [IterRecord(0, energy(t1, t2, b), float("nan"), 0)]

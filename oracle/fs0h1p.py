@@ -87,11 +87,13 @@ class HbarEA:
         return s1, s2
 
 
-def solve(V, f, o, t1, t2, act, tol=1e-10, max_iter=300, diis_dim=6):
+def solve(V, f, o, t1, t2, act, tol=1e-10, max_iter=300, diis_dim=6, shift=None):
     """(0h,1p) FS-CCSD.  act: virtual (local) indices of the active spinors.
     Each iteration: Jacobi step s_new = s + rho/D, error s_new - s, residual
     max |s_new - s|; DIIS(diis_dim) over (s_new, error) as in oracle/ccsd (the
     paper is silent on acceleration; plain Jacobi diverges on these Hamiltonians).
+    shift = (s, n): the intruder-state shifted equations of oracle/intruder.py,
+    rho + (D - D~) s = 0 stepped with 1/D~ (D~ = D - s (s/(s+|D|))^n); None = unshifted.
     Returns (Heff, eigenvalues sorted by real part, s1, s2, n_iter, converged)."""
     nv = t1.shape[1]
     na = len(act)
@@ -107,6 +109,12 @@ def solve(V, f, o, t1, t2, act, tol=1e-10, max_iter=300, diis_dim=6):
     D1[:, act] = 1.0  # P-space entries are not updated
     D2 = (ex[:, None, None, None] + eo[None, :, None, None]
           - ev[None, None, :, None] - ev[None, None, None, :])
+    if shift is not None and shift[0] > 0.0:
+        sh, nn = float(shift[0]), int(shift[1])
+        D1s = D1 - sh * (sh / (sh + np.abs(D1))) ** nn
+        D2s = D2 - sh * (sh / (sh + np.abs(D2))) ** nn
+    else:
+        D1s, D2s = D1, D2
     s1 = np.zeros((na, nv), dtype=np.complex128)
     s2 = np.zeros((na, o, nv, nv), dtype=np.complex128)
     Heff = None
@@ -119,8 +127,10 @@ def solve(V, f, o, t1, t2, act, tol=1e-10, max_iter=300, diis_dim=6):
         Heff = sig1[:, act].T                  # Heff[y, x] = (Hbar (P+S))_x at active y
         rho1 = sig1 - np.einsum("ya,yx->xa", s1, Heff)
         rho2 = sig2 - np.einsum("yjab,yx->xjab", s2, Heff)
+        rho1 = rho1 + (D1 - D1s) * s1  # the shifted equations (zero when unshifted)
+        rho2 = rho2 + (D2 - D2s) * s2
         rho1[:, ~inactive] = 0.0
-        d1, d2 = rho1 / D1, rho2 / D2
+        d1, d2 = rho1 / D1s, rho2 / D2s
         d1[:, ~inactive] = 0.0
         res = max(np.max(np.abs(d1)), np.max(np.abs(d2)))
         new = np.concatenate([(s1 + d1).ravel(), (s2 + d2).ravel()])

@@ -58,3 +58,34 @@ def test_elementwise_recipe_matches_dense():
         y = A(r, s, p, q) - A(s, r, p, q) - A(r, s, q, p) + A(s, r, q, p)
         v = 0.5 * (x + np.conj(y)) if (g[p] + g[q] - g[r] - g[s]) % prob.G == 0 else 0
         assert abs(V[p, q, r, s] - v) < 1e-14
+
+
+def test_real_recipe_is_real_antisymmetric_symmetric_and_scaled():
+    import numpy as np
+    from oracle import integrals
+    from paper_2004_03682_gb300 import synthetic as syn
+    prob = syn.make_problem(31, 3, 7, 2)
+    V = integrals.real_integrals(prob)
+    assert np.max(np.abs(V.imag)) == 0.0
+    tol = 1e-14 * np.max(np.abs(V))
+    np.testing.assert_allclose(V, -V.transpose(1, 0, 2, 3), atol=tol, rtol=0)
+    np.testing.assert_allclose(V, -V.transpose(0, 1, 3, 2), atol=tol, rtol=0)
+    np.testing.assert_allclose(V, V.transpose(2, 3, 0, 1), atol=tol, rtol=0)
+    o = prob.n_occ
+    t = V[o:, o:, :o, :o].transpose(2, 3, 0, 1) / integrals.denominators2(prob.eps_occ, prob.eps_virt)
+    assert abs(np.max(np.abs(t)) - 0.05) < 1e-15
+    # the real part of the complex recipe, up to the scale
+    Vc = integrals.unscaled_integrals(prob)
+    ratio = V[np.abs(Vc.real) > 1e-3] / Vc.real[np.abs(Vc.real) > 1e-3]
+    assert np.max(np.abs(ratio - ratio.flat[0])) < 1e-12
+
+
+def test_real_ccsd_solution_is_real():
+    import numpy as np
+    from oracle import ccsd, integrals
+    from paper_2004_03682_gb300 import synthetic as syn
+    prob = syn.make_problem(33, 4, 12, 2)
+    b = ccsd.Blocks(integrals.real_integrals(prob), integrals.fock(prob), 4)
+    t1, t2, E, nit, conv, _ = ccsd.solve(b, tol=1e-11, max_iter=400)
+    assert conv
+    assert abs(E.imag) < 1e-14 and np.max(np.abs(t2.imag)) < 1e-14 and np.max(np.abs(t1.imag)) < 1e-14

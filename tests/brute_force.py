@@ -185,3 +185,30 @@ def ea_eom_matrix(f, V, o, t1, t2):
     B = np.stack(basis, axis=1)
     M = B.conj().T @ Hbar1 @ B - ecc * np.eye(B.shape[1])
     return M, labels
+
+
+def triples_energy(f, V, o, t1, t2):
+    """(T) by explicit second quantisation: c_mu = <mu|H T2|0>, d_mu = <mu|H T1|0> on the
+    triple excitations mu = a+ b+ c+ k j i |0> (i<j<k, a<b<c), E = sum conj(c + d) c / D_mu.
+    H is the full Hamiltonian of Eq. (ham); for mu != 0 it projects like H_N.  f must be
+    diagonal (a Hartree-Fock reference)."""
+    n = f.shape[0]
+    no, nv = t1.shape
+    sp = Space(n, o)
+    h, eref = core_hamiltonian(f, V, o)
+    H = sp.operator(hamiltonian_terms(h, V))
+    ref = (1 << o) - 1
+    phi0 = sp.vector([], ref)
+    T2 = sp.operator(cluster_terms(np.zeros_like(t1), t2, o))
+    T1 = sp.operator(cluster_terms(t1, np.zeros_like(t2), o))
+    cv = H @ (T2 @ phi0)
+    dv = H @ (T1 @ phi0)
+    eps = np.real(np.diag(f))
+    E = 0.0 + 0.0j
+    for i, j, k in itertools.combinations(range(no), 3):
+        for a, b, c in itertools.combinations(range(nv), 3):
+            mu = sp.vector([(o + a, 1), (o + b, 1), (o + c, 1), (k, 0), (j, 0), (i, 0)], ref)
+            cm, dm = np.vdot(mu, cv), np.vdot(mu, dv)
+            D = eps[i] + eps[j] + eps[k] - eps[o + a] - eps[o + b] - eps[o + c]
+            E += np.conj(cm + dm) * cm / D
+    return complex(E)

@@ -36,9 +36,17 @@ WORKLOADS = {
     # o=60 v=400 Z8 with packed <ab||cd> and tau pairs.  Level shift 32 Eh: the
     # synthetic Hamiltonian is strongly coupled at this size (E_MP2 = -2531 Eh) and the
     # unshifted iteration diverges from the MP2 guess (the fixed point is the same).
-    # Six BF16 slices: five move E by 1.8e-8 Eh after one iteration, six by 7e-11.
+    # BF16 slices: 5 for the particle-particle ladder and ring products (nearly all the
+    # tensor work), 6 for the other products (hole-hole ladder, F intermediates, T1 terms,
+    # t1- and F-coupled T2 terms), which set the energy's accuracy: five everywhere move E
+    # by 1.8e-8 Eh after one iteration and 9e-7 after two, this split by 5e-11 and 5e-9
+    # (measured by the accuracy leg of every run).
     "ccsd_z8_o60_v400": dict(name="ccsd_z8_o60_v400", n_occ=60, n_virt=400, G=8, seed=3001, shift=32.0,
-                             slices=6),
+                             slices=6, slices_major=5),
+    # the same workload in real arithmetic (the real part of the recipe; the paper's real
+    # double groups): real emulated products, a quarter of the complex tensor work
+    "ccsd_z8_o60_v400_real": dict(name="ccsd_z8_o60_v400_real", n_occ=60, n_virt=400, G=8, seed=3001, shift=32.0,
+                                  slices=6, slices_major=5, real=True),
     "ccsd_z8_o40_v200": dict(name="ccsd_z8_o40_v200", n_occ=40, n_virt=200, G=8, seed=2001, shift=8.0,
                              slices=5),
     # a smaller case of the same kernels (a few GB on the device), for ncu captures
@@ -46,6 +54,10 @@ WORKLOADS = {
                              slices=5),
     "ccsd_c1_o10_v40": dict(name="ccsd_c1_o10_v40", n_occ=10, n_virt=40, G=1, seed=1001, shift=0.0,
                             slices=5),
+    # the learned-guess family: 448 training and 64 held-out o=10 v=40 C1 members; the
+    # line reports time to the converged energy of the held-out set on four paths
+    "family_o10_v40": dict(name="family_o10_v40", n_occ=10, n_virt=40, G=1, seed=4000, shift=0.0, slices=5,
+                           family=True),
 }
 DEFAULT_WORKLOAD = "ccsd_z8_o60_v400"
 WORKLOAD = WORKLOADS[DEFAULT_WORKLOAD]
@@ -269,20 +281,25 @@ def run_reference(args):
 # k_emu_gemm DRAM read + write per launch of the top contraction, from a one-pass ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum), keyed by (workload, contraction,
 # slices); None once the kernel has changed since the capture
-TRAFFIC_BYTES = {}
+TRAFFIC_BYTES = {("ccsd_z8_o60_v400", "Qring", 5): 27.685e9 + 1.169e9}
 
 
-def accuracy_leg(prob, shift, slices, k=3, device=0):
+def slice_label(S, Smaj):
+    return f"{S}" if not Smaj or Smaj == S else f"{Smaj}/{S}"
+
+
+def accuracy_leg(prob, shift, configs, k=3, device=0, real=False):
     """Emulated vs plain FP64 GPU path from the same MP2 guess: |dE| after each of the
-    first k iterations and max |dT2| after k, for each slice count (untimed).  The FP64
-    path is the one the oracle parity tests validate."""
+    first k iterations and max |dT2| after k, for each slice configuration (untimed):
+    (n_slices, n_slices_major) pairs, labelled "major/other" ("S" when uniform).  The
+    FP64 path is the one the oracle parity tests validate."""
     import torch
     from paper_2004_03682_gb300 import expgb
 
-    def run(prec, S):
+    def run(prec, S, Smaj=0):
         torch.cuda.empty_cache()
         ctx = expgb.from_problems([prob], precision=prec, n_slices=S, conv_tol=1e-30, max_iter=k + 1,
-                                  device=device, level_shift=shift)
+                                  device=device, level_shift=shift, n_slices_major=Smaj, real_arith=real)
         ctx.init_integrals([prob.seed])
         recs, _, _ = ctx.iterate(k, raise_numeric=False)
         _, t2 = ctx.get_amplitudes(0)
@@ -294,15 +311,15 @@ def accuracy_leg(prob, shift, slices, k=3, device=0):
            "iterations": list(range(1, k + 1)), "E_fp64": [[e.real, e.imag] for e in e64],
            "fp64_ms_per_iteration": ms64[1:] if len(ms64) > 1 else ms64,
            "max_abs_T2": float(t64.abs().max().item()), "dE_vs_fp64": {}, "max_dT2_vs_fp64": {}}
-    for S in slices:
-        e, t2, _ = run(expgb.EXP_EMU_BF16, S)
-        out["dE_vs_fp64"][str(S)] = [abs(a - b) for a, b in zip(e, e64)]
-        out["max_dT2_vs_fp64"][str(S)] = float((t2 - t64).abs().max().item())
+    for S, Smaj in configs:
+        e, t2, _ = run(expgb.EXP_EMU_BF16, S, Smaj)
+        lab = slice_label(S, Smaj)
+        out["dE_vs_fp64"][lab] = [abs(a - b) for a, b in zip(e, e64)]
+        out["max_dT2_vs_fp64"][lab] = float((t2 - t64).abs().max().item())
         del t2
     del t64
     torch.cuda.empty_cache()
-    meets = [S for S in slices if max(out["dE_vs_fp64"][str(S)]) <= 1e-8]
-    out["slices_meeting_1e-8"] = meets
+    out["slices_meeting_1e-8"] = [lab for lab, d in out["dE_vs_fp64"].items() if max(d) <= 1e-8]
     return out
 
 
@@ -315,6 +332,114 @@ def l2_note(prob):
             f"~{t2:.2f} GB each, re-read every step)")
 
 
+def _family_solve(probs, model, precision, tol, max_iter, device):
+    """One context over `probs`: guess (MP2, or the model's), then iterations until every
+    instance has converged or failed, or max_iter.  Returns the per-instance energies
+    and states, the iteration at which each converged, the per-iteration device times,
+    and the host-synchronised wall times of the guess and of the whole solve."""
+    import numpy as np
+    import torch
+    from paper_2004_03682_gb300 import expgb
+    ctx = expgb.from_problems(probs, precision=precision, conv_tol=tol, max_iter=max_iter, device=device)
+    ctx.init_integrals([p.seed for p in probs], scale_mult=[p.scale_mult for p in probs])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    if model is not None:
+        model.apply(ctx)
+    torch.cuda.synchronize()
+    guess_s = time.perf_counter() - t0
+    recs, _, _ = ctx.iterate(max_iter, raise_numeric=False)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    conv_at, prev = [], 0
+    for it, r in enumerate(recs, 1):
+        conv_at += [it] * (r["n_converged"] - prev)
+        prev = r["n_converged"]
+    states = np.array([ctx.state(k) for k in range(len(probs))])
+    energies = np.array([ctx.energy(k) if states[k] == 1 else complex(np.nan, np.nan) for k in range(len(probs))])
+    launches = ctx.launches
+    ctx.close()
+    ms = [r["ms"] for r in recs]
+    last = max(conv_at) if conv_at else 0
+    return dict(energies=energies, states=states, conv_at=conv_at, wall_s=wall, guess_s=guess_s,
+                to_last_s=guess_s + sum(ms[:last]) * 1e-3, n_iter=len(recs), launches=launches)
+
+
+def run_family(args):
+    """Time to the converged energies (residual < 2e-11) of the 64 held-out members on four
+    paths: plain FP64 one instance at a time (MP2 guess), FP64 batched, emulated batched
+    (MP2 guess), emulated batched with the learned guess (the MLP trained on the 448
+    training members' converged amplitudes by the project's kernels; solving the training
+    set and training are reported apart).  Members whose iteration diverges are frozen as
+    failed; a few neither converge nor diverge within 1500 iterations.  Per path: the time
+    until the last converging member has converged (the guess plus the device time of the
+    iterations up to that point; for the plain path the sum over the converging members of
+    their own solves), the wall time of the whole solve up to the iteration cap, and the
+    median iteration count.  The integrals are generated before the clock starts."""
+    import numpy as np
+    import torch
+    from paper_2004_03682_gb300 import build, expgb, learned
+    from paper_2004_03682_gb300 import synthetic as syn
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    build.build()
+    tol, max_iter = 2e-11, 1500
+    probs = [syn.family_member(k) for k in range(512)]
+    train, test = probs[:448], probs[448:]
+    t0 = time.perf_counter()
+    ctx, tr = learned._solve(train, max_iter=max_iter, conv_tol=tol, device=local)
+    model = expgb.Mlp(seed=0, bf16=True, device=local)
+    model.add_training_data(ctx)
+    ctx.close()
+    t1 = time.perf_counter()
+    losses = model.train(20, batch=65536, lr=2e-3, seed=0)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t1
+    E, F = expgb.EXP_EMU_BF16, expgb.EXP_FP64
+    paths = {"emulated_batched_mp2": _family_solve(test, None, E, tol, max_iter, local)}
+    with Clocks(local) as clk:
+        paths["emulated_batched_learned"] = _family_solve(test, model, E, tol, max_iter, local)
+    paths["fp64_batched_mp2"] = _family_solve(test, None, F, tol, max_iter, local)
+    one = dict(energies=[], states=[], conv_at=[], wall_s=0.0, to_last_s=0.0)
+    for p in test:
+        r = _family_solve([p], None, F, tol, max_iter, local)
+        one["energies"].append(r["energies"][0])
+        one["states"].append(r["states"][0])
+        one["conv_at"] += r["conv_at"]
+        one["wall_s"] += r["wall_s"]
+        if r["states"][0] == 1:
+            one["to_last_s"] += r["to_last_s"]
+    one["energies"] = np.array(one["energies"])
+    paths["fp64_plain_mp2"] = one
+    ref = one["energies"]
+
+    def summ(r):
+        e = r["energies"]
+        both = np.isfinite(e) & np.isfinite(ref)
+        st = np.asarray(r["states"])
+        return {"time_to_last_converged_s": r["to_last_s"], "wall_to_cap_s": r["wall_s"],
+                "converged": int(np.sum(st == 1)), "failed": int(np.sum(st == 2)),
+                "median_iterations": float(np.median(r["conv_at"])) if r["conv_at"] else None,
+                "max_abs_dE_vs_fp64_plain": float(np.max(np.abs(e[both] - ref[both]))) if both.any() else None}
+    out = {k: summ(v) for k, v in paths.items()}
+    best = paths["emulated_batched_learned"]
+    iters = float(np.sum(best["conv_at"]))  # instance-iterations of the converging members
+    line = {"metric": METRIC, "value": iters / best["to_last_s"], "unit": UNIT, "n_gpus": ws, "steps": 1,
+            "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16x5-sliced f64 emulation (FP64 update, DIIS, energy)", "data": "synthetic",
+            "config": {"workload": "family_o10_v40", "members": "0..447 train, 448..511 held out",
+                       "conv_tol": tol, "max_iter": max_iter,
+                       "l2": "64 held-out instances solved together; inputs re-read every iteration"},
+            "time_to_converged": out,
+            "speedup_vs_fp64_plain": one["to_last_s"] / best["to_last_s"],
+            "training": {"train_solve_s": t1 - t0, "train_converged": int(tr["n_conv"]), "epochs": 20,
+                         "train_s": train_s, "loss_first": float(losses[0]), "loss_last": float(losses[-1])},
+            "gpu_launches": best["launches"], "clocks": clk.summary()}
+    model.close()
+    if rank == 0:
+        print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -322,6 +447,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--precision", choices=["emu", "fp64"], default="emu")
     ap.add_argument("--slices", type=int, default=None, help="BF16 slices (default: the workload's)")
+    ap.add_argument("--slices-major", type=int, default=None,
+                    help="BF16 slices of the particle-particle ladder and ring products (default: the workload's)")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-accuracy", action="store_true", help="skip the emulated-vs-FP64 leg")
@@ -330,12 +457,19 @@ def main():
     WORKLOAD = WORKLOADS[args.workload]
     if args.slices is None:
         args.slices = WORKLOAD["slices"]
+        if args.slices_major is None:
+            args.slices_major = WORKLOAD.get("slices_major", 0)
+    if args.slices_major is None:
+        args.slices_major = 0
+    smaj = args.slices_major or args.slices  # slices of the top (ladder / ring) product
     if args.warmup < 3:
         args.warmup = 3
     ws, rank, local = dist_env()
 
     if args.impl == "reference":
         return run_reference(args)
+    if WORKLOAD.get("family"):
+        return run_family(args)
 
     import numpy as np
     import torch
@@ -352,8 +486,10 @@ def main():
     prec = expgb.EXP_EMU_BF16 if args.precision == "emu" else expgb.EXP_FP64
     prob = syn.make_problem(WORKLOAD["seed"] + rank, WORKLOAD["n_occ"], WORKLOAD["n_virt"], WORKLOAD["G"])
     total = args.warmup + args.steps + 5
+    real = bool(WORKLOAD.get("real", False))
     ctx = expgb.from_problems([prob], precision=prec, n_slices=args.slices, conv_tol=1e-30,
-                              max_iter=10 * total, device=local, level_shift=WORKLOAD["shift"])
+                              max_iter=10 * total, device=local, level_shift=WORKLOAD["shift"],
+                              n_slices_major=args.slices_major, real_arith=real)
     ctx.init_integrals([prob.seed])
     ctx.iterate(args.warmup, raise_numeric=False)
     torch.cuda.synchronize()
@@ -376,7 +512,8 @@ def main():
     ms_max, n_all = aggregate_over_ranks(ms, n_it, dist, f"cuda:{local}")
     value = n_all / (ms_max / 1e3)
     macs = ctx.work_per_iteration()
-    ctflops = n_all * macs * 8 / (ms_max * 1e-3) / 1e12  # complex flops credited (8 per complex MAC)
+    fpm = 2 if WORKLOAD.get("real", False) else 8  # FP64 flops credited per algorithmic MAC (real / complex)
+    ctflops = n_all * macs * fpm / (ms_max * 1e-3) / 1e12
     # roofline of the dominant contraction, timed alone with CUDA events on the context stream
     site, kms, kmacs = ctx.profile_top(reps=3)
     pk = peaks()
@@ -387,15 +524,16 @@ def main():
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                 "peak_src": f"FP64 = {pk['src']} bf16 x nominal FP64/BF16 ratio (1.25/2250)"}
     else:
-        pairs = args.slices * (args.slices + 1) // 2
-        # executed BF16 tensor flops: 4 real MACs per complex MAC (real embedding) x slice pairs x 2
-        achieved = kmacs * 4 * pairs * 2 / (kms * 1e-3) / 1e12
-        eff = kmacs * 8 / (kms * 1e-3) / 1e12
-        traffic = TRAFFIC_BYTES.get((WORKLOAD["name"], site, args.slices))
-        roof = {"bound": "tensor", "kernel": f"k_emu_gemm<{args.slices}> ({site})", "achieved": achieved,
+        pairs = smaj * (smaj + 1) // 2
+        # executed BF16 tensor flops: 4 real MACs per complex MAC (real embedding; 1 in real
+        # arithmetic) x slice pairs x 2
+        achieved = kmacs * (1 if real else 4) * pairs * 2 / (kms * 1e-3) / 1e12
+        eff = kmacs * fpm / (kms * 1e-3) / 1e12
+        traffic = TRAFFIC_BYTES.get((WORKLOAD["name"], site, smaj))
+        roof = {"bound": "tensor", "kernel": f"k_emu_gemm<{smaj}> ({site})", "achieved": achieved,
                 "peak": pk["bf16"], "unit": "TFLOP/s", "frac": achieved / pk["bf16"], "traffic": traffic,
                 "peak_src": f"{pk['src']} bf16 dense (burst)", "ms_per_launch": kms,
-                "complex_macs_per_launch": kmacs, "effective_complex_fp64_tflops": eff}
+                "macs_per_launch": kmacs, "effective_fp64_tflops": eff}
     ctx.close()
 
     # e2e: the public API end to end (create from host arrays, generate integrals,
@@ -403,7 +541,8 @@ def main():
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     ctx2 = expgb.from_problems([prob], precision=prec, n_slices=args.slices, conv_tol=1e-30,
-                               max_iter=10 * total, device=local, level_shift=WORKLOAD["shift"])
+                               max_iter=10 * total, device=local, level_shift=WORKLOAD["shift"],
+                               n_slices_major=args.slices_major, real_arith=real)
     ctx2.init_integrals([prob.seed])
     recs2, _, _ = ctx2.iterate(args.steps, raise_numeric=False)
     _ = ctx2.energy(0)
@@ -417,7 +556,11 @@ def main():
 
     acc = None
     if args.precision == "emu" and not args.no_accuracy and rank == 0:
-        acc = accuracy_leg(prob, WORKLOAD["shift"], [args.slices, args.slices - 1], k=3, device=local)
+        confs = [(args.slices, args.slices_major)]
+        for c2 in [(smaj, 0), (args.slices, 0), (smaj - 1, 0)]:
+            if c2 not in confs and (c2[0], c2[0]) not in confs and 3 <= c2[0] <= 6:
+                confs.append(c2)
+        acc = accuracy_leg(prob, WORKLOAD["shift"], confs, k=3, device=local, real=real)
 
     if rank != 0:
         if dist:
@@ -431,18 +574,24 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / max(n_it, 1), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if args.precision == "fp64" else f"bf16x{args.slices}-sliced f64 emulation",
+            "dtype": "f64" if args.precision == "fp64" else (
+                f"bf16x{args.slices}-sliced f64 emulation" if smaj == args.slices else
+                f"bf16-sliced f64 emulation ({smaj} slices: particle-particle ladder and ring products; "
+                f"{args.slices}: the others)"),
             "data": "synthetic",
             "config": {"workload": WORKLOAD["name"], "n_occ": WORKLOAD["n_occ"], "n_virt": WORKLOAD["n_virt"],
                        "irreps": f"Z{WORKLOAD['G']}", "seed": WORKLOAD["seed"], "precision": args.precision,
                        "slices": args.slices if args.precision == "emu" else None,
-                       "level_shift": WORKLOAD["shift"], "packed": True, "l2": l2_note(prob)},
-            "complex_tflops": ctflops, "complex_macs_per_iter": macs,
+                       "slices_major": smaj if args.precision == "emu" else None,
+                       "level_shift": WORKLOAD["shift"], "packed": True, "real_arith": real,
+                       "l2": l2_note(prob)},
+            "effective_fp64_tflops": ctflops, "flops_per_mac": fpm, "macs_per_iter": macs,
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk.summary(), "status": st}
     if acc is not None:
-        line["dE_vs_fp64"] = acc["dE_vs_fp64"][str(args.slices)]
-        line["max_dT2_vs_fp64"] = acc["max_dT2_vs_fp64"][str(args.slices)]
+        lab = slice_label(args.slices, args.slices_major)
+        line["dE_vs_fp64"] = acc["dE_vs_fp64"][lab]
+        line["max_dT2_vs_fp64"] = acc["max_dT2_vs_fp64"][lab]
         line["accuracy"] = acc
     print(json.dumps(line))
     if dist:

@@ -96,6 +96,28 @@ typedef struct {
                               the update, DIIS vectors and energy on t1 plus the a<b, i<j entries of
                               t2 (same fixed point and DIIS matrix as full vectors); 0: full pair
                               compounds everywhere */
+  int n_slices_major;      /* with EXP_EMU_BF16: BF16 slices (3..6; 0 = n_slices) for the products that
+                              carry nearly all of the tensor work -- the particle-particle ladder
+                              <ab||cd> tau_ij^cd, its W_abef companion X_amij = <am||ef> tau_ij^ef,
+                              and the two ring products (t2 W_mbej and the t2 <mn||ef> term of
+                              W_mbej).  Every other emulated product (the hole-hole ladder and
+                              W_mnij, the F intermediates, the T1-equation terms, the t1- and
+                              F-coupled T2 terms) takes n_slices: those form or apply
+                              intermediates whose errors act on every amplitude alike and set the
+                              energy's accuracy, at a small share of the work. */
+  double denom_shift;      /* s >= 0: intruder-state denominator shift (Sec. II.A, after Eq. (sectors)):
+                              every energy denominator D of the amplitude equations is replaced by
+                              D~ = D - s (s / (s + |D|))^n ("dynamic": a near-zero or positive D moves
+                              by about -s, one with |D| >> s hardly at all), in both sectors:
+                              (0h,0p) D~ t = RHS(t) (guess V/D~), (0h,1p) rho + (D - D~) s = 0 stepped
+                              with 1/D~.  The solution depends on s; exp_pade_zero extrapolates
+                              results at several s to s = 0.  0 = the plain equations. */
+  int denom_shift_n;       /* n >= 1, the attenuation power of the dynamic shift (ignored when s = 0) */
+  int real_arith;          /* 1: real Hamiltonian, real arithmetic (the paper's real double groups, Sec. II.C,
+                              Table tab:time): the integrals are the recipe's real part (the recipe on
+                              Re A), and the emulated products run as real GEMMs (A' = Re A, one B row
+                              per output column: a quarter of the complex tensor work); storage stays
+                              complex with zero imaginary parts, the FP64 kernels unchanged.  0: complex. */
 } exp_config;
 
 /* Create a context: validates the config, builds the symmetry-blocked layouts
@@ -163,6 +185,17 @@ exp_status exp_energy(exp_ctx* ctx, int inst, double* e_re, double* e_im);
  * the Bloch iteration did not converge within max_iter. */
 exp_status exp_fs_sector_0h1p(exp_ctx* ctx, int inst, double* heff, double* eig_re, double* eig_im,
                               int* n_iter);
+
+/* Zero-shift extrapolation of results computed with denominator shifts (Sec. II.A;
+ * Sec. III.A: dynamic shifts with Pade extrapolation to the zero-shift limit): the
+ * values E_k (m complex numbers, (re, im) pairs, host) at scales x_k (m doubles, host)
+ * are fitted by E(x) = (a0 + a1 x + ... + aL x^L) / (1 + b1 x + ... + bM x^M) through the
+ * linear conditions a0 + ... + aL x_k^L - E_k (b1 x_k + ... + bM x_k^M) = E_k (solved
+ * exactly when m = L + M + 1, in least squares when m is larger, by Householder QR); *out (host, one
+ * (re, im) pair) receives a0 = E(0).  With the dynamic shift of power n the natural
+ * scale is x_k = s_k^(n+1) (the leading order of D - D~ for |D| >> s).  Host only, no
+ * GPU work.  EINVAL if m < L + M + 1, m > 64, L < 0, M < 0 or the system is singular. */
+exp_status exp_pade_zero(int m, const double* x, const double* values, int L, int M, double* out);
 
 /* Copy amplitudes of instance `inst` between the context and caller device
  * buffers, dense layout: t1[i][a] (n_occ x n_virt), t2[i][j][a][b]; complex128,

@@ -2,6 +2,7 @@
 // mapping, the iteration loop with CUDA-graph replay, amplitude I/O.
 #include <algorithm>
 #include <cmath>
+#include <complex>
 #include <cstdio>
 #include <string>
 #include <cstring>
@@ -49,6 +50,13 @@ static void check_config(const exp_config* cfg) {
   if (cfg->precision != EXP_FP64 && cfg->precision != EXP_EMU_BF16) throw ExpError{EXP_EINVAL, "bad precision"};
   if (cfg->precision == EXP_EMU_BF16 && (cfg->n_slices < 3 || cfg->n_slices > 6))
     throw ExpError{EXP_EINVAL, "n_slices must be in 3..6"};
+  if (cfg->precision == EXP_EMU_BF16 && cfg->n_slices_major != 0 &&
+      (cfg->n_slices_major < 3 || cfg->n_slices_major > 6))
+    throw ExpError{EXP_EINVAL, "n_slices_major must be 0 or in 3..6"};
+  if (cfg->real_arith != 0 && cfg->real_arith != 1) throw ExpError{EXP_EINVAL, "real_arith must be 0 or 1"};
+  if (!(cfg->denom_shift >= 0) || !std::isfinite(cfg->denom_shift)) throw ExpError{EXP_EINVAL, "denom_shift must be >= 0"};
+  if (cfg->denom_shift > 0 && (cfg->denom_shift_n < 1 || cfg->denom_shift_n > 16))
+    throw ExpError{EXP_EINVAL, "denom_shift_n must be in 1..16"};
   if (cfg->diis_dim < 0 || cfg->diis_dim > EXP_MAX_DIIS) throw ExpError{EXP_EINVAL, "diis_dim must be in 0..8"};
   if (!(cfg->conv_tol > 0)) throw ExpError{EXP_EINVAL, "conv_tol must be > 0"};
   if (!(cfg->level_shift >= 0) || !std::isfinite(cfg->level_shift)) throw ExpError{EXP_EINVAL, "level_shift must be >= 0"};
@@ -487,7 +495,7 @@ extern "C" exp_status exp_zgemm(const exp_allocator* alloc, void* stream, int pr
     Tensor TA, TB;
     TA.L = LA; TA.d = (cplx*)A; TA.is = LA.size;
     TB.L = LB; TB.d = (cplx*)B; TB.is = LB.size;
-    EmuPlan* ep = emu_plan(c, g, &TA, &TB, false, false);
+    EmuPlan* ep = emu_plan(c, g, &TA, &TB, false, false, true, "");
     emu_run(c, ep, g, (const cplx*)A, (const cplx*)B, (cplx*)C, LA.size, LB.size, LC.size, alpha, beta != 0);
   } else {
     launch_gemm_fp64(c, g, (const cplx*)A, (const cplx*)B, (cplx*)C, LA.size, LB.size, LC.size, alpha, beta != 0);
@@ -514,6 +522,67 @@ extern "C" exp_status exp_zgemm(const exp_allocator* alloc, void* stream, int pr
     c.dfree_all();
     return EXP_ECUDA;
   }
+}
+
+// Pade [L/M] fit through m points, E(0) = a0: unknowns (a0..aL, b1..bM), rows
+// a0 + a1 x + ... + aL x^L - E (b1 x + ... + bM x^M) = E, solved in the least-squares
+// sense (exactly when m = L + M + 1) by complex Householder QR and back substitution
+// (the rows are Vandermonde-like, so the normal equations would square their condition).
+extern "C" exp_status exp_pade_zero(int m, const double* x, const double* values, int L, int M, double* out) {
+  g_err.clear();
+  if (!x || !values || !out || L < 0 || M < 0 || m > 64 || m < L + M + 1) {
+    g_err = "exp_pade_zero: need L, M >= 0 and L + M + 1 <= m <= 64 points";
+    return EXP_EINVAL;
+  }
+  typedef std::complex<double> Z;
+  const int nu = L + 1 + M;
+  std::vector<Z> A(size_t(m) * nu), e(m);
+  auto a = [&](int r, int c) -> Z& { return A[size_t(r) * nu + c]; };
+  for (int k = 0; k < m; ++k) {
+    e[k] = Z(values[2 * k], values[2 * k + 1]);
+    double p = 1.0;
+    for (int j = 0; j <= L; ++j, p *= x[k]) a(k, j) = p;
+    p = x[k];
+    for (int j = 1; j <= M; ++j, p *= x[k]) a(k, L + j) = -e[k] * p;
+  }
+  double amax = 0.0;
+  for (auto& v : A) amax = std::max(amax, std::abs(v));
+  // Householder: for column c, v = x + e^{i arg x0} |x| e1 over rows c..m-1; apply to A and e
+  for (int c = 0; c < nu; ++c) {
+    double nrm = 0.0;
+    for (int r = c; r < m; ++r) nrm += std::norm(a(r, c));
+    nrm = std::sqrt(nrm);
+    if (!(nrm > 1e-15 * amax)) {
+      g_err = "exp_pade_zero: singular system";
+      return EXP_EINVAL;
+    }
+    const Z x0 = a(c, c);
+    const Z ph = std::abs(x0) > 0.0 ? x0 / std::abs(x0) : Z(1.0);
+    std::vector<Z> v(m - c);
+    for (int r = c; r < m; ++r) v[r - c] = a(r, c);
+    v[0] += ph * nrm;
+    double vn = 0.0;
+    for (auto& q : v) vn += std::norm(q);
+    for (int cc = c; cc < nu; ++cc) {  // A <- (I - 2 v v^H / v^H v) A
+      Z d = 0.0;
+      for (int r = c; r < m; ++r) d += std::conj(v[r - c]) * a(r, cc);
+      d *= 2.0 / vn;
+      for (int r = c; r < m; ++r) a(r, cc) -= d * v[r - c];
+    }
+    Z d = 0.0;
+    for (int r = c; r < m; ++r) d += std::conj(v[r - c]) * e[r];
+    d *= 2.0 / vn;
+    for (int r = c; r < m; ++r) e[r] -= d * v[r - c];
+  }
+  std::vector<Z> coef(nu);
+  for (int i = nu - 1; i >= 0; --i) {
+    Z acc = e[i];
+    for (int j = i + 1; j < nu; ++j) acc -= a(i, j) * coef[j];
+    coef[i] = acc / a(i, i);
+  }
+  out[0] = coef[0].real();
+  out[1] = coef[0].imag();
+  return EXP_OK;
 }
 
 extern "C" int64_t exp_kernel_launches(const exp_ctx* x) { return x ? x->c.launches : 0; }

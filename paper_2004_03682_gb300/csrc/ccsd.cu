@@ -62,9 +62,11 @@ struct MaxOp { __device__ double operator()(double a, double b) const { return n
 struct AddOp { __device__ double operator()(double a, double b) const { return a + b; } };
 
 // Dinv = 1 / (D - sigma), once per context (the update then needs no FP64 divide)
-__global__ void k_inv_denom(const double* __restrict__ D, double* __restrict__ Dinv, int64_t n, double shift) {
+// (with an intruder-state shift ds, D~ = dyn_shift(D) stands for D: the shifted equations)
+__global__ void k_inv_denom(const double* __restrict__ D, double* __restrict__ Dinv, int64_t n, double shift,
+                            double ds, int dn) {
   for (int64_t k = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; k < n; k += int64_t(gridDim.x) * blockDim.x)
-    Dinv[k] = 1.0 / (D[k] - shift);
+    Dinv[k] = 1.0 / (dyn_shift(D[k], ds, dn) - shift);
 }
 
 // t_new = (R - sigma t) / (D - sigma) over the whole amplitude vector (sigma = 0:
@@ -402,11 +404,11 @@ __device__ __forceinline__ int64_t pk_full(const PackDims& D, const int32_t* __r
 // Dinv = 1 / (D - sigma) on the packed vector
 __global__ void k_inv_denom_pk(const double* __restrict__ Dn, double* __restrict__ Dinv, int64_t namp, int64_t npk,
                                int64_t n1, PackDims D, const int32_t* __restrict__ rfull,
-                               const int32_t* __restrict__ cfull, double shift) {
+                               const int32_t* __restrict__ cfull, double shift, double ds, int dn) {
   const int inst = blockIdx.y;
   for (int64_t k = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; k < npk; k += int64_t(gridDim.x) * blockDim.x) {
     const int64_t f = k < n1 ? k : n1 + pk_full(D, rfull, cfull, k - n1);
-    Dinv[inst * npk + k] = 1.0 / (Dn[inst * namp + f] - shift);
+    Dinv[inst * npk + k] = 1.0 / (dyn_shift(Dn[inst * namp + f], ds, dn) - shift);
   }
 }
 
@@ -618,14 +620,15 @@ __global__ void k_rescale(cplx* __restrict__ V, int64_t vis, int64_t n, const do
 }
 
 // t2 = V_abij / D (MP2 first-order amplitudes), t1 = 0
+// (with an intruder-state shift: V / D~, the first Jacobi step of the shifted equations)
 __global__ void k_mp2_guess(cplx* __restrict__ T, const double* __restrict__ D, const cplx* __restrict__ Vd,
-                            int64_t vis, int64_t n1, int64_t namp) {
+                            int64_t vis, int64_t n1, int64_t namp, double ds, int dn) {
   const int inst = blockIdx.y;
   for (int64_t k = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; k < namp; k += int64_t(gridDim.x) * blockDim.x) {
     cplx out = make_double2(0, 0);
     if (k >= n1) {
       const cplx v = Vd[inst * vis + (k - n1)];
-      const double d = D[inst * namp + k];
+      const double d = dyn_shift(D[inst * namp + k], ds, dn);
       out = make_double2(v.x / d, v.y / d);
     }
     T[inst * namp + k] = out;
@@ -803,7 +806,8 @@ static void zero_pair_diag(Ctx& c) {
 
 void ccsd_guess(Ctx& c) {
   CcsdState& s = S(c);
-  k_mp2_guess<<<dim3(grid_for(c.namp), c.ninst), 256, 0, c.stream>>>(c.d_T, c.d_D, s.Vd->d, s.Vd->is, c.n1, c.namp);
+  k_mp2_guess<<<dim3(grid_for(c.namp), c.ninst), 256, 0, c.stream>>>(c.d_T, c.d_D, s.Vd->d, s.Vd->is, c.n1, c.namp,
+                                                                      c.cfg.denom_shift, c.cfg.denom_shift_n);
   KCHECK(c);
   ccsd_mark_guessed(c);
 }
@@ -1069,10 +1073,12 @@ void ccsd_iteration(Ctx& c) {
   if (!s.dinv_ready) {  // D and sigma are fixed for the context's life
     if (s.pk.on)
       k_inv_denom_pk<<<dim3(grid_for(s.pk.n), c.ninst), 256, 0, c.stream>>>(
-          c.d_D, s.pk.d_Dinv, c.namp, s.pk.n, c.n1, s.pk.D, s.pk.vv->d_full, s.pk.oo->d_full, c.cfg.level_shift);
+          c.d_D, s.pk.d_Dinv, c.namp, s.pk.n, c.n1, s.pk.D, s.pk.vv->d_full, s.pk.oo->d_full, c.cfg.level_shift,
+          c.cfg.denom_shift, c.cfg.denom_shift_n);
     else
       k_inv_denom<<<dim3(grid_for(c.namp * c.ninst)), 256, 0, c.stream>>>(c.d_D, s.d_Dinv, c.namp * c.ninst,
-                                                                          c.cfg.level_shift);
+                                                                          c.cfg.level_shift, c.cfg.denom_shift,
+                                                                          c.cfg.denom_shift_n);
     KCHECK(c);
     s.dinv_ready = true;
   }

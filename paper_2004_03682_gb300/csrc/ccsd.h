@@ -4,6 +4,16 @@
 
 #include "engine.h"
 
+// intruder-state dynamic shift of an energy denominator (exp_config.denom_shift):
+// D~ = D - s (s / (s + |D|))^n; s = 0 leaves D unchanged
+__host__ __device__ __forceinline__ double dyn_shift(double D, double s, int n) {
+  if (!(s > 0.0)) return D;
+  const double r = s / (s + fabs(D));
+  double p = s;
+  for (int k = 0; k < n; ++k) p *= r;
+  return D - p;
+}
+
 Layout L4(Ctx& c, int s0, int g0, int s1, int g1, int s2, int g2, int s3, int g3, int nrow);
 Layout L2(Ctx& c, int s0, int g0, int s1, int g1);
 void ccsd_setup(Ctx& c);

@@ -714,7 +714,7 @@ void einsum(Ctx& c, const std::string& site, cplx alpha, Operand A, Operand B, T
       ds_prepare(c, P->g);
     }
     // a B operand in the arena is not a tensor other contractions could share slices of
-    if (P->emulate) P->emu = emu_plan(c, P->g, P->A, P->B, A.v != nullptr, B.v != nullptr, !P->permB);
+    if (P->emulate) P->emu = emu_plan(c, P->g, P->A, P->B, A.v != nullptr, B.v != nullptr, !P->permB, site);
   } else {
     P = it->second.get();
     if (P->swapped) std::swap(A, B);

@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(256) k_fs_update(const cplx* __restrict__ R, c
                                                    const int8_t* __restrict__ role, const cplx* __restrict__ T,
                                                    cplx* __restrict__ Tn, cplx* __restrict__ En, int64_t namp, int dim,
                                                    const int* __restrict__ state, double* __restrict__ part,
-                                                   double shift) {
+                                                   double shift, double ds, int dn) {
   __shared__ double sh[32];
   const int inst = blockIdx.y;
   const int* st = state + inst * 4;
@@ -127,8 +127,11 @@ __global__ void __launch_bounds__(256) k_fs_update(const cplx* __restrict__ R, c
       cplx tn = t, e = make_double2(0.0, 0.0);
       if (role[k] == ROLE_Q) {
         const cplx r = R[off + k], x = X[off + k];
-        const double d0 = D0[off + k], df = Dfs[off + k];
-        const double rr = r.x - d0 * t.x - x.x, ri = r.y - d0 * t.y - x.y;
+        const double d0 = D0[off + k], df0 = Dfs[off + k];
+        // intruder-state shift (ds > 0): the shifted equations rho + (D - D~) s = 0,
+        // stepped with 1/D~ (ds = 0: D~ = D, the plain Bloch equation)
+        const double df = dyn_shift(df0, ds, dn), dd = df0 - df;
+        const double rr = r.x - d0 * t.x - x.x + dd * t.x, ri = r.y - d0 * t.y - x.y + dd * t.y;
         // level shift away from zero in the denominator's sign: |D| grows by sigma,
         // the step shrinks, the fixed point (zero residual) stays
         const double q = 1.0 / (df < 0.0 ? df - shift : df + shift);
@@ -417,7 +420,7 @@ void fs_step(Ctx& c, const double* Dfs, const int8_t* role, const cplx* XV) {
   ccsd_update_step(c, [&](double* part, int nb) {
     k_fs_update<<<dim3(nb, c.ninst), 256, 0, c.stream>>>(c.d_R, c.d_D, Dfs, XV, role, c.d_T, c.d_diis_t, c.d_diis_e,
                                                          c.namp, c.cfg.diis_dim, c.d_diis_state, part,
-                                                         c.cfg.level_shift);
+                                                         c.cfg.level_shift, c.cfg.denom_shift, c.cfg.denom_shift_n);
     KCHECK(c);
   }, false);
 }

@@ -73,7 +73,9 @@ struct EmuProb {
   int64_t a_ex, b_ex;           // offsets of the exponent arrays (per instance)
   int64_t ws;                   // split-K partials offset (complex, per instance)
   int32_t M, N, K, Kp;          // Kp = 2 Kh, Kh = K rounded up to 16
-  int32_t tiles_m, tiles_n, tile0, pad0;  // tile0: first GEMM work item
+  int32_t tiles_m, tiles_n, tile0, nh;    // tile0: first GEMM work item; nh: halves of the K' axis
+                                         // (2: complex operands, A' = [Re A | Im A]; 1: real operands,
+                                         // A' = Re A and one B row per output column)
   int32_t ksplit, kcb, arows, brows;     // K splits, k-blocks per split (multiple of KC_BLOCKS),
                                          // rows stored per A / B slice tile (a problem with a
                                          // single row / column tile keeps only its 8-row groups
@@ -200,11 +202,16 @@ __device__ __forceinline__ double scaled_i128(__int128 R, int e) {
 
 // K half of the real embedding (each half padded to 16) and the number of
 // 32-wide k ranges a half spans (the split kernels' CTA count per tile)
-__host__ __device__ __forceinline__ int kh_of(const EmuProb& P) { return P.Kp / 2; }
-__host__ __device__ __forceinline__ int nkh_of(const EmuProb& P) { return (P.Kp / 2 + KB - 1) / KB; }
+__host__ __device__ __forceinline__ int kh_of(const EmuProb& P) { return P.Kp / P.nh; }
+__host__ __device__ __forceinline__ int nkh_of(const EmuProb& P) { return (P.Kp / P.nh + KB - 1) / KB; }
 // split-A units (8-groups) per row of a work item: 2 when a half is 16 wide, else 4
-__host__ __device__ __forceinline__ int gpr_of(const EmuProb& P) { return P.Kp == 32 ? 2 : 4; }
+__host__ __device__ __forceinline__ int gpr_of(const EmuProb& P) { return kh_of(P) == 16 ? 2 : 4; }
+// output columns per tile: BN / 2 complex columns (real embedding), or BN real ones
+__host__ __device__ __forceinline__ int ocols_of(const EmuProb& P, int BN) { return P.nh == 2 ? BN / 2 : BN; }
 
+// Index of the last problem whose first unit (tile, split-A or split-B unit) is <= x.
+// Those first units do not decrease along the list (a problem with no units shares
+// its successor's), so this is the problem that owns unit x.
 // One work item of the persistent GEMM: (instance, K split, row tile, column tile).
 struct EmuWork {
   int pi, inst, ks, mt, nt, kb0, nkb, nkb_all;
@@ -390,17 +397,19 @@ __global__ void __launch_bounds__(THREADS, 1)
       for (int j = 0; j < HW; ++j) R[j] = 0;
       // 8-column groups of this warp that hold outputs (warp-uniform): none when the
       // warp's 32 rows are all past M
-      const int ncv = 2 * min(P.N - W.nt * (SH::BN / 2), SH::BN / 2);
+      const bool cpx = P.nh == 2;  // complex: output column pairs (Re, Im); real: one per column
+      const int ncv = cpx ? 2 * min(P.N - W.nt * (SH::BN / 2), SH::BN / 2) : min(P.N - W.nt * SH::BN, SH::BN);
       int nv8 = min(max((ncv - h * HW + 7) / 8, 0), HW / 8);
       if (W.mt * BM + q * 32 >= P.M) nv8 = 0;
       // the tile's row / column exponents, loaded before the accumulators are ready
       const int gi = W.mt * BM + row;
-      const int j0 = W.nt * (SH::BN / 2) + h * (HW / 2);  // first complex column of this warp
+      // first output column of this warp
+      const int j0 = cpx ? W.nt * (SH::BN / 2) + h * (HW / 2) : W.nt * SH::BN + h * HW;
       const int ei = gi < P.M ? Aex[W.inst * aex_is + P.a_ex + gi] : 0;
-      int fj[HW / 2];
+      int fj[HW / 2];  // complex columns' exponents (real columns load theirs at the store)
 #pragma unroll
       for (int jj = 0; jj < HW / 2; ++jj)
-        fj[jj] = (gi < P.M && j0 + jj < P.N) ? Bex[W.inst * bex_is + P.b_ex + j0 + jj] : 0;
+        fj[jj] = (cpx && gi < P.M && j0 + jj < P.N) ? Bex[W.inst * bex_is + P.b_ex + j0 + jj] : 0;
       for (int ch = 0; ch < nchunks; ++ch, ++gc) {
         const int buf = gc & 1;
         if (!mbar_wait(&accf[buf], (gc >> 1) & 1, abort, gerr, wns)) { ok = false; break; }
@@ -424,6 +433,37 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
       if (!ok) break;
       if (gi >= P.M) continue;
+      if (!cpx) {  // real operands: column u of the warp is output column j0 + u, imaginary part 0
+        if (P.ksplit > 1) {
+          longlong2* Wp = reinterpret_cast<longlong2*>(ws + W.inst * ws_is + P.ws) + int64_t(W.ks) * P.M * P.N +
+                          int64_t(gi) * P.N;
+#pragma unroll
+          for (int u = 0; u < HW; ++u)
+            if (j0 + u < P.N) Wp[j0 + u] = make_longlong2(R[u], 0ll);
+        } else {
+          cplx* Crow = C + W.inst * c_is + P.c_off + int64_t(gi) * P.N;
+#pragma unroll
+          for (int u = 0; u < HW; ++u) {
+            const int gj = j0 + u;
+            if (gj < P.N) {
+              const int e = ei + Bex[W.inst * bex_is + P.b_ex + gj] - BETA * (S + 1);
+              double vr, vi;
+              if (alpha_e != ALPHA_GENERAL) {
+                const int k = alpha_e < 0 ? -alpha_e - ALPHA_NEG_BIAS : alpha_e - ALPHA_POS_BIAS;
+                vr = scaled_i64(alpha_e < 0 ? -R[u] : R[u], e + k);
+                vi = 0.0;
+              } else {
+                const double re = scaled_i64(R[u], e);
+                vr = alpha.x * re;
+                vi = alpha.y * re;
+              }
+              if (beta) { const cplx o = Crow[gj]; vr += o.x; vi += o.y; }
+              Crow[gj] = make_double2(vr, vi);
+            }
+          }
+        }
+        continue;
+      }
       if (P.ksplit > 1) {  // the exact integer partial; the reduction adds them exactly
         longlong2* Wp = reinterpret_cast<longlong2*>(ws + W.inst * ws_is + P.ws) + int64_t(W.ks) * P.M * P.N +
                         int64_t(gi) * P.N;
@@ -674,35 +714,37 @@ __global__ void __launch_bounds__(256) k_split_a(const EmuProb* __restrict__ pro
     if (!live || k0 >= Kh || r >= P.arows) continue;
     uint4 sr[S], si[S], dummy[S];
     slice8<S>(xr, sh, sr, false, dummy);
-    slice8<S>(xi, sh, si, false, dummy);
     const int at = P.arows * KB;
     __nv_bfloat16* o = out + inst * out_is + P.a_sl + int64_t(mt) * nkb * (S * at);
     __nv_bfloat16* o_re = o + kpos_off(r, k0, at, S);
-    __nv_bfloat16* o_im = o + kpos_off(r, Kh + k0, at, S);
 #pragma unroll
-    for (int s2 = 0; s2 < S; ++s2) {
-      *reinterpret_cast<uint4*>(o_re + s2 * at) = sr[s2];
-      *reinterpret_cast<uint4*>(o_im + s2 * at) = si[s2];
+    for (int s2 = 0; s2 < S; ++s2) *reinterpret_cast<uint4*>(o_re + s2 * at) = sr[s2];
+    if (P.nh == 2) {  // complex operands: the Im half of the K' axis
+      slice8<S>(xi, sh, si, false, dummy);
+      __nv_bfloat16* o_im = o + kpos_off(r, Kh + k0, at, S);
+#pragma unroll
+      for (int s2 = 0; s2 < S; ++s2) *reinterpret_cast<uint4*>(o_im + s2 * at) = si[s2];
     }
   }
 }
 
 // B'' rows n' = 2j + c: c = 0 -> [Re B_j ; -Im B_j], c = 1 -> [Im B_j ; Re B_j] over the
-// two K halves (positions k and Kh + k).  Work item = (column tile nt, 32-wide range
-// kbh of the half); unit = (column j, 8-group), lanes along j so the strided column
-// reads coalesce; grid-stride over all units.
+// two K halves (positions k and Kh + k); real operands (nh = 1): row j = Re B_j over the
+// one K range.  Work item = (column tile nt, 32-wide range kbh of the half); unit =
+// (column j, 8-group), lanes along j so the strided column reads coalesce; grid-stride
+// over all units.
 template <int S>
 __global__ void __launch_bounds__(256) k_split_b(const EmuProb* __restrict__ probs, int nprobs, int64_t total,
                                                  const cplx* __restrict__ B, int64_t b_is, const int* __restrict__ ex,
                                                  int64_t ex_is, __nv_bfloat16* __restrict__ out, int64_t out_is) {
   using SH = Shape<S>;
-  constexpr int NJ = SH::BN / 2;
   const int inst = blockIdx.y;
   for (int64_t U = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; U < total; U += int64_t(gridDim.x) * blockDim.x) {
     int pi = 0;
     while (pi + 1 < nprobs && U >= probs[pi + 1].bu0) ++pi;
     const EmuProb& P = probs[pi];
-    const int nj = P.brows / 2;  // stored columns per tile (NJ unless compact)
+    const int NJ = ocols_of(P, SH::BN);   // output columns per tile
+    const int nj = P.brows / P.nh;  // stored columns per tile (NJ unless compact); nh B rows a column
     const int UB = nj * (KB / 8);
     const int64_t lu = U - P.bu0;
     const int lt = int(lu / UB), u = int(lu - int64_t(lt) * UB);
@@ -727,9 +769,15 @@ __global__ void __launch_bounds__(256) k_split_b(const EmuProb* __restrict__ pro
     }
     uint4 sr[S], si[S], sin_[S], dummy[S];
     slice8<S>(xr, sh, sr, false, dummy);
-    slice8<S>(xi, sh, si, true, sin_);
     const int bt = P.brows * KB;
     __nv_bfloat16* o = out + inst * out_is + P.b_sl + int64_t(nt) * nkb * (S * bt);
+    if (P.nh == 1) {  // real operands: row j = Re B_j
+      __nv_bfloat16* r0 = o + kpos_off(jl, k0, bt, S);
+#pragma unroll
+      for (int s2 = 0; s2 < S; ++s2) *reinterpret_cast<uint4*>(r0 + s2 * bt) = sr[s2];
+      continue;
+    }
+    slice8<S>(xi, sh, si, true, sin_);
     __nv_bfloat16* re0 = o + kpos_off(2 * jl, k0, bt, S);
     __nv_bfloat16* im0 = o + kpos_off(2 * jl, Kh + k0, bt, S);
     __nv_bfloat16* re1 = o + kpos_off(2 * jl + 1, k0, bt, S);
@@ -812,7 +860,9 @@ static void launch_emu_reduce(const EmuProb* d, int np, int max_ksplit, const cp
 // ---------------------------------------------------------------------------
 // K' = 2K with each half padded to 16; callers keep K <= EMU_MAX_K, so this stays far
 // inside int (the slice and split-K offsets derived from it are int64)
-static int kp_of(int K) { return 2 * ((std::max(K, 1) + 15) / 16) * 16; }
+static int kp_of(int K, int nh = 2) {
+  return nh == 2 ? 2 * ((std::max(K, 1) + 15) / 16) * 16 : ((std::max(K, 1) + 31) / 32) * 32;
+}
 
 // grid of a warp-per-item kernel (8 warps per CTA) and of a thread-per-unit kernel
 static int row_exp_blocks(int64_t items, int sms) {
@@ -941,8 +991,16 @@ static void set_smem_attr() {
 
 static int bn_of(int S) { return S <= 5 ? 48 : 32; }
 
+bool emu_major_site(const std::string& site) {
+  // the particle-particle ladder, X_amij (its t1 companion over <am||ef>), the two ring products
+  static const char* const kMajor[] = {"R2pp", "Xamij", "Qring", "Wmbej3"};
+  for (const char* m : kMajor)
+    if (site == m) return true;
+  return false;
+}
+
 EmuPlan* emu_plan(Ctx& c, const GemmPlan& g, const Tensor* A, const Tensor* B, bool a_const, bool b_const,
-                  bool b_shareable) {
+                  bool b_shareable, const std::string& site) {
   EmuState* st = (EmuState*)c.emu_state;
   if (!st) {
     st = new EmuState();
@@ -953,7 +1011,7 @@ EmuPlan* emu_plan(Ctx& c, const GemmPlan& g, const Tensor* A, const Tensor* B, b
   }
   EmuPlan* p = new EmuPlan();
   st->plans.push_back(p);
-  p->S = c.cfg.n_slices;
+  p->S = (c.cfg.n_slices_major > 0 && emu_major_site(site)) ? c.cfg.n_slices_major : c.cfg.n_slices;
   p->a_const = a_const;
   p->b_const = b_const;
   p->d_err = st->d_err;
@@ -961,8 +1019,10 @@ EmuPlan* emu_plan(Ctx& c, const GemmPlan& g, const Tensor* A, const Tensor* B, b
   int64_t asl = 0, bsl = 0, aex = 0, bex = 0;
   int64_t au0 = 0, bu0 = 0;
   int64_t tiles_mn = 0;
+  const int nh = c.cfg.real_arith ? 1 : 2;  // real operands: no Im half, one B row per column
+  const int ocols = nh == 2 ? BN / 2 : BN;
   for (auto& q : g.h_probs)
-    tiles_mn += int64_t((q.M + BM - 1) / BM) * ((q.N + BN / 2 - 1) / (BN / 2));
+    tiles_mn += int64_t((q.M + BM - 1) / BM) * ((q.N + ocols - 1) / ocols);
   tiles_mn *= c.ninst;
   const int64_t sms = std::max(c.sm_count, 1);
   p->fuse_a = true;
@@ -975,11 +1035,12 @@ EmuPlan* emu_plan(Ctx& c, const GemmPlan& g, const Tensor* A, const Tensor* B, b
     e.N = q.N;
     e.K = q.K;
     if (q.K > EMU_MAX_K) throw ExpError{EXP_EINVAL, "emulated GEMM: K above 2^26"};
-    e.Kp = kp_of(q.K);  // [Re | Im], each half padded to 16
+    e.nh = nh;
+    e.Kp = kp_of(q.K, nh);  // [Re | Im], each half padded to 16 (real: Re padded to 32)
     e.tiles_m = (q.M + BM - 1) / BM;
-    e.tiles_n = (q.N + BN / 2 - 1) / (BN / 2);
+    e.tiles_n = (q.N + ocols - 1) / ocols;
     e.arows = e.tiles_m == 1 ? (q.M + 7) / 8 * 8 : BM;
-    e.brows = e.tiles_n == 1 ? (2 * q.N + 7) / 8 * 8 : BN;
+    e.brows = e.tiles_n == 1 ? (nh * q.N + 7) / 8 * 8 : BN;  // nh B rows per output column
     if (q.K > 32) p->fuse_a = false;
     const int nkb = e.Kp / KB;
     p->chunks.push_back((nkb + KC_BLOCKS - 1) / KC_BLOCKS);
@@ -998,7 +1059,7 @@ EmuPlan* emu_plan(Ctx& c, const GemmPlan& g, const Tensor* A, const Tensor* B, b
     e.au0 = au0;
     e.bu0 = bu0;
     au0 += int64_t(e.tiles_m) * nkh_of(e) * e.arows * gpr_of(e);
-    bu0 += int64_t(e.tiles_n) * nkh_of(e) * (e.brows / 2) * (KB / 8);
+    bu0 += int64_t(e.tiles_n) * nkh_of(e) * (e.brows / nh) * (KB / 8);
     p->h.push_back(e);
   }
   p->tiles_mn = tiles_mn;
@@ -1322,6 +1383,7 @@ exp_status noalloc_launch(cudaStream_t st, unsigned char* base, int M, int N, in
   e.M = M;
   e.N = N;
   e.K = K;
+  e.nh = 2;
   e.Kp = kp_of(K);
   e.tiles_m = (M + BM - 1) / BM;
   e.tiles_n = (N + BN / 2 - 1) / (BN / 2);

@@ -350,7 +350,7 @@ static void finish_op(Ctx& c, PackedOp* op, bool a_const, double alpha = 1.0) {
   P->gemm_beta = false;
   P->g = make_gemm_plan(c, op->A.L, op->B.L, op->C.L);
   P->emulate = emu_wanted(c, P->g, op->site);
-  if (P->emulate) P->emu = emu_plan(c, P->g, &op->A, &op->B, a_const, false, op->offB < 0);
+  if (P->emulate) P->emu = emu_plan(c, P->g, &op->A, &op->B, a_const, false, op->offB < 0, op->site);
 }
 
 static void run_op(Ctx& c, PackedOp* op, const std::function<void()>& before, const std::function<void()>& after) {

@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(256) k_generate(cplx* __restrict__ dst, int64_
                                                   const ChunkRef* __restrict__ chunks, Map4 map,
                                                   int n, const uint64_t* __restrict__ seeds,
                                                   const double* __restrict__ scales,
-                                                  const int* __restrict__ genmap) {
+                                                  const int* __restrict__ genmap, int real) {
   const ChunkRef ch = chunks[blockIdx.x];
   const GenTask T = tasks[ch.task];
   const int inst = blockIdx.y;
@@ -211,7 +211,8 @@ __global__ void __launch_bounds__(256) k_generate(cplx* __restrict__ dst, int64_
       continue;
     }
     const cplx v = v_element(g[map.m[0]], g[map.m[1]], g[map.m[2]], g[map.m[3]], uint64_t(n), seed);
-    dst[dp] = make_double2(sc * v.x, sc * v.y);
+    // real arithmetic: the recipe on Re A, i.e. the real part (every step is real-linear)
+    dst[dp] = make_double2(sc * v.x, real ? 0.0 : sc * v.y);
   }
 }
 
@@ -222,7 +223,8 @@ void launch_generate(Ctx& c, cplx* dst, int64_t is, const GenTask* d_tasks, cons
   // generator tasks use padded dims: slot k of a rank-4 tensor is dim k
   for (int k = 0; k < 4; ++k) m.m[k] = map[k];
   k_generate<<<dim3(n_chunks, c.ninst), 256, 0, c.stream>>>(dst, is, d_tasks, d_chunks, m,
-                                                            c.n_gen, c.d_seed, c.d_scale, c.d_genmap);
+                                                            c.n_gen, c.d_seed, c.d_scale, c.d_genmap,
+                                                            c.cfg.real_arith);
   KCHECK(c);
 }
 
@@ -380,7 +382,7 @@ __global__ void __launch_bounds__(256) k_generate_pairs(cplx* __restrict__ dst, 
                                                         const int32_t* __restrict__ cpair, int n,
                                                         const uint64_t* __restrict__ seeds,
                                                         const double* __restrict__ scales,
-                                                        const int* __restrict__ genmap, int herm) {
+                                                        const int* __restrict__ genmap, int herm, int real) {
   const int inst = blockIdx.y;
   dst += inst * is;
   const uint64_t seed = seeds[inst];
@@ -406,7 +408,7 @@ __global__ void __launch_bounds__(256) k_generate_pairs(cplx* __restrict__ dst, 
     cplx v = make_double2(0.0, 0.0);
     if (!ghost) {
       const cplx w = v_element(uint64_t(gi[0]), uint64_t(gi[1]), uint64_t(gi[2]), uint64_t(gi[3]), uint64_t(n), seed);
-      v = make_double2(sc * w.x, sc * w.y);
+      v = make_double2(sc * w.x, real ? 0.0 : sc * w.y);
     }
     dst[e] = v;
     if (herm && q > p) dst[D.blk[g] + int64_t(q) * D.nc[g] + p] = make_double2(v.x, -v.y);
@@ -418,6 +420,7 @@ void launch_generate_pairs(Ctx& c, cplx* dst, int64_t is, const PackDims& D, con
   if (total == 0) return;
   const int blocks = int(std::min<int64_t>((total + 255) / 256, int64_t(std::max(c.sm_count, 1)) * 8));
   k_generate_pairs<<<dim3(blocks, c.ninst), 256, 0, c.stream>>>(dst, is, D, R.d_pair, C.d_pair, c.n_gen, c.d_seed,
-                                                                c.d_scale, c.d_genmap, &R == &C ? 1 : 0);
+                                                                c.d_scale, c.d_genmap, &R == &C ? 1 : 0,
+                                                                c.cfg.real_arith);
   KCHECK(c);
 }

@@ -43,7 +43,8 @@ class Config(C.Structure):
                 ("conv_tol", C.c_double), ("max_iter", C.c_int), ("guess", C.c_int),
                 ("emu_min_macs", C.c_double), ("n_active", C.c_int),
                 ("active_virt", C.POINTER(C.c_int32)), ("level_shift", C.c_double),
-                ("packed", C.c_int)]
+                ("packed", C.c_int), ("n_slices_major", C.c_int),
+                ("denom_shift", C.c_double), ("denom_shift_n", C.c_int), ("real_arith", C.c_int)]
 
 
 class IterInfo(C.Structure):
@@ -107,6 +108,9 @@ def lib():
     for name in ("exp_mlp_create", "exp_mlp_add_training_data", "exp_mlp_train", "exp_mlp_apply",
                  "exp_mlp_params", "exp_mlp_loss_grad"):
         getattr(L, name).restype = C.c_int
+    L.exp_pade_zero.argtypes = [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int, C.c_int,
+                                C.POINTER(C.c_double)]
+    L.exp_pade_zero.restype = C.c_int
     L.exp_test_emu_wait.argtypes = [C.c_int, C.c_double]
     L.exp_test_emu_wait.restype = C.c_int
     L.exp_kernel_launches.argtypes = [P]
@@ -159,7 +163,8 @@ class Context:
     def __init__(self, n_occ, n_virt, irrep_occ, irrep_virt, eps_occ, eps_virt, n_inst=1,
                  precision=EXP_FP64, n_slices=5, diis_dim=6, conv_tol=1e-9, max_iter=500,
                  guess=EXP_GUESS_MP2, device=0, emu_min_macs=0.0, active=None, level_shift=0.0,
-                 packed=True, allocator=None):
+                 packed=True, allocator=None, n_slices_major=0, denom_shift=0.0, denom_shift_n=1,
+                 real_arith=False):
         import torch
         self._torch = torch
         L = lib()
@@ -183,7 +188,8 @@ class Context:
             self._keep.append(ac)
         cfg = Config(self.n_inst, self.n_occ, self.n_virt, len(io), pio, piv, peo, pev,
                      int(precision), int(n_slices), int(diis_dim), float(conv_tol), int(max_iter),
-                     int(guess), float(emu_min_macs), self.n_active, pa, float(level_shift), int(bool(packed)))
+                     int(guess), float(emu_min_macs), self.n_active, pa, float(level_shift), int(bool(packed)),
+                     int(n_slices_major), float(denom_shift), int(denom_shift_n), int(bool(real_arith)))
         h = C.c_void_p()
         st = L.exp_create(C.byref(cfg), C.byref(self.alloc.struct), C.c_void_p(self.stream.cuda_stream),
                           C.byref(h))
@@ -401,6 +407,21 @@ def zgemm(A, B, C=None, alpha=1.0, beta=False, precision=EXP_FP64, n_slices=5):
     if st != 0:
         raise ExpError(st, L.exp_last_error(None).decode())
     return Cm
+
+
+def pade_zero(x, values, L, M) -> complex:
+    """E(0) of the [L/M] Pade fit of complex values at scales x (exp_pade_zero, host)."""
+    Lb = lib()
+    xa = np.ascontiguousarray(x, dtype=np.float64)
+    v = np.asarray(values, dtype=np.complex128)
+    va = np.ascontiguousarray(np.stack([v.real, v.imag], -1).reshape(-1))
+    out = np.zeros(2)
+    dp = C.POINTER(C.c_double)
+    st = Lb.exp_pade_zero(len(xa), xa.ctypes.data_as(dp), va.ctypes.data_as(dp), int(L), int(M),
+                          out.ctypes.data_as(dp))
+    if st != 0:
+        raise ExpError(st, Lb.exp_last_error(None).decode())
+    return complex(out[0], out[1])
 
 
 def _byref(x):

@@ -8,6 +8,7 @@ captured inside an NVTX range, so that a profiler can select it with
     python -m paper_2004_03682_gb300.profile_run --occ 60 --virt 400 --irreps 8 --seed 3001 --slices 6 --shift 32
 
     python -m paper_2004_03682_gb300.profile_run --zgemm 2048 2048 2048 --slices 6        # range "zgemm"
+    python -m paper_2004_03682_gb300.profile_run --family 512                               # range "iter3"
 
 Without --top the range holds one whole CCSD iteration (the CUDA graph the bench
 replays); with --top it holds the contraction with the most complex multiply-adds per
@@ -15,8 +16,10 @@ iteration, or the one at call site --site (``Context.profile_top``): one full pr
 (slicing passes and GEMM) and one more launch of its GEMM kernel.  With --zgemm M N K
 the range holds one emulated complex GEMM of that shape through exp_zgemm (seeded
 operands, a few hundred MB: a bounded case for full profiler captures of the tensor-core
-kernel).  Prints the iteration times (or the top contraction's site, time and work, or
-the GEMM time) as one line.
+kernel).  With --family N the workload is the first N members of the learned-guess
+family (o=10 v=40 C1, all in one context; --occ/--virt/--irreps ignored).  Prints the
+iteration times (or the top contraction's site, time and work, or the GEMM time) as one
+line.
 """
 from __future__ import annotations
 
@@ -40,15 +43,18 @@ def main():
     ap.add_argument("--site", default=None, help="with --top: this call site instead of the largest")
     ap.add_argument("--zgemm", type=int, nargs=3, default=None, metavar=("M", "N", "K"),
                     help="one emulated complex GEMM of this shape instead of a CCSD workload")
+    ap.add_argument("--family", type=int, default=0, help="the first N learned-guess family members, batched")
+    ap.add_argument("--slices-major", type=int, default=0, help="slices of the ladder and ring products")
     a = ap.parse_args()
     if a.zgemm:
         return zgemm_case(*a.zgemm, a.slices)
-    prob = syn.make_problem(a.seed, a.occ, a.virt, a.irreps)
+    probs = ([syn.family_member(k) for k in range(a.family)] if a.family else
+             [syn.make_problem(a.seed, a.occ, a.virt, a.irreps)])
     prec = expgb.EXP_FP64 if a.fp64 else expgb.EXP_EMU_BF16
-    ctx = expgb.from_problems([prob], conv_tol=1e-30, max_iter=50, precision=prec, n_slices=a.slices,
-                              level_shift=a.shift)
-    ctx.init_integrals([prob.seed])
-    recs, _, _ = ctx.iterate(2)
+    ctx = expgb.from_problems(probs, conv_tol=1e-30, max_iter=50, precision=prec, n_slices=a.slices,
+                              level_shift=0.0 if a.family else a.shift, n_slices_major=a.slices_major)
+    ctx.init_integrals([p.seed for p in probs], scale_mult=[p.scale_mult for p in probs])
+    recs, _, _ = ctx.iterate(2, raise_numeric=False)
     torch.cuda.synchronize()
     if a.top:
         torch.cuda.nvtx.range_push("top")
@@ -58,7 +64,7 @@ def main():
         print(f"top {site} {ms:.4f} ms {macs:.4e} complex MACs")
     else:
         torch.cuda.nvtx.range_push("iter3")
-        recs3, _, _ = ctx.iterate(1)
+        recs3, _, _ = ctx.iterate(1, raise_numeric=False)
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
         print("iteration ms", [round(r["ms"], 3) for r in recs + recs3])

@@ -1,10 +1,12 @@
 """Write stored oracle results (calls only oracle/ and the seeded input module).
 
-    python tests/golden/make_golden.py
+    python tests/golden/make_golden.py [c1] [family]
 """
 import json
 import os
 import sys
+
+import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
@@ -27,5 +29,38 @@ def c1():
     print(out)
 
 
+def _solve_member(k, tol, max_iter):
+    prob = syn.family_member(k)
+    b = ccsd.Blocks(integrals.integrals(prob), integrals.fock(prob), prob.n_occ)
+    with np.errstate(all="ignore"):
+        t1, t2, E, nit, conv, recs = ccsd.solve(b, tol=tol, max_iter=max_iter)
+    ok = bool(conv) and bool(np.isfinite(E))
+    return dict(converged=ok, e_re=float(E.real), e_im=float(E.imag), n_iter=int(nit), scale_mult=float(prob.scale_mult))
+
+
+def family(fixed=(0, 17)):
+    """Converged energies of members of the learned-guess family (o=10 v=40 C1, integral
+    scale x U[0.5,1.5], virtual floor U[0.1,0.6]), each solved alone by the oracle: the
+    members `fixed`, and the last held-out member (448..511) whose oracle solve converges
+    (some members diverge from the MP2 guess; their solves are recorded as such)."""
+    out = dict(members={}, tol=1e-12, max_iter=1500,
+               source="oracle/ccsd.py solve() per member, MP2 guess, DIIS(6), residual < tol")
+    for k in fixed:
+        out["members"][str(k)] = _solve_member(k, out["tol"], out["max_iter"])
+        print(k, out["members"][str(k)], flush=True)
+    for k in range(511, 447, -1):
+        r = _solve_member(k, out["tol"], out["max_iter"])
+        out["members"][str(k)] = r
+        print(k, r, flush=True)
+        if r["converged"]:
+            out["last_held_out_converged"] = k
+            break
+    json.dump(out, open(os.path.join(HERE, "family_o10_v40.json"), "w"), indent=1)
+
+
 if __name__ == "__main__":
-    c1()
+    which = sys.argv[1:] or ["c1", "family"]
+    if "c1" in which:
+        c1()
+    if "family" in which:
+        family()

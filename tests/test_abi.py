@@ -48,13 +48,19 @@ def _cfg(expgb, **over):
                        io.ctypes.data_as(C.POINTER(C.c_int32)), iv.ctypes.data_as(C.POINTER(C.c_int32)),
                        eo.ctypes.data_as(C.POINTER(C.c_double)), ev.ctypes.data_as(C.POINTER(C.c_double)),
                        d["precision"], d["n_slices"], d["diis_dim"], d["conv_tol"], d["max_iter"], d["guess"], 0.0,
-                       d.get("n_active", 0), None, d.get("level_shift", 0.0), d.get("packed", 1))
+                       d.get("n_active", 0), None, d.get("level_shift", 0.0), d.get("packed", 1),
+                       d.get("n_slices_major", 0), d.get("denom_shift", 0.0), d.get("denom_shift_n", 1),
+                       d.get("real_arith", 0))
     return cfg, keep
 
 
 @pytest.mark.parametrize("bad", [dict(n_occ=5), dict(n_irrep=17), dict(diis_dim=9), dict(conv_tol=0.0),
                                  dict(max_iter=0), dict(precision=7), dict(precision=1, n_slices=2),
-                                 dict(n_inst=0), dict(n_active=2), dict(level_shift=-1.0)])
+                                 dict(n_inst=0), dict(n_active=2), dict(level_shift=-1.0),
+                                 dict(precision=1, n_slices=5, n_slices_major=2),
+                                 dict(precision=1, n_slices=5, n_slices_major=7),
+                                 dict(denom_shift=-0.1), dict(denom_shift=0.2, denom_shift_n=0),
+                                 dict(real_arith=2)])
 def test_create_rejects_bad_config_on_host(lib, bad):
     from paper_2004_03682_gb300 import expgb
     cfg, keep = _cfg(expgb, **bad)
@@ -95,3 +101,23 @@ def test_zgemm_rejects_bad_arguments_on_host(lib):
 def test_profile_top_rejects_null_context(lib):
     ms, macs = C.c_double(), C.c_double()
     assert lib.exp_profile_top(None, 1, None, 0, C.byref(ms), C.byref(macs)) == 1
+
+
+@pytest.mark.parametrize("L,M,m", [(1, 1, 3), (2, 1, 4), (1, 1, 6), (3, 0, 5)])
+def test_pade_zero_matches_oracle_on_the_host(lib, L, M, m):
+    """exp_pade_zero (host code of the library, no GPU) against the oracle's fit."""
+    from oracle import intruder
+    from paper_2004_03682_gb300 import expgb
+    rng = np.random.default_rng(m + 7 * L)
+    x = np.sort(rng.uniform(0.001, 0.1, m))
+    vals = (-1.33 + 0.002j) + (0.5 + 0.1j) * x / (1 + 2.0 * x) + 1e-7 * rng.standard_normal(m)
+    got = expgb.pade_zero(x, vals, L, M)
+    ref = intruder.pade_zero(x, vals, L, M)
+    assert abs(got - ref) < 1e-9 * abs(ref)
+
+
+def test_pade_zero_rejects_too_few_points(lib):
+    from paper_2004_03682_gb300 import expgb
+    with pytest.raises(expgb.ExpError) as e:
+        expgb.pade_zero([0.1, 0.2], [1.0, 2.0], 1, 1)
+    assert e.value.status == 1

@@ -237,3 +237,17 @@ def test_profile_top_selects_a_contraction_by_name(expgb):
     assert site == "R2a" and ms2 > 0 and 0 < macs2 <= macs
     with pytest.raises(expgb.ExpError):
         ctx.profile_top(reps=1, site="no_such_site")
+
+
+def test_emulated_split_slice_counts_c1_o10_v40(expgb):
+    """n_slices_major: the particle-particle ladder and ring products at 5 slices, every
+    other emulated product at 6 (the split the o=60 v=400 bench runs): converged energy
+    within 1e-8 Eh of the oracle's fixed point."""
+    g = json.load(open(os.path.join(HERE, "golden", "ccsd_c1_o10_v40.json")))
+    prob = syn.make_problem(g["seed"], g["n_occ"], g["n_virt"], g["G"])
+    ctx = expgb.from_problems([prob], conv_tol=1e-9, max_iter=g["max_iter"], precision=expgb.EXP_EMU_BF16,
+                              n_slices=6, n_slices_major=5, emu_min_macs=1e3)
+    ctx.init_integrals([prob.seed])
+    _, conv, _ = ctx.iterate(g["max_iter"])
+    assert conv
+    assert abs(ctx.energy(0) - complex(g["e_re"], g["e_im"])) < 1e-8

@@ -66,3 +66,41 @@ def test_sign_slip_is_caught():
     E_wrong = complex(np.sum(np.conj(c - d) * c / D) / 36.0)
     Ebf = bf.triples_energy(f, V, 3, t1, t2)
     assert abs(E_wrong - Ebf) > 1e-6 * abs(Ebf)
+
+
+@pytest.mark.parametrize("no,nv,G", [(4, 6, 1), (5, 8, 2)])
+def test_per_triple_energies_sum_to_the_energy(no, nv, G):
+    """The split over occupied triples is exact, and only i<j<k carry energy."""
+    rng = np.random.default_rng(no + nv + G)
+    prob = syn.make_problem(720 + no + nv + G, no, nv, G)
+    V, f = integrals.integrals(prob), integrals.fock(prob)
+    b = ccsd.Blocks(V, f, no)
+    t1, t2 = _random_t(rng, no, nv, prob)
+    e = triples.per_triple(t1, t2, b)
+    E = triples.energy(t1, t2, b)
+    assert abs(np.sum(e) - E) < 1e-14 * max(1.0, abs(E))
+    for i in range(no):
+        for j in range(no):
+            for k in range(no):
+                if not (i < j < k):
+                    assert e[i, j, k] == 0
+    assert np.count_nonzero(e) > 0
+
+
+@pytest.mark.parametrize("no,nv,G", [(4, 7, 1), (5, 9, 2), (6, 10, 4)])
+def test_sampled_triple_energy_matches_dense(no, nv, G):
+    """One triple from generated integral slices equals the dense per-triple energy, for
+    every i<j<k (the slice generator is itself pinned to the dense integrals)."""
+    from oracle import sampled
+    rng = np.random.default_rng(10 * no + nv + G)
+    prob = syn.make_problem(730 + no + nv + G, no, nv, G)
+    V, f = integrals.integrals(prob), integrals.fock(prob)
+    b = ccsd.Blocks(V, f, no)
+    t1, t2 = _random_t(rng, no, nv, prob)
+    e = triples.per_triple(t1, t2, b)
+    ints = sampled.Integrals(prob)
+    for i in range(no):
+        for j in range(i + 1, no):
+            for k in range(j + 1, no):
+                ek = triples.triple_energy(prob, ints, t1, t2, i, j, k)
+                assert abs(ek - e[i, j, k]) < 1e-14 + 1e-12 * abs(e[i, j, k])

@@ -204,6 +204,45 @@ exp_status exp_pade_zero(int m, const double* x, const double* values, int L, in
 exp_status exp_get_amplitudes(exp_ctx* ctx, int inst, void* t1_dev, void* t2_dev);
 exp_status exp_set_amplitudes(exp_ctx* ctx, int inst, const void* t1_dev, const void* t2_dev);
 
+/* Result of exp_ccsd_t. */
+typedef struct {
+  double e_re, e_im;     /* E(T), hartree */
+  double ms;             /* device time of the call on the context stream (CUDA events) */
+  double macs;           /* complex multiply-adds of the connected-triples contractions the
+                            triples i<j<k need (the method's work) */
+  double macs_run;       /* complex multiply-adds the block products executed (>= macs: a block
+                            product also covers index orders no triple of the block uses) */
+  int64_t n_triples;     /* occupied triples i<j<k */
+  int n_block_triples;   /* occupied block triples processed */
+  int block;             /* occupied spinors per block */
+} exp_t3_info;
+
+/* The perturbative triples correction (T) of CCSD(T) (the model list of Sec. III.A)
+ * for instance `inst`, from the amplitudes the context holds (converged by
+ * exp_ccsd_iterate, or set by exp_set_amplitudes), for the Hartree-Fock reference
+ * of the synthetic Hamiltonian (f diagonal):
+ *   c_ijk^abc = P(i/jk) P(a/bc) [ sum_e <bc||ei> t_jk^ae - sum_m <ma||jk> t_im^bc ],
+ *   d_ijk^abc = P(i/jk) P(a/bc) t_i^a <bc||jk>,  P(p/qr) f = f - f(p<->q) - f(p<->r),
+ *   E(T) = sum over i<j<k, a<b<c of conj(c + d) c / (e_i + e_j + e_k - e_a - e_b - e_c).
+ * The connected contractions run as symmetry-blocked grouped products in the
+ * context's precision (EXP_EMU_BF16: the BF16-sliced emulation with n_slices slices;
+ * EXP_FP64: the FP64 kernel); the permutations, the disconnected term, the
+ * denominators and every sum are FP64, and the result does not depend on the work
+ * decomposition.  block: occupied spinors per block of the schedule (0: the largest
+ * whose block products fit the scratch budget; a larger value than n_occ means
+ * n_occ); every block size gives the same bits.  info (host, nullable) receives E(T)
+ * and the work counts;
+ * per_triple (host, nullable, 2 * n_triples doubles) receives each triple's
+ * (re, im) energy at index C(k,3) + C(j,2) + i of its i<j<k (spinor order of the
+ * config).  Needs about 16 GiB of scratch for the block products at most, plus
+ * dense t2 and <bc||jk> (n_occ^2 n_virt^2 each) and the fixed operands
+ * (n_occ n_virt^2 (n_virt + n_occ) / (2 G)).  Synchronises.  ESTATE before
+ * exp_init_integrals or before any amplitudes exist, and for a context with an
+ * active space; EINVAL for inst out of range, block < 0 or more than 65535 virtual
+ * spinors;
+ * ETIMEOUT if a bounded wait of the emulated GEMM gave up. */
+exp_status exp_ccsd_t(exp_ctx* ctx, int inst, int block, exp_t3_info* info, double* per_triple);
+
 /* Algorithmic work of one (0h,0p) iteration, all instances: complex
  * multiply-adds of every contraction over the symmetry-allowed blocks (what the
  * grouped GEMMs execute).  Valid after the first iteration has been planned. */

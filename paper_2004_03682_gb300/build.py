@@ -10,7 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libexpgb.so")
-UNITS = ["engine", "tensor", "gemm_fp64", "gemm_emu", "packed", "ccsd", "fs", "mlp", "api"]
+UNITS = ["engine", "tensor", "gemm_fp64", "gemm_emu", "packed", "ccsd", "fs", "mlp", "triples", "api"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "--expt-relaxed-constexpr"]

@@ -398,6 +398,14 @@ extern "C" exp_status exp_set_amplitudes(exp_ctx* x, int inst, const void* t1, c
   API_END(x)
 }
 
+extern "C" exp_status exp_ccsd_t(exp_ctx* x, int inst, int block, exp_t3_info* info, double* per_triple) {
+  API_BEGIN
+  if (!x) throw ExpError{EXP_EINVAL, "null context"};
+  ccsd_t(x->c, inst, block, info, per_triple);
+  return EXP_OK;
+  API_END(x)
+}
+
 extern "C" exp_status exp_work_per_iteration(const exp_ctx* x, double* macs) {
   API_BEGIN
   if (!x || !macs) throw ExpError{EXP_EINVAL, "null argument"};

@@ -32,3 +32,5 @@ void ccsd_update_step(Ctx& c, const std::function<void(double*, int)>& upd, bool
 int ccsd_count_converged(Ctx& c);
 const Tensor* ccsd_driver_integral(Ctx& c);
 void ccsd_mark_guessed(Ctx& c);
+// the (T) correction of instance inst (triples.cu)
+void ccsd_t(Ctx& c, int inst, int block, exp_t3_info* info, double* per_triple);

@@ -20,3 +20,26 @@ void emu_run(Ctx& c, EmuPlan* p, const GemmPlan& g, const cplx* A, const cplx* B
              int64_t ais, int64_t bis, int64_t cis, cplx alpha, bool beta, bool gemm_only = false);
 void emu_release(Ctx& c);
 
+// Operand sets for grouped products whose operand pairing is chosen at run time (the
+// block products of the (T) correction).  The members of a set are sliced together;
+// a product pairs an A member (rows x K, row-major) with a B member (K x cols,
+// row-major) of the same K and writes C (rows x cols, row-major) = alpha A B.  The
+// products of one call share one launch; each product needs K short enough for one
+// exact int64 accumulation (K' up to 2^(13 - 7 (S - 6)) KC terms: far above (T)'s).
+struct EmuSet;
+struct EmuSetMat {
+  int64_t src;  // element offset of the member in the source array
+  int rows;     // A: rows; B: columns
+  int K;
+};
+struct EmuSetProd {
+  int a, b;       // member indices in the A and the B set
+  int64_t c_off;  // element offset of the product's C in the output array
+};
+EmuSet* emu_set_new(Ctx& c, int S, bool b_side);
+// lay out the members (growing the set's device buffers when needed), then scan
+// their exponents and write their slice tiles from src
+void emu_set_slice(Ctx& c, EmuSet* s, const std::vector<EmuSetMat>& mats, const cplx* src);
+void emu_set_multiply(Ctx& c, const EmuSet* A, const EmuSet* B, const std::vector<EmuSetProd>& prods, cplx* C,
+                      cplx alpha);
+void emu_set_free(Ctx& c, EmuSet* s);

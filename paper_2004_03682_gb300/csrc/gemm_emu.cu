@@ -212,6 +212,23 @@ __host__ __device__ __forceinline__ int ocols_of(const EmuProb& P, int BN) { ret
 // Index of the last problem whose first unit (tile, split-A or split-B unit) is <= x.
 // Those first units do not decrease along the list (a problem with no units shares
 // its successor's), so this is the problem that owns unit x.
+enum UnitKind { UNIT_TILE, UNIT_A, UNIT_B };
+template <UnitKind U>
+__device__ __forceinline__ int64_t first_unit(const EmuProb& q) {
+  return U == UNIT_TILE ? int64_t(q.tile0) : U == UNIT_A ? q.au0 : q.bu0;
+}
+template <UnitKind U>
+__device__ __forceinline__ int prob_of_unit(const EmuProb* probs, int nprobs, int64_t x) {
+  int lo = 0, hi = nprobs - 1;
+#pragma unroll 1
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (first_unit<U>(probs[mid]) <= x) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
 // One work item of the persistent GEMM: (instance, K split, row tile, column tile).
 struct EmuWork {
   int pi, inst, ks, mt, nt, kb0, nkb, nkb_all;
@@ -220,8 +237,7 @@ __device__ __forceinline__ EmuWork emu_work(const EmuProb* probs, int nprobs, in
   EmuWork W;
   W.inst = w / n_tiles;
   const int tile = w - W.inst * n_tiles;
-  int pi = 0;
-  while (pi + 1 < nprobs && probs[pi + 1].tile0 <= tile) ++pi;
+  const int pi = prob_of_unit<UNIT_TILE>(probs, nprobs, tile);
   const EmuProb& P = probs[pi];
   W.pi = pi;
   int lt = tile - P.tile0;
@@ -673,8 +689,7 @@ __global__ void __launch_bounds__(256) k_split_a(const EmuProb* __restrict__ pro
   for (int64_t U0 = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; U0 < total32; U0 += int64_t(gridDim.x) * blockDim.x) {
     const bool live = U0 < total;
     const int64_t U = live ? U0 : total - 1;
-    int pi = 0;
-    while (pi + 1 < nprobs && U >= probs[pi + 1].au0) ++pi;
+    const int pi = prob_of_unit<UNIT_A>(probs, nprobs, U);
     const EmuProb& P = probs[pi];
     const int gpr = gpr_of(P);
     const int UA = P.arows * gpr;
@@ -740,8 +755,7 @@ __global__ void __launch_bounds__(256) k_split_b(const EmuProb* __restrict__ pro
   using SH = Shape<S>;
   const int inst = blockIdx.y;
   for (int64_t U = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; U < total; U += int64_t(gridDim.x) * blockDim.x) {
-    int pi = 0;
-    while (pi + 1 < nprobs && U >= probs[pi + 1].bu0) ++pi;
+    const int pi = prob_of_unit<UNIT_B>(probs, nprobs, U);
     const EmuProb& P = probs[pi];
     const int NJ = ocols_of(P, SH::BN);   // output columns per tile
     const int nj = P.brows / P.nh;  // stored columns per tile (NJ unless compact); nh B rows a column
@@ -969,6 +983,9 @@ struct EmuState {
   int* d_err = nullptr;
   cplx* tune_buf = nullptr;  // scratch output for the autotuner's trial launches
   int64_t tune_cap = 0;
+  std::vector<EmuProb> set_recs;  // product records of operand-set launches (emu_set_multiply)
+  EmuProb* set_d = nullptr;
+  int64_t set_cap = 0;
 };
 
 bool emu_wanted(Ctx& c, const GemmPlan& g, const std::string&) {
@@ -1316,6 +1333,213 @@ void emu_release(Ctx& c) {
   for (auto* p : st->plans) delete p;
   delete st;
   c.emu_state = nullptr;
+}
+
+// ---------------------------------------------------------------------------
+// Operand sets: matrices sliced once and multiplied in grouped products chosen at
+// run time (the block products of the (T) correction, whose pairing of operands
+// changes from launch to launch).  A set holds the members' slice tiles and
+// exponents in the layout of one side of k_emu_gemm; a product record takes the
+// A-side fields of one member and the B-side fields of another.
+struct EmuSet {
+  int S = 5;
+  bool b_side = false;
+  int nh = 2;
+  std::vector<EmuProb> h;  // one record per member, the fields of its side filled
+  EmuProb* d = nullptr;
+  int64_t d_cap = 0;  // records
+  __nv_bfloat16* sl = nullptr;
+  int64_t sl_cap = 0;  // bf16 elements
+  int* ex = nullptr;
+  int64_t ex_cap = 0;  // exponents
+  int64_t units = 0;   // split-kernel units
+  int64_t n_scan = 0;  // exponent-scan work items
+  int64_t n_ex = 0;
+};
+
+static EmuState* emu_state_of(Ctx& c) {
+  EmuState* st = (EmuState*)c.emu_state;
+  if (!st) {
+    st = new EmuState();
+    c.emu_state = st;
+    st->d_err = (int*)c.dalloc(sizeof(int));
+    CK(cudaMemsetAsync(st->d_err, 0, sizeof(int), c.stream));
+    c.d_emu_err = st->d_err;
+  }
+  return st;
+}
+
+EmuSet* emu_set_new(Ctx& c, int S, bool b_side) {
+  if (S < 3 || S > 6) throw ExpError{EXP_EINVAL, "emulated product: slice count outside 3..6"};
+  emu_state_of(c);
+  EmuSet* s = new EmuSet();
+  s->S = S;
+  s->b_side = b_side;
+  s->nh = c.cfg.real_arith ? 1 : 2;
+  return s;
+}
+
+void emu_set_free(Ctx& c, EmuSet* s) {
+  if (!s) return;
+  if (s->d) c.dfree(s->d);
+  if (s->sl) c.dfree(s->sl);
+  if (s->ex) c.dfree(s->ex);
+  delete s;
+}
+
+template <typename T>
+static void grow(Ctx& c, T*& p, int64_t& cap, int64_t need) {
+  if (need <= cap) return;
+  if (p) {
+    CK(cudaStreamSynchronize(c.stream));  // earlier launches may still read the old buffer
+    c.dfree(p);
+  }
+  cap = std::max<int64_t>(need, cap + cap / 2);
+  p = (T*)c.dalloc(sizeof(T) * size_t(cap));
+}
+
+template <int S>
+static void set_slice_s(Ctx& c, EmuSet* s, const cplx* src) {
+  const int np = int(s->h.size());
+  k_fill_int<<<dim3(int(std::max<int64_t>(1, std::min<int64_t>((s->n_ex + 255) / 256, 1024)))), 256, 0, c.stream>>>(
+      s->ex, s->n_ex, EXP_ZERO);
+  KCHECK(c);
+  if (s->n_scan) {
+    if (!s->b_side)
+      k_row_exp<<<dim3(row_exp_blocks(s->n_scan, c.sm_count), 1), 256, 0, c.stream>>>(s->d, np, src, 0, s->ex, 0,
+                                                                                   s->n_scan);
+    else
+      k_col_exp<<<dim3(unsigned(s->n_scan), 1), 256, 0, c.stream>>>(s->d, np, src, 0, s->ex, 0);
+    KCHECK(c);
+  }
+  if (!s->units) return;
+  if (!s->b_side)
+    k_split_a<S, false><<<dim3(split_blocks(s->units, c.sm_count), 1), 256, 0, c.stream>>>(s->d, np, s->units, src, 0,
+                                                                                          s->ex, 0, s->sl, 0);
+  else
+    k_split_b<S><<<dim3(split_blocks(s->units, c.sm_count), 1), 256, 0, c.stream>>>(s->d, np, s->units, src, 0, s->ex,
+                                                                                   0, s->sl, 0);
+  KCHECK(c);
+}
+
+void emu_set_slice(Ctx& c, EmuSet* s, const std::vector<EmuSetMat>& mats, const cplx* src) {
+  const int S = s->S, nh = s->nh;
+  const int BN = bn_of(S);
+  const int ocols = nh == 2 ? BN / 2 : BN;
+  s->h.clear();
+  int64_t sl = 0, ex = 0, u0 = 0, scan = 0;
+  for (const EmuSetMat& m : mats) {
+    if (m.rows < 0 || m.K < 0 || m.K > EMU_MAX_K) throw ExpError{EXP_EINVAL, "emulated product: member shape"};
+    EmuProb e{};
+    e.nh = nh;
+    e.K = m.K;
+    e.Kp = kp_of(m.K, nh);
+    const int nkb = e.Kp / KB;
+    if (!s->b_side) {
+      e.a_src = m.src;
+      e.M = m.rows;
+      e.tiles_m = (m.rows + BM - 1) / BM;
+      e.arows = e.tiles_m == 1 ? (m.rows + 7) / 8 * 8 : BM;
+      e.a_sl = sl;
+      e.a_ex = ex;
+      e.au0 = u0;
+      sl += int64_t(e.tiles_m) * nkb * S * e.arows * KB;
+      u0 += int64_t(e.tiles_m) * nkh_of(e) * e.arows * gpr_of(e);
+      scan += int64_t(m.rows) * std::max((m.K + ROW_KR - 1) / ROW_KR, 1);
+    } else {
+      e.b_src = m.src;
+      e.N = m.rows;
+      e.tiles_n = (m.rows + ocols - 1) / ocols;
+      e.brows = e.tiles_n == 1 ? (nh * m.rows + 7) / 8 * 8 : BN;
+      e.b_sl = sl;
+      e.b_ex = ex;
+      e.bu0 = u0;
+      sl += int64_t(e.tiles_n) * nkb * S * e.brows * KB;
+      u0 += int64_t(e.tiles_n) * nkh_of(e) * (e.brows / nh) * (KB / 8);
+      scan += int64_t((m.rows + 31) / 32) * std::max((m.K + 255) / 256, 1);
+    }
+    ex += m.rows;
+    s->h.push_back(e);
+  }
+  if (s->b_side && scan > INT32_MAX) throw ExpError{EXP_EINVAL, "emulated product: operand set too large"};
+  s->units = u0;
+  s->n_scan = scan;
+  s->n_ex = std::max<int64_t>(ex, 1);
+  if (s->h.empty()) return;
+  grow(c, s->sl, s->sl_cap, std::max<int64_t>(sl, 1));
+  grow(c, s->ex, s->ex_cap, s->n_ex);
+  grow(c, s->d, s->d_cap, int64_t(s->h.size()));
+  upload(c, s->d, s->h.data(), sizeof(EmuProb) * s->h.size());
+  switch (S) {
+    case 3: set_slice_s<3>(c, s, src); break;
+    case 4: set_slice_s<4>(c, s, src); break;
+    case 5: set_slice_s<5>(c, s, src); break;
+    default: set_slice_s<6>(c, s, src); break;
+  }
+}
+
+template <int S>
+static void set_multiply_s(Ctx& c, const EmuProb* d, int np, int n_tiles, const EmuSet* A, const EmuSet* B, cplx* C,
+                           cplx alpha, int* gerr) {
+  set_smem_attr<S>();
+  k_emu_gemm<S><<<dim3(std::min(n_tiles, std::max(c.sm_count, 1))), THREADS, Shape<S>::SMEM, c.stream>>>(
+      d, np, n_tiles, n_tiles, EMU_GM, A->sl, B->sl, A->ex, B->ex, C, 0, 0, 0, 0, 0, alpha, alpha_code(alpha), 0, gerr,
+      nullptr, 0, emu_wait_test());
+  KCHECK(c);
+}
+
+void emu_set_multiply(Ctx& c, const EmuSet* A, const EmuSet* B, const std::vector<EmuSetProd>& prods, cplx* C,
+                      cplx alpha) {
+  if (A->b_side || !B->b_side || A->S != B->S || A->nh != B->nh)
+    throw ExpError{EXP_EINVAL, "emulated product: operand sets do not match"};
+  const int S = A->S;
+  const int64_t cmax = max_chunks_per_split(S);
+  EmuState* st = emu_state_of(c);
+  std::vector<EmuProb>& h = st->set_recs;
+  h.clear();
+  int64_t tile0 = 0;
+  for (const EmuSetProd& t : prods) {
+    if (t.a < 0 || t.a >= int(A->h.size()) || t.b < 0 || t.b >= int(B->h.size()))
+      throw ExpError{EXP_EINVAL, "emulated product: member index"};
+    const EmuProb& a = A->h[t.a];
+    const EmuProb& b = B->h[t.b];
+    if (a.K != b.K) throw ExpError{EXP_EINVAL, "emulated product: members of different K"};
+    if (a.M == 0 || b.N == 0) continue;
+    EmuProb e{};
+    e.a_sl = a.a_sl;
+    e.a_ex = a.a_ex;
+    e.b_sl = b.b_sl;
+    e.b_ex = b.b_ex;
+    e.c_off = t.c_off;
+    e.M = a.M;
+    e.N = b.N;
+    e.K = a.K;
+    e.Kp = a.Kp;
+    e.nh = a.nh;
+    e.tiles_m = a.tiles_m;
+    e.tiles_n = b.tiles_n;
+    e.arows = a.arows;
+    e.brows = b.brows;
+    const int64_t chunks = (e.Kp / KB + KC_BLOCKS - 1) / KC_BLOCKS;
+    // one exact int64 accumulation per output: no split-K partials for these products
+    if (chunks > cmax) throw ExpError{EXP_EINVAL, "emulated product: K too long for one exact accumulation"};
+    e.ksplit = 1;
+    e.kcb = int32_t(chunks * KC_BLOCKS);
+    e.tile0 = int32_t(tile0);
+    tile0 += int64_t(e.tiles_m) * e.tiles_n;
+    if (tile0 > INT32_MAX) throw ExpError{EXP_EINVAL, "emulated product: too many output tiles in one launch"};
+    h.push_back(e);
+  }
+  if (h.empty()) return;
+  grow(c, st->set_d, st->set_cap, int64_t(h.size()));
+  upload(c, st->set_d, h.data(), sizeof(EmuProb) * h.size());
+  const int np = int(h.size()), nt = int(tile0);
+  switch (S) {
+    case 3: set_multiply_s<3>(c, st->set_d, np, nt, A, B, C, alpha, st->d_err); break;
+    case 4: set_multiply_s<4>(c, st->set_d, np, nt, A, B, C, alpha, st->d_err); break;
+    case 5: set_multiply_s<5>(c, st->set_d, np, nt, A, B, C, alpha, st->d_err); break;
+    default: set_multiply_s<6>(c, st->set_d, np, nt, A, B, C, alpha, st->d_err); break;
+  }
 }
 
 // ---------------------------------------------------------------------------

@@ -19,6 +19,8 @@ EXP_FP64, EXP_EMU_BF16, EXP_EMU_DS = 0, 1, 2
 EXP_GUESS_MP2, EXP_GUESS_USER = 0, 1
 STATUS = {0: "EXP_OK", 1: "EXP_EINVAL", 2: "EXP_ENOMEM", 3: "EXP_ECUDA", 4: "EXP_ENOTCONV",
           5: "EXP_ENUMERIC", 6: "EXP_ETIMEOUT", 7: "EXP_ESTATE"}
+(EXP_OK, EXP_EINVAL, EXP_ENOMEM, EXP_ECUDA, EXP_ENOTCONV, EXP_ENUMERIC, EXP_ETIMEOUT,
+ EXP_ESTATE) = range(8)
 
 
 class ExpError(RuntimeError):
@@ -45,6 +47,12 @@ class Config(C.Structure):
                 ("active_virt", C.POINTER(C.c_int32)), ("level_shift", C.c_double),
                 ("packed", C.c_int), ("n_slices_major", C.c_int),
                 ("denom_shift", C.c_double), ("denom_shift_n", C.c_int), ("real_arith", C.c_int)]
+
+
+class T3Info(C.Structure):
+    _fields_ = [("e_re", C.c_double), ("e_im", C.c_double), ("ms", C.c_double), ("macs", C.c_double),
+                ("macs_run", C.c_double), ("n_triples", C.c_int64), ("n_block_triples", C.c_int),
+                ("block", C.c_int)]
 
 
 class IterInfo(C.Structure):
@@ -78,6 +86,8 @@ def lib():
     L.exp_fs_sector_0h1p.restype = C.c_int
     L.exp_set_amplitudes.argtypes = [P, C.c_int, P, P]
     L.exp_work_per_iteration.argtypes = [P, C.POINTER(C.c_double)]
+    L.exp_ccsd_t.argtypes = [P, C.c_int, C.c_int, C.POINTER(T3Info), C.POINTER(C.c_double)]
+    L.exp_ccsd_t.restype = C.c_int
     L.exp_work_per_iteration.restype = C.c_int
     L.exp_profile_top.argtypes = [P, C.c_int, C.c_char_p, C.c_int, C.POINTER(C.c_double),
                                   C.POINTER(C.c_double)]
@@ -240,6 +250,19 @@ class Context:
             self._check(st)
         H = (heff[0::2] + 1j * heff[1::2]).reshape(na, na)
         return H, er + 1j * ei, nit.value, st
+
+    def ccsd_t(self, inst=0, per_triple=False, block=0):
+        """(T) correction of instance `inst` from its current amplitudes: (E(T), info dict,
+        per-triple energies or None).  The per-triple array holds the energy of each i<j<k
+        at index C(k,3) + C(j,2) + i.  block: occupied spinors per block (0: automatic)."""
+        info = T3Info()
+        n3 = self.n_occ * (self.n_occ - 1) * (self.n_occ - 2) // 6
+        buf = np.zeros(2 * max(n3, 1)) if per_triple else None
+        ptr = buf.ctypes.data_as(C.POINTER(C.c_double)) if per_triple else None
+        self._check(self.L.exp_ccsd_t(self.h, int(inst), int(block), C.byref(info), ptr))
+        d = {k: getattr(info, k) for k, _ in T3Info._fields_}
+        e3 = (buf[0:2 * n3:2] + 1j * buf[1:2 * n3:2]) if per_triple else None
+        return complex(info.e_re, info.e_im), d, e3
 
     def state(self, inst=0) -> int:
         """0 iterating, 1 converged, 2 failed."""

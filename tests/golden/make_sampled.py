@@ -1,7 +1,7 @@
 """Write sampled right-hand-side values of full-size workloads (calls only oracle/ and
 the seeded input module).
 
-    python tests/golden/make_sampled.py [c3]
+    python tests/golden/make_sampled.py [c3] [t3]
 
 For the precision workload o=60, v=400, Z8 (seed 3001): R2_ij^ab and R1_i^a of the CCSD
 equations (oracle/sampled.py, the right-hand sides of D t = R) at seeded trial
@@ -10,6 +10,9 @@ on sampled elements spread over all irreps: one virtual spinor per irrep and nin
 occupied spinors for R2 (every symmetry-allowed i<j, a<b), two virtuals per irrep and
 all occupied spinors for R1.  The dense oracle cannot hold these integrals (0.7 TB), so
 the oracle evaluates each requested element from integral slices generated on demand.
+
+For o=40, v=200, Z8 (seed 2001): the (T) energies e_ijk of sampled occupied triples at
+seeded trial amplitudes (seed 23), from oracle/triples.py triple_energy.
 """
 import json
 import os
@@ -25,6 +28,7 @@ from oracle import sampled  # noqa: E402
 from paper_2004_03682_gb300 import synthetic as syn  # noqa: E402
 
 C3 = dict(name="rhs_z8_o60_v400", seed=3001, n_occ=60, n_virt=400, G=8, trial_seed=17)
+T3_C2 = dict(name="t3_z8_o40_v200", seed=2001, n_occ=40, n_virt=200, G=8, trial_seed=23)
 
 
 def choose_samples(prob, n_occ_r2=9):
@@ -74,7 +78,47 @@ def sampled_rhs(spec):
     print(path, len(s2), len(s1), out["seconds"])
 
 
+def choose_triples(prob):
+    """Deterministic occupied triples i<j<k: the lowest spinor of each nonempty occupied
+    irrep, taken three at a time cyclically (mixed irreps), plus the three lowest spinors
+    of the largest irrep (one irrep) and the three highest occupied spinors."""
+    o, G = prob.n_occ, prob.G
+    go = prob.irrep_of[:o]
+    low = [int(np.nonzero(go == g)[0][0]) for g in range(G) if np.any(go == g)]
+    tri = set()
+    for n in range(len(low)):
+        t = sorted({low[n], low[(n + 1) % len(low)], low[(n + 2) % len(low)]})
+        if len(t) == 3:
+            tri.add(tuple(t))
+    big = int(np.argmax(np.bincount(go, minlength=G)))
+    idx = [int(x) for x in np.nonzero(go == big)[0][:3]]
+    if len(idx) == 3:
+        tri.add(tuple(idx))
+    tri.add((o - 3, o - 2, o - 1))
+    return sorted(tri)
+
+
+def sampled_t3(spec):
+    """(T) energies e_ijk of sampled occupied triples at seeded trial amplitudes
+    (oracle/triples.py triple_energy, integral slices from oracle/sampled.py)."""
+    from oracle import triples
+    prob = syn.make_problem(spec["seed"], spec["n_occ"], spec["n_virt"], spec["G"])
+    t0 = time.perf_counter()
+    t1, t2 = syn.trial_amplitudes(prob, spec["trial_seed"])
+    I = sampled.Integrals(prob)
+    tris = choose_triples(prob)
+    e3 = [triples.triple_energy(prob, I, t1, t2, i, j, k) for i, j, k in tris]
+    out = dict(spec, mp2_scale=I.s, triples=tris, e3=[[z.real, z.imag] for z in e3],
+               seconds=time.perf_counter() - t0,
+               source="oracle/triples.py triple_energy at synthetic.trial_amplitudes(prob, trial_seed)")
+    path = os.path.join(HERE, spec["name"] + ".json")
+    json.dump(out, open(path, "w"))
+    print(path, len(tris), out["seconds"])
+
+
 if __name__ == "__main__":
     which = sys.argv[1:] or ["c3"]
     if "c3" in which:
         sampled_rhs(C3)
+    if "t3" in which:
+        sampled_t3(T3_C2)

@@ -132,7 +132,7 @@ def solve(V, f, o, t1, t2, act, tol=1e-10, max_iter=300, diis_dim=6, shift=None)
         rho1[:, ~inactive] = 0.0
         d1, d2 = rho1 / D1s, rho2 / D2s
         d1[:, ~inactive] = 0.0
-        res = max(np.max(np.abs(d1)), np.max(np.abs(d2)))
+        res = max(np.max(np.abs(d1), initial=0.0), np.max(np.abs(d2), initial=0.0))
         new = np.concatenate([(s1 + d1).ravel(), (s2 + d2).ravel()])
         if res < tol:
             s1, s2 = new[:n1].reshape(s1.shape), new[n1:].reshape(s2.shape)

@@ -58,6 +58,10 @@ WORKLOADS = {
     # line reports time to the converged energy of the held-out set on four paths
     "family_o10_v40": dict(name="family_o10_v40", n_occ=10, n_virt=40, G=1, seed=4000, shift=0.0, slices=5,
                            family=True),
+    # the (T) correction of CCSD(T) at o=40 v=200 Z8, from the CCSD amplitudes of the
+    # o=40 v=200 workload (converged with level shift 8); one step = one evaluation
+    "triples_z8_o40_v200": dict(name="triples_z8_o40_v200", n_occ=40, n_virt=200, G=8, seed=2001, shift=8.0,
+                                slices=6, slices_major=5, triples=True),
 }
 DEFAULT_WORKLOAD = "ccsd_z8_o60_v400"
 WORKLOAD = WORKLOADS[DEFAULT_WORKLOAD]
@@ -440,6 +444,145 @@ def run_family(args):
         print(json.dumps(line))
 
 
+def _t3_cpu_leg(prob, t1, t2, seconds=20.0):
+    """The oracle's (T) (oracle.triples.triple_energy, integral slices generated on demand)
+    on as many occupied triples of the workload as fit in about `seconds` of host time,
+    after its one-time <bc||jk> block; modelled to corrections/s as (time per triple x
+    number of triples)^-1."""
+    from oracle import sampled, triples
+    o = prob.n_occ
+    t0 = time.perf_counter()
+    ints = sampled.Integrals(prob)
+    setup = time.perf_counter() - t0
+    done, t1s = 0, time.perf_counter()
+    tri = [(i, i + 1, i + 2) for i in range(0, o - 2, 3)]
+    for i, j, k in tri:
+        triples.triple_energy(prob, ints, t1, t2, i, j, k)
+        done += 1
+        if time.perf_counter() - t1s > seconds:
+            break
+    per = (time.perf_counter() - t1s) / max(done, 1)
+    n3 = o * (o - 1) * (o - 2) // 6
+    return {"value": 1.0 / (per * n3 + setup), "unit": "corrections/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"oracle triple_energy on {done} triples of the workload, {per:.2f} s each, plus "
+                      f"{setup:.1f} s for its integral setup; modelled on all {n3} triples"}
+
+
+def run_triples(args):
+    """One step = one (T) evaluation (exp_ccsd_t) at o=40 v=200 Z8 from the CCSD amplitudes
+    of that workload (iterated with level shift 8 until converged, or 400 iterations).
+    value = evaluations per second (device time, CUDA events on the context stream around
+    the K calls); effective FP64 TFLOP/s credits 8 flops per complex MAC the triples i<j<k
+    need.  Roofline: the stage with the larger device time (the block products, or the
+    per-triple energy kernel), from the call's own CUDA events.  Accuracy: E(T) of the
+    emulated path against the FP64 path on the same amplitudes."""
+    import numpy as np
+    import torch
+    from paper_2004_03682_gb300 import build, expgb
+    from paper_2004_03682_gb300 import synthetic as syn
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    build.build()
+    prob = syn.make_problem(WORKLOAD["seed"] + rank, WORKLOAD["n_occ"], WORKLOAD["n_virt"], WORKLOAD["G"])
+    E_, F_ = expgb.EXP_EMU_BF16, expgb.EXP_FP64
+    ctx = expgb.from_problems([prob], precision=E_ if args.precision == "emu" else F_, n_slices=args.slices,
+                              n_slices_major=args.slices_major, conv_tol=1e-8, max_iter=400, device=local,
+                              level_shift=WORKLOAD["shift"])
+    ctx.init_integrals([prob.seed])
+    _, conv, _ = ctx.iterate(400, raise_numeric=False)
+    e_ccsd = ctx.energy(0)
+    for _ in range(args.warmup):
+        ctx.ccsd_t(0)
+    torch.cuda.synchronize()
+    l0 = ctx.launches
+    infos = []
+    with Clocks(local) as clk:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(ctx.stream)
+        for _ in range(args.steps):
+            Et, info, _ = ctx.ccsd_t(0)
+            infos.append(info)
+        e1.record(ctx.stream)
+        torch.cuda.synchronize()
+    launches = ctx.launches - l0
+    ms = e0.elapsed_time(e1)
+    ms_max, n_all = aggregate_over_ranks(ms, args.steps, None, f"cuda:{local}")
+    info = infos[-1]
+    value = n_all / (ms_max / 1e3)
+    eff = info["macs"] * 8 * n_all / (ms_max * 1e-3) / 1e12
+    pk = peaks()
+    mp = float(np.mean([i["ms_products"] for i in infos]))
+    me = float(np.mean([i["ms_energy"] for i in infos]))
+    if mp >= me:
+        if args.precision == "emu":
+            pairs = args.slices * (args.slices + 1) // 2
+            ach = info["macs_run"] * 4 * pairs * 2 / (mp * 1e-3) / 1e12
+            roof = {"bound": "tensor", "kernel": f"k_emu_gemm<{args.slices}> ((T) block products, all launches of "
+                                                 "one evaluation)", "achieved": ach, "peak": pk["bf16"],
+                    "unit": "TFLOP/s", "frac": ach / pk["bf16"], "traffic": None,
+                    "peak_src": f"{pk['src']} bf16 dense (burst)", "ms_per_evaluation": mp}
+        else:
+            peak = pk["bf16"] * FP64_NOMINAL_TFLOPS / BF16_NOMINAL_TFLOPS
+            ach = info["macs_run"] * 8 / (mp * 1e-3) / 1e12
+            roof = {"bound": "tensor", "kernel": "k_gemm_fp64 ((T) block products)", "achieved": ach, "peak": peak,
+                    "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+                    "peak_src": f"FP64 = {pk['src']} bf16 x nominal FP64/BF16 ratio (1.25/2250)",
+                    "ms_per_evaluation": mp}
+    else:
+        # algorithmic bytes: the energy kernel reads each block-product element a triple needs
+        # once (16 B; t1, <bc||jk> and the index tables come from L2)
+        nbytes = info["x_elems"] * 16 * info["macs"] / max(info["macs_run"], 1.0)
+        ach = nbytes / (me * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": "k_t3_energy (per-triple energies, all launches of one evaluation)",
+                "achieved": ach, "peak": pk["hbm"], "unit": "GB/s", "frac": ach / pk["hbm"], "traffic": None,
+                "peak_src": f"{pk['src']} HBM copy", "ms_per_evaluation": me}
+    acc = None
+    if args.precision == "emu" and not args.no_accuracy and rank == 0:
+        t1, t2 = ctx.get_amplitudes(0)
+        ref = expgb.from_problems([prob], precision=F_, device=local)
+        ref.init_integrals([prob.seed])
+        ref.set_amplitudes(0, t1, t2)
+        Ef, inf_f, _ = ref.ccsd_t(0)
+        ref.close()
+        acc = {"E_T_emulated": [Et.real, Et.imag], "E_T_fp64": [Ef.real, Ef.imag], "dE_T": abs(Et - Ef),
+               "fp64_ms": inf_f["ms"]}
+    # e2e: the public API from host amplitudes (create, integrals, set amplitudes, one (T))
+    t1h, t2h = (x.cpu() for x in ctx.get_amplitudes(0))
+    ctx.close()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    c2 = expgb.from_problems([prob], precision=E_ if args.precision == "emu" else F_, n_slices=args.slices,
+                             device=local)
+    c2.init_integrals([prob.seed])
+    c2.set_amplitudes(0, t1h, t2h)
+    Ee, _, _ = c2.ccsd_t(0)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    c2.close()
+    e2e = {"value": 1.0 / e2e_s, "unit": "corrections/s", "h2d_bytes_per_step": (t1h.numel() + t2h.numel()) * 16,
+           "d2h_bytes_per_step": 16 * 8,
+           "includes": "exp_create + exp_init_integrals + exp_set_amplitudes (pinned copy of t1, t2) + exp_ccsd_t"}
+    cpu = _t3_cpu_leg(prob, t1h.numpy(), t2h.numpy()) if rank == 0 else None
+    line = {"metric": "ccsd_t_per_s", "value": value, "unit": "corrections/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": (f"bf16x{args.slices}-sliced f64 emulation (block products), double-single element arithmetic, "
+                      "FP64 sums") if args.precision == "emu" else "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD["name"], "n_occ": prob.n_occ, "n_virt": prob.n_virt, "irreps": "Z8",
+                       "seed": prob.seed, "ccsd_converged": bool(conv), "e_ccsd": [e_ccsd.real, e_ccsd.imag],
+                       "block": info["block"], "block_triples": info["n_block_triples"],
+                       "triples": info["n_triples"],
+                       "l2": "inputs larger than L2 (block-product outputs up to 16 GiB per block triple, "
+                             "dense t2 and <bc||jk> 1 GB each)"},
+            "E_T": [Et.real, Et.imag], "macs_needed": info["macs"], "macs_run": info["macs_run"],
+            "effective_fp64_tflops": eff, "ms_products": mp, "ms_energy": me, "roofline": roof,
+            "accuracy": acc, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary()}
+    if rank == 0:
+        print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -470,6 +613,8 @@ def main():
         return run_reference(args)
     if WORKLOAD.get("family"):
         return run_family(args)
+    if WORKLOAD.get("triples"):
+        return run_triples(args)
 
     import numpy as np
     import torch

@@ -208,10 +208,14 @@ exp_status exp_set_amplitudes(exp_ctx* ctx, int inst, const void* t1_dev, const 
 typedef struct {
   double e_re, e_im;     /* E(T), hartree */
   double ms;             /* device time of the call on the context stream (CUDA events) */
+  double ms_products;    /* of which the block-product launches (the connected contractions) */
+  double ms_energy;      /* of which the per-triple energy launches */
   double macs;           /* complex multiply-adds of the connected-triples contractions the
                             triples i<j<k need (the method's work) */
   double macs_run;       /* complex multiply-adds the block products executed (>= macs: a block
                             product also covers index orders no triple of the block uses) */
+  double x_elems;        /* complex elements the block products wrote (each read at most once by
+                            the energy kernel) */
   int64_t n_triples;     /* occupied triples i<j<k */
   int n_block_triples;   /* occupied block triples processed */
   int block;             /* occupied spinors per block */
@@ -226,8 +230,10 @@ typedef struct {
  *   E(T) = sum over i<j<k, a<b<c of conj(c + d) c / (e_i + e_j + e_k - e_a - e_b - e_c).
  * The connected contractions run as symmetry-blocked grouped products in the
  * context's precision (EXP_EMU_BF16: the BF16-sliced emulation with n_slices slices;
- * EXP_FP64: the FP64 kernel); the permutations, the disconnected term, the
- * denominators and every sum are FP64, and the result does not depend on the work
+ * EXP_FP64: the FP64 kernel).  The permutations, the disconnected term, the
+ * denominators and the energy terms run in FP64 under EXP_FP64 and in double-single
+ * FP32 (about 48 bits) under EXP_EMU_BF16; the sums over elements and triples are FP64
+ * in fixed order, so the result does not depend on the work
  * decomposition.  block: occupied spinors per block of the schedule (0: the largest
  * whose block products fit the scratch budget; a larger value than n_occ means
  * n_occ); every block size gives the same bits.  info (host, nullable) receives E(T)

@@ -28,10 +28,13 @@
 // members B_{p,h} are written and, in the emulated precision, sliced once.  For each
 // block triple I <= J <= K the three orderings (I; J x K), (J; I x K), (K; J x I)
 // gather their A members and run as one grouped product launch that writes X for
-// every (p; q, r) the block triple's i<j<k need; then one CTA per triple i<j<k forms
-// c (three X per P(a/bc) term), d, D and its energy, and writes that per-triple
-// energy.  A fixed-order sum of the per-triple energies gives E(T): the result does
-// not depend on the launch configuration.
+// every (p; q, r) the block triple's i<j<k need; then one CTA per triple i<j<k and
+// pair irrep of (b, c) forms c (three X per P(a/bc) term), d, D and its energy.
+// Fixed-order sums over the pair irreps, then over the triples, give the per-triple
+// energies and E(T): the result does not depend on the launch configuration.  The
+// element arithmetic runs in FP64 under EXP_FP64 and in double-single FP32 (about
+// 48 bits, each pair's sum added in FP64) under the emulated precision, where the
+// FP64 pipe would bound it.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -39,6 +42,7 @@
 
 #include "ccsd.h"
 #include "emu.h"
+#include "fpbits.h"
 #include "gen.h"
 
 namespace {
@@ -174,85 +178,153 @@ __device__ __forceinline__ cplx cmul(cplx a, cplx b) {
   return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-// Energy of one triple i<j<k per CTA: sum over a<b<c (a, b, c with G_a + G_b + G_c =
-// G_i + G_j + G_k) of conj(c + d) c / D.  Thread = pair (b, c), looping over a < b.
+// ---------------------------------------------------------------------------
+// Double-single arithmetic (x = hi + lo, two FP32 numbers, about 48 bits) for the
+// per-element work of the emulated precision: GB300's FP32 pipe runs many times its
+// FP64 rate.  Error-free sums (Knuth) and products (Dekker, through FMA) with the
+// rounding intrinsics, so the compiler cannot contract them.
+struct dsc {  // complex double-single
+  float2 re, im;
+};
+__device__ __forceinline__ float2 ds_norm(float s, float e) {  // |e| small against s
+  const float h = __fadd_rn(s, e);
+  return make_float2(h, __fsub_rn(e, __fsub_rn(h, s)));
+}
+__device__ __forceinline__ float2 ds_add(float2 a, float2 b) {
+  const float s = __fadd_rn(a.x, b.x);
+  const float z = __fsub_rn(s, a.x);
+  const float e = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, z)), __fsub_rn(b.x, z));
+  return ds_norm(s, __fadd_rn(e, __fadd_rn(a.y, b.y)));
+}
+__device__ __forceinline__ float2 ds_neg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 ds_mul(float2 a, float2 b) {
+  const float p = __fmul_rn(a.x, b.x);
+  const float e = __fmaf_rn(a.x, b.x, -p);
+  return ds_norm(p, __fmaf_rn(a.x, b.y, __fmaf_rn(a.y, b.x, e)));
+}
+// 1 / a: the FP32 reciprocal refined by one Newton step in double-single
+__device__ __forceinline__ float2 ds_rcp(float2 a) {
+  const float r = __frcp_rn(a.x);
+  const float2 q = ds_mul(a, make_float2(r, 0.f));
+  const float2 e = ds_add(make_float2(1.f, 0.f), ds_neg(q));
+  return ds_add(make_float2(r, 0.f), ds_mul(make_float2(r, 0.f), e));
+}
+__device__ __forceinline__ dsc dsc_of(cplx z) { return dsc{ds_split(z.x), ds_split(z.y)}; }
+__device__ __forceinline__ dsc dsc_add(dsc a, dsc b) { return dsc{ds_add(a.re, b.re), ds_add(a.im, b.im)}; }
+__device__ __forceinline__ dsc dsc_sub(dsc a, dsc b) { return dsc{ds_add(a.re, ds_neg(b.re)), ds_add(a.im, ds_neg(b.im))}; }
+__device__ __forceinline__ dsc dsc_mul(dsc a, dsc b) {
+  return dsc{ds_add(ds_mul(a.re, b.re), ds_neg(ds_mul(a.im, b.im))), ds_add(ds_mul(a.re, b.im), ds_mul(a.im, b.re))};
+}
+
+// Energy of one triple i<j<k and one pair irrep h of (b, c) per CTA: the sum over
+// a<b<c with G_b + G_c = h (and G_a = G_i + G_j + G_k - h) of conj(c + d) c / D.
+// Thread = pair (b, c) of h, looping over a < b.  The per-(ordering, pair irrep)
+// bases of the three X blocks and of the pair's rows are formed once per CTA.  DS:
+// the element arithmetic in double-single (the emulated precision), each pair's sum
+// added in FP64; otherwise FP64 throughout.  Output: e3h[idx G + h].
+template <bool DS>
 __global__ void __launch_bounds__(T3_THREADS) k_t3_energy(const T3Tri* __restrict__ tris, T3Block Bk, T3Tables T,
                                                           const cplx* __restrict__ X, const int64_t* __restrict__ xoff,
                                                           const int32_t* __restrict__ rowoff,
                                                           const cplx* __restrict__ t1, const cplx* __restrict__ V,
                                                           const double* __restrict__ eps, int o, int v,
-                                                          cplx* __restrict__ e3) {
+                                                          cplx* __restrict__ e3h) {
   const T3Tri tr = tris[blockIdx.x];
+  const int h = blockIdx.y;
   const int G = T.G;
+  __shared__ int64_t sxb[3][EXP_MAX_G];  // X block of ordering w, pair irrep hh: element offset
+  __shared__ int32_t srb[3][EXP_MAX_G];  // its first row of the triple's pair (q, r)
+  __shared__ int32_t snp[EXP_MAX_G];     // pairs per irrep
+  __shared__ double red[2][T3_THREADS / 32];
   const int P[3] = {tr.i, tr.j, tr.k}, Q[3] = {tr.j, tr.i, tr.j}, R[3] = {tr.k, tr.k, tr.i};
-  int slot[3], pl[3], gp[3];
-#pragma unroll
-  for (int w = 0; w < 3; ++w) {
-    slot[w] = (Q[w] - Bk.q0[w]) * Bk.nr[w] + (R[w] - Bk.r0[w]);
-    pl[w] = P[w] - Bk.p0[w];
-    gp[w] = T.go[P[w]];
+  if (int(threadIdx.x) < 3 * G) {
+    const int w = threadIdx.x / G, hh = threadIdx.x - w * G;
+    const int slot = (Q[w] - Bk.q0[w]) * Bk.nr[w] + (R[w] - Bk.r0[w]);
+    const int g = ((hh - T.go[P[w]]) % G + G) % G;
+    srb[w][hh] = rowoff[(w * G + g) * Bk.nb * Bk.nb + slot];
+    sxb[w][hh] = xoff[(w * Bk.nb + (P[w] - Bk.p0[w])) * G + hh];
   }
+  if (int(threadIdx.x) < G) snp[threadIdx.x] = T.npair[threadIdx.x];
+  __syncthreads();
   const int gijk = (T.go[tr.i] + T.go[tr.j] + T.go[tr.k]) % G;
-  const double eijk = eps[tr.i] + eps[tr.j] + eps[tr.k];
+  const int ga = ((gijk - h) % G + G) % G;
+  const int na = T.vcnt[ga], a0 = T.voff[ga];
+  const int n = snp[h];
+  const int32_t* pr = T.pairs + T.poff[h];
   const double* ev = eps + o;
-  const int nb2 = Bk.nb * Bk.nb;
+  const double eijk = eps[tr.i] + eps[tr.j] + eps[tr.k];
+  const int gx[3] = {T.go[tr.i], T.go[tr.j], T.go[tr.k]};
+  const int Yx[3] = {tr.j, tr.i, tr.j}, Zx[3] = {tr.k, tr.k, tr.i};
 
-  // Y(alpha; pair column col of irrep h) = X^(i;jk) - X^(j;ik) - X^(k;ji)
-  auto Y = [&](int alpha, int h, int col) {
-    const int al = alpha - T.voff[T.gv[alpha]];
-    const int64_t np = T.npair[h];
-    cplx y = make_double2(0.0, 0.0);
-#pragma unroll
-    for (int w = 0; w < 3; ++w) {
-      const int g = ((h - gp[w]) % G + G) % G;
-      const int64_t row = rowoff[(w * G + g) * nb2 + slot[w]] + al;
-      const cplx x = X[xoff[(w * Bk.nb + pl[w]) * G + h] + row * np + col];
-      if (w == 0) y = x;
-      else y = csub(y, x);
-    }
-    return y;
+  // Y(alpha; pair column col of irrep hh) = X^(i;jk) - X^(j;ik) - X^(k;ji)  (FP64 sums)
+  auto Y = [&](int alpha, int hh, int col) {
+    const int64_t al = alpha - T.voff[T.gv[alpha]];
+    const int64_t np = snp[hh];
+    const cplx x0 = X[sxb[0][hh] + (srb[0][hh] + al) * np + col];
+    const cplx x1 = X[sxb[1][hh] + (srb[1][hh] + al) * np + col];
+    const cplx x2 = X[sxb[2][hh] + (srb[2][hh] + al) * np + col];
+    return make_double2(x0.x - x1.x - x2.x, x0.y - x1.y - x2.y);
   };
-  // <bc||yz> from the dense V[y][z][b][c], t1[x][a]
   auto Vv = [&](int b, int c, int y, int z) { return V[((int64_t(y) * o + z) * v + b) * v + c]; };
-  auto t = [&](int x, int a) { return t1[int64_t(x) * v + a]; };
 
   double sr = 0.0, si = 0.0;
-  for (int h = 0; h < G; ++h) {
-    const int ga = ((gijk - h) % G + G) % G;
-    const int na = T.vcnt[ga], a0 = T.voff[ga];
-    const int n = T.npair[h];
-    const int32_t* pr = T.pairs + T.poff[h];
-    for (int u = threadIdx.x; u < n; u += blockDim.x) {
-      const int b = pr[u] >> 16, c = pr[u] & 0xFFFF;
-      const double ebc = ev[b] + ev[c];
-      for (int a = a0; a < a0 + na && a < b; ++a) {
-        // c_abc = Y(a; bc) - Y(b; ac) + Y(c; ab)
-        const int hac = (T.gv[a] + T.gv[c]) % G, hab = (T.gv[a] + T.gv[b]) % G;
-        const int cac = T.pidx[a * v + c] - 1, cab = T.pidx[a * v + b] - 1;
-        const cplx cc = cadd(csub(Y(a, h, u), Y(b, hac, cac)), Y(c, hab, cab));
-        // d_abc = P(i/jk) P(a/bc) t_i^a <bc||jk>
-        cplx d = make_double2(0.0, 0.0);
-        const int X3[3] = {tr.i, tr.j, tr.k}, Y3[3] = {tr.j, tr.i, tr.j}, Z3[3] = {tr.k, tr.k, tr.i};
+  for (int u = threadIdx.x; u < n; u += blockDim.x) {
+    const int b = pr[u] >> 16, c = pr[u] & 0xFFFF;
+    const int gb = T.gv[b], gc = T.gv[c];
+    const double dbc = eijk - ev[b] - ev[c];
+    double pr_re = 0.0, pr_im = 0.0;                          // FP64 path: this pair's sum
+    float2 ar = make_float2(0.f, 0.f), ai = make_float2(0.f, 0.f);  // DS path
+    const float2 dbc_ds = DS ? ds_split(dbc) : make_float2(0.f, 0.f);
+    for (int a = a0; a < a0 + na && a < b; ++a) {
+      // c_abc = Y(a; bc) - Y(b; ac) + Y(c; ab)
+      const int hac = (ga + gc) % G, hab = (ga + gb) % G;
+      const int cac = T.pidx[a * v + c] - 1, cab = T.pidx[a * v + b] - 1;
+      const cplx y1 = Y(a, h, u), y2 = Y(b, hac, cac), y3 = Y(c, hab, cab);
+      if (DS) {
+        const dsc cc = dsc_add(dsc_sub(dsc_of(y1), dsc_of(y2)), dsc_of(y3));
+        // d_abc = P(i/jk) P(a/bc) t_i^a <bc||jk>: only t1 of matching irreps is nonzero
+        dsc d = dsc{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
 #pragma unroll
         for (int w = 0; w < 3; ++w) {
-          const int x = X3[w], y = Y3[w], z = Z3[w];
-          cplx s = make_double2(0.0, 0.0);
-          if (T.gv[a] == T.go[x]) s = cadd(s, cmul(t(x, a), Vv(b, c, y, z)));
-          if (T.gv[b] == T.go[x]) s = csub(s, cmul(t(x, b), Vv(a, c, y, z)));
-          if (T.gv[c] == T.go[x]) s = csub(s, cmul(t(x, c), Vv(b, a, y, z)));
-          if (w == 0) d = s;
-          else d = csub(d, s);
+          const int x = P[w], y = Yx[w], z = Zx[w];
+          const bool neg = w > 0;
+          if (ga == gx[w]) { const dsc s = dsc_mul(dsc_of(t1[int64_t(x) * v + a]), dsc_of(Vv(b, c, y, z))); d = neg ? dsc_sub(d, s) : dsc_add(d, s); }
+          if (gb == gx[w]) { const dsc s = dsc_mul(dsc_of(t1[int64_t(x) * v + b]), dsc_of(Vv(a, c, y, z))); d = neg ? dsc_add(d, s) : dsc_sub(d, s); }
+          if (gc == gx[w]) { const dsc s = dsc_mul(dsc_of(t1[int64_t(x) * v + c]), dsc_of(Vv(b, a, y, z))); d = neg ? dsc_add(d, s) : dsc_sub(d, s); }
         }
-        const double D = eijk - ev[a] - ebc;
-        const double wr = cc.x + d.x, wi = cc.y + d.y;
-        // conj(c + d) c / D
-        sr += (wr * cc.x + wi * cc.y) / D;
-        si += (wr * cc.y - wi * cc.x) / D;
+        const dsc wv = dsc_add(cc, d);
+        const float2 rD = ds_rcp(ds_add(dbc_ds, ds_neg(ds_split(ev[a]))));
+        // conj(w) c / D
+        const float2 pre = ds_add(ds_mul(wv.re, cc.re), ds_mul(wv.im, cc.im));
+        const float2 pim = ds_add(ds_mul(wv.re, cc.im), ds_neg(ds_mul(wv.im, cc.re)));
+        ar = ds_add(ar, ds_mul(pre, rD));
+        ai = ds_add(ai, ds_mul(pim, rD));
+      } else {
+        const cplx cc = make_double2(y1.x - y2.x + y3.x, y1.y - y2.y + y3.y);
+        double dr = 0.0, di = 0.0;
+#pragma unroll
+        for (int w = 0; w < 3; ++w) {
+          const int x = P[w], y = Yx[w], z = Zx[w];
+          const double sg = w > 0 ? -1.0 : 1.0;
+          if (ga == gx[w]) { const cplx s = cmul(t1[int64_t(x) * v + a], Vv(b, c, y, z)); dr += sg * s.x; di += sg * s.y; }
+          if (gb == gx[w]) { const cplx s = cmul(t1[int64_t(x) * v + b], Vv(a, c, y, z)); dr -= sg * s.x; di -= sg * s.y; }
+          if (gc == gx[w]) { const cplx s = cmul(t1[int64_t(x) * v + c], Vv(b, a, y, z)); dr -= sg * s.x; di -= sg * s.y; }
+        }
+        const double rD = 1.0 / (dbc - ev[a]);
+        const double wr = cc.x + dr, wi = cc.y + di;
+        pr_re += (wr * cc.x + wi * cc.y) * rD;
+        pr_im += (wr * cc.y - wi * cc.x) * rD;
       }
+    }
+    if (DS) {
+      sr += ds_to_double(ar.x, ar.y);
+      si += ds_to_double(ai.x, ai.y);
+    } else {
+      sr += pr_re;
+      si += pr_im;
     }
   }
   // fixed-order block reduction
-  __shared__ double red[2][T3_THREADS / 32];
   for (int off = 16; off; off >>= 1) {
     sr += __shfl_down_sync(0xffffffffu, sr, off);
     si += __shfl_down_sync(0xffffffffu, si, off);
@@ -264,12 +336,25 @@ __global__ void __launch_bounds__(T3_THREADS) k_t3_energy(const T3Tri* __restric
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double a = 0.0, b = 0.0;
+    double x = 0.0, y = 0.0;
     for (int w = 0; w < int(blockDim.x >> 5); ++w) {
-      a += red[0][w];
-      b += red[1][w];
+      x += red[0][w];
+      y += red[1][w];
     }
-    e3[tr.idx] = make_double2(a, b);
+    e3h[int64_t(tr.idx) * G + h] = make_double2(x, y);
+  }
+}
+
+// per-triple energy = sum over the pair irreps of its parts, fixed order
+__global__ void __launch_bounds__(T3_THREADS) k_t3_fold(const cplx* __restrict__ e3h, int64_t n, int G,
+                                                        cplx* __restrict__ e3) {
+  for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < n; t += int64_t(gridDim.x) * blockDim.x) {
+    double x = 0.0, y = 0.0;
+    for (int h = 0; h < G; ++h) {
+      x += e3h[t * G + h].x;
+      y += e3h[t * G + h].y;
+    }
+    e3[t] = make_double2(x, y);
   }
 }
 
@@ -634,7 +719,8 @@ void ccsd_t(Ctx& c, int inst, int block, exp_t3_info* info, double* per_triple) 
   cplx* Abuf = (cplx*)sc.get(sizeof(cplx) * size_t(std::max<int64_t>(max_a, 1)));
   cplx* X = (cplx*)sc.get(sizeof(cplx) * size_t(std::max<int64_t>(max_x, 1)));
   cplx* e3 = (cplx*)sc.get(sizeof(cplx) * size_t(std::max<int64_t>(ntri, 1)));
-  CK(cudaMemsetAsync(e3, 0, sizeof(cplx) * size_t(std::max<int64_t>(ntri, 1)), c.stream));
+  cplx* e3h = (cplx*)sc.get(sizeof(cplx) * size_t(std::max<int64_t>(ntri, 1)) * G);  // per (triple, pair irrep)
+  CK(cudaMemsetAsync(e3h, 0, sizeof(cplx) * size_t(std::max<int64_t>(ntri, 1)) * G, c.stream));
   const size_t nb2 = size_t(nb) * nb;
   int32_t* d_rowoff = (int32_t*)sc.get(sizeof(int32_t) * 3 * G * nb2);
   int64_t* d_xoff = (int64_t*)sc.get(sizeof(int64_t) * 3 * size_t(nb) * G);
@@ -642,15 +728,30 @@ void ccsd_t(Ctx& c, int inst, int block, exp_t3_info* info, double* per_triple) 
   T3AUnit* d_units = (T3AUnit*)sc.get(sizeof(T3AUnit) * 3 * G * nb2);
   GemmProb* d_fp = (GemmProb*)sc.get(sizeof(GemmProb) * 3 * size_t(nb) * G);
 
-  double macs_need = 0.0, macs_run = 0.0;
+  double macs_need = 0.0, macs_run = 0.0, x_total = 0.0;
   int n_bt = 0;
   BlockPlan bp;
+  // per block triple: events around its product launch and its energy launch
+  std::vector<cudaEvent_t> evs;
+  struct EvGuard {
+    std::vector<cudaEvent_t>& e;
+    ~EvGuard() {
+      for (auto x : e) cudaEventDestroy(x);
+    }
+  } evg{evs};
+  auto mark = [&]() {
+    cudaEvent_t e;
+    CK(cudaEventCreate(&e));
+    evs.push_back(e);
+    CK(cudaEventRecord(e, c.stream));
+  };
   for (int I = 0; I < nblk; ++I)
     for (int J = I; J < nblk; ++J)
       for (int K = J; K < nblk; ++K) {
         plan_block(H, nb, I, J, K, boff, bp, true);
         if (bp.tris.empty()) continue;
         ++n_bt;
+        x_total += double(bp.x_elems);
         macs_need += bp.macs_need;
         macs_run += bp.macs_run;
         // A members
@@ -661,8 +762,9 @@ void ccsd_t(Ctx& c, int inst, int block, exp_t3_info* info, double* per_triple) 
         }
         for (auto& z : bp.zeros) CK(cudaMemsetAsync(X + z.first, 0, sizeof(cplx) * size_t(z.second), c.stream));
         // X = A B for every product of the three orderings
+        if (emulated) emu_set_slice(c, sc.A, bp.amats, Abuf);
+        mark();
         if (emulated) {
-          emu_set_slice(c, sc.A, bp.amats, Abuf);
           emu_set_multiply(c, sc.A, sc.B, bp.prods, X, make_double2(1.0, 0.0));
         } else if (!bp.fprods.empty()) {
           GemmPlan g;
@@ -683,15 +785,28 @@ void ccsd_t(Ctx& c, int inst, int block, exp_t3_info* info, double* per_triple) 
           OneInstance one(c);
           launch_gemm_fp64(c, g, Abuf, Bbuf, X, 0, 0, 0, make_double2(1.0, 0.0), false);
         }
+        mark();
         // energies of the block triple's i<j<k
         upload(c, d_rowoff, bp.rowoff.data(), sizeof(int32_t) * bp.rowoff.size());
         upload(c, d_xoff, bp.xoff.data(), sizeof(int64_t) * bp.xoff.size());
         upload(c, d_tris, bp.tris.data(), sizeof(T3Tri) * bp.tris.size());
-        k_t3_energy<<<unsigned(bp.tris.size()), T3_THREADS, 0, c.stream>>>(d_tris, bp.bk, DT.T, X, d_xoff, d_rowoff, t1d,
-                                                                            Vd, eps, o, v, e3);
+        mark();
+        const dim3 eg(unsigned(bp.tris.size()), unsigned(G));
+        if (emulated)
+          k_t3_energy<true><<<eg, T3_THREADS, 0, c.stream>>>(d_tris, bp.bk, DT.T, X, d_xoff, d_rowoff, t1d, Vd, eps, o, v,
+                                                             e3h);
+        else
+          k_t3_energy<false><<<eg, T3_THREADS, 0, c.stream>>>(d_tris, bp.bk, DT.T, X, d_xoff, d_rowoff, t1d, Vd, eps, o,
+                                                              v, e3h);
         KCHECK(c);
+        mark();
       }
   cplx* d_E = (cplx*)sc.get(sizeof(cplx));
+  if (ntri) {
+    k_t3_fold<<<unsigned(std::min<int64_t>((ntri + T3_THREADS - 1) / T3_THREADS, 4096)), T3_THREADS, 0, c.stream>>>(
+        e3h, ntri, G, e3);
+    KCHECK(c);
+  }
   k_t3_sum<<<1, T3_THREADS, 0, c.stream>>>(e3, ntri, d_E);
   KCHECK(c);
   CK(cudaEventRecord(sc.ev[1], c.stream));
@@ -707,15 +822,28 @@ void ccsd_t(Ctx& c, int inst, int block, exp_t3_info* info, double* per_triple) 
   }
   float ms = 0.f;
   CK(cudaEventElapsedTime(&ms, sc.ev[0], sc.ev[1]));
+  double ms_prod = 0.0, ms_en = 0.0;
+  for (size_t k = 0; k + 3 < evs.size(); k += 4) {
+    float a = 0.f, b = 0.f;
+    CK(cudaEventElapsedTime(&a, evs[k], evs[k + 1]));
+    CK(cudaEventElapsedTime(&b, evs[k + 2], evs[k + 3]));
+    ms_prod += a;
+    ms_en += b;
+  }
   if (c.profile)
-    fprintf(stderr, "[exp_t3] o=%d v=%d G=%d nb=%d block triples %d: %.3f ms, %.3e needed / %.3e run complex MACs\n", o,
-            v, G, nb, n_bt, ms, macs_need, macs_run);
+    fprintf(stderr,
+            "[exp_t3] o=%d v=%d G=%d nb=%d block triples %d: %.3f ms (products %.3f, energies %.3f), %.3e needed / "
+            "%.3e run complex MACs\n",
+            o, v, G, nb, n_bt, ms, ms_prod, ms_en, macs_need, macs_run);
   if (info) {
     info->e_re = E.x;
     info->e_im = E.y;
     info->ms = ms;
+    info->ms_products = ms_prod;
+    info->ms_energy = ms_en;
     info->macs = macs_need;
     info->macs_run = macs_run;
+    info->x_elems = x_total;
     info->n_triples = ntri;
     info->n_block_triples = n_bt;
     info->block = nb;

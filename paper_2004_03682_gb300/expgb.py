@@ -50,8 +50,9 @@ class Config(C.Structure):
 
 
 class T3Info(C.Structure):
-    _fields_ = [("e_re", C.c_double), ("e_im", C.c_double), ("ms", C.c_double), ("macs", C.c_double),
-                ("macs_run", C.c_double), ("n_triples", C.c_int64), ("n_block_triples", C.c_int),
+    _fields_ = [("e_re", C.c_double), ("e_im", C.c_double), ("ms", C.c_double), ("ms_products", C.c_double),
+                ("ms_energy", C.c_double), ("macs", C.c_double),
+                ("macs_run", C.c_double), ("x_elems", C.c_double), ("n_triples", C.c_int64), ("n_block_triples", C.c_int),
                 ("block", C.c_int)]
 
 

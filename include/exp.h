@@ -186,6 +186,28 @@ exp_status exp_energy(exp_ctx* ctx, int inst, double* e_re, double* e_im);
 exp_status exp_fs_sector_0h1p(exp_ctx* ctx, int inst, double* heff, double* eig_re, double* eig_im,
                               int* n_iter);
 
+/* Step V for the (0h,2p) sector (Eq. (sectors), the next sector after (0h,1p); the
+ * paper's KCs2+ -> KCs scheme reaches KCs through it): with T and the (0h,1p)
+ * amplitudes converged and fixed (the (0h,1p) sector is run first when it has not
+ * been), solve for the two-valence-particle amplitudes s_xy^ab (x < y active, a < b
+ * not both active) the Bloch equation projected on the two-particle determinants,
+ *   Q Hbar Omega P = Q Omega P H_eff,   H_eff = P Hbar Omega P,   Omega = {exp(S1 + S2)},
+ * in connected form: rho_xy^ab = [Hbar Omega]_conn - sum_z s_zy^ab H1_zx
+ * - sum_w s_xw^ab H1_wy - 1/2 sum_zw tau_zw^ab H2_zw,xy (H1 the (0h,1p) H_eff, H2 the
+ * connected two-particle part, tau_zw^ab = s_zw^ab + c_z^a c_w^b - c_z^b c_w^a with
+ * c = P + S1), iterated s <- s + rho / (e_x + e_y - e_a - e_b) with DIIS through the same
+ * grouped contraction launches; then H_eff = H1 (x) 1 + 1 (x) H1 + H2 on the pairs is
+ * diagonalised per pair irrep on the device.  Reports instance `inst`: heff (host,
+ * npair^2 (re, im), npair = n_active (n_active - 1) / 2; row = pair (z, w), column =
+ * pair (x, y), pairs x < y in the order (0,1), (0,2), ..., (1,2), ... of the active
+ * slots; nullable), eig_re / eig_im (host, npair, sorted by real then imaginary part:
+ * double-attachment energies relative to the CCSD ground state), *n_iter (nullable).
+ * ESTATE with fewer than two active spinors or when the (0h,1p) sector did not
+ * converge; EINVAL when a pair-irrep block exceeds 32 pairs; ENOTCONV if the
+ * (0h,2p) iteration did not converge within max_iter. */
+exp_status exp_fs_sector_0h2p(exp_ctx* ctx, int inst, double* heff, double* eig_re, double* eig_im,
+                              int* n_iter);
+
 /* Zero-shift extrapolation of results computed with denominator shifts (Sec. II.A;
  * Sec. III.A: dynamic shifts with Pade extrapolation to the zero-shift limit): the
  * values E_k (m complex numbers, (re, im) pairs, host) at scales x_k (m doubles, host)

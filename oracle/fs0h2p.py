@@ -260,3 +260,79 @@ def solve(V, f, o, t1, t2, e_cc, act, s1, s2, tol=1e-10, max_iter=300, diis_dim=
         s = new
     w = np.linalg.eigvals(Heff)
     return Heff, w[np.lexsort((w.imag, w.real))], s, pairs, qpairs, max_iter, False
+
+
+def solve_ghost(V, f, o, t1, t2, act, s1, s2, tol=1e-11, max_iter=500):
+    """The same sector built a second way, for sizes the determinant basis cannot hold:
+    every active spinor x becomes a non-interacting occupied "ghost" g_x (no integrals,
+    zero orbital energy) whose CCSD amplitudes carry the valence amplitudes (t_{g_x}^a =
+    s_x^a with t_{g_x}^x = 1, t_{g_x j}^{ab} = s_xj^ab, t_{g_x g_y}^{ab} = s_xy^ab), so the
+    connected part of Hbar Omega |xy> is the CCSD doubles residual of oracle.ccsd at
+    (g_x, g_y).  The disconnected products of the Bloch equation cancel against the
+    (0h,1p) equations, leaving
+        rho_xy^ab = R_{g_x g_y}^{ab} - sum_z s_zy^ab H1_zx - sum_w s_xw^ab H1_wy
+                    - 1/2 sum_zw tau_zw^ab H2_zw,xy,
+    H1 the (0h,1p) H_eff (the singles residual at the active columns), H2_zw,xy the
+    doubles residual at (a, b) = (z, w) and tau_zw^ab = s_zw^ab + c_z^a c_w^b - c_z^b c_w^a.
+    H_eff = H1 (x) 1 + 1 (x) H1 + H2 on the pairs x < y.  Returns (H_eff, sorted
+    eigenvalues, converged)."""
+    n = f.shape[0]
+    nv = n - o
+    na = len(act)
+    no = o + na
+    idx = np.r_[np.arange(o), no + np.arange(nv)]  # real spinors in the extended order
+    Ve = np.zeros((no + nv,) * 4, complex)
+    Ve[np.ix_(idx, idx, idx, idx)] = V
+    fe = np.zeros((no + nv, no + nv), complex)
+    fe[np.ix_(idx, idx)] = f
+    b = ccsd.Blocks(Ve, fe, no)
+    t1e = np.zeros((no, nv), complex)
+    t1e[:o] = t1
+    t1e[o:] = s1
+    t1e[o + np.arange(na), act] = 1.0  # P
+    t2e = np.zeros((no, no, nv, nv), complex)
+    t2e[:o, :o] = t2
+    t2e[o:, :o] = s2
+    t2e[:o, o:] = -s2.transpose(1, 0, 2, 3)
+    actset = set(int(a) for a in act)
+    # the unknowns: x<y, a<b, not both a and b active; each step is taken on these and
+    # written into the four antisymmetric copies (a step on all copies separately lets
+    # rounding grow a symmetric part that the equations do not damp)
+    up = np.zeros((na, na, nv, nv), bool)
+    for x, y in itertools.combinations(range(na), 2):
+        for a, bq in itertools.combinations(range(nv), 2):
+            up[x, y, a, bq] = not (a in actset and bq in actset)
+
+    def anti(u):
+        full = np.zeros((na, na, nv, nv), complex)
+        full[up] = u
+        return full - full.transpose(1, 0, 2, 3) - full.transpose(0, 1, 3, 2) + full.transpose(1, 0, 3, 2)
+
+    eps = np.real(np.diag(f))
+    ex, ev = eps[o + act], eps[o:]
+    D = ex[:, None, None, None] + ex[None, :, None, None] - ev[None, None, :, None] - ev[None, None, None, :]
+    sg = np.zeros((na, na, nv, nv), complex)
+    diis = ccsd.DIIS(6)
+    for it in range(max_iter):
+        t2e[o:, o:] = sg
+        r1, r2 = ccsd.residual(t1e, t2e, b)
+        H1 = r1[o:, act].T                                   # H1[z, x]
+        c = t1e[o:]
+        tau = sg + np.einsum("za,wb->zwab", c, c) - np.einsum("zb,wa->zwab", c, c)
+        H2 = r2[o:, o:][:, :, act][:, :, :, act].transpose(2, 3, 0, 1)  # H2[z, w, x, y]
+        rho = (r2[o:, o:] - np.einsum("zyab,zx->xyab", sg, H1) - np.einsum("xwab,wy->xyab", sg, H1)
+               - 0.5 * np.einsum("zwab,zwxy->xyab", tau, H2))
+        d = rho[up] / D[up]
+        res = np.max(np.abs(d), initial=0.0)
+        new = sg[up] + d
+        if res < tol:
+            sg = anti(new)
+            break
+        diis.push(new, d)
+        sg = anti(diis.extrapolate())
+    pairs = [(x, y) for x in range(na) for y in range(x + 1, na)]
+    I = np.eye(na)
+    Hp = np.array([[H1[z, x] * I[w, y] + I[z, x] * H1[w, y] - H1[w, x] * I[z, y] - I[w, x] * H1[z, y] + H2[z, w, x, y]
+                    for x, y in pairs] for z, w in pairs])
+    w = np.linalg.eigvals(Hp)
+    return Hp, w[np.lexsort((w.imag, w.real))], res < tol

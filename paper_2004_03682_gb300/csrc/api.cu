@@ -369,6 +369,14 @@ extern "C" exp_status exp_fs_sector_0h1p(exp_ctx* x, int inst, double* heff, dou
   API_END(x)
 }
 
+extern "C" exp_status exp_fs_sector_0h2p(exp_ctx* x, int inst, double* heff, double* eig_re, double* eig_im,
+                                         int* n_iter) {
+  API_BEGIN
+  if (!x) throw ExpError{EXP_EINVAL, "null context"};
+  return fs2_entry(x->c, inst, heff, eig_re, eig_im, n_iter);
+  API_END(x)
+}
+
 extern "C" exp_status exp_get_amplitudes(exp_ctx* x, int inst, void* t1, void* t2) {
   API_BEGIN
   if (!x || !t1 || !t2) throw ExpError{EXP_EINVAL, "null argument"};

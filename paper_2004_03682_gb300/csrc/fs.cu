@@ -9,13 +9,17 @@
 // index (the same TTGT engine).  H_eff is diagonalised per irrep block on the
 // device (Hessenberg reduction + Wilkinson-shifted QR, complex FP64).
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <complex>
+#include <map>
 
 #include "ccsd.h"
 #include "fs.h"
 
-enum : int8_t { ROLE_REAL = 0, ROLE_Q = 1, ROLE_P = 2, ROLE_ZERO = 3 };
+// ROLE_MIRROR: a copy of an unknown under the antisymmetry of t2, written from its canonical
+// element after every step
+enum : int8_t { ROLE_REAL = 0, ROLE_Q = 1, ROLE_P = 2, ROLE_ZERO = 3, ROLE_MIRROR = 4 };
 
 struct HPair {
   int64_t src;   // offset of t1(a = act[y], i = g_x) in the amplitude vector
@@ -39,12 +43,19 @@ struct FsState {
   bool converged = false;
   int n_iter = 0;
   std::vector<cplx> h_heff, h_eig;
+  void* fs2 = nullptr;  // the (0h,2p) sector's state (Fs2State, below)
+  int64_t* d_mir = nullptr;  // mirrored copies of the one-ghost doubles
+  int64_t n_mir = 0;
 };
 
 static FsState& F(Ctx& c) { return *reinterpret_cast<FsState*>(c.fs_state); }
 
+static void fs2_release(FsState& s);
+
 void fs_release(Ctx& c) {
-  delete reinterpret_cast<FsState*>(c.fs_state);
+  FsState* s = reinterpret_cast<FsState*>(c.fs_state);
+  if (s) fs2_release(*s);
+  delete s;
   c.fs_state = nullptr;
 }
 
@@ -260,6 +271,68 @@ __global__ void k_fs_eig(const cplx* __restrict__ heff, int nact, const int* __r
   for (int r = 0; r < n; ++r) eig[int64_t(inst) * nact + b0 + r] = make_double2(H[r][r].re, H[r][r].im);
 }
 
+// copies of the canonical unknowns: Tn[dst] = +-Tn[src] in the slot k_fs_update wrote
+__global__ void k_fs_mirror(const int64_t* __restrict__ mir, int64_t n, cplx* __restrict__ Tn, int64_t namp, int dim,
+                            const int* __restrict__ state) {
+  const int inst = blockIdx.y;
+  const int* st = state + inst * 4;
+  if (st[2]) return;
+  const int slot = dim > 0 ? (st[1] + 1) % dim : 0;
+  cplx* T = Tn + (int64_t(inst) * (dim > 0 ? dim : 1) + slot) * namp;
+  for (int64_t k = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; k < n; k += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t d = mir[2 * k], sw = mir[2 * k + 1];
+    const int64_t s = sw & 0x7FFFFFFFFFFFFFFFll;
+    const cplx v = T[s];
+    T[d] = sw < 0 ? make_double2(-v.x, -v.y) : v;
+  }
+}
+
+__global__ void k_set_roles(int8_t* __restrict__ role, const int64_t* __restrict__ idx, int64_t n, int stride,
+                            int8_t value) {
+  for (int64_t k = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; k < n; k += int64_t(gridDim.x) * blockDim.x)
+    role[idx[k * stride]] = value;
+}
+
+// Element offsets in a blocked rank-4 layout from a table of its sub-blocks per irrep tuple.
+struct BlockAddr {
+  int G = 1;
+  int sp[4] = {0, 0, 0, 0};
+  int64_t base_off = 0;  // added to every offset (the t2 part of the amplitude vector)
+  std::vector<SubBlock> sb;
+  std::vector<const SubBlock*> tab;
+  std::vector<int> irr[SP_COUNT], off[SP_COUNT];
+  BlockAddr(const Ctx& c, const Layout& L, int64_t base) : G(c.G), base_off(base) {
+    for (int k = 0; k < 4; ++k) sp[k] = L.sp[k];
+    enumerate_blocks(L, c.spaces, sb);
+    tab.assign(size_t(G) * G * G * G, nullptr);
+    for (auto& b : sb) tab[((size_t(b.irr[0]) * G + b.irr[1]) * G + b.irr[2]) * G + b.irr[3]] = &b;
+    for (int s = 0; s < SP_COUNT; ++s) {
+      const Space& S = c.spaces[s];
+      irr[s].assign(S.n, 0);
+      off[s] = S.off;
+      for (int g = 0; g < G; ++g)
+        for (int k = 0; k < S.cnt[g]; ++k) irr[s][S.off[g] + k] = g;
+    }
+  }
+  int64_t at(int i0, int i1, int i2, int i3) const {
+    const int i[4] = {i0, i1, i2, i3};
+    int g[4];
+    for (int k = 0; k < 4; ++k) g[k] = irr[sp[k]][i[k]];
+    const SubBlock* B = tab[((size_t(g[0]) * G + g[1]) * G + g[2]) * G + g[3]];
+    if (!B) return -1;
+    int64_t o = B->base;
+    for (int k = 0; k < 4; ++k) o += (i[k] - off[sp[k]][g[k]]) * B->st[k];
+    return base_off + o;
+  }
+};
+
+// mirror entry: destination, source with the sign in bit 63
+static void add_mirror(std::vector<int64_t>& m, int64_t dst, int64_t src, bool neg) {
+  if (dst < 0 || src < 0) return;
+  m.push_back(dst);
+  m.push_back(neg ? int64_t(uint64_t(src) | (uint64_t(1) << 63)) : src);
+}
+
 // ---------------------------------------------------------------------------
 static void fs_setup(Ctx& c) {
   FsState* s = new FsState();
@@ -295,6 +368,34 @@ static void fs_setup(Ctx& c) {
     KCHECK(c);
     const int sg2[2] = {+1, -1}, sg4[4] = {+1, +1, -1, -1};
     launch_fill_denom(c, s->d_Dfs + off, c.namp, dt, dc, int(ch.size()), rank, rank == 2 ? sg2 : sg4, c.d_eps_fs);
+  }
+  // one-ghost doubles: the unknown is t2(a, b, g_x, j) with a < b; (b, a, g_x, j),
+  // (a, b, j, g_x) and (b, a, j, g_x) are its signed copies
+  {
+    const BlockAddr A(c, c.t2.L, c.n1);
+    std::vector<int64_t> mir;
+    for (int gx = 0; gx < c.no; ++gx) {
+      if (c.occ_ghost[gx] < 0) continue;
+      for (int j = 0; j < c.no; ++j) {
+        if (c.occ_ghost[j] >= 0) continue;
+        for (int a = 0; a < c.nv; ++a)
+          for (int b = a + 1; b < c.nv; ++b) {
+            const int64_t p = A.at(a, b, gx, j);
+            if (p < 0) continue;  // symmetry-forbidden
+            add_mirror(mir, A.at(b, a, gx, j), p, true);
+            add_mirror(mir, A.at(a, b, j, gx), p, true);
+            add_mirror(mir, A.at(b, a, j, gx), p, false);
+          }
+      }
+    }
+    s->n_mir = int64_t(mir.size() / 2);
+    s->d_mir = (int64_t*)c.dalloc(sizeof(int64_t) * std::max<size_t>(mir.size(), 2));
+    upload(c, s->d_mir, mir.data(), sizeof(int64_t) * mir.size());
+    if (s->n_mir) {
+      k_set_roles<<<int(std::min<int64_t>((s->n_mir + 255) / 256, 4096)), 256, 0, c.stream>>>(s->d_role, s->d_mir,
+                                                                                           s->n_mir, 2, ROLE_MIRROR);
+      KCHECK(c);
+    }
   }
   // H_eff gather list: t1(a = act[y], i = g_x) -> Hg(m = g_y, i = g_x), irreps equal
   s->Hg = *new_tensor(c, L2(c, SP_OCC, +1, SP_OCC, -1), true);
@@ -363,7 +464,7 @@ static void fs_run(Ctx& c) {
     einsum(c, "FSx1", make_double2(1, 0), {&c.t1, nullptr, "am"}, {&s.Hg, nullptr, "mi"}, s.X1, "ai", false);
     einsum(c, "FSx2", make_double2(1, 0), {&c.t2, nullptr, "abmj"}, {&s.Hg, nullptr, "mi"}, s.X2, "abij", false,
            {{1.0, "abij"}, {-1.0, "abji"}});
-    fs_step(c, s.d_Dfs, s.d_role, s.d_XV);
+    fs_step(c, s.d_Dfs, s.d_role, s.d_XV, s.d_mir, s.n_mir);
     s.n_iter = it;
     const int nconv = ccsd_count_converged(c);
     if (nconv < 0) throw ExpError{EXP_ENUMERIC, "NaN/Inf in the (0h,1p) amplitudes"};
@@ -416,11 +517,277 @@ exp_status fs_entry(Ctx& c, int inst, double* heff, double* eig_re, double* eig_
 }
 
 // one Bloch update + DIIS for every instance (kernels shared with the (0h,0p) path)
-void fs_step(Ctx& c, const double* Dfs, const int8_t* role, const cplx* XV) {
+void fs_step(Ctx& c, const double* Dfs, const int8_t* role, const cplx* XV, const int64_t* mir, int64_t n_mir) {
   ccsd_update_step(c, [&](double* part, int nb) {
     k_fs_update<<<dim3(nb, c.ninst), 256, 0, c.stream>>>(c.d_R, c.d_D, Dfs, XV, role, c.d_T, c.d_diis_t, c.d_diis_e,
                                                          c.namp, c.cfg.diis_dim, c.d_diis_state, part,
                                                          c.cfg.level_shift, c.cfg.denom_shift, c.cfg.denom_shift_n);
     KCHECK(c);
+    if (n_mir) {  // the signed copies follow their canonical element before DIIS sees the vector
+      k_fs_mirror<<<dim3(int(std::min<int64_t>((n_mir + 255) / 256, 2048)), c.ninst), 256, 0, c.stream>>>(
+          mir, n_mir, c.d_diis_t, c.namp, c.cfg.diis_dim, c.d_diis_state);
+      KCHECK(c);
+    }
   }, false);
+}
+
+// ---------------------------------------------------------------------------
+// The (0h,2p) sector (Eq. (sectors): after (0h,0p) and (0h,1p), whose amplitudes stay
+// fixed).  In the ghost picture the two-valence-particle amplitudes s_xy^ab are the
+// doubles t_{g_x g_y}^{ab} (both occupied indices ghosts), zero until now.  The
+// Bloch equation of the sector, projected on the two-particle determinants, is the
+// CCSD residual at those elements minus the terms of Omega H_eff,
+//     rho_xy^ab = R_{g_x g_y}^{ab} - sum_z s_zy^ab H1_zx - sum_w s_xw^ab H1_wy
+//                 - 1/2 sum_zw tau_{g_z g_w}^{ab} H2_zw,xy,
+// with H1 the converged (0h,1p) H_eff and H2_zw,xy the residual at the active-active
+// elements (a = z, b = w): the connected two-particle part of the (0h,2p) H_eff, which
+// is H1 (x) 1 + 1 (x) H1 + H2 on the pairs x < y.  The first two terms are the (0h,1p)
+// S H_eff contraction over the ghost index; the last is the hole-hole ladder with H2
+// in place of W_mnij.  Updated: the canonical elements (g_x before g_y, a < b, not both
+// active) by rho / (e_x + e_y - e_a - e_b); the other three copies are written from
+// them with the antisymmetry signs (steps taken on every copy separately let rounding
+// grow a symmetric part the equations do not damp).
+
+struct Fs2State {
+  int8_t* d_role = nullptr;      // [namp]
+  int64_t* d_mir = nullptr;      // [n_mir][2]: destination, source | sign in bit 63
+  int64_t n_mir = 0;
+  Tensor H2;                     // (m n | i j), ghost entries only
+  HPair* d_pairs = nullptr;      // residual at t2(act z, act w, g_x, g_y) -> H2(g_z, g_w, g_x, g_y)
+  int n_pairs = 0;
+  cplx* d_h2 = nullptr;          // [ninst][na^4]: H2[z, w, x, y]
+  cplx* d_heff = nullptr;        // [ninst][np^2]: pair H_eff
+  cplx* d_eig = nullptr;         // [ninst][np]
+  int* d_blk = nullptr;
+  int* d_blk_off = nullptr;
+  int npair = 0;
+  bool done = false, converged = false;
+  int n_iter = 0;
+  std::vector<cplx> h_heff, h_eig;
+};
+
+static Fs2State& F2(Ctx& c) { return *reinterpret_cast<Fs2State*>(F(c).fs2); }
+static void fs2_release(FsState& s) {
+  delete reinterpret_cast<Fs2State*>(s.fs2);
+  s.fs2 = nullptr;
+}
+
+static void fs2_setup(Ctx& c) {
+  FsState& s1 = F(c);
+  Fs2State* s = new Fs2State();
+  s1.fs2 = s;
+  const int na = c.nact;
+  const Layout& L = c.t2.L;
+  std::vector<SubBlock> sb;
+  enumerate_blocks(L, c.spaces, sb);
+  const Space& SO = c.spaces[SP_OCC];
+  const Space& SV = c.spaces[SP_VIRT];
+  auto irr = [&](const Space& S, int l) {
+    int g = 0;
+    while (g + 1 < c.G && S.off[g + 1] <= l) ++g;
+    return g;
+  };
+  // sub-block of each (G_a, G_b, G_i, G_j) tuple of the t2 layout (a, b | i, j)
+  std::map<std::array<int, 4>, const SubBlock*> blk;
+  for (auto& b : sb) blk[{b.irr[0], b.irr[1], b.irr[2], b.irr[3]}] = &b;
+  auto addr = [&](int a, int b, int i, int j) -> int64_t {
+    const int ga = irr(SV, a), gb = irr(SV, b), gi = irr(SO, i), gj = irr(SO, j);
+    auto it = blk.find({ga, gb, gi, gj});
+    if (it == blk.end()) return -1;
+    const SubBlock& B = *it->second;
+    return c.n1 + B.base + (a - SV.off[ga]) * B.st[0] + (b - SV.off[gb]) * B.st[1] + (i - SO.off[gi]) * B.st[2] +
+           (j - SO.off[gj]) * B.st[3];
+  };
+  std::vector<int> gl(na, -1);  // ghost local occupied index of each active slot
+  for (int l = 0; l < c.no; ++l)
+    if (c.occ_ghost[l] >= 0) gl[c.occ_ghost[l]] = l;
+  std::vector<int> slot_of(c.nv, -1);
+  for (int k = 0; k < na; ++k) slot_of[c.act[k]] = k;
+  std::vector<int64_t> canon, mir;
+  for (int x = 0; x < na; ++x)
+    for (int y = 0; y < na; ++y) {
+      if (x == y) continue;
+      for (int a = 0; a < c.nv; ++a)
+        for (int b = 0; b < c.nv; ++b) {
+          if (a == b || (slot_of[a] >= 0 && slot_of[b] >= 0)) continue;
+          const int64_t p = addr(a, b, gl[x], gl[y]);
+          if (p < 0) continue;  // symmetry-forbidden
+          const bool gx_first = gl[x] < gl[y];
+          if (gx_first && a < b) {
+            canon.push_back(p);
+            continue;
+          }
+          // source: the canonical copy, sign = (-1)^(number of swaps)
+          const int i0 = gx_first ? x : y, j0 = gx_first ? y : x;
+          const int a0 = a < b ? a : b, b0 = a < b ? b : a;
+          const int64_t src = addr(a0, b0, gl[i0], gl[j0]);
+          const bool neg = (gx_first != (a < b));  // exactly one swap
+          mir.push_back(p);
+          mir.push_back(neg ? int64_t(uint64_t(src) | (uint64_t(1) << 63)) : src);
+        }
+    }
+  s->n_mir = int64_t(mir.size() / 2);
+  s->d_role = (int8_t*)c.dalloc(c.namp);
+  CK(cudaMemsetAsync(s->d_role, ROLE_REAL, c.namp, c.stream));
+  int64_t* d_canon = (int64_t*)c.dalloc(sizeof(int64_t) * std::max<size_t>(canon.size(), 1));
+  upload(c, d_canon, canon.data(), sizeof(int64_t) * canon.size());
+  s->d_mir = (int64_t*)c.dalloc(sizeof(int64_t) * std::max<size_t>(mir.size(), 2));
+  upload(c, s->d_mir, mir.data(), sizeof(int64_t) * mir.size());
+  if (!canon.empty()) {
+    k_set_roles<<<int(std::min<int64_t>((int64_t(canon.size()) + 255) / 256, 4096)), 256, 0, c.stream>>>(
+        s->d_role, d_canon, int64_t(canon.size()), 1, ROLE_Q);
+    KCHECK(c);
+  }
+  if (s->n_mir) {
+    k_set_roles<<<int(std::min<int64_t>((s->n_mir + 255) / 256, 4096)), 256, 0, c.stream>>>(s->d_role, s->d_mir,
+                                                                                         s->n_mir, 2, ROLE_MIRROR);
+    KCHECK(c);
+  }
+  // H2 gather: residual at t2(a = act z, b = act w, i = g_x, j = g_y) -> H2(g_z, g_w, g_x, g_y)
+  s->H2 = *new_tensor(c, L4(c, SP_OCC, +1, SP_OCC, +1, SP_OCC, -1, SP_OCC, -1, 2), true);
+  std::vector<SubBlock> hb;
+  enumerate_blocks(s->H2.L, c.spaces, hb);
+  std::map<std::array<int, 4>, const SubBlock*> hblk;
+  for (auto& b : hb) hblk[{b.irr[0], b.irr[1], b.irr[2], b.irr[3]}] = &b;
+  auto haddr = [&](int m, int n, int i, int j) -> int64_t {
+    const int g[4] = {irr(SO, m), irr(SO, n), irr(SO, i), irr(SO, j)};
+    auto it = hblk.find({g[0], g[1], g[2], g[3]});
+    if (it == hblk.end()) return -1;
+    const SubBlock& B = *it->second;
+    return B.base + (m - SO.off[g[0]]) * B.st[0] + (n - SO.off[g[1]]) * B.st[1] + (i - SO.off[g[2]]) * B.st[2] +
+           (j - SO.off[g[3]]) * B.st[3];
+  };
+  std::vector<HPair> hp;
+  for (int z = 0; z < na; ++z)
+    for (int w = 0; w < na; ++w)
+      for (int x = 0; x < na; ++x)
+        for (int y = 0; y < na; ++y) {
+          if (z == w || x == y) continue;
+          const int64_t src = addr(c.act[z], c.act[w], gl[x], gl[y]);
+          const int64_t dst = haddr(gl[z], gl[w], gl[x], gl[y]);
+          if (src < 0 || dst < 0) continue;
+          hp.push_back(HPair{src, dst, ((z * na + w) * na + x) * na + y, 0});
+        }
+  s->n_pairs = int(hp.size());
+  s->d_pairs = (HPair*)c.dalloc(sizeof(HPair) * std::max<size_t>(hp.size(), 1));
+  upload(c, s->d_pairs, hp.data(), sizeof(HPair) * hp.size());
+  const int64_t na4 = int64_t(na) * na * na * na;
+  s->d_h2 = (cplx*)c.dalloc(sizeof(cplx) * std::max<int64_t>(na4, 1) * c.ninst);
+  CK(cudaMemsetAsync(s->d_h2, 0, sizeof(cplx) * std::max<int64_t>(na4, 1) * c.ninst, c.stream));
+  // pairs x < y grouped by pair irrep for the eigensolver
+  s->npair = na * (na - 1) / 2;
+  std::vector<int> pblk, pblk_off(c.G + 1, 0);
+  for (int g = 0; g < c.G; ++g) {
+    pblk_off[g] = int(pblk.size());
+    int k = 0;
+    for (int x = 0; x < na; ++x)
+      for (int y = x + 1; y < na; ++y, ++k)
+        if ((irr(SV, c.act[x]) + irr(SV, c.act[y])) % c.G == g) pblk.push_back(k);
+  }
+  pblk_off[c.G] = int(pblk.size());
+  s->d_blk = (int*)c.dalloc(sizeof(int) * std::max(s->npair, 1));
+  s->d_blk_off = (int*)c.dalloc(sizeof(int) * (c.G + 1));
+  upload(c, s->d_blk, pblk.data(), sizeof(int) * pblk.size());
+  upload(c, s->d_blk_off, pblk_off.data(), sizeof(int) * (c.G + 1));
+  s->d_heff = (cplx*)c.dalloc(sizeof(cplx) * std::max(s->npair * s->npair, 1) * c.ninst);
+  s->d_eig = (cplx*)c.dalloc(sizeof(cplx) * std::max(s->npair, 1) * c.ninst);
+}
+
+static void fs2_run(Ctx& c) {
+  FsState& s1 = F(c);
+  Fs2State& s = F2(c);
+  const int na = c.nact;
+  const int64_t nam = c.namp;
+  ccsd_reset_diis(c);
+  s.n_iter = 0;
+  s.converged = false;
+  Tensor* tau = work_tensor(c, "tau", c.t2.L);
+  for (int it = 1; it <= c.cfg.max_iter; ++it) {
+    ccsd_rhs(c);
+    // H2 from the residual at the active-active elements (t = 0 there)
+    k_fs_heff<<<dim3(1, c.ninst), 256, 0, c.stream>>>(s.d_pairs, s.n_pairs, c.d_R, c.d_D, c.d_T, nam, s.H2.d, s.H2.is,
+                                                      s.d_h2, na * na, c.d_diis_state);
+    KCHECK(c);
+    // Omega H_eff terms: P(ij) sum_m t_abmj H1_mi (ghost m) + 1/2 sum_mn tau_abmn H2_mnij
+    einsum(c, "FSx2", make_double2(1, 0), {&c.t2, nullptr, "abmj"}, {&s1.Hg, nullptr, "mi"}, s1.X2, "abij", false,
+           {{1.0, "abij"}, {-1.0, "abji"}});
+    einsum(c, "FS2hh", make_double2(0.5, 0), {tau, nullptr, "abmn"}, {&s.H2, nullptr, "mnij"}, s1.X2, "abij", true);
+    fs_step(c, s1.d_Dfs, s.d_role, s1.d_XV, s.d_mir, s.n_mir);
+    s.n_iter = it;
+    const int nconv = ccsd_count_converged(c);
+    if (nconv < 0) throw ExpError{EXP_ENUMERIC, "NaN/Inf in the (0h,2p) amplitudes"};
+    if (nconv == c.ninst) { s.converged = true; break; }
+  }
+  // the (0h,2p) H_eff on the pairs x < y: H1 (x) 1 + 1 (x) H1 + H2, then its eigenvalues
+  const int np = s.npair;
+  const int64_t na4 = int64_t(na) * na * na * na;
+  std::vector<cplx> h2(size_t(std::max<int64_t>(na4, 1)) * c.ninst);
+  CK(cudaMemcpyAsync(h2.data(), s.d_h2, sizeof(cplx) * h2.size(), cudaMemcpyDeviceToHost, c.stream));
+  CK(cudaStreamSynchronize(c.stream));
+  std::vector<std::pair<int, int>> pr;
+  for (int x = 0; x < na; ++x)
+    for (int y = x + 1; y < na; ++y) pr.push_back({x, y});
+  s.h_heff.assign(size_t(np) * np * c.ninst, make_double2(0.0, 0.0));
+  for (int k = 0; k < c.ninst; ++k) {
+    const cplx* H1 = s1.h_heff.data() + size_t(k) * na * na;  // H1[y * na + x]
+    const cplx* H2 = h2.data() + size_t(k) * na4;
+    for (int r = 0; r < np; ++r)
+      for (int q = 0; q < np; ++q) {
+        const int z = pr[r].first, w = pr[r].second, x = pr[q].first, y = pr[q].second;
+        cplx v = H2[((z * na + w) * na + x) * na + y];
+        auto add = [&](double sg, cplx h) { v.x += sg * h.x; v.y += sg * h.y; };
+        if (w == y) add(1.0, H1[z * na + x]);
+        if (z == x) add(1.0, H1[w * na + y]);
+        if (z == y) add(-1.0, H1[w * na + x]);
+        if (w == x) add(-1.0, H1[z * na + y]);
+        s.h_heff[(size_t(k) * np + r) * np + q] = v;
+      }
+  }
+  if (np) {
+    upload(c, s.d_heff, s.h_heff.data(), sizeof(cplx) * s.h_heff.size());
+    int* d_err = (int*)c.dalloc(sizeof(int));
+    CK(cudaMemsetAsync(d_err, 0, sizeof(int), c.stream));
+    k_fs_eig<<<c.ninst, 32, 0, c.stream>>>(s.d_heff, np, s.d_blk, s.d_blk_off, c.G, s.d_eig, d_err);
+    KCHECK(c);
+    int err = 0;
+    s.h_eig.resize(size_t(np) * c.ninst);
+    CK(cudaMemcpyAsync(&err, d_err, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+    CK(cudaMemcpyAsync(s.h_eig.data(), s.d_eig, sizeof(cplx) * s.h_eig.size(), cudaMemcpyDeviceToHost, c.stream));
+    CK(cudaStreamSynchronize(c.stream));
+    if (err == 1) throw ExpError{EXP_EINVAL, "an irrep block of the (0h,2p) H_eff is larger than 32"};
+    if (err == 2) throw ExpError{EXP_ENUMERIC, "(0h,2p) H_eff eigensolver did not converge"};
+  }
+  s.done = true;
+}
+
+exp_status fs2_entry(Ctx& c, int inst, double* heff, double* eig_re, double* eig_im, int* n_iter) {
+  if (c.nact < 2) throw ExpError{EXP_ESTATE, "the (0h,2p) sector needs at least two active spinors"};
+  if (inst < 0 || inst >= c.ninst) throw ExpError{EXP_EINVAL, "instance out of range"};
+  if (!c.fs_state || !F(c).done) {
+    const exp_status st = fs_entry(c, inst, nullptr, nullptr, nullptr, nullptr);
+    if (st != EXP_OK) throw ExpError{EXP_ESTATE, "the (0h,1p) sector has not converged"};
+  }
+  if (!F(c).converged) throw ExpError{EXP_ESTATE, "the (0h,1p) sector has not converged"};
+  if (!F(c).fs2) {
+    fs2_setup(c);
+    fs2_run(c);
+  }
+  Fs2State& s = F2(c);
+  const int np = s.npair;
+  if (heff)
+    for (int k = 0; k < np * np; ++k) {
+      heff[2 * k] = s.h_heff[size_t(inst) * np * np + k].x;
+      heff[2 * k + 1] = s.h_heff[size_t(inst) * np * np + k].y;
+    }
+  std::vector<std::complex<double>> w(np);
+  for (int k = 0; k < np; ++k) w[k] = {s.h_eig[size_t(inst) * np + k].x, s.h_eig[size_t(inst) * np + k].y};
+  std::sort(w.begin(), w.end(), [](const std::complex<double>& a, const std::complex<double>& b) {
+    return a.real() != b.real() ? a.real() < b.real() : a.imag() < b.imag();
+  });
+  for (int k = 0; k < np; ++k) {
+    if (eig_re) eig_re[k] = w[k].real();
+    if (eig_im) eig_im[k] = w[k].imag();
+  }
+  if (n_iter) *n_iter = s.n_iter;
+  return s.converged ? EXP_OK : EXP_ENOTCONV;
 }

@@ -85,6 +85,9 @@ def lib():
     L.exp_fs_sector_0h1p.argtypes = [P, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                      C.POINTER(C.c_double), C.POINTER(C.c_int)]
     L.exp_fs_sector_0h1p.restype = C.c_int
+    L.exp_fs_sector_0h2p.argtypes = [P, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                     C.POINTER(C.c_double), C.POINTER(C.c_int)]
+    L.exp_fs_sector_0h2p.restype = C.c_int
     L.exp_set_amplitudes.argtypes = [P, C.c_int, P, P]
     L.exp_work_per_iteration.argtypes = [P, C.POINTER(C.c_double)]
     L.exp_ccsd_t.argtypes = [P, C.c_int, C.c_int, C.POINTER(T3Info), C.POINTER(C.c_double)]
@@ -264,6 +267,21 @@ class Context:
         d = {k: getattr(info, k) for k, _ in T3Info._fields_}
         e3 = (buf[0:2 * n3:2] + 1j * buf[1:2 * n3:2]) if per_triple else None
         return complex(info.e_re, info.e_im), d, e3
+
+    def fs_sector_0h2p(self, inst=0):
+        """(H_eff over the active pairs x<y, eigenvalues, n_iter, status) of the (0h,2p) sector."""
+        na = self.n_active
+        npr = na * (na - 1) // 2
+        heff = np.zeros(2 * max(npr * npr, 1))
+        er, ei = np.zeros(max(npr, 1)), np.zeros(max(npr, 1))
+        nit = C.c_int(0)
+        dp = C.POINTER(C.c_double)
+        st = self.L.exp_fs_sector_0h2p(self.h, int(inst), heff.ctypes.data_as(dp), er.ctypes.data_as(dp),
+                                       ei.ctypes.data_as(dp), C.byref(nit))
+        if st not in (0, 4):
+            self._check(st)
+        H = (heff[0:2 * npr * npr:2] + 1j * heff[1:2 * npr * npr:2]).reshape(npr, npr)
+        return H, er[:npr] + 1j * ei[:npr], nit.value, st
 
     def state(self, inst=0) -> int:
         """0 iterating, 1 converged, 2 failed."""

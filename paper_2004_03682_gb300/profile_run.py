@@ -9,6 +9,8 @@ captured inside an NVTX range, so that a profiler can select it with
 
     python -m paper_2004_03682_gb300.profile_run --zgemm 2048 2048 2048 --slices 6        # range "zgemm"
     python -m paper_2004_03682_gb300.profile_run --family 512                               # range "iter3"
+    python -m paper_2004_03682_gb300.profile_run --t3 --slices 6                            # range "t3"
+    python -m paper_2004_03682_gb300.profile_run --occ 24 --virt 120 --t3 --t3-block 4      # range "t3"
 
 Without --top the range holds one whole CCSD iteration (the CUDA graph the bench
 replays); with --top it holds the contraction with the most complex multiply-adds per
@@ -19,7 +21,8 @@ operands, a few hundred MB: a bounded case for full profiler captures of the ten
 kernel).  With --family N the workload is the first N members of the learned-guess
 family (o=10 v=40 C1, all in one context; --occ/--virt/--irreps ignored).  Prints the
 iteration times (or the top contraction's site, time and work, or the GEMM time) as one
-line.
+line.  With --t3 the range holds one (T) evaluation (exp_ccsd_t, block size --t3-block,
+0 = automatic) from the amplitudes of two CCSD iterations, after one untimed evaluation.
 """
 from __future__ import annotations
 
@@ -45,6 +48,8 @@ def main():
                     help="one emulated complex GEMM of this shape instead of a CCSD workload")
     ap.add_argument("--family", type=int, default=0, help="the first N learned-guess family members, batched")
     ap.add_argument("--slices-major", type=int, default=0, help="slices of the ladder and ring products")
+    ap.add_argument("--t3", action="store_true", help="capture one (T) evaluation")
+    ap.add_argument("--t3-block", type=int, default=0, help="with --t3: occupied block size (0 = automatic)")
     a = ap.parse_args()
     if a.zgemm:
         return zgemm_case(*a.zgemm, a.slices)
@@ -56,7 +61,16 @@ def main():
     ctx.init_integrals([p.seed for p in probs], scale_mult=[p.scale_mult for p in probs])
     recs, _, _ = ctx.iterate(2, raise_numeric=False)
     torch.cuda.synchronize()
-    if a.top:
+    if a.t3:
+        ctx.ccsd_t(0, block=a.t3_block)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("t3")
+        E, info, _ = ctx.ccsd_t(0, block=a.t3_block)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        print(f"t3 {info['ms']:.3f} ms (products {info['ms_products']:.3f}, energies {info['ms_energy']:.3f}), "
+              f"block {info['block']}, E(T) {E}")
+    elif a.top:
         torch.cuda.nvtx.range_push("top")
         site, ms, macs = ctx.profile_top(reps=1, site=a.site)
         torch.cuda.synchronize()

@@ -12,8 +12,6 @@
     the H_eff terms of Omega H_eff, sum_z s_zy^ab H1_zx + sum_w s_xw^ab H1_wy
     + 1/2 sum_zw tau_zw^ab H2_zw,xy.  The two routes share no code and must give the
     same H_eff eigenvalues."""
-import itertools
-
 import numpy as np
 import pytest
 
@@ -73,70 +71,6 @@ def test_two_electrons_on_empty_reference_equal_full_ci(seed, nv, G, nact, gener
         assert np.min(np.abs(fci - e.real)) < 1e-9, (e, fci)
 
 
-def _ghost_route(V, f, o, t1, t2, act, s1, s2, tol=1e-11, max_iter=500):
-    """The (0h,2p) sector through ghost occupied spinors and the CCSD residual."""
-    n = f.shape[0]
-    nv = n - o
-    na = len(act)
-    no = o + na
-    idx = np.r_[np.arange(o), no + np.arange(nv)]  # real spinors in the extended order
-    Ve = np.zeros((no + nv,) * 4, complex)
-    Ve[np.ix_(idx, idx, idx, idx)] = V
-    fe = np.zeros((no + nv, no + nv), complex)
-    fe[np.ix_(idx, idx)] = f
-    b = ccsd.Blocks(Ve, fe, no)
-    t1e = np.zeros((no, nv), complex)
-    t1e[:o] = t1
-    t1e[o:] = s1
-    t1e[o + np.arange(na), act] = 1.0  # P
-    t2e = np.zeros((no, no, nv, nv), complex)
-    t2e[:o, :o] = t2
-    t2e[o:, :o] = s2
-    t2e[:o, o:] = -s2.transpose(1, 0, 2, 3)
-    actset = set(int(a) for a in act)
-    # the unknowns: x<y, a<b, not both a and b active; each step is taken on these and
-    # written into the four antisymmetric copies (a step on all copies separately lets
-    # rounding grow a symmetric part that the equations do not damp)
-    up = np.zeros((na, na, nv, nv), bool)
-    for x, y in itertools.combinations(range(na), 2):
-        for a, bq in itertools.combinations(range(nv), 2):
-            up[x, y, a, bq] = not (a in actset and bq in actset)
-
-    def anti(u):
-        full = np.zeros((na, na, nv, nv), complex)
-        full[up] = u
-        return full - full.transpose(1, 0, 2, 3) - full.transpose(0, 1, 3, 2) + full.transpose(1, 0, 3, 2)
-
-    eps = np.real(np.diag(f))
-    ex, ev = eps[o + act], eps[o:]
-    D = ex[:, None, None, None] + ex[None, :, None, None] - ev[None, None, :, None] - ev[None, None, None, :]
-    sg = np.zeros((na, na, nv, nv), complex)
-    diis = ccsd.DIIS(6)
-    for it in range(max_iter):
-        t2e[o:, o:] = sg
-        r1, r2 = ccsd.residual(t1e, t2e, b)
-        H1 = r1[o:, act].T                                   # H1[z, x]
-        c = t1e[o:]
-        tau = sg + np.einsum("za,wb->zwab", c, c) - np.einsum("zb,wa->zwab", c, c)
-        H2 = r2[o:, o:][:, :, act][:, :, :, act].transpose(2, 3, 0, 1)  # H2[z, w, x, y]
-        rho = (r2[o:, o:] - np.einsum("zyab,zx->xyab", sg, H1) - np.einsum("xwab,wy->xyab", sg, H1)
-               - 0.5 * np.einsum("zwab,zwxy->xyab", tau, H2))
-        d = rho[up] / D[up]
-        res = np.max(np.abs(d), initial=0.0)
-        new = sg[up] + d
-        if res < tol:
-            sg = anti(new)
-            break
-        diis.push(new, d)
-        sg = anti(diis.extrapolate())
-    pairs = [(x, y) for x in range(na) for y in range(x + 1, na)]
-    I = np.eye(na)
-    Hp = np.array([[H1[z, x] * I[w, y] + I[z, x] * H1[w, y] - H1[w, x] * I[z, y] - I[w, x] * H1[z, y] + H2[z, w, x, y]
-                    for x, y in pairs] for z, w in pairs])
-    w = np.linalg.eigvals(Hp)
-    return Hp, w[np.lexsort((w.imag, w.real))], res < tol
-
-
 @pytest.mark.parametrize("seed,no,nv,G,nact", [(911, 2, 5, 1, 2), (916, 2, 6, 2, 3), (918, 3, 6, 2, 2),
                                                (921, 2, 6, 4, 3)])
 def test_occupied_reference_equals_ghost_construction(seed, no, nv, G, nact):
@@ -151,7 +85,7 @@ def test_occupied_reference_equals_ghost_construction(seed, no, nv, G, nact):
     assert np.max(np.abs(s2)) > 1e-5
     Heff, w, s, pairs, qp, nit, conv = fs0h2p.solve(V, f, no, t1, t2, E, act, s1, s2, tol=1e-11, max_iter=600)
     assert conv
-    Hg, wg, conv_g = _ghost_route(V, f, no, t1, t2, act, s1, s2)
+    Hg, wg, conv_g = fs0h2p.solve_ghost(V, f, no, t1, t2, act, s1, s2)
     assert conv_g
     np.testing.assert_allclose(np.sort_complex(w), np.sort_complex(wg), atol=1e-9, rtol=0)
 
@@ -168,7 +102,7 @@ def test_sign_slip_in_normal_product_is_caught(monkeypatch):
     t1, t2, E, _, conv, _ = ccsd.solve(b, tol=1e-12, max_iter=600)
     act = np.argsort(prob.eps_virt)[:2]
     H1, w1, s1, s2, _, conv = fs0h1p.solve(V, f, 2, t1, t2, act, tol=1e-12, max_iter=600)
-    Hg, wg, conv_g = _ghost_route(V, f, 2, t1, t2, act, s1, s2)
+    Hg, wg, conv_g = fs0h2p.solve_ghost(V, f, 2, t1, t2, act, s1, s2)
     right = fs0h2p.normal_product
     monkeypatch.setattr(fs0h2p, "normal_product", lambda ops, o: (right(ops, o)[0], 1))
     Heff, w, s, pairs, qp, nit, conv = fs0h2p.solve(V, f, 2, t1, t2, E, act, s1, s2, tol=1e-11, max_iter=600)

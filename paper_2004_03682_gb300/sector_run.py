@@ -4,9 +4,11 @@ iteration on emulated contractions with pair-packed tau products, then the (0h,1
 Bloch iteration and the eigenvalues of H_eff.  Every step runs through the C ABI.
 
     python -m paper_2004_03682_gb300.sector_run --occ 80 --virt 480 --irreps 16 --active 16 --tol 1e-3
+    python -m paper_2004_03682_gb300.sector_run --occ 24 --virt 120 --irreps 8 --active 8 --tol 1e-6 --shift 8 --sector2
 
 Prints one JSON line: times per (0h,0p) and per (0h,1p) iteration, iteration
-counts, the H_eff eigenvalues and the peak device memory.
+counts, the H_eff eigenvalues and the peak device memory; with --sector2 also the
+(0h,2p) sector's iterations, time and eigenvalues.
 """
 from __future__ import annotations
 
@@ -45,6 +47,7 @@ def main():
     ap.add_argument("--max-iter", type=int, default=200)
     ap.add_argument("--train", type=int, default=64)
     ap.add_argument("--epochs", type=int, default=20)
+    ap.add_argument("--sector2", action="store_true", help="then the (0h,2p) sector")
     a = ap.parse_args()
 
     model, losses = (None, []) if a.train <= 0 else train_guess(a.train, a.epochs)
@@ -78,6 +81,14 @@ def main():
         fs_s = time.perf_counter() - t1
         out.update(fs_iterations=n_fs, fs_status=st_fs, fs_s=fs_s, fs_ms_per_iteration=1e3 * fs_s / max(n_fs, 1),
                    eigenvalues=[[float(z.real), float(z.imag)] for z in eig])
+        if a.sector2 and st_fs == 0:
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+            H2, eig2, n2, st2 = ctx.fs_sector_0h2p(0)
+            torch.cuda.synchronize()
+            s2 = time.perf_counter() - t2
+            out.update(fs2_iterations=n2, fs2_status=st2, fs2_s=s2, fs2_ms_per_iteration=1e3 * s2 / max(n2, 1),
+                       eigenvalues2=[[float(z.real), float(z.imag)] for z in eig2])
     out["peak_device_gb"] = torch.cuda.max_memory_allocated() / 1e9
     ctx.close()
     print(json.dumps(out))

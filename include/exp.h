@@ -25,6 +25,17 @@
  *     exp_last_error() gives a one-line message for the last failure.
  *   - A context is not thread-safe; distinct contexts are independent.
  *   - Complex numbers are (re, im) pairs of IEEE doubles.
+ *
+ * Environment variables read at exp_create (diagnostics and timing studies only; none
+ * changes a result bit):
+ *   EXP_PROFILE=1       iterations run eagerly (no CUDA graph), with per-contraction and
+ *                       per-stage times and the (T) stage times on stderr;
+ *   EXP_AUTOTUNE=0      keep the default work decomposition of the emulated products
+ *                       instead of timing the candidates on their first run;
+ *   EXP_KSPLIT_MULT=m   with EXP_AUTOTUNE=0: this K-split multiplier (0 = no split);
+ *   EXP_GROUP_ROWS=g    with EXP_AUTOTUNE=0: g row tiles per group of the work order.
+ * Split-K partials are exact integers added in 128 bits, so no decomposition changes a
+ * bit of an emulated product.
  */
 #ifndef EXPGB_EXP_H
 #define EXPGB_EXP_H

@@ -39,7 +39,9 @@ Parity: pinned by tests/test_oracle_fs2.py:
     carrying the valence amplitudes through the CCSD residual of oracle.ccsd): the
     oracle's converged S2 zeroes that construction's residual and the H_eff
     eigenvalues agree;
-  * a planted sign slip in the normal product is caught by the full-CI pin.
+  * a planted sign slip in the normal product is caught by the comparison with the
+    ghost construction (with occupied spinors; on an empty reference that term feeds only
+    two-particle components, which S2 absorbs).
 """
 from __future__ import annotations
 

@@ -4,10 +4,12 @@
 //     h1 = relu(W1 x + b1), h2 = relu(W2 h1 + b2), y = W3 h2 + b3,
 //     t2 = (1 + y0 + i y1) t_MP2,
 // trained on converged amplitudes of earlier solves (loss: mean |t2 - t2_conv|^2 /
-// 0.05^2, Adam).  Hand-written forward, backward and update kernels: FP32
-// accumulation with BF16-rounded weights and activations (bf16 mode) or plain
-// FP32 (check mode).  The paper has no counterpart; the guess only changes the
-// starting point of the amplitude iteration, never its fixed point.
+// 0.05^2, Adam).  Hand-written forward, backward and update kernels.  bf16 mode:
+// weights and activations rounded to BF16, and the three width-128 layer products
+// (h1 W2^T forward, gz2 W2 and gz2^T h1 backward, the gradients rounded to BF16 as
+// operands) on the tensor cores, mma m16n8k16 with FP32 accumulation; check mode:
+// plain FP32 on the SIMT pipes.  The paper has no counterpart; the guess only changes
+// the starting point of the amplitude iteration, never its fixed point.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -27,6 +29,37 @@ constexpr int TS = 32;  // samples per CTA tile
 constexpr int MLP_SMEM = (2 * W * W + W * NF + 2 * W + NO * W + NO + 3 * TS * W + TS * NF + TS * NO) * 4 + 64;
 
 __device__ __forceinline__ float rb(float x, int bf) { return bf ? __bfloat162float(__float2bfloat16_rn(x)) : x; }
+
+// ---------------------------------------------------------------------------
+// The width-128 layer products in the bf16 mode run on the tensor cores: warp-level
+// mma.m16n8k16 with BF16 operands and FP32 accumulation.  Fragment layout (PTX ISA,
+// m16n8k16 .bf16; g = lane / 4, t = lane % 4): A registers {(g, 2t), (g + 8, 2t),
+// (g, 2t + 8), (g + 8, 2t + 8)} with the next column in the high half; B registers
+// {(2t, g), (2t + 8, g)} with the next row in the high half; D {(g, 2t), (g, 2t + 1),
+// (g + 8, 2t), (g + 8, 2t + 1)}.
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+__device__ __forceinline__ void mma_16816(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+// D[16 x 8] += A[r0 .. r0+16, k0 .. k0+16] B[k0 .. k0+16, c0 .. c0+8] for element accessors
+// A(r, k), B(k, c) (values already on the BF16 grid, or rounded here)
+template <typename FA, typename FB>
+__device__ __forceinline__ void mma_tile(float (&d)[4], int r0, int c0, int k0, FA A, FB B) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const uint32_t a[4] = {pack_bf16(A(r0 + g, k0 + 2 * t), A(r0 + g, k0 + 2 * t + 1)),
+                         pack_bf16(A(r0 + g + 8, k0 + 2 * t), A(r0 + g + 8, k0 + 2 * t + 1)),
+                         pack_bf16(A(r0 + g, k0 + 2 * t + 8), A(r0 + g, k0 + 2 * t + 9)),
+                         pack_bf16(A(r0 + g + 8, k0 + 2 * t + 8), A(r0 + g + 8, k0 + 2 * t + 9))};
+  const uint32_t b[2] = {pack_bf16(B(k0 + 2 * t, c0 + g), B(k0 + 2 * t + 1, c0 + g)),
+                         pack_bf16(B(k0 + 2 * t + 8, c0 + g), B(k0 + 2 * t + 9, c0 + g))};
+  mma_16816(d, a, b);
+}
 
 struct Smem {
   float* W2;   // [u][k]
@@ -83,11 +116,35 @@ __device__ void forward_tile(Smem& m, int ns, int bf) {
     m.h1[e] = s < ns ? rb(fmaxf(z, 0.f), bf) : 0.f;
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < TS * W; e += blockDim.x) {
-    const int s = e / W, u = e % W;
-    float z = m.b2[u];
-    for (int k = 0; k < W; ++k) z += m.W2T[k * W + u] * m.h1[s * W + k];
-    m.h2[e] = s < ns ? rb(fmaxf(z, 0.f), bf) : 0.f;
+  if (bf) {
+    // z2 = h1 W2^T on the tensor cores: warp w takes the 16 units 16w .. 16w + 15 of all
+    // TS = 32 samples (two 16-row by two 8-column tiles, K = 128 in steps of 16)
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    float d[2][2][4] = {};
+    auto A = [&](int r, int k) { return m.h1[r * W + k]; };
+    auto B = [&](int k, int c) { return m.W2[c * W + k]; };
+#pragma unroll
+    for (int k0 = 0; k0 < W; k0 += 16)
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt) mma_tile(d[mt][nt], 16 * mt, 16 * w + 8 * nt, k0, A, B);
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int s = 16 * mt + g + (q >> 1) * 8, u = 16 * w + 8 * nt + 2 * t + (q & 1);
+          m.h2[s * W + u] = s < ns ? rb(fmaxf(d[mt][nt][q] + m.b2[u], 0.f), bf) : 0.f;
+        }
+  } else {
+    for (int e = threadIdx.x; e < TS * W; e += blockDim.x) {
+      const int s = e / W, u = e % W;
+      float z = m.b2[u];
+      for (int k = 0; k < W; ++k) z += m.W2T[k * W + u] * m.h1[s * W + k];
+      m.h2[e] = s < ns ? rb(fmaxf(z, 0.f), bf) : 0.f;
+    }
   }
   __syncthreads();
   for (int e = threadIdx.x; e < TS * NO; e += blockDim.x) {
@@ -163,12 +220,32 @@ __global__ void __launch_bounds__(256) k_mlp_grad(const float* __restrict__ P, c
       m.g[e] = m.h2[e] > 0.f ? a : 0.f;
     }
     __syncthreads();
+    if (bf) {
+      // gW2 += gz2^T h1 on the tensor cores (gz2 rounded to BF16): warp w holds the 16 rows
+      // u = 16w .. 16w + 15 of all 128 columns, 16 column tiles x 4 entries per thread
+      const int w = threadIdx.x >> 5;
+      auto A = [&](int u, int sm_) { return m.g[sm_ * W + u]; };
+      auto B = [&](int sm_, int k) { return m.h1[sm_ * W + k]; };
 #pragma unroll
-    for (int j = 0; j < W * W / 256; ++j) {
-      const int e = threadIdx.x + 256 * j, u = e / W, k = e % W;
-      float a = 0.f;
-      for (int s = 0; s < ns; ++s) a += m.g[s * W + u] * m.h1[s * W + k];
-      gW2[j] += a;
+      for (int k0 = 0; k0 < TS; k0 += 16)
+#pragma unroll
+        for (int nt = 0; nt < W / 8; ++nt) {
+          float* acc = gW2 + 4 * nt;
+          float d[4] = {acc[0], acc[1], acc[2], acc[3]};
+          mma_tile(d, 16 * w, 8 * nt, k0, A, B);
+          acc[0] = d[0];
+          acc[1] = d[1];
+          acc[2] = d[2];
+          acc[3] = d[3];
+        }
+    } else {
+#pragma unroll
+      for (int j = 0; j < W * W / 256; ++j) {
+        const int e = threadIdx.x + 256 * j, u = e / W, k = e % W;
+        float a = 0.f;
+        for (int s = 0; s < ns; ++s) a += m.g[s * W + u] * m.h1[s * W + k];
+        gW2[j] += a;
+      }
     }
     if (threadIdx.x < W) {
       float a = 0.f;
@@ -176,11 +253,33 @@ __global__ void __launch_bounds__(256) k_mlp_grad(const float* __restrict__ P, c
       ab2[threadIdx.x] += a;
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < TS * W; e += blockDim.x) {  // gz1 = (gz2 W2) . relu'(z1), over h2
-      const int s = e / W, k = e % W;
-      float a = 0.f;
-      for (int u = 0; u < W; ++u) a += m.g[s * W + u] * m.W2[u * W + k];
-      m.h2[e] = m.h1[e] > 0.f ? a : 0.f;
+    if (bf) {  // gz1 = (gz2 W2) . relu'(z1), over h2: on the tensor cores, warp w the columns 16w ..
+      const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+      float d[2][2][4] = {};
+      auto A = [&](int sm_, int u) { return m.g[sm_ * W + u]; };
+      auto B = [&](int u, int k) { return m.W2T[k * W + u]; };
+#pragma unroll
+      for (int k0 = 0; k0 < W; k0 += 16)
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+          for (int nt = 0; nt < 2; ++nt) mma_tile(d[mt][nt], 16 * mt, 16 * w + 8 * nt, k0, A, B);
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int sm_ = 16 * mt + g + (q >> 1) * 8, k = 16 * w + 8 * nt + 2 * t + (q & 1);
+            m.h2[sm_ * W + k] = m.h1[sm_ * W + k] > 0.f ? d[mt][nt][q] : 0.f;
+          }
+    } else {
+      for (int e = threadIdx.x; e < TS * W; e += blockDim.x) {  // gz1 = (gz2 W2) . relu'(z1), over h2
+        const int s = e / W, k = e % W;
+        float a = 0.f;
+        for (int u = 0; u < W; ++u) a += m.g[s * W + u] * m.W2[u * W + k];
+        m.h2[e] = m.h1[e] > 0.f ? a : 0.f;
+      }
     }
     __syncthreads();
     for (int e = threadIdx.x; e < W * NF; e += blockDim.x) {
@@ -196,8 +295,19 @@ __global__ void __launch_bounds__(256) k_mlp_grad(const float* __restrict__ P, c
     }
   }
   __syncthreads();
+  if (bf) {  // gW2 fragments: warp w rows 16w + g (+8), column tile nt, columns 2t (+1)
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
 #pragma unroll
-  for (int j = 0; j < W * W / 256; ++j) atomicAdd(&grad[OFF_W2 + threadIdx.x + 256 * j], gW2[j]);
+    for (int nt = 0; nt < W / 8; ++nt)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int u = 16 * w + g + (q >> 1) * 8, k = 8 * nt + 2 * t + (q & 1);
+        atomicAdd(&grad[OFF_W2 + u * W + k], gW2[4 * nt + q]);
+      }
+  } else {
+#pragma unroll
+    for (int j = 0; j < W * W / 256; ++j) atomicAdd(&grad[OFF_W2 + threadIdx.x + 256 * j], gW2[j]);
+  }
   atomicAdd(&grad[OFF_W3 + threadIdx.x], gW3);
   if (threadIdx.x < NO) atomicAdd(&grad[OFF_B3 + threadIdx.x], gb3);
   for (int e = threadIdx.x; e < W * NF; e += blockDim.x) atomicAdd(&grad[OFF_W1 + e], aW1[e]);

@@ -51,6 +51,31 @@ def test_gradient_bf16_close_to_oracle(expgb):
     assert np.linalg.norm(g - gr) < 3e-2 * np.linalg.norm(gr)
 
 
+def _round_bf16(a):
+    """Round to the nearest BF16 value (ties to even), as __float2bfloat16_rn does."""
+    b = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def test_bf16_loss_matches_rounded_oracle(expgb):
+    """bf16 mode: the loss through the tensor-core layer products equals the FP64 oracle
+    forward with the weights and hidden activations rounded to BF16 where the kernels round
+    them, up to FP32 accumulation order and the occasional activation that rounds to the
+    other BF16 neighbour (relative 2e-3; a wrong fragment layout is off by order one)."""
+    p, x, tmp2, target = _batch(500, 11)
+    m = expgb.Mlp(seed=1, bf16=True)
+    m.params(set=p)
+    L, _ = m.loss_grad(x, tmp2, target)
+    W1, b1, W2, b2, W3, b3 = omlp.unflatten(p)
+    h1 = _round_bf16(np.maximum(x.astype(np.float64) @ _round_bf16(W1).T + b1, 0.0))
+    h2 = _round_bf16(np.maximum(h1 @ _round_bf16(W2).T + b2, 0.0))
+    y = h2 @ _round_bf16(W3).T + b3
+    pred = (1.0 + y[:, 0] + 1j * y[:, 1]) * tmp2
+    Lr = float(np.mean(np.abs(pred - target) ** 2) / 0.05 ** 2)
+    assert abs(L - Lr) < 2e-3 * abs(Lr), (L, Lr)
+
+
 def test_untrained_model_is_the_mp2_guess(expgb):
     prob = syn.make_problem(77, 4, 12, G=2)
     a = expgb.from_problems([prob])

@@ -298,14 +298,22 @@ __global__ void k_tau3(cplx* __restrict__ tau, cplx* __restrict__ taut, cplx* __
     const int ii = T.g0[2] + i2, jj = T.g0[3] + i3;
     const int64_t p = T.base + i0 * T.st[0] + i1 * T.st[1] + i2 * T.st[2] + i3 * T.st[3];
     const cplx x = t2[p];
-    double ar = 0.0, ai = 0.0, br = 0.0, bi = 0.0;
     const int kai = t1i[a * no + ii], kbj = t1i[b * no + jj];
+    const int kbi = t1i[b * no + ii], kaj = t1i[a * no + jj];
+    if ((kai < 0 || kbj < 0) && (kbi < 0 || kaj < 0)) {
+      // no t1 product is symmetry-allowed here (most elements under Z_G): the same values
+      // without the FP64 adds of zero (GB300's FP64 pipe bounds this kernel otherwise)
+      tau[p] = x;
+      taut[p] = x;
+      zeta[p] = make_double2(0.5 * x.x, 0.5 * x.y);
+      continue;
+    }
+    double ar = 0.0, ai = 0.0, br = 0.0, bi = 0.0;
     if (kai >= 0 && kbj >= 0) {
       const cplx u = t1[kai], w = t1[kbj];
       ar = u.x * w.x - u.y * w.y;
       ai = u.x * w.y + u.y * w.x;
     }
-    const int kbi = t1i[b * no + ii], kaj = t1i[a * no + jj];
     if (kbi >= 0 && kaj >= 0) {
       const cplx u = t1[kbi], w = t1[kaj];
       br = u.x * w.x - u.y * w.y;

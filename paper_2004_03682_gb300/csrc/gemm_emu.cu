@@ -430,18 +430,29 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int buf = gc & 1;
         if (!mbar_wait(&accf[buf], (gc >> 1) & 1, abort, gerr, wns)) { ok = false; break; }
         fence_after();
+        // the diagonals in groups of 48 staged values: every load of a group is issued
+        // before its one wait (the waits, not the conversions, bound the epilogue of
+        // short products); each diagonal is still added in the same order
+        constexpr int DG = HW == 16 ? 3 : 2;
 #pragma unroll
-        for (int dgi = 0; dgi < S; ++dgi) {
-          const int shift = BETA * (S - 1 - dgi);
-          uint32_t v[HW];
+        for (int d0 = 0; d0 < S; d0 += DG) {
+          uint32_t v[DG][HW];
 #pragma unroll
-          for (int j8 = 0; j8 < HW / 8; ++j8)
-            if (j8 < nv8)
-              tmem_ld8(tmem + (uint32_t(q * 32) << 16) + buf * 256 + dgi * SH::BN + h * HW + j8 * 8, v + j8 * 8);
+          for (int dd = 0; dd < DG; ++dd)
+#pragma unroll
+            for (int j8 = 0; j8 < HW / 8; ++j8)
+              if (d0 + dd < S && j8 < nv8)
+                tmem_ld8(tmem + (uint32_t(q * 32) << 16) + buf * 256 + (d0 + dd) * SH::BN + h * HW + j8 * 8,
+                         v[dd] + j8 * 8);
           tmem_wait_ld();
 #pragma unroll
-          for (int u = 0; u < HW; ++u)
-            if (u < nv8 * 8) R[u] += (long long)__float2int_rn(__uint_as_float(v[u])) << shift;
+          for (int dd = 0; dd < DG; ++dd) {
+            if (d0 + dd >= S) break;
+            const int shift = BETA * (S - 1 - (d0 + dd));
+#pragma unroll
+            for (int u = 0; u < HW; ++u)
+              if (u < nv8 * 8) R[u] += (long long)__float2int_rn(__uint_as_float(v[dd][u])) << shift;
+          }
         }
         fence_before();
         __syncwarp();

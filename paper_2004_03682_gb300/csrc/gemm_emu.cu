@@ -20,7 +20,7 @@
 // bulk copies of pre-tiled slice tiles (the split kernels write them in the
 // canonical no-swizzle K-major UMMA layout), warp 1 issues tcgen05.mma (one
 // MMA per A slice s covers all diagonals s+1..S+1 by stacking the B slices
-// along N), warps 2-5 drain the double-buffered TMEM accumulators.
+// along N), the other 12 (six slices: 16) warps drain the double-buffered TMEM accumulators.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -41,8 +41,6 @@ constexpr int KB = 32;         // real K per smem k-block (4 core matrices of 8 
 constexpr int BETA = 7;        // bits per slice
 constexpr int KC_BLOCKS = 16;  // k-blocks per exact chunk: KC = 512 real terms
 constexpr int EMU_GM = 8;      // default row tiles per group of the GEMM work order (tuned per plan)
-constexpr int THREADS = 320;   // 10 warps: producer, MMA issuer, 8 epilogue warps
-constexpr int EPI_WARPS = 8;
 #define EXP_ZERO (-1100)       // exponent of an all-zero row / column (any x 2^-EXP_ZERO stays 0)
 // alpha encodings for the GEMM epilogue: alpha = +2^k -> k + ALPHA_POS_BIAS,
 // alpha = -2^k -> -(k + ALPHA_NEG_BIAS), anything else -> ALPHA_GENERAL
@@ -53,6 +51,13 @@ constexpr int EPI_WARPS = 8;
 template <int S>
 struct Shape {
   static constexpr int BN = S <= 5 ? 48 : 32;  // real output columns per tile
+  // epilogue: WPQ warps on each TMEM lane quarter, each HW = BN / WPQ real columns of
+  // every diagonal (more warps per tile shorten the per-warp chain of TMEM loads and
+  // integer folds that bounds short-K products); warps 0 and 1 load and issue MMAs
+  static constexpr int WPQ = BN == 32 ? 4 : 3;
+  static constexpr int EPI = 4 * WPQ;
+  static constexpr int HW = BN / WPQ;
+  static constexpr int THREADS = 64 + 32 * EPI;
   static constexpr int A_TILE = BM * KB;       // bf16 elements per slice tile
   static constexpr int B_TILE = BN * KB;
   static constexpr int A_STAGE = S * A_TILE * 2;  // bytes
@@ -65,6 +70,7 @@ struct Shape {
   static_assert(2 * ACC <= 512, "TMEM");
   static_assert(S * BN <= 256, "MMA N");
   static_assert(BN % 16 == 0, "N multiple of 16");
+  static_assert(HW % 8 == 0 && HW * WPQ == BN, "epilogue columns per warp");
 };
 
 struct EmuProb {
@@ -263,7 +269,7 @@ __device__ __forceinline__ EmuWork emu_work(const EmuProb* probs, int nprobs, in
 // the epilogue of one tile overlaps the MMAs of the next and the producer
 // prefetches across tile boundaries.
 template <int S>
-__global__ void __launch_bounds__(THREADS, 1)
+__global__ void __launch_bounds__(Shape<S>::THREADS, 1)
     k_emu_gemm(const EmuProb* probs, int nprobs, int n_tiles, int n_work, int gm,
                const __nv_bfloat16* __restrict__ Asl, const __nv_bfloat16* __restrict__ Bsl,
                const int* __restrict__ Aex, const int* __restrict__ Bex, cplx* __restrict__ C, int64_t asl_is,
@@ -298,7 +304,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
-    for (int b = 0; b < 2; ++b) { mbar_init(&accf[b], 1); mbar_init(&acce[b], EPI_WARPS); }
+    for (int b = 0; b < 2; ++b) { mbar_init(&accf[b], 1); mbar_init(&acce[b], SH::EPI); }
     mbar_init(drain, 1);
     *abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -395,10 +401,10 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
     }
   } else {
-    // ---- epilogue: 8 warps, one TMEM lane (= output row) per thread.  A warp may
-    // only read its own lane quarter (warp % 4); the two warps of a quarter take
-    // one half of the BN columns of every diagonal each.
-    constexpr int HW = SH::BN / 2;  // real columns per epilogue warp
+    // ---- epilogue: SH::EPI warps, one TMEM lane (= output row) per thread.  A warp
+    // may only read its own lane quarter (warp % 4); the WPQ warps of a quarter take
+    // one HW-column share of the BN columns of every diagonal each.
+    constexpr int HW = SH::HW;  // real columns per epilogue warp
     const int q = warp & 3;
     const int h = (warp - 2) >> 2;
     const int row = q * 32 + lane;
@@ -430,10 +436,10 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int buf = gc & 1;
         if (!mbar_wait(&accf[buf], (gc >> 1) & 1, abort, gerr, wns)) { ok = false; break; }
         fence_after();
-        // the diagonals in groups of 48 staged values: every load of a group is issued
+        // the diagonals in groups of 32 staged values: every load of a group is issued
         // before its one wait (the waits, not the conversions, bound the epilogue of
         // short products); each diagonal is still added in the same order
-        constexpr int DG = HW == 16 ? 3 : 2;
+        constexpr int DG = 32 / HW < S ? 32 / HW : S;
 #pragma unroll
         for (int d0 = 0; d0 < S; d0 += DG) {
           uint32_t v[DG][HW];
@@ -1195,7 +1201,8 @@ static void launch_product(Ctx& c, EmuPlan* p, cplx* C, int64_t cis, cplx alpha,
   const int np = int(p->h.size());
   set_smem_attr<S>();
   const int n_work = p->n_tiles * c.ninst;
-  k_emu_gemm<S><<<dim3(std::min(n_work, std::max(c.sm_count, 1))), THREADS, Shape<S>::SMEM, c.stream>>>(
+  k_emu_gemm<S><<<dim3(std::min(n_work, std::max(c.sm_count, 1))), Shape<S>::THREADS, Shape<S>::SMEM,
+                  c.stream>>>(
       p->d, np, p->n_tiles, n_work, p->gm, p->asl, p->bsl, p->aex, p->bex, C, p->asl_is, p->bsl_is, p->aex_is,
       p->bex_is, cis, alpha, p->red_elems ? ALPHA_GENERAL : alpha_code(alpha), beta ? 1 : 0, p->d_err, p->d_ws, p->ws_is,
       emu_wait_test());
@@ -1493,7 +1500,8 @@ template <int S>
 static void set_multiply_s(Ctx& c, const EmuProb* d, int np, int n_tiles, const EmuSet* A, const EmuSet* B, cplx* C,
                            cplx alpha, int* gerr) {
   set_smem_attr<S>();
-  k_emu_gemm<S><<<dim3(std::min(n_tiles, std::max(c.sm_count, 1))), THREADS, Shape<S>::SMEM, c.stream>>>(
+  k_emu_gemm<S><<<dim3(std::min(n_tiles, std::max(c.sm_count, 1))), Shape<S>::THREADS, Shape<S>::SMEM,
+                  c.stream>>>(
       d, np, n_tiles, n_tiles, EMU_GM, A->sl, B->sl, A->ex, B->ex, C, 0, 0, 0, 0, 0, alpha, alpha_code(alpha), 0, gerr,
       nullptr, 0, emu_wait_test());
   KCHECK(c);
@@ -1697,7 +1705,7 @@ exp_status noalloc_launch(cudaStream_t st, unsigned char* base, int M, int N, in
     return EXP_ECUDA;
   }
   const int n_work = int(tiles_mn * e.ksplit);
-  k_emu_gemm<S><<<dim3(unsigned(std::min(n_work, sms)), 1), THREADS, SH::SMEM, st>>>(
+  k_emu_gemm<S><<<dim3(unsigned(std::min(n_work, sms)), 1), SH::THREADS, SH::SMEM, st>>>(
       d_probs, 1, n_work, n_work, EMU_GM, asl, bsl, aex, bex, Cout, 0, 0, 0, 0, 0, alpha,
       e.ksplit > 1 ? ALPHA_GENERAL : alpha_code(alpha), beta, d_err, ws, 0, EmuWaitTest{2000000000ull, -1, 0});
   if (!launched("k_emu_gemm")) return EXP_ECUDA;

@@ -473,7 +473,7 @@ def run_triples(args):
     of that workload (iterated with level shift 8 until converged, or 400 iterations).
     value = evaluations per second (device time, CUDA events on the context stream around
     the K calls); effective FP64 TFLOP/s credits 8 flops per complex MAC the triples i<j<k
-    need.  Roofline: the stage with the larger device time (the block products, or the
+    need.  Roofline: the stage with the larger device time (the products, or the
     per-triple energy kernel), from the call's own CUDA events.  Accuracy: E(T) of the
     emulated path against the FP64 path on the same amplitudes."""
     import numpy as np
@@ -518,20 +518,20 @@ def run_triples(args):
         if args.precision == "emu":
             pairs = args.slices * (args.slices + 1) // 2
             ach = info["macs_run"] * 4 * pairs * 2 / (mp * 1e-3) / 1e12
-            roof = {"bound": "tensor", "kernel": f"k_emu_gemm<{args.slices}> ((T) block products, all launches of "
+            roof = {"bound": "tensor", "kernel": f"k_emu_gemm<{args.slices}> ((T) products, all launches of "
                                                  "one evaluation)", "achieved": ach, "peak": pk["bf16"],
                     "unit": "TFLOP/s", "frac": ach / pk["bf16"], "traffic": None,
                     "peak_src": f"{pk['src']} bf16 dense (burst)", "ms_per_evaluation": mp}
         else:
             peak = pk["bf16"] * FP64_NOMINAL_TFLOPS / BF16_NOMINAL_TFLOPS
             ach = info["macs_run"] * 8 / (mp * 1e-3) / 1e12
-            roof = {"bound": "tensor", "kernel": "k_gemm_fp64 ((T) block products)", "achieved": ach, "peak": peak,
+            roof = {"bound": "tensor", "kernel": "k_gemm_fp64 ((T) products)", "achieved": ach, "peak": peak,
                     "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
                     "peak_src": f"FP64 = {pk['src']} bf16 x nominal FP64/BF16 ratio (1.25/2250)",
                     "ms_per_evaluation": mp}
     else:
-        # algorithmic bytes: the energy kernel reads each block-product element a triple needs
-        # once (16 B; t1, <bc||jk> and the index tables come from L2)
+        # algorithmic bytes: the energy kernel reads each product output element once
+        # (16 B; t1, <bc||jk> and the index tables come from L2)
         nbytes = info["x_elems"] * 16 * info["macs"] / max(info["macs_run"], 1.0)
         ach = nbytes / (me * 1e-3) / 1e9
         roof = {"bound": "hbm", "kernel": "k_t3_energy (per-triple energies, all launches of one evaluation)",
@@ -567,14 +567,14 @@ def run_triples(args):
     line = {"metric": "ccsd_t_per_s", "value": value, "unit": "corrections/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None,
-            "dtype": (f"bf16x{args.slices}-sliced f64 emulation (block products), double-single element arithmetic, "
+            "dtype": (f"bf16x{args.slices}-sliced f64 emulation (products), double-single element arithmetic, "
                       "FP64 sums") if args.precision == "emu" else "f64",
             "data": "synthetic",
             "config": {"workload": WORKLOAD["name"], "n_occ": prob.n_occ, "n_virt": prob.n_virt, "irreps": "Z8",
                        "seed": prob.seed, "ccsd_converged": bool(conv), "e_ccsd": [e_ccsd.real, e_ccsd.imag],
                        "block": info["block"], "block_triples": info["n_block_triples"],
                        "triples": info["n_triples"],
-                       "l2": "inputs larger than L2 (block-product outputs up to 16 GiB per block triple, "
+                       "l2": "inputs larger than L2 (product outputs up to 16 GiB per batch of triples, "
                              "dense t2 and <bc||jk> 1 GB each)"},
             "E_T": [Et.real, Et.imag], "macs_needed": info["macs"], "macs_run": info["macs_run"],
             "effective_fp64_tflops": eff, "ms_products": mp, "ms_energy": me, "roofline": roof,

@@ -241,16 +241,16 @@ exp_status exp_set_amplitudes(exp_ctx* ctx, int inst, const void* t1_dev, const 
 typedef struct {
   double e_re, e_im;     /* E(T), hartree */
   double ms;             /* device time of the call on the context stream (CUDA events) */
-  double ms_products;    /* of which the block-product launches (the connected contractions) */
+  double ms_products;    /* of which the product launches (the connected contractions) */
   double ms_energy;      /* of which the per-triple energy launches */
   double macs;           /* complex multiply-adds of the connected-triples contractions the
                             triples i<j<k need (the method's work) */
-  double macs_run;       /* complex multiply-adds the block products executed (>= macs: a block
-                            product also covers index orders no triple of the block uses) */
-  double x_elems;        /* complex elements the block products wrote (each read at most once by
-                            the energy kernel) */
+  double macs_run;       /* complex multiply-adds of the products launched (each (triple, pair
+                            irrep) product covers exactly its three terms: equal to macs) */
+  double x_elems;        /* complex elements of the products' outputs Y (one per triple, pair
+                            irrep, virtual a and pair b<c; each read once by the energy kernel) */
   int64_t n_triples;     /* occupied triples i<j<k */
-  int n_block_triples;   /* occupied block triples processed */
+  int n_block_triples;   /* batches (the triples of one occupied block triple) processed */
   int block;             /* occupied spinors per block */
 } exp_t3_info;
 

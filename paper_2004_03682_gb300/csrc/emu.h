@@ -21,20 +21,28 @@ void emu_run(Ctx& c, EmuPlan* p, const GemmPlan& g, const cplx* A, const cplx* B
 void emu_release(Ctx& c);
 
 // Operand sets for grouped products whose operand pairing is chosen at run time (the
-// block products of the (T) correction).  The members of a set are sliced together;
-// a product pairs an A member (rows x K, row-major) with a B member (K x cols,
-// row-major) of the same K and writes C (rows x cols, row-major) = alpha A B.  The
-// products of one call share one launch; each product needs K short enough for one
-// exact int64 accumulation (K' up to 2^(13 - 7 (S - 6)) KC terms: far above (T)'s).
+// products of the (T) correction).  The members of a set are sliced together; a
+// product pairs an A member (rows x K, row-major) with a B member (K x cols,
+// row-major) of the same K and writes C (rows x cols, row-major) = alpha A B, or the
+// sum of up to three such pairs (segments) with equal rows and cols: C = alpha
+// sum_w A_w B_w, accumulated exactly over the concatenated K (a product whose
+// segments all have K = 0 leaves its C as it is).  Members of one
+// exponent group (same rows / cols) share their row (A) or column (B) exponents, the
+// maximum over the group; the segments of one product must come from one A group and
+// one B group.  The products of one call share one launch; each product needs a total
+// K short enough for one exact int64 accumulation (K' up to 2^(13 - 7 (S - 6)) KC
+// terms: far above (T)'s).
 struct EmuSet;
 struct EmuSetMat {
   int64_t src;  // element offset of the member in the source array
   int rows;     // A: rows; B: columns
   int K;
+  int ex_group = -1;  // members with the same group >= 0 share one exponent vector
 };
 struct EmuSetProd {
-  int a, b;       // member indices in the A and the B set
+  int a, b;       // member indices in the A and the B set (first segment)
   int64_t c_off;  // element offset of the product's C in the output array
+  int a1 = -1, b1 = -1, a2 = -1, b2 = -1;  // second and third segments (-1: none)
 };
 EmuSet* emu_set_new(Ctx& c, int S, bool b_side);
 // lay out the members (growing the set's device buffers when needed), then scan

@@ -88,6 +88,12 @@ struct EmuProb {
                                          // in use: a prefix of the canonical tile)
   int64_t au0, bu0;  // first split-A / split-B unit of this problem (units: 8-groups of one row / column)
   int64_t red0;      // first output of this problem in the split-K reduction order
+  // segmented products (operand sets): k-blocks [0, nkb0) read the slice tiles at
+  // a_sl / b_sl, [nkb0, nkb0 + nkb1) those at a_sl1 / b_sl1, the rest those at a_sl2 /
+  // b_sl2, each member tiled over its own k-blocks; nkb1 = 0: one segment
+  int64_t a_sl1, b_sl1, a_sl2, b_sl2;
+  int32_t nkb0, nkb1;
+  int64_t rx0, cx0;  // first row- / column-exponent scan item of this problem
 };
 
 // Limit of every bounded wait inside k_emu_gemm, and the timeout test hook (see
@@ -218,10 +224,10 @@ __host__ __device__ __forceinline__ int ocols_of(const EmuProb& P, int BN) { ret
 // Index of the last problem whose first unit (tile, split-A or split-B unit) is <= x.
 // Those first units do not decrease along the list (a problem with no units shares
 // its successor's), so this is the problem that owns unit x.
-enum UnitKind { UNIT_TILE, UNIT_A, UNIT_B };
+enum UnitKind { UNIT_TILE, UNIT_A, UNIT_B, UNIT_RX, UNIT_CX };
 template <UnitKind U>
 __device__ __forceinline__ int64_t first_unit(const EmuProb& q) {
-  return U == UNIT_TILE ? int64_t(q.tile0) : U == UNIT_A ? q.au0 : q.bu0;
+  return U == UNIT_TILE ? int64_t(q.tile0) : U == UNIT_A ? q.au0 : U == UNIT_B ? q.bu0 : U == UNIT_RX ? q.rx0 : q.cx0;
 }
 template <UnitKind U>
 __device__ __forceinline__ int prob_of_unit(const EmuProb* probs, int nprobs, int64_t x) {
@@ -239,11 +245,14 @@ __device__ __forceinline__ int prob_of_unit(const EmuProb* probs, int nprobs, in
 struct EmuWork {
   int pi, inst, ks, mt, nt, kb0, nkb, nkb_all;
 };
-__device__ __forceinline__ EmuWork emu_work(const EmuProb* probs, int nprobs, int n_tiles, int w, int GMr) {
+// t2p (nullable): the problem of every work item of one instance, for launches whose
+// problem list is too long for shared memory (one load instead of a binary search).
+__device__ __forceinline__ EmuWork emu_work(const EmuProb* probs, int nprobs, int n_tiles, int w, int GMr,
+                                            const int* __restrict__ t2p) {
   EmuWork W;
   W.inst = w / n_tiles;
   const int tile = w - W.inst * n_tiles;
-  const int pi = prob_of_unit<UNIT_TILE>(probs, nprobs, tile);
+  const int pi = t2p ? t2p[tile] : prob_of_unit<UNIT_TILE>(probs, nprobs, tile);
   const EmuProb& P = probs[pi];
   W.pi = pi;
   int lt = tile - P.tile0;
@@ -274,7 +283,8 @@ __global__ void __launch_bounds__(Shape<S>::THREADS, 1)
                const __nv_bfloat16* __restrict__ Asl, const __nv_bfloat16* __restrict__ Bsl,
                const int* __restrict__ Aex, const int* __restrict__ Bex, cplx* __restrict__ C, int64_t asl_is,
                int64_t bsl_is, int64_t aex_is, int64_t bex_is, int64_t c_is, cplx alpha, int alpha_e, int beta,
-               int* __restrict__ gerr, cplx* __restrict__ ws, int64_t ws_is, EmuWaitTest wt) {
+               int* __restrict__ gerr, cplx* __restrict__ ws, int64_t ws_is, EmuWaitTest wt,
+               const int* __restrict__ t2p) {
   using SH = Shape<S>;
   constexpr int STAGES = SH::STAGES;
   const unsigned long long wns = wt.wait_ns;
@@ -325,31 +335,44 @@ __global__ void __launch_bounds__(Shape<S>::THREADS, 1)
       uint32_t g = 0;  // k-blocks issued by this CTA
       bool stop = false;
       for (int w = blockIdx.x; w < n_work && !stop; w += gridDim.x) {
-        const EmuWork W = emu_work(probs, nprobs, n_tiles, w, gm);
+        const EmuWork W = emu_work(probs, nprobs, n_tiles, w, gm, t2p);
         const EmuProb& P = probs[W.pi];
         const int at = P.arows * KB, bt = P.brows * KB;  // stored slice tile sizes (elements)
-        const __nv_bfloat16* Ab = Asl + W.inst * asl_is + P.a_sl + (int64_t(W.mt) * W.nkb_all + W.kb0) * (S * at);
-        const __nv_bfloat16* Bb = Bsl + W.inst * bsl_is + P.b_sl + (int64_t(W.nt) * W.nkb_all + W.kb0) * (S * bt);
+        const __nv_bfloat16* Ai = Asl + W.inst * asl_is;
+        const __nv_bfloat16* Bi = Bsl + W.inst * bsl_is;
         for (int kb = 0; kb < W.nkb; ++kb, ++g) {
           const int st = g % STAGES;
           if (g >= STAGES && !mbar_wait(&empty[st], ((g / STAGES) & 1) ^ 1, abort, gerr, wns)) { stop = true; break; }
           if (int(g) == skip_g) continue;
+          // this k-block's slice tiles: its segment's members, tiled over their own k-blocks
+          const int kg = W.kb0 + kb;
+          int64_t as = P.a_sl, bs = P.b_sl;
+          int nk = W.nkb_all, kl = kg;
+          if (P.nkb1 > 0) {
+            if (kg < P.nkb0) {
+              nk = P.nkb0;
+            } else if (kg < P.nkb0 + P.nkb1) {
+              as = P.a_sl1, bs = P.b_sl1, nk = P.nkb1, kl = kg - P.nkb0;
+            } else {
+              as = P.a_sl2, bs = P.b_sl2, nk = W.nkb_all - P.nkb0 - P.nkb1, kl = kg - P.nkb0 - P.nkb1;
+            }
+          }
+          const __nv_bfloat16* Ak = Ai + as + (int64_t(W.mt) * nk + kl) * (S * at);
+          const __nv_bfloat16* Bk = Bi + bs + (int64_t(W.nt) * nk + kl) * (S * bt);
           uint8_t* sA = smem + st * SH::STAGE;
           uint8_t* sB = sA + SH::A_STAGE;
           mbar_expect_tx(&full[st], uint32_t(S * (at + bt) * 2));
           // rows past the stored prefix keep stale data: they only feed output rows /
           // columns beyond M / N, which the epilogue never stores
           if (P.arows == BM) {
-            bulk_g2s(sA, Ab + int64_t(kb) * S * at, SH::A_STAGE, &full[st]);
+            bulk_g2s(sA, Ak, SH::A_STAGE, &full[st]);
           } else {
-            for (int s2 = 0; s2 < S; ++s2)
-              bulk_g2s(sA + s2 * SH::A_TILE * 2, Ab + (int64_t(kb) * S + s2) * at, at * 2, &full[st]);
+            for (int s2 = 0; s2 < S; ++s2) bulk_g2s(sA + s2 * SH::A_TILE * 2, Ak + int64_t(s2) * at, at * 2, &full[st]);
           }
           if (P.brows == SH::BN) {
-            bulk_g2s(sB, Bb + int64_t(kb) * S * bt, SH::B_STAGE, &full[st]);
+            bulk_g2s(sB, Bk, SH::B_STAGE, &full[st]);
           } else {
-            for (int s2 = 0; s2 < S; ++s2)
-              bulk_g2s(sB + s2 * SH::B_TILE * 2, Bb + (int64_t(kb) * S + s2) * bt, bt * 2, &full[st]);
+            for (int s2 = 0; s2 < S; ++s2) bulk_g2s(sB + s2 * SH::B_TILE * 2, Bk + int64_t(s2) * bt, bt * 2, &full[st]);
           }
         }
       }
@@ -368,7 +391,7 @@ __global__ void __launch_bounds__(Shape<S>::THREADS, 1)
       uint32_t g = 0, gc = 0;  // k-blocks consumed, accumulator chunks started
       bool stop = false;
       for (int w = blockIdx.x; w < n_work && !stop; w += gridDim.x) {
-        const EmuWork W = emu_work(probs, nprobs, n_tiles, w, gm);
+        const EmuWork W = emu_work(probs, nprobs, n_tiles, w, gm, t2p);
         for (int kb = 0; kb < W.nkb; ++kb, ++g) {
           const int st = g % STAGES;
           const bool first = (kb % KC_BLOCKS) == 0;
@@ -411,7 +434,7 @@ __global__ void __launch_bounds__(Shape<S>::THREADS, 1)
     uint32_t gc = 0;
     bool ok = true;
     for (int w = blockIdx.x; w < n_work && ok; w += gridDim.x) {
-      const EmuWork W = emu_work(probs, nprobs, n_tiles, w, gm);
+      const EmuWork W = emu_work(probs, nprobs, n_tiles, w, gm, t2p);
       const EmuProb& P = probs[W.pi];
       const int nchunks = (W.nkb + KC_BLOCKS - 1) / KC_BLOCKS;
       long long R[HW];
@@ -544,6 +567,13 @@ __global__ void __launch_bounds__(Shape<S>::THREADS, 1)
   }
 }
 
+// The problem of every work item of a single-split launch: t2p[tile0 + x] = problem.
+__global__ void __launch_bounds__(256) k_tile_probs(const EmuProb* __restrict__ probs, int* __restrict__ t2p) {
+  const EmuProb& P = probs[blockIdx.x];
+  const int n = P.tiles_m * P.tiles_n;
+  for (int x = threadIdx.x; x < n; x += blockDim.x) t2p[P.tile0 + x] = blockIdx.x;
+}
+
 // ---------------------------------------------------------------------------
 // Split kernels.  Exponent E of a row (column) = smallest integer with
 // max |Re|, |Im| < 2^E (0 for an all-zero row).
@@ -571,14 +601,9 @@ __global__ void __launch_bounds__(256) k_row_exp(const EmuProb* __restrict__ pro
   const int inst = blockIdx.y, lane = threadIdx.x & 31;
   const int64_t stride = int64_t(gridDim.x) * (blockDim.x >> 5);
   for (int64_t it = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); it < n_items; it += stride) {
-    int64_t t = it;
-    int pi = 0;
-    for (;; ++pi) {  // work items: per problem M * ceil(K / ROW_KR)
-      const int64_t items = int64_t(probs[pi].M) * max((probs[pi].K + ROW_KR - 1) / ROW_KR, 1);
-      if (t < items || pi + 1 >= nprobs) break;
-      t -= items;
-    }
-    const EmuProb& P = probs[pi];
+    // work items: per problem M * ceil(K / ROW_KR), the problem's first at rx0
+    const EmuProb& P = probs[prob_of_unit<UNIT_RX>(probs, nprobs, it)];
+    const int64_t t = it - P.rx0;
     const int nk = max((P.K + ROW_KR - 1) / ROW_KR, 1);
     const int r = int(t / nk), kc = int(t % nk);
     if (r >= P.M) continue;
@@ -599,13 +624,9 @@ __global__ void __launch_bounds__(256) k_col_exp(const EmuProb* __restrict__ pro
                                                  int64_t ex_is) {
   __shared__ unsigned long long sh[8][33];
   const int inst = blockIdx.y;
-  int t = blockIdx.x, pi = 0;
-  for (;; ++pi) {
-    const int items = ((probs[pi].N + 31) / 32) * max((probs[pi].K + 255) / 256, 1);
-    if (t < items || pi + 1 >= nprobs) break;
-    t -= items;
-  }
-  const EmuProb P = probs[pi];
+  // work items: per problem ceil(N / 32) * ceil(K / 256), the problem's first at cx0
+  const EmuProb P = probs[prob_of_unit<UNIT_CX>(probs, nprobs, int64_t(blockIdx.x))];
+  const int t = int(int64_t(blockIdx.x) - P.cx0);
   const int nk = max((P.K + 255) / 256, 1);
   const int ct = t / nk, kc = t % nk;
   const int cl = threadIdx.x & 31, rl = threadIdx.x >> 5;
@@ -1003,6 +1024,8 @@ struct EmuState {
   std::vector<EmuProb> set_recs;  // product records of operand-set launches (emu_set_multiply)
   EmuProb* set_d = nullptr;
   int64_t set_cap = 0;
+  int* set_t2p = nullptr;  // work item -> product of such a launch
+  int64_t set_t2p_cap = 0;
 };
 
 bool emu_wanted(Ctx& c, const GemmPlan& g, const std::string&) {
@@ -1088,6 +1111,8 @@ EmuPlan* emu_plan(Ctx& c, const GemmPlan& g, const Tensor* A, const Tensor* B, b
     bex += q.N;
     p->total_rows += q.M;
     p->total_cols += q.N;
+    e.rx0 = p->n_rowexp;
+    e.cx0 = p->n_colexp;
     p->n_rowexp += q.M * std::max((q.K + ROW_KR - 1) / ROW_KR, 1);
     p->n_colexp += ((q.N + 31) / 32) * std::max((q.K + 255) / 256, 1);
     e.au0 = au0;
@@ -1205,7 +1230,7 @@ static void launch_product(Ctx& c, EmuPlan* p, cplx* C, int64_t cis, cplx alpha,
                   c.stream>>>(
       p->d, np, p->n_tiles, n_work, p->gm, p->asl, p->bsl, p->aex, p->bex, C, p->asl_is, p->bsl_is, p->aex_is,
       p->bex_is, cis, alpha, p->red_elems ? ALPHA_GENERAL : alpha_code(alpha), beta ? 1 : 0, p->d_err, p->d_ws, p->ws_is,
-      emu_wait_test());
+      emu_wait_test(), nullptr);
   KCHECK(c);
   if (reduce && p->red_elems) {
     int mks = 1;
@@ -1355,7 +1380,7 @@ void emu_release(Ctx& c) {
 
 // ---------------------------------------------------------------------------
 // Operand sets: matrices sliced once and multiplied in grouped products chosen at
-// run time (the block products of the (T) correction, whose pairing of operands
+// run time (the products of the (T) correction, whose pairing of operands
 // changes from launch to launch).  A set holds the members' slice tiles and
 // exponents in the layout of one side of k_emu_gemm; a product record takes the
 // A-side fields of one member and the B-side fields of another.
@@ -1446,8 +1471,23 @@ void emu_set_slice(Ctx& c, EmuSet* s, const std::vector<EmuSetMat>& mats, const 
   const int ocols = nh == 2 ? BN / 2 : BN;
   s->h.clear();
   int64_t sl = 0, ex = 0, u0 = 0, scan = 0;
+  std::vector<std::pair<int64_t, int>> grp;  // exponent group -> (offset, rows)
   for (const EmuSetMat& m : mats) {
     if (m.rows < 0 || m.K < 0 || m.K > EMU_MAX_K) throw ExpError{EXP_EINVAL, "emulated product: member shape"};
+    // the member's exponent vector: its own, or its group's (made by the first member)
+    int64_t ex_at = ex;
+    bool own = true;
+    if (m.ex_group >= 0) {
+      if (size_t(m.ex_group) >= grp.size()) grp.resize(size_t(m.ex_group) + 1, {-1, 0});
+      auto& gr = grp[size_t(m.ex_group)];
+      if (gr.first >= 0) {
+        if (gr.second != m.rows) throw ExpError{EXP_EINVAL, "emulated product: exponent group of unequal members"};
+        ex_at = gr.first;
+        own = false;
+      } else {
+        gr = {ex, m.rows};
+      }
+    }
     EmuProb e{};
     e.nh = nh;
     e.K = m.K;
@@ -1459,10 +1499,11 @@ void emu_set_slice(Ctx& c, EmuSet* s, const std::vector<EmuSetMat>& mats, const 
       e.tiles_m = (m.rows + BM - 1) / BM;
       e.arows = e.tiles_m == 1 ? (m.rows + 7) / 8 * 8 : BM;
       e.a_sl = sl;
-      e.a_ex = ex;
+      e.a_ex = ex_at;
       e.au0 = u0;
       sl += int64_t(e.tiles_m) * nkb * S * e.arows * KB;
       u0 += int64_t(e.tiles_m) * nkh_of(e) * e.arows * gpr_of(e);
+      e.rx0 = scan;
       scan += int64_t(m.rows) * std::max((m.K + ROW_KR - 1) / ROW_KR, 1);
     } else {
       e.b_src = m.src;
@@ -1470,13 +1511,14 @@ void emu_set_slice(Ctx& c, EmuSet* s, const std::vector<EmuSetMat>& mats, const 
       e.tiles_n = (m.rows + ocols - 1) / ocols;
       e.brows = e.tiles_n == 1 ? (nh * m.rows + 7) / 8 * 8 : BN;
       e.b_sl = sl;
-      e.b_ex = ex;
+      e.b_ex = ex_at;
       e.bu0 = u0;
       sl += int64_t(e.tiles_n) * nkb * S * e.brows * KB;
       u0 += int64_t(e.tiles_n) * nkh_of(e) * (e.brows / nh) * (KB / 8);
+      e.cx0 = scan;
       scan += int64_t((m.rows + 31) / 32) * std::max((m.K + 255) / 256, 1);
     }
-    ex += m.rows;
+    if (own) ex += m.rows;
     s->h.push_back(e);
   }
   if (s->b_side && scan > INT32_MAX) throw ExpError{EXP_EINVAL, "emulated product: operand set too large"};
@@ -1498,12 +1540,12 @@ void emu_set_slice(Ctx& c, EmuSet* s, const std::vector<EmuSetMat>& mats, const 
 
 template <int S>
 static void set_multiply_s(Ctx& c, const EmuProb* d, int np, int n_tiles, const EmuSet* A, const EmuSet* B, cplx* C,
-                           cplx alpha, int* gerr) {
+                           cplx alpha, int* gerr, const int* t2p) {
   set_smem_attr<S>();
   k_emu_gemm<S><<<dim3(std::min(n_tiles, std::max(c.sm_count, 1))), Shape<S>::THREADS, Shape<S>::SMEM,
                   c.stream>>>(
       d, np, n_tiles, n_tiles, EMU_GM, A->sl, B->sl, A->ex, B->ex, C, 0, 0, 0, 0, 0, alpha, alpha_code(alpha), 0, gerr,
-      nullptr, 0, emu_wait_test());
+      nullptr, 0, emu_wait_test(), t2p);
   KCHECK(c);
 }
 
@@ -1518,11 +1560,17 @@ void emu_set_multiply(Ctx& c, const EmuSet* A, const EmuSet* B, const std::vecto
   h.clear();
   int64_t tile0 = 0;
   for (const EmuSetProd& t : prods) {
-    if (t.a < 0 || t.a >= int(A->h.size()) || t.b < 0 || t.b >= int(B->h.size()))
-      throw ExpError{EXP_EINVAL, "emulated product: member index"};
+    const int sa[3] = {t.a, t.a1, t.a2}, sb[3] = {t.b, t.b1, t.b2};
+    int nseg = 0;
+    for (int w = 0; w < 3; ++w) {
+      if (sa[w] < 0 && sb[w] < 0 && w > 0) continue;
+      if (sa[w] < 0 || sa[w] >= int(A->h.size()) || sb[w] < 0 || sb[w] >= int(B->h.size()))
+        throw ExpError{EXP_EINVAL, "emulated product: member index"};
+      if (w != nseg) throw ExpError{EXP_EINVAL, "emulated product: segments out of order"};
+      ++nseg;
+    }
     const EmuProb& a = A->h[t.a];
     const EmuProb& b = B->h[t.b];
-    if (a.K != b.K) throw ExpError{EXP_EINVAL, "emulated product: members of different K"};
     if (a.M == 0 || b.N == 0) continue;
     EmuProb e{};
     e.a_sl = a.a_sl;
@@ -1532,13 +1580,44 @@ void emu_set_multiply(Ctx& c, const EmuSet* A, const EmuSet* B, const std::vecto
     e.c_off = t.c_off;
     e.M = a.M;
     e.N = b.N;
-    e.K = a.K;
-    e.Kp = a.Kp;
     e.nh = a.nh;
     e.tiles_m = a.tiles_m;
     e.tiles_n = b.tiles_n;
     e.arows = a.arows;
     e.brows = b.brows;
+    // the segments that hold K, in order
+    struct Seg {
+      int64_t asl, bsl;
+      int nkb;
+    } sg[3];
+    int ns = 0;
+    for (int w = 0; w < nseg; ++w) {
+      const EmuProb& aw = A->h[sa[w]];
+      const EmuProb& bw = B->h[sb[w]];
+      if (aw.K != bw.K) throw ExpError{EXP_EINVAL, "emulated product: members of different K"};
+      // one exponent per output row and column across the segments, one tiling
+      if (aw.M != a.M || aw.a_ex != a.a_ex || bw.N != b.N || bw.b_ex != b.b_ex)
+        throw ExpError{EXP_EINVAL, "emulated product: segments outside one exponent group"};
+      if (aw.K == 0) continue;
+      e.K += aw.K;
+      e.Kp += aw.Kp;
+      sg[ns++] = Seg{aw.a_sl, bw.b_sl, aw.Kp / KB};
+    }
+    if (ns > 0) {
+      e.a_sl = sg[0].asl;
+      e.b_sl = sg[0].bsl;
+    }
+    if (ns > 1) {
+      e.nkb0 = sg[0].nkb;
+      e.nkb1 = sg[1].nkb;
+      e.a_sl1 = sg[1].asl;
+      e.b_sl1 = sg[1].bsl;
+    }
+    if (ns > 2) {
+      e.a_sl2 = sg[2].asl;
+      e.b_sl2 = sg[2].bsl;
+    }
+    if (e.K == 0) continue;  // no K at all: C is left as it is (the caller clears it)
     const int64_t chunks = (e.Kp / KB + KC_BLOCKS - 1) / KC_BLOCKS;
     // one exact int64 accumulation per output: no split-K partials for these products
     if (chunks > cmax) throw ExpError{EXP_EINVAL, "emulated product: K too long for one exact accumulation"};
@@ -1553,11 +1632,19 @@ void emu_set_multiply(Ctx& c, const EmuSet* A, const EmuSet* B, const std::vecto
   grow(c, st->set_d, st->set_cap, int64_t(h.size()));
   upload(c, st->set_d, h.data(), sizeof(EmuProb) * h.size());
   const int np = int(h.size()), nt = int(tile0);
+  // a list longer than the kernel's shared-memory copy: the work items' problems as a table
+  const int* t2p = nullptr;
+  if (np * int64_t(sizeof(EmuProb)) > 4096) {
+    grow(c, st->set_t2p, st->set_t2p_cap, int64_t(nt));
+    k_tile_probs<<<np, 256, 0, c.stream>>>(st->set_d, st->set_t2p);
+    KCHECK(c);
+    t2p = st->set_t2p;
+  }
   switch (S) {
-    case 3: set_multiply_s<3>(c, st->set_d, np, nt, A, B, C, alpha, st->d_err); break;
-    case 4: set_multiply_s<4>(c, st->set_d, np, nt, A, B, C, alpha, st->d_err); break;
-    case 5: set_multiply_s<5>(c, st->set_d, np, nt, A, B, C, alpha, st->d_err); break;
-    default: set_multiply_s<6>(c, st->set_d, np, nt, A, B, C, alpha, st->d_err); break;
+    case 3: set_multiply_s<3>(c, st->set_d, np, nt, A, B, C, alpha, st->d_err, t2p); break;
+    case 4: set_multiply_s<4>(c, st->set_d, np, nt, A, B, C, alpha, st->d_err, t2p); break;
+    case 5: set_multiply_s<5>(c, st->set_d, np, nt, A, B, C, alpha, st->d_err, t2p); break;
+    default: set_multiply_s<6>(c, st->set_d, np, nt, A, B, C, alpha, st->d_err, t2p); break;
   }
 }
 
@@ -1707,7 +1794,7 @@ exp_status noalloc_launch(cudaStream_t st, unsigned char* base, int M, int N, in
   const int n_work = int(tiles_mn * e.ksplit);
   k_emu_gemm<S><<<dim3(unsigned(std::min(n_work, sms)), 1), SH::THREADS, SH::SMEM, st>>>(
       d_probs, 1, n_work, n_work, EMU_GM, asl, bsl, aex, bex, Cout, 0, 0, 0, 0, 0, alpha,
-      e.ksplit > 1 ? ALPHA_GENERAL : alpha_code(alpha), beta, d_err, ws, 0, EmuWaitTest{2000000000ull, -1, 0});
+      e.ksplit > 1 ? ALPHA_GENERAL : alpha_code(alpha), beta, d_err, ws, 0, EmuWaitTest{2000000000ull, -1, 0}, nullptr);
   if (!launched("k_emu_gemm")) return EXP_ECUDA;
   if (e.ksplit > 1) {
     launch_emu_reduce(d_probs, 1, e.ksplit, ws, 0, Cout, 0, aex, 0, bex, 0, S, alpha, beta, int64_t(M) * N, 1, sms, st);

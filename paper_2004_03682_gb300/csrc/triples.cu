@@ -18,23 +18,29 @@
 //   A_qr[a, k] = [ t_qr^ae | -<ma||qr> ],    B_p[k, bc] = [ <bc||ep> ; t_pm^bc ].
 //
 // Under the Z_G symmetry of Sec. II.C, e and m carry the same irrep G = h - G(p)
-// (h = G(b) + G(c)), and a carries G(q) + G(r) - G.  So for one p and one pair irrep h
-// the contraction is a single matrix product with K = v_G + o_G: its B operand
-// B_{p,h} is the same for the whole evaluation, its rows (q, r, a) run over every
-// occupied pair of a block.  Y is antisymmetric in (b, c), so X keeps the pair-packed
-// columns b < c only.
+// (h = G(b) + G(c)), and a carries G(i) + G(j) + G(k) - h for all three terms.  So for
+// one triple and one pair irrep h, Y is a single matrix product over the K of the
+// three terms concatenated (K_w = v_G + o_G of each), computed transposed:
 //
-// Schedule.  The occupied spinors (irrep-sorted) are cut into blocks of nb.  The B
-// members B_{p,h} are written and, in the emulated precision, sliced once.  For each
-// block triple I <= J <= K the three orderings (I; J x K), (J; I x K), (K; J x I)
-// gather their A members and run as one grouped product launch that writes X for
-// every (p; q, r) the block triple's i<j<k need; then one CTA per triple i<j<k and
-// pair irrep of (b, c) forms c (three X per P(a/bc) term), d, D and its energy.
-// Fixed-order sums over the pair irreps, then over the triples, give the per-triple
-// energies and E(T): the result does not depend on the launch configuration.  The
-// element arithmetic runs in FP64 under EXP_FP64 and in double-single FP32 (about
-// 48 bits, each pair's sum added in FP64) under the emulated precision, where the
-// FP64 pipe would bound it.
+//   Y_ijk^T[bc, a] = sum_w  Bt_{p_w,h}[bc, k] s_w A_{q_w r_w}^T[k, a],
+//
+// (p, q, r, s)_w = (i, j, k, +), (j, i, k, -), (k, j, i, -), with Bt_{p,h} = B_{p,h}^T
+// the same for the whole evaluation and the three A^T segments gathered per triple.
+// Y is antisymmetric in (b, c), so it keeps the pair-packed rows b < c only.
+//
+// Schedule.  The members Bt_{p,h} are written and, in the emulated precision, sliced
+// once, all members of one h sharing one exponent per row bc.  The occupied spinors
+// (irrep-sorted) are cut into blocks of nb, and the triples i<j<k of each block triple
+// I <= J <= K form one batch: its A^T segments are gathered (and sliced, the three
+// of one (triple, h) sharing one exponent per column a), one grouped launch forms Y
+// for every (triple, h) of the batch -- each product accumulating its three segments
+// exactly, on the tensor cores -- then one CTA per triple and pair irrep of (b, c)
+// forms c (three Y per P(a/bc) term), d, D and its energy.  Fixed-order sums over the
+// pair irreps, then over the triples, give the per-triple energies and E(T): the
+// result does not depend on the batching.  The element arithmetic runs in FP64 under
+// EXP_FP64 (where the three segments are three FP64 product launches into Y) and in
+// double-single FP32 (about 48 bits, each pair's sum added in FP64) under the emulated
+// precision, where the FP64 pipe would bound it.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -101,13 +107,14 @@ __global__ void __launch_bounds__(T3_THREADS) k_t3_dense4(cplx* __restrict__ dst
   }
 }
 
-// One row of a B member B_{p,h} (K = v_G + o_G rows, npair[h] columns): rows k < v_G
-// are <bc||ep> (e = voff[G] + k), the rest t_pm^bc (m = ooff[G] + k - v_G).
+// One row k of a member Bt_{p,h} = B_{p,h}^T (npair[h] rows x K columns, K = v_G + o_G):
+// columns k < v_G are <bc||ep> (e = voff[G] + k), the rest t_pm^bc (m = ooff[G] + k - v_G).
 struct T3BRow {
-  int64_t dst;  // element offset of the row in the B buffer
+  int64_t dst;  // element offset of the member in the Bt buffer
   int p, h;
-  int kind;     // 0: integral row (index = e), 1: amplitude row (index = m)
+  int kind;     // 0: integral column (index = e), 1: amplitude column (index = m)
   int index;
+  int k, K;     // this column and the member's column count
 };
 
 __global__ void __launch_bounds__(T3_THREADS) k_t3_brows(cplx* __restrict__ B, const T3BRow* __restrict__ rows,
@@ -116,37 +123,40 @@ __global__ void __launch_bounds__(T3_THREADS) k_t3_brows(cplx* __restrict__ B, c
   const T3BRow R = rows[blockIdx.x];
   const int n = T.npair[R.h];
   const int32_t* pr = T.pairs + T.poff[R.h];
-  cplx* dst = B + R.dst;
+  cplx* dst = B + R.dst + R.k;
   for (int u = threadIdx.x; u < n; u += blockDim.x) {
     const int b = pr[u] >> 16, c = pr[u] & 0xFFFF;
+    cplx y;
     if (R.kind == 0) {
       const cplx x = v_element(uint64_t(o + b), uint64_t(o + c), uint64_t(o + R.index), uint64_t(R.p), uint64_t(ngen), seed);
-      dst[u] = make_double2(sc * x.x, real ? 0.0 : sc * x.y);
+      y = make_double2(sc * x.x, real ? 0.0 : sc * x.y);
     } else {
-      dst[u] = t2[((int64_t(R.p) * o + R.index) * v + b) * v + c];
+      y = t2[((int64_t(R.p) * o + R.index) * v + b) * v + c];
     }
+    dst[int64_t(u) * R.K] = y;
   }
 }
 
-// The rows (q, r, a) of one occupied pair in an A member of irrep G (K = v_G + o_G):
-// [ t_qr^ae | -<ma||qr> ], read from the dense t2[q][r][a][e] and W[q][r][a][m] = <ma||qr>.
-struct T3AUnit {
-  int64_t dst;  // element offset of the pair's first row in the A buffer
+// One segment of a (triple, h) product: s A_qr^T (K x na, row-major) with
+// A_qr[a, k] = [ t_qr^ae | -<ma||qr> ] of irrep G, read from the dense t2[q][r][a][e]
+// and W[q][r][a][m] = <ma||qr>.
+struct T3Seg {
+  int64_t dst;  // element offset of the segment in the segment buffer
   int q, r;
-  int a0, na;   // first virtual and count of the irrep G(q) + G(r) - G
-  int g;        // G
-  int K;
+  int a0, na;   // first virtual and count of the irrep of a
+  int g, K;     // G and v_G + o_G
+  int neg;      // s = -1
 };
 
-__global__ void __launch_bounds__(T3_THREADS) k_t3_arows(cplx* __restrict__ A, const T3AUnit* __restrict__ units,
-                                                         T3Tables T, const cplx* __restrict__ t2,
-                                                         const cplx* __restrict__ W, int o, int v) {
-  const T3AUnit U = units[blockIdx.x];
+__global__ void __launch_bounds__(T3_THREADS) k_t3_segs(cplx* __restrict__ Sg, const T3Seg* __restrict__ segs,
+                                                        T3Tables T, const cplx* __restrict__ t2,
+                                                        const cplx* __restrict__ W, int o, int v) {
+  const T3Seg U = segs[blockIdx.x];
   const int ve = T.vcnt[U.g], e0 = T.voff[U.g], m0 = T.ooff[U.g];
   const int64_t qr = int64_t(U.q) * o + U.r;
   const int64_t n = int64_t(U.na) * U.K;
   for (int64_t x = threadIdx.x; x < n; x += blockDim.x) {
-    const int al = int(x / U.K), k = int(x - int64_t(al) * U.K);
+    const int k = int(x / U.na), al = int(x - int64_t(k) * U.na);
     const int a = U.a0 + al;
     cplx y;
     if (k < ve) {
@@ -155,25 +165,15 @@ __global__ void __launch_bounds__(T3_THREADS) k_t3_arows(cplx* __restrict__ A, c
       const cplx w = W[(qr * v + a) * o + m0 + (k - ve)];
       y = make_double2(-w.x, -w.y);
     }
-    A[U.dst + x] = y;
+    Sg[U.dst + x] = U.neg ? make_double2(-y.x, -y.y) : y;
   }
 }
-
-// Where X^(p;qr) lives for one block triple: ordering w (0: (I; J x K), 1: (J; I x K),
-// 2: (K; J x I)) has p in block P_w and pairs (q, r) in Q_w x R_w.
-struct T3Block {
-  int p0[3], q0[3], r0[3];  // first spinor of P_w, Q_w, R_w
-  int nr[3];                // |R_w| (pair slot = (q - q0) |R_w| + (r - r0))
-  int nb;                   // block size (stride of the per-p tables)
-};
 
 struct T3Tri {
   int i, j, k;
   int idx;  // position of the triple in the per-triple output (combinatorial number of i<j<k)
 };
 
-__device__ __forceinline__ cplx cadd(cplx a, cplx b) { return make_double2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ cplx csub(cplx a, cplx b) { return make_double2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ cplx cmul(cplx a, cplx b) {
   return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
@@ -218,52 +218,43 @@ __device__ __forceinline__ dsc dsc_mul(dsc a, dsc b) {
 
 // Energy of one triple i<j<k and one pair irrep h of (b, c) per CTA: the sum over
 // a<b<c with G_b + G_c = h (and G_a = G_i + G_j + G_k - h) of conj(c + d) c / D.
-// Thread = pair (b, c) of h, looping over a < b.  The per-(ordering, pair irrep)
-// bases of the three X blocks and of the pair's rows are formed once per CTA.  DS:
-// the element arithmetic in double-single (the emulated precision), each pair's sum
-// added in FP64; otherwise FP64 throughout.  Output: e3h[idx G + h].
+// Thread = pair (b, c) of h, looping over a < b.  The triple's Y^T blocks per pair
+// irrep (offset, columns) are read once per CTA.  DS: the element arithmetic in
+// double-single (the emulated precision), each pair's sum added in FP64; otherwise
+// FP64 throughout.  Output: e3h[idx G + h].
 template <bool DS>
-__global__ void __launch_bounds__(T3_THREADS) k_t3_energy(const T3Tri* __restrict__ tris, T3Block Bk, T3Tables T,
-                                                          const cplx* __restrict__ X, const int64_t* __restrict__ xoff,
-                                                          const int32_t* __restrict__ rowoff,
+__global__ void __launch_bounds__(T3_THREADS) k_t3_energy(const T3Tri* __restrict__ tris, T3Tables T,
+                                                          const cplx* __restrict__ Yt, const int64_t* __restrict__ yoff,
                                                           const cplx* __restrict__ t1, const cplx* __restrict__ V,
                                                           const double* __restrict__ eps, int o, int v,
                                                           cplx* __restrict__ e3h) {
   const T3Tri tr = tris[blockIdx.x];
   const int h = blockIdx.y;
   const int G = T.G;
-  __shared__ int64_t sxb[3][EXP_MAX_G];  // X block of ordering w, pair irrep hh: element offset
-  __shared__ int32_t srb[3][EXP_MAX_G];  // its first row of the triple's pair (q, r)
-  __shared__ int32_t snp[EXP_MAX_G];     // pairs per irrep
+  __shared__ int64_t syo[EXP_MAX_G];  // Y^T block of pair irrep hh: element offset (rows bc, columns a)
+  __shared__ int32_t sna[EXP_MAX_G];  // its columns
   __shared__ double red[2][T3_THREADS / 32];
-  const int P[3] = {tr.i, tr.j, tr.k}, Q[3] = {tr.j, tr.i, tr.j}, R[3] = {tr.k, tr.k, tr.i};
-  if (int(threadIdx.x) < 3 * G) {
-    const int w = threadIdx.x / G, hh = threadIdx.x - w * G;
-    const int slot = (Q[w] - Bk.q0[w]) * Bk.nr[w] + (R[w] - Bk.r0[w]);
-    const int g = ((hh - T.go[P[w]]) % G + G) % G;
-    srb[w][hh] = rowoff[(w * G + g) * Bk.nb * Bk.nb + slot];
-    sxb[w][hh] = xoff[(w * Bk.nb + (P[w] - Bk.p0[w])) * G + hh];
-  }
-  if (int(threadIdx.x) < G) snp[threadIdx.x] = T.npair[threadIdx.x];
-  __syncthreads();
+  const int P[3] = {tr.i, tr.j, tr.k};
   const int gijk = (T.go[tr.i] + T.go[tr.j] + T.go[tr.k]) % G;
+  if (int(threadIdx.x) < G) {
+    const int hh = threadIdx.x;
+    syo[hh] = yoff[int64_t(blockIdx.x) * G + hh];
+    sna[hh] = T.vcnt[((gijk - hh) % G + G) % G];
+  }
+  __syncthreads();
   const int ga = ((gijk - h) % G + G) % G;
   const int na = T.vcnt[ga], a0 = T.voff[ga];
-  const int n = snp[h];
+  const int n = T.npair[h];
   const int32_t* pr = T.pairs + T.poff[h];
   const double* ev = eps + o;
   const double eijk = eps[tr.i] + eps[tr.j] + eps[tr.k];
   const int gx[3] = {T.go[tr.i], T.go[tr.j], T.go[tr.k]};
   const int Yx[3] = {tr.j, tr.i, tr.j}, Zx[3] = {tr.k, tr.k, tr.i};
 
-  // Y(alpha; pair column col of irrep hh) = X^(i;jk) - X^(j;ik) - X^(k;ji)  (FP64 sums)
+  // Y(alpha; pair column col of irrep hh) = X^(i;jk) - X^(j;ik) - X^(k;ji), one product
   auto Y = [&](int alpha, int hh, int col) {
     const int64_t al = alpha - T.voff[T.gv[alpha]];
-    const int64_t np = snp[hh];
-    const cplx x0 = X[sxb[0][hh] + (srb[0][hh] + al) * np + col];
-    const cplx x1 = X[sxb[1][hh] + (srb[1][hh] + al) * np + col];
-    const cplx x2 = X[sxb[2][hh] + (srb[2][hh] + al) * np + col];
-    return make_double2(x0.x - x1.x - x2.x, x0.y - x1.y - x2.y);
+    return Yt[syo[hh] + int64_t(col) * sna[hh] + al];
   };
   auto Vv = [&](int b, int c, int y, int z) { return V[((int64_t(y) * o + z) * v + b) * v + c]; };
 
@@ -470,117 +461,87 @@ DevTables upload_tables(Ctx& c, const HostTables& H) {
 int64_t choose3(int64_t n) { return n < 3 ? 0 : n * (n - 1) * (n - 2) / 6; }
 int64_t choose2(int64_t n) { return n < 2 ? 0 : n * (n - 1) / 2; }
 
-// One block triple's plan: the A members (ordering w, irrep g), the products and
-// where each X block and each pair's rows sit.
+// One batch (the triples i<j<k of a block triple): the A^T segments, the products
+// and where each (triple, h) block of Y^T sits.
 struct BlockPlan {
-  T3Block bk{};
-  int ns[3] = {0, 0, 0};                  // |P_w|, used for the per-p tables
-  std::vector<EmuSetMat> amats;           // [3 G] A members (src, rows, K)
-  std::vector<T3AUnit> aunits;            // gather units
-  std::vector<int32_t> rowoff;            // [3 G nb^2]
-  std::vector<int64_t> xoff;              // [3 nb G]
-  std::vector<EmuSetProd> prods;          // products (A member, B member, X offset)
-  std::vector<GemmProb> fprods;           // the same products for the FP64 kernel
-  std::vector<std::pair<int64_t, int64_t>> zeros;  // X regions of K = 0 products (offset, count)
   std::vector<T3Tri> tris;
-  int64_t a_elems = 0, x_elems = 0;
+  std::vector<T3Seg> segs;                // gather units, one per segment with K > 0
+  std::vector<EmuSetMat> smats;           // the segments as B-set members (K x na), one exponent group per (triple, h)
+  std::vector<EmuSetProd> prods;          // per (triple, h): its segments with their Bt members
+  std::vector<GemmProb> fprods[3];        // FP64: the w-th segment of every product
+  std::vector<int64_t> yoff;              // [tris G] Y^T block of (triple, h)
+  std::vector<std::pair<int64_t, int64_t>> zeros;  // Y^T blocks of products with no K (offset, count)
+  int64_t y_elems = 0, s_elems = 0;
   double macs_run = 0.0, macs_need = 0.0;
 };
 
-// Blocks: [b nb, min((b + 1) nb, o)).  Pairs (q, r) of ordering w are kept when some p
-// of P_w completes them to a triple i<j<k: w = 0 (p = i; q = j, r = k), 1 (p = j; q = i,
-// r = k), 2 (p = k; q = j, r = i).
+// Blocks: [b nb, min((b + 1) nb, o)).  The batch of block triple I <= J <= K is its
+// triples i<j<k with i in I, j in J, k in K.
 void plan_block(const HostTables& H, int nb, int I, int J, int K, const std::vector<int64_t>& boff,
                 BlockPlan& bp, bool build) {
   const int o = H.o, G = H.G;
   auto lo = [&](int b) { return b * nb; };
   auto hi = [&](int b) { return std::min((b + 1) * nb, o); };
-  const int PB[3] = {I, J, K}, QB[3] = {J, I, J}, RB[3] = {K, K, I};
-  bp.bk.nb = nb;
-  for (int w = 0; w < 3; ++w) {
-    bp.bk.p0[w] = lo(PB[w]);
-    bp.bk.q0[w] = lo(QB[w]);
-    bp.bk.r0[w] = lo(RB[w]);
-    bp.bk.nr[w] = hi(RB[w]) - lo(RB[w]);
-    bp.ns[w] = hi(PB[w]) - lo(PB[w]);
-  }
-  const int nb2 = nb * nb;
-  bp.amats.assign(3 * G, EmuSetMat{0, 0, 0});
   if (build) {
-    bp.rowoff.assign(size_t(3) * G * nb2, 0);
-    bp.xoff.assign(size_t(3) * nb * G, -1);
-    bp.aunits.clear();
-    bp.prods.clear();
-    bp.fprods.clear();
-    bp.zeros.clear();
     bp.tris.clear();
+    bp.segs.clear();
+    bp.smats.clear();
+    bp.prods.clear();
+    for (auto& f : bp.fprods) f.clear();
+    bp.yoff.clear();
+    bp.zeros.clear();
   }
-  bp.a_elems = bp.x_elems = 0;
+  bp.y_elems = bp.s_elems = 0;
   bp.macs_run = bp.macs_need = 0.0;
-  // does some p of P_w make (q, r) part of a triple i<j<k?
-  auto pair_used = [&](int w, int q, int r) {
-    const int p0 = lo(PB[w]), p1 = hi(PB[w]);
-    if (w == 0) return q < r && p0 < q;               // i < j < k: p < q < r
-    if (w == 1) return std::max(p0, q + 1) <= std::min(p1 - 1, r - 1);  // q < p < r
-    return r < q && p1 - 1 > q;                        // r < q < p
-  };
-  for (int w = 0; w < 3; ++w)
-    for (int g = 0; g < G; ++g) {
-      const int Kg = H.vcnt[g] + H.ocnt[g];
-      int64_t rows = 0;
-      for (int q = lo(QB[w]); q < hi(QB[w]); ++q)
-        for (int r = lo(RB[w]); r < hi(RB[w]); ++r) {
-          const int slot = (q - lo(QB[w])) * bp.bk.nr[w] + (r - lo(RB[w]));
-          if (!pair_used(w, q, r)) continue;
-          const int ga = ((H.go[q] + H.go[r] - g) % G + G) % G;
-          const int na = H.vcnt[ga];
-          if (build) {
-            bp.rowoff[(size_t(w) * G + g) * nb2 + slot] = int32_t(rows);
-            if (na && Kg) bp.aunits.push_back(T3AUnit{bp.a_elems + rows * Kg, q, r, H.voff[ga], na, g, Kg});
-          }
-          rows += na;
-        }
-      bp.amats[w * G + g] = EmuSetMat{bp.a_elems, int(rows), Kg};
-      bp.a_elems += rows * Kg;
-    }
-  // products: X^(p;.)[h] = A_(w, h - G(p)) B_(p, h)
-  for (int w = 0; w < 3; ++w)
-    for (int p = lo(PB[w]); p < hi(PB[w]); ++p)
-      for (int h = 0; h < G; ++h) {
-        const int g = ((h - H.go[p]) % G + G) % G;
-        const EmuSetMat& am = bp.amats[w * G + g];
-        const int64_t n = H.npair[h];
-        if (am.rows == 0 || n == 0) continue;
-        if (build) bp.xoff[(size_t(w) * nb + (p - lo(PB[w]))) * G + h] = bp.x_elems;
-        if (build && am.K == 0) {
-          bp.zeros.push_back({bp.x_elems, int64_t(am.rows) * n});
-        } else if (build) {
-          bp.prods.push_back(EmuSetProd{w * G + g, p * G + h, bp.x_elems});
-          GemmProb f{};
-          f.a = am.src;
-          f.b = boff[size_t(p) * G + h];
-          f.c = bp.x_elems;
-          f.M = am.rows;
-          f.N = int32_t(n);
-          f.K = am.K;
-          bp.fprods.push_back(f);
-        }
-        bp.macs_run += double(am.rows) * double(n) * double(am.K);
-        bp.x_elems += int64_t(am.rows) * n;
-      }
-  // triples i<j<k of the block triple, and the products they need
+  int tl = 0;
   for (int i = lo(I); i < hi(I); ++i)
     for (int j = std::max(lo(J), i + 1); j < hi(J); ++j)
-      for (int k = std::max(lo(K), j + 1); k < hi(K); ++k) {
-        const int gijk = (H.go[i] + H.go[j] + H.go[k]) % G;
-        const int Pn[3] = {i, j, k};
-        for (int w = 0; w < 3; ++w)
-          for (int h = 0; h < G; ++h) {
-            const int ga = ((gijk - h) % G + G) % G;
-            const int g = ((h - H.go[Pn[w]]) % G + G) % G;
-            bp.macs_need += double(H.vcnt[ga]) * double(H.npair[h]) * double(H.vcnt[g] + H.ocnt[g]);
-          }
+      for (int k = std::max(lo(K), j + 1); k < hi(K); ++k, ++tl) {
         if (build) bp.tris.push_back(T3Tri{i, j, k, int(choose3(k) + choose2(j) + i)});
+        const int gijk = (H.go[i] + H.go[j] + H.go[k]) % G;
+        const int Pw[3] = {i, j, k}, Qw[3] = {j, i, j}, Rw[3] = {k, k, i};
+        for (int h = 0; h < G; ++h) {
+          const int ga = ((gijk - h) % G + G) % G;
+          const int na = H.vcnt[ga];
+          const int64_t n = H.npair[h];
+          if (build) bp.yoff.push_back(bp.y_elems);
+          if (na == 0 || n == 0) continue;
+          EmuSetProd pd{-1, -1, bp.y_elems};
+          int* sa[3] = {&pd.a, &pd.a1, &pd.a2};
+          int* sb[3] = {&pd.b, &pd.b1, &pd.b2};
+          int ns = 0, ksum = 0;
+          for (int w = 0; w < 3; ++w) {
+            const int g = ((h - H.go[Pw[w]]) % G + G) % G;
+            const int Kw = H.vcnt[g] + H.ocnt[g];
+            bp.macs_need += double(na) * double(n) * double(Kw);
+            if (Kw == 0) continue;
+            if (build) {
+              bp.segs.push_back(T3Seg{bp.s_elems, Qw[w], Rw[w], H.voff[ga], na, g, Kw, w > 0 ? 1 : 0});
+              *sa[ns] = Pw[w] * G + h;
+              *sb[ns] = int(bp.smats.size());
+              bp.smats.push_back(EmuSetMat{bp.s_elems, na, Kw, tl * G + h});
+              GemmProb f{};
+              f.a = boff[size_t(Pw[w]) * G + h];
+              f.b = bp.s_elems;
+              f.c = bp.y_elems;
+              f.M = int32_t(n);
+              f.N = na;
+              f.K = Kw;
+              bp.fprods[ns].push_back(f);
+            }
+            ++ns;
+            ksum += Kw;
+            bp.s_elems += int64_t(Kw) * na;
+          }
+          if (build) {
+            if (ns)
+              bp.prods.push_back(pd);
+            else
+              bp.zeros.push_back({bp.y_elems, n * na});
+          }
+          bp.macs_run += double(na) * double(n) * double(ksum);
+          bp.y_elems += n * na;
+        }
       }
 }
 
@@ -662,7 +623,7 @@ void ccsd_t(Ctx& c, int inst, int block, exp_t3_info* info, double* per_triple) 
   cplx* Wd = (cplx*)sc.get(sizeof(cplx) * size_t(o) * o * v * o);  // Wd[q][r][a][m] = <ma||qr>
   dense4(Wd, T3Dense4{{o, o, v, o}, {0, 0, o, 0}, {3, 2, 0, 1}});
 
-  // B members B_{p,h} (K = v_G + o_G rows x npair[h] columns, G = h - G(p))
+  // members Bt_{p,h} = B_{p,h}^T (npair[h] rows x K = v_G + o_G columns, G = h - G(p))
   std::vector<int64_t> boff(size_t(o) * G);
   std::vector<EmuSetMat> bmats(size_t(o) * G);
   std::vector<T3BRow> brows;
@@ -672,11 +633,11 @@ void ccsd_t(Ctx& c, int inst, int block, exp_t3_info* info, double* per_triple) 
       const int g = ((h - H.go[p]) % G + G) % G;
       const int K = H.vcnt[g] + H.ocnt[g], N = H.npair[h];
       boff[size_t(p) * G + h] = bsz;
-      bmats[size_t(p) * G + h] = EmuSetMat{bsz, N, K};
+      bmats[size_t(p) * G + h] = EmuSetMat{bsz, N, K, h};  // one row exponent per (h, bc) over every p
       if (N)
         for (int k = 0; k < K; ++k) {
           const bool vr = k < H.vcnt[g];
-          brows.push_back(T3BRow{bsz + int64_t(k) * N, p, h, vr ? 0 : 1, vr ? H.voff[g] + k : H.ooff[g] + k - H.vcnt[g]});
+          brows.push_back(T3BRow{bsz, p, h, vr ? 0 : 1, vr ? H.voff[g] + k : H.ooff[g] + k - H.vcnt[g], k, K});
         }
       bsz += int64_t(K) * N;
     }
@@ -689,49 +650,48 @@ void ccsd_t(Ctx& c, int inst, int block, exp_t3_info* info, double* per_triple) 
     KCHECK(c);
   }
   if (emulated) {
-    sc.B = emu_set_new(c, c.cfg.n_slices, true);
     sc.A = emu_set_new(c, c.cfg.n_slices, false);
-    emu_set_slice(c, sc.B, bmats, Bbuf);
+    sc.B = emu_set_new(c, c.cfg.n_slices, true);
+    emu_set_slice(c, sc.A, bmats, Bbuf);
   }
 
-  // block size: the largest whose A and X buffers fit the budget
+  // block size: the largest whose segment and Y^T buffers fit the budget
   const int64_t budget = int64_t(1) << 30;  // complex elements (16 GiB)
   const int nbmax = std::max(1, std::min(o, block > 0 ? block : 64));
   int nb = 1;
-  int64_t max_a = 0, max_x = 0;
+  int64_t max_s = 0, max_y = 0;
   for (int cand = nbmax; cand >= 1; --cand) {
     const int nblk = (o + cand - 1) / cand;
-    int64_t ma = 0, mx = 0;
+    int64_t ms = 0, my = 0;
     BlockPlan probe;
     for (int I = 0; I < nblk; ++I)
       for (int J = I; J < nblk; ++J)
         for (int K = J; K < nblk; ++K) {
           plan_block(H, cand, I, J, K, boff, probe, false);
-          ma = std::max(ma, probe.a_elems);
-          mx = std::max(mx, probe.x_elems);
+          ms = std::max(ms, probe.s_elems);
+          my = std::max(my, probe.y_elems);
         }
     nb = cand;
-    max_a = ma;
-    max_x = mx;
-    if (block > 0 || ma + mx <= budget) break;  // a requested block size is taken as given
+    max_s = ms;
+    max_y = my;
+    if (block > 0 || ms + my <= budget) break;  // a requested block size is taken as given
   }
   const int nblk = o ? (o + nb - 1) / nb : 0;
-  cplx* Abuf = (cplx*)sc.get(sizeof(cplx) * size_t(std::max<int64_t>(max_a, 1)));
-  cplx* X = (cplx*)sc.get(sizeof(cplx) * size_t(std::max<int64_t>(max_x, 1)));
+  cplx* Sbuf = (cplx*)sc.get(sizeof(cplx) * size_t(std::max<int64_t>(max_s, 1)));
+  cplx* Yt = (cplx*)sc.get(sizeof(cplx) * size_t(std::max<int64_t>(max_y, 1)));
   cplx* e3 = (cplx*)sc.get(sizeof(cplx) * size_t(std::max<int64_t>(ntri, 1)));
   cplx* e3h = (cplx*)sc.get(sizeof(cplx) * size_t(std::max<int64_t>(ntri, 1)) * G);  // per (triple, pair irrep)
   CK(cudaMemsetAsync(e3h, 0, sizeof(cplx) * size_t(std::max<int64_t>(ntri, 1)) * G, c.stream));
-  const size_t nb2 = size_t(nb) * nb;
-  int32_t* d_rowoff = (int32_t*)sc.get(sizeof(int32_t) * 3 * G * nb2);
-  int64_t* d_xoff = (int64_t*)sc.get(sizeof(int64_t) * 3 * size_t(nb) * G);
-  T3Tri* d_tris = (T3Tri*)sc.get(sizeof(T3Tri) * nb2 * nb);
-  T3AUnit* d_units = (T3AUnit*)sc.get(sizeof(T3AUnit) * 3 * G * nb2);
-  GemmProb* d_fp = (GemmProb*)sc.get(sizeof(GemmProb) * 3 * size_t(nb) * G);
+  const size_t nb3 = size_t(nb) * nb * nb;  // triples of a batch, at most
+  int64_t* d_yoff = (int64_t*)sc.get(sizeof(int64_t) * nb3 * G);
+  T3Tri* d_tris = (T3Tri*)sc.get(sizeof(T3Tri) * nb3);
+  T3Seg* d_segs = (T3Seg*)sc.get(sizeof(T3Seg) * nb3 * G * 3);
+  GemmProb* d_fp = (GemmProb*)sc.get(sizeof(GemmProb) * nb3 * G);
 
-  double macs_need = 0.0, macs_run = 0.0, x_total = 0.0;
+  double macs_need = 0.0, macs_run = 0.0, y_total = 0.0;
   int n_bt = 0;
   BlockPlan bp;
-  // per block triple: events around its product launch and its energy launch
+  // per batch: events around its product launch and its energy launch
   std::vector<cudaEvent_t> evs;
   struct EvGuard {
     std::vector<cudaEvent_t>& e;
@@ -751,53 +711,55 @@ void ccsd_t(Ctx& c, int inst, int block, exp_t3_info* info, double* per_triple) 
         plan_block(H, nb, I, J, K, boff, bp, true);
         if (bp.tris.empty()) continue;
         ++n_bt;
-        x_total += double(bp.x_elems);
+        y_total += double(bp.y_elems);
         macs_need += bp.macs_need;
         macs_run += bp.macs_run;
-        // A members
-        if (!bp.aunits.empty()) {
-          upload(c, d_units, bp.aunits.data(), sizeof(T3AUnit) * bp.aunits.size());
-          k_t3_arows<<<unsigned(bp.aunits.size()), T3_THREADS, 0, c.stream>>>(Abuf, d_units, DT.T, t2d, Wd, o, v);
+        // the A^T segments of every (triple, h)
+        if (!bp.segs.empty()) {
+          upload(c, d_segs, bp.segs.data(), sizeof(T3Seg) * bp.segs.size());
+          k_t3_segs<<<unsigned(bp.segs.size()), T3_THREADS, 0, c.stream>>>(Sbuf, d_segs, DT.T, t2d, Wd, o, v);
           KCHECK(c);
         }
-        for (auto& z : bp.zeros) CK(cudaMemsetAsync(X + z.first, 0, sizeof(cplx) * size_t(z.second), c.stream));
-        // X = A B for every product of the three orderings
-        if (emulated) emu_set_slice(c, sc.A, bp.amats, Abuf);
+        for (auto& z : bp.zeros) CK(cudaMemsetAsync(Yt + z.first, 0, sizeof(cplx) * size_t(z.second), c.stream));
+        if (emulated) emu_set_slice(c, sc.B, bp.smats, Sbuf);
         mark();
+        // Y^T = sum of the segment products, for every (triple, h) of the batch
         if (emulated) {
-          emu_set_multiply(c, sc.A, sc.B, bp.prods, X, make_double2(1.0, 0.0));
-        } else if (!bp.fprods.empty()) {
-          GemmPlan g;
-          g.tm = g.tn = 64;
-          int tile0 = 0;
-          for (GemmProb& f : bp.fprods) {
-            f.tiles_m = (f.M + g.tm - 1) / g.tm;
-            f.tiles_n = (f.N + g.tn - 1) / g.tn;
-            f.ksplit = 1;
-            f.kchunk = (f.K + 7) / 8 * 8;
-            f.tile0 = tile0;
-            tile0 += f.tiles_m * f.tiles_n;
+          emu_set_multiply(c, sc.A, sc.B, bp.prods, Yt, make_double2(1.0, 0.0));
+        } else {
+          for (int w = 0; w < 3; ++w) {
+            std::vector<GemmProb>& fp = bp.fprods[w];
+            if (fp.empty()) continue;
+            GemmPlan g;
+            g.tm = g.tn = 64;
+            int tile0 = 0;
+            for (GemmProb& f : fp) {
+              f.tiles_m = (f.M + g.tm - 1) / g.tm;
+              f.tiles_n = (f.N + g.tn - 1) / g.tn;
+              f.ksplit = 1;
+              f.kchunk = (f.K + 7) / 8 * 8;
+              f.tile0 = tile0;
+              tile0 += f.tiles_m * f.tiles_n;
+            }
+            g.n_tiles = tile0;
+            g.n_probs = int(fp.size());
+            upload(c, d_fp, fp.data(), sizeof(GemmProb) * fp.size());
+            g.d_probs = d_fp;
+            OneInstance one(c);
+            // the first segment of every product writes its Y^T block, the others add to it
+            launch_gemm_fp64(c, g, Bbuf, Sbuf, Yt, 0, 0, 0, make_double2(1.0, 0.0), w > 0);
           }
-          g.n_tiles = tile0;
-          g.n_probs = int(bp.fprods.size());
-          upload(c, d_fp, bp.fprods.data(), sizeof(GemmProb) * bp.fprods.size());
-          g.d_probs = d_fp;
-          OneInstance one(c);
-          launch_gemm_fp64(c, g, Abuf, Bbuf, X, 0, 0, 0, make_double2(1.0, 0.0), false);
         }
         mark();
-        // energies of the block triple's i<j<k
-        upload(c, d_rowoff, bp.rowoff.data(), sizeof(int32_t) * bp.rowoff.size());
-        upload(c, d_xoff, bp.xoff.data(), sizeof(int64_t) * bp.xoff.size());
+        // energies of the batch's i<j<k
+        upload(c, d_yoff, bp.yoff.data(), sizeof(int64_t) * bp.yoff.size());
         upload(c, d_tris, bp.tris.data(), sizeof(T3Tri) * bp.tris.size());
         mark();
         const dim3 eg(unsigned(bp.tris.size()), unsigned(G));
         if (emulated)
-          k_t3_energy<true><<<eg, T3_THREADS, 0, c.stream>>>(d_tris, bp.bk, DT.T, X, d_xoff, d_rowoff, t1d, Vd, eps, o, v,
-                                                             e3h);
+          k_t3_energy<true><<<eg, T3_THREADS, 0, c.stream>>>(d_tris, DT.T, Yt, d_yoff, t1d, Vd, eps, o, v, e3h);
         else
-          k_t3_energy<false><<<eg, T3_THREADS, 0, c.stream>>>(d_tris, bp.bk, DT.T, X, d_xoff, d_rowoff, t1d, Vd, eps, o,
-                                                              v, e3h);
+          k_t3_energy<false><<<eg, T3_THREADS, 0, c.stream>>>(d_tris, DT.T, Yt, d_yoff, t1d, Vd, eps, o, v, e3h);
         KCHECK(c);
         mark();
       }
@@ -843,7 +805,7 @@ void ccsd_t(Ctx& c, int inst, int block, exp_t3_info* info, double* per_triple) 
     info->ms_energy = ms_en;
     info->macs = macs_need;
     info->macs_run = macs_run;
-    info->x_elems = x_total;
+    info->x_elems = y_total;
     info->n_triples = ntri;
     info->n_block_triples = n_bt;
     info->block = nb;

@@ -210,6 +210,7 @@ extern "C" void exp_destroy(exp_ctx* x) {
   if (c.pev0) cudaEventDestroy(c.pev0);
   if (c.pev1) cudaEventDestroy(c.pev1);
   if (c.h_stats) cudaFreeHost(c.h_stats);
+  staging_release(c);
   fs_release(c);
   try { emu_release(c); } catch (...) {}
   packed_release(c);

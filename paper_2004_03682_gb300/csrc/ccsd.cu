@@ -1176,6 +1176,20 @@ void ccsd_dense_io(Ctx& c, int inst, cplx* t1d, cplx* t2d, bool to_dense) {
   }
 }
 
+// <ab||ij> of instance inst (the scaled driver integral, held in the t2 layout) as the
+// dense dst[i][j][a][b]; symmetry-forbidden entries are zero.  A context without ghost
+// spinors only.
+void ccsd_dense_driver_integral(Ctx& c, int inst, cplx* dst) {
+  CcsdState& s = S(c);
+  CK(cudaMemsetAsync(dst, 0, sizeof(cplx) * size_t(c.no_real) * c.no_real * c.nv * c.nv, c.stream));
+  if (s.t2tasks.n_chunks) {
+    k_dense_io<<<s.t2tasks.n_chunks, 256, 0, c.stream>>>(const_cast<cplx*>(s.Vd->d), int64_t(inst) * s.Vd->is,
+                                                         s.Vd->is, dst, s.t2tasks.d_tasks, s.t2tasks.d_chunks, 4,
+                                                         c.no, c.nv, 1, c.d_occreal, c.no_real);
+    KCHECK(c);
+  }
+}
+
 const Tensor* ccsd_driver_integral(Ctx& c) { return S(c).Vd; }
 
 void ccsd_mark_guessed(Ctx& c) {

@@ -31,6 +31,9 @@ void ccsd_update_step(Ctx& c, const std::function<void(double*, int)>& upd, bool
                       bool packed = false);
 int ccsd_count_converged(Ctx& c);
 const Tensor* ccsd_driver_integral(Ctx& c);
+// <ab||ij> of instance inst as the dense [i][j][a][b] (zero where symmetry forbids);
+// contexts without ghost spinors
+void ccsd_dense_driver_integral(Ctx& c, int inst, cplx* dst);
 void ccsd_mark_guessed(Ctx& c);
 // the (T) correction of instance inst (triples.cu)
 void ccsd_t(Ctx& c, int inst, int block, exp_t3_info* info, double* per_triple);

@@ -3,6 +3,7 @@
 // planner (Sec. II.B: permute operands into supermatrices, one grouped GEMM
 // over all symmetry blocks (Fig. "mult"), permute the result back).
 #include <algorithm>
+#include <cstring>
 #include <cstdio>
 #include <sstream>
 
@@ -156,6 +157,49 @@ void upload(Ctx& c, void* dst, const void* src, size_t bytes) {
   CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c.stream));
   // host buffers are temporaries: make the copy complete before they go away
   CK(cudaStreamSynchronize(c.stream));
+}
+
+void upload_async(Ctx& c, void* dst, const void* src, size_t bytes) {
+  if (!bytes) return;
+  Ctx::Staging& s = c.stg;
+  if (!s.host[0]) {
+    const size_t cap = size_t(32) << 20;
+    for (int h = 0; h < 2; ++h) {
+      CK(cudaMallocHost((void**)&s.host[h], cap));
+      CK(cudaEventCreateWithFlags(&s.ev[h], cudaEventDisableTiming));
+    }
+    s.cap = cap;
+  }
+  if (bytes > s.cap / 4) {
+    upload(c, dst, src, bytes);
+    return;
+  }
+  if (s.used + bytes > s.cap) {  // this half is full: the other one, once its copies have run
+    CK(cudaEventRecord(s.ev[s.cur], c.stream));
+    s.pending[s.cur] = true;
+    s.cur ^= 1;
+    s.used = 0;
+    if (s.pending[s.cur]) {
+      CK(cudaEventSynchronize(s.ev[s.cur]));
+      s.pending[s.cur] = false;
+    }
+  }
+  uint8_t* h = s.host[s.cur] + s.used;
+  memcpy(h, src, bytes);
+  CK(cudaMemcpyAsync(dst, h, bytes, cudaMemcpyHostToDevice, c.stream));
+  s.used += (bytes + 255) & ~size_t(255);
+}
+
+void staging_release(Ctx& c) {
+  Ctx::Staging& s = c.stg;
+  for (int h = 0; h < 2; ++h) {
+    if (s.host[h]) cudaFreeHost(s.host[h]);
+    if (s.ev[h]) cudaEventDestroy(s.ev[h]);
+    s.host[h] = nullptr;
+    s.ev[h] = nullptr;
+    s.pending[h] = false;
+  }
+  s.cap = s.used = 0;
 }
 
 Tensor* new_tensor(Ctx& c, const Layout& L, bool zero) {

@@ -293,6 +293,16 @@ struct Ctx {
   Arena op_arena;     // permuted operands and GEMM outputs of one contraction
   Arena slice_arena;  // per-iteration operand slices of one emulated product
 
+  // pinned staging for stream-ordered uploads (upload_async): two halves used in turn,
+  // each released by an event once the copies out of it have run
+  struct Staging {
+    uint8_t* host[2] = {nullptr, nullptr};
+    size_t cap = 0, used = 0;
+    int cur = 0;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    bool pending[2] = {false, false};
+  } stg;
+
   void* dalloc(size_t bytes);
   void dfree(void* p);
   void dfree_all();
@@ -323,6 +333,10 @@ void permute_into(Ctx& c, const std::string& site, Tensor& dst, const char* dlab
                   const Tensor& src, const char* slabels, bool accumulate,
                   std::vector<std::pair<double, std::string>> terms = {});
 void upload(Ctx& c, void* dst, const void* src, size_t bytes);
+// the same copy, stream-ordered: the host data are staged in pinned memory and the
+// call returns at once (large copies fall back to upload)
+void upload_async(Ctx& c, void* dst, const void* src, size_t bytes);
+void staging_release(Ctx& c);
 
 struct CudaError {
   cudaError_t e;

@@ -1529,7 +1529,7 @@ void emu_set_slice(Ctx& c, EmuSet* s, const std::vector<EmuSetMat>& mats, const 
   grow(c, s->sl, s->sl_cap, std::max<int64_t>(sl, 1));
   grow(c, s->ex, s->ex_cap, s->n_ex);
   grow(c, s->d, s->d_cap, int64_t(s->h.size()));
-  upload(c, s->d, s->h.data(), sizeof(EmuProb) * s->h.size());
+  upload_async(c, s->d, s->h.data(), sizeof(EmuProb) * s->h.size());
   switch (S) {
     case 3: set_slice_s<3>(c, s, src); break;
     case 4: set_slice_s<4>(c, s, src); break;
@@ -1630,7 +1630,7 @@ void emu_set_multiply(Ctx& c, const EmuSet* A, const EmuSet* B, const std::vecto
   }
   if (h.empty()) return;
   grow(c, st->set_d, st->set_cap, int64_t(h.size()));
-  upload(c, st->set_d, h.data(), sizeof(EmuProb) * h.size());
+  upload_async(c, st->set_d, h.data(), sizeof(EmuProb) * h.size());
   const int np = int(h.size()), nt = int(tile0);
   // a list longer than the kernel's shared-memory copy: the work items' problems as a table
   const int* t2p = nullptr;

@@ -619,7 +619,7 @@ void ccsd_t(Ctx& c, int inst, int block, exp_t3_info* info, double* per_triple) 
     KCHECK(c);
   };
   cplx* Vd = (cplx*)sc.get(sizeof(cplx) * size_t(o) * o * v * v);  // Vd[j][k][b][c] = <bc||jk>
-  dense4(Vd, T3Dense4{{o, o, v, v}, {0, 0, o, o}, {2, 3, 0, 1}});
+  ccsd_dense_driver_integral(c, inst, Vd);  // the context's own (scaled) driver integral
   cplx* Wd = (cplx*)sc.get(sizeof(cplx) * size_t(o) * o * v * o);  // Wd[q][r][a][m] = <ma||qr>
   dense4(Wd, T3Dense4{{o, o, v, o}, {0, 0, o, 0}, {3, 2, 0, 1}});
 
@@ -716,7 +716,7 @@ void ccsd_t(Ctx& c, int inst, int block, exp_t3_info* info, double* per_triple) 
         macs_run += bp.macs_run;
         // the A^T segments of every (triple, h)
         if (!bp.segs.empty()) {
-          upload(c, d_segs, bp.segs.data(), sizeof(T3Seg) * bp.segs.size());
+          upload_async(c, d_segs, bp.segs.data(), sizeof(T3Seg) * bp.segs.size());
           k_t3_segs<<<unsigned(bp.segs.size()), T3_THREADS, 0, c.stream>>>(Sbuf, d_segs, DT.T, t2d, Wd, o, v);
           KCHECK(c);
         }
@@ -743,7 +743,7 @@ void ccsd_t(Ctx& c, int inst, int block, exp_t3_info* info, double* per_triple) 
             }
             g.n_tiles = tile0;
             g.n_probs = int(fp.size());
-            upload(c, d_fp, fp.data(), sizeof(GemmProb) * fp.size());
+            upload_async(c, d_fp, fp.data(), sizeof(GemmProb) * fp.size());
             g.d_probs = d_fp;
             OneInstance one(c);
             // the first segment of every product writes its Y^T block, the others add to it
@@ -752,8 +752,8 @@ void ccsd_t(Ctx& c, int inst, int block, exp_t3_info* info, double* per_triple) 
         }
         mark();
         // energies of the batch's i<j<k
-        upload(c, d_yoff, bp.yoff.data(), sizeof(int64_t) * bp.yoff.size());
-        upload(c, d_tris, bp.tris.data(), sizeof(T3Tri) * bp.tris.size());
+        upload_async(c, d_yoff, bp.yoff.data(), sizeof(int64_t) * bp.yoff.size());
+        upload_async(c, d_tris, bp.tris.data(), sizeof(T3Tri) * bp.tris.size());
         mark();
         const dim3 eg(unsigned(bp.tris.size()), unsigned(G));
         if (emulated)

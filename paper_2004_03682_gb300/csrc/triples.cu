@@ -493,6 +493,9 @@ void plan_block(const HostTables& H, int nb, int I, int J, int K, const std::vec
   }
   bp.y_elems = bp.s_elems = 0;
   bp.macs_run = bp.macs_need = 0.0;
+  // products grouped by pair irrep: one h's members Bt_{p,h} (all p) then stay in L2
+  // while its products run
+  std::vector<std::vector<EmuSetProd>> by_h(build ? G : 0);
   int tl = 0;
   for (int i = lo(I); i < hi(I); ++i)
     for (int j = std::max(lo(J), i + 1); j < hi(J); ++j)
@@ -535,7 +538,7 @@ void plan_block(const HostTables& H, int nb, int I, int J, int K, const std::vec
           }
           if (build) {
             if (ns)
-              bp.prods.push_back(pd);
+              by_h[h].push_back(pd);
             else
               bp.zeros.push_back({bp.y_elems, n * na});
           }
@@ -543,6 +546,7 @@ void plan_block(const HostTables& H, int nb, int I, int J, int K, const std::vec
           bp.y_elems += n * na;
         }
       }
+  for (auto& v : by_h) bp.prods.insert(bp.prods.end(), v.begin(), v.end());
 }
 
 // RAII guard: the FP64 grouped kernel launches one grid row per context instance;

@@ -223,7 +223,7 @@ __device__ __forceinline__ dsc dsc_mul(dsc a, dsc b) {
 // double-single (the emulated precision), each pair's sum added in FP64; otherwise
 // FP64 throughout.  Output: e3h[idx G + h].
 template <bool DS>
-__global__ void __launch_bounds__(T3_THREADS) k_t3_energy(const T3Tri* __restrict__ tris, T3Tables T,
+__global__ void __launch_bounds__(T3_THREADS, 3) k_t3_energy(const T3Tri* __restrict__ tris, T3Tables T,
                                                           const cplx* __restrict__ Yt, const int64_t* __restrict__ yoff,
                                                           const cplx* __restrict__ t1, const cplx* __restrict__ V,
                                                           const double* __restrict__ eps, int o, int v,

@@ -735,7 +735,8 @@ void ccsd_t(Ctx& c, int inst, int block, exp_t3_info* info, double* per_triple) 
             std::vector<GemmProb>& fp = bp.fprods[w];
             if (fp.empty()) continue;
             GemmPlan g;
-            g.tm = g.tn = 64;
+            g.tm = 64;  // N = the virtuals of one irrep: 16-wide column tiles
+            g.tn = 16;
             int tile0 = 0;
             for (GemmProb& f : fp) {
               f.tiles_m = (f.M + g.tm - 1) / g.tm;

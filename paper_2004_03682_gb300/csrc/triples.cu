@@ -28,6 +28,10 @@
 // the same for the whole evaluation and the three A^T segments gathered per triple.
 // Y is antisymmetric in (b, c), so it keeps the pair-packed rows b < c only.
 //
+// Operands.  The integrals are the context's own: <bc||jk> copied out of its driver
+// integral, <ma||qr> and <bc||ep> gathered from layouts it caches (derived by a permute
+// from a held layout of the same symmetry family); t1 and t2 from its amplitudes.
+//
 // Schedule.  The members Bt_{p,h} are written and, in the emulated precision, sliced
 // once, all members of one h sharing one exponent per row bc.  The occupied spinors
 // (irrep-sorted) are cut into blocks of nb, and the triples i<j<k of each block triple
@@ -49,7 +53,6 @@
 #include "ccsd.h"
 #include "emu.h"
 #include "fpbits.h"
-#include "gen.h"
 
 namespace {
 
@@ -73,67 +76,82 @@ struct T3Tables {
   const int32_t* pidx = nullptr;   // [v * v] column of pair (b, c) in its irrep block + 1 (b < c), 0 otherwise
 };
 
-// Dense integral block dst[i0][i1][i2][i3] = scale <p q || r s>, the four V arguments
-// taken from slots m[0..3] (global index g0[slot] + i[slot]); symmetry-forbidden
-// tuples (G_p + G_q - G_r - G_s != 0 mod G) are zero, as in every stored block.
-struct T3Dense4 {
-  int n[4];
-  int g0[4];
-  int m[4];
-};
-
-__global__ void __launch_bounds__(T3_THREADS) k_t3_dense4(cplx* __restrict__ dst, T3Dense4 D, int64_t count, int ngen,
-                                                          uint64_t seed, double sc, int real, const int* __restrict__ girr,
-                                                          int G) {
-  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < count; e += int64_t(gridDim.x) * blockDim.x) {
-    int64_t r = e;
-    int i[4];
-    i[3] = int(r % D.n[3]);
-    r /= D.n[3];
-    i[2] = int(r % D.n[2]);
-    r /= D.n[2];
-    i[1] = int(r % D.n[1]);
-    i[0] = int(r / D.n[1]);
-    int g[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) g[k] = D.g0[D.m[k]] + i[D.m[k]];
-    const int s = girr[g[0]] + girr[g[1]] - girr[g[2]] - girr[g[3]];
-    if (((s % G) + G) % G != 0) {
-      dst[e] = make_double2(0.0, 0.0);
-      continue;
-    }
-    const cplx v = v_element(uint64_t(g[0]), uint64_t(g[1]), uint64_t(g[2]), uint64_t(g[3]), uint64_t(ngen), seed);
-    dst[e] = make_double2(sc * v.x, real ? 0.0 : sc * v.y);
-  }
-}
-
-// One row k of a member Bt_{p,h} = B_{p,h}^T (npair[h] rows x K columns, K = v_G + o_G):
-// columns k < v_G are <bc||ep> (e = voff[G] + k), the rest t_pm^bc (m = ooff[G] + k - v_G).
+// The amplitude columns of a member Bt_{p,h} = B_{p,h}^T (npair[h] rows x K columns,
+// K = v_G + o_G): column k >= v_G is t_pm^bc (m = ooff[G] + k - v_G); the integral
+// columns k < v_G (<bc||ep>) come from the context's integrals (k_t3_gather_bt).
 struct T3BRow {
   int64_t dst;  // element offset of the member in the Bt buffer
   int p, h;
-  int kind;     // 0: integral column (index = e), 1: amplitude column (index = m)
-  int index;
+  int m;        // the occupied index of this column
   int k, K;     // this column and the member's column count
 };
 
 __global__ void __launch_bounds__(T3_THREADS) k_t3_brows(cplx* __restrict__ B, const T3BRow* __restrict__ rows,
-                                                         T3Tables T, const cplx* __restrict__ t2, int o, int v, int ngen,
-                                                         uint64_t seed, double sc, int real) {
+                                                         T3Tables T, const cplx* __restrict__ t2, int o, int v) {
   const T3BRow R = rows[blockIdx.x];
   const int n = T.npair[R.h];
   const int32_t* pr = T.pairs + T.poff[R.h];
   cplx* dst = B + R.dst + R.k;
   for (int u = threadIdx.x; u < n; u += blockDim.x) {
     const int b = pr[u] >> 16, c = pr[u] & 0xFFFF;
-    cplx y;
-    if (R.kind == 0) {
-      const cplx x = v_element(uint64_t(o + b), uint64_t(o + c), uint64_t(o + R.index), uint64_t(R.p), uint64_t(ngen), seed);
-      y = make_double2(sc * x.x, real ? 0.0 : sc * x.y);
-    } else {
-      y = t2[((int64_t(R.p) * o + R.index) * v + b) * v + c];
-    }
-    dst[int64_t(u) * R.K] = y;
+    dst[int64_t(u) * R.K] = t2[((int64_t(R.p) * o + R.m) * v + b) * v + c];
+  }
+}
+
+// Gathers from an integral tensor of the context (its layout's sub-blocks as
+// generator tasks, 4096 elements per chunk; slot k of an element has global spinor index
+// g0[k] + i[k], virtual ones from o on).  Dense: dst[sum_k x_k ds[k]] with x_k the slot's
+// local index.  Members: slots (b, c, e, p) of <bc||ep> into Bt_{p,h}[pair (b, c)][e].
+__device__ __forceinline__ void t3_task_index(const GenTask& Tk, int64_t e, int i[4]) {
+  int64_t r = e;
+  i[3] = int(r % Tk.n[3]);
+  r /= Tk.n[3];
+  i[2] = int(r % Tk.n[2]);
+  r /= Tk.n[2];
+  i[1] = int(r % Tk.n[1]);
+  i[0] = int(r / Tk.n[1]);
+}
+
+struct T3Dense {
+  int64_t ds[4];  // destination stride of each slot's local index
+  int virt[4];    // slot holds a virtual spinor (local index = global - o)
+};
+
+__global__ void __launch_bounds__(T3_THREADS) k_t3_gather_dense(cplx* __restrict__ dst, const cplx* __restrict__ src,
+                                                                const GenTask* __restrict__ tasks,
+                                                                const ChunkRef* __restrict__ chunks, T3Dense D, int o) {
+  const ChunkRef ch = chunks[blockIdx.x];
+  const GenTask Tk = tasks[ch.task];
+  const int64_t end = min(ch.start + (int64_t)4096, Tk.count);
+  for (int64_t e = ch.start + threadIdx.x; e < end; e += blockDim.x) {
+    int i[4];
+    t3_task_index(Tk, e, i);
+    int64_t d = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) d += int64_t(Tk.g0[k] + i[k] - (D.virt[k] ? o : 0)) * D.ds[k];
+    dst[d] = src[Tk.base + i[0] * Tk.st[0] + i[1] * Tk.st[1] + i[2] * Tk.st[2] + i[3] * Tk.st[3]];
+  }
+}
+
+__global__ void __launch_bounds__(T3_THREADS) k_t3_gather_bt(cplx* __restrict__ Bt, const cplx* __restrict__ src,
+                                                             const GenTask* __restrict__ tasks,
+                                                             const ChunkRef* __restrict__ chunks, T3Tables T,
+                                                             const int64_t* __restrict__ boff, int o, int v) {
+  const ChunkRef ch = chunks[blockIdx.x];
+  const GenTask Tk = tasks[ch.task];
+  const int64_t end = min(ch.start + (int64_t)4096, Tk.count);
+  const int G = T.G;
+  for (int64_t e = ch.start + threadIdx.x; e < end; e += blockDim.x) {
+    int i[4];
+    t3_task_index(Tk, e, i);
+    const int b = Tk.g0[0] + i[0] - o, c = Tk.g0[1] + i[1] - o;
+    if (b >= c) continue;  // the members keep b < c
+    const int ee = Tk.g0[2] + i[2] - o, p = Tk.g0[3] + i[3];
+    const int h = (T.gv[b] + T.gv[c]) % G, g = T.gv[ee];
+    const int K = T.vcnt[g] + T.ocnt[g];
+    const int64_t u = T.pidx[int64_t(b) * v + c] - 1;
+    Bt[boff[int64_t(p) * G + h] + u * K + (ee - T.voff[g])] =
+        src[Tk.base + i[0] * Tk.st[0] + i[1] * Tk.st[1] + i[2] * Tk.st[2] + i[3] * Tk.st[3]];
   }
 }
 
@@ -602,11 +620,6 @@ void ccsd_t(Ctx& c, int inst, int block, exp_t3_info* info, double* per_triple) 
   CK(cudaEventCreate(&sc.ev[1]));
   CK(cudaEventRecord(sc.ev[0], c.stream));
 
-  uint64_t seed = 0;
-  CK(cudaMemcpyAsync(&seed, c.d_seed + inst, sizeof(seed), cudaMemcpyDeviceToHost, c.stream));
-  CK(cudaStreamSynchronize(c.stream));
-  const double scale = c.h_scale[inst];
-  const int real = c.cfg.real_arith;
   const double* eps = c.d_eps + size_t(inst) * (o + v);
   const DevTables DT = upload_tables(c, H);
   sc.bufs.push_back(DT.mem);
@@ -615,17 +628,45 @@ void ccsd_t(Ctx& c, int inst, int block, exp_t3_info* info, double* per_triple) 
   cplx* t1d = (cplx*)sc.get(sizeof(cplx) * size_t(o) * v);
   cplx* t2d = (cplx*)sc.get(sizeof(cplx) * size_t(o) * o * v * v);
   ccsd_dense_io(c, inst, t1d, t2d, true);
-  auto dense4 = [&](cplx* dst, T3Dense4 D) {
-    const int64_t n = int64_t(D.n[0]) * D.n[1] * D.n[2] * D.n[3];
-    if (!n) return;
-    const int blocks = int(std::min<int64_t>((n + T3_THREADS - 1) / T3_THREADS, int64_t(std::max(c.sm_count, 1)) * 32));
-    k_t3_dense4<<<blocks, T3_THREADS, 0, c.stream>>>(dst, D, n, c.n_gen, seed, scale, real, DT.T.girr, G);
-    KCHECK(c);
-  };
   cplx* Vd = (cplx*)sc.get(sizeof(cplx) * size_t(o) * o * v * v);  // Vd[j][k][b][c] = <bc||jk>
   ccsd_dense_driver_integral(c, inst, Vd);  // the context's own (scaled) driver integral
+  // An integral of the context in the layout (slot k = argument k, two row slots):
+  // cached by the context (derived by a permute from a layout of its symmetry family
+  // when one is held, else drawn once), with its sub-blocks as gather tasks on the device.
+  struct Gathered {
+    const Tensor* t = nullptr;
+    const GenTask* tasks = nullptr;
+    const ChunkRef* chunks = nullptr;
+    int n_chunks = 0;
+  };
+  auto held = [&](const IntRef& V) {
+    Gathered g;
+    const int ident[4] = {0, 1, 2, 3};
+    g.t = integral(c, V, ident, 2);
+    std::vector<GenTask> tk;
+    std::vector<ChunkRef> ch;
+    gen_tasks(c, g.t->L, tk, ch);
+    GenTask* d_tk = (GenTask*)sc.get(sizeof(GenTask) * std::max<size_t>(tk.size(), 1));
+    ChunkRef* d_ch = (ChunkRef*)sc.get(sizeof(ChunkRef) * std::max<size_t>(ch.size(), 1));
+    upload_async(c, d_tk, tk.data(), sizeof(GenTask) * tk.size());
+    upload_async(c, d_ch, ch.data(), sizeof(ChunkRef) * ch.size());
+    g.tasks = d_tk;
+    g.chunks = d_ch;
+    g.n_chunks = int(ch.size());
+    return g;
+  };
   cplx* Wd = (cplx*)sc.get(sizeof(cplx) * size_t(o) * o * v * o);  // Wd[q][r][a][m] = <ma||qr>
-  dense4(Wd, T3Dense4{{o, o, v, o}, {0, 0, o, 0}, {3, 2, 0, 1}});
+  {
+    const IntRef OVOO{{SP_OCC, SP_VIRT, SP_OCC, SP_OCC}};
+    const Gathered gw = held(OVOO);  // slots (m, a, q, r); forbidden blocks stay zero
+    CK(cudaMemsetAsync(Wd, 0, sizeof(cplx) * size_t(o) * o * v * o, c.stream));
+    const T3Dense D{{1, o, int64_t(o) * v * o, int64_t(v) * o}, {0, 1, 0, 0}};
+    if (gw.n_chunks) {
+      k_t3_gather_dense<<<unsigned(gw.n_chunks), T3_THREADS, 0, c.stream>>>(Wd, gw.t->d + size_t(inst) * gw.t->is,
+                                                                            gw.tasks, gw.chunks, D, o);
+      KCHECK(c);
+    }
+  }
 
   // members Bt_{p,h} = B_{p,h}^T (npair[h] rows x K = v_G + o_G columns, G = h - G(p))
   std::vector<int64_t> boff(size_t(o) * G);
@@ -639,18 +680,25 @@ void ccsd_t(Ctx& c, int inst, int block, exp_t3_info* info, double* per_triple) 
       boff[size_t(p) * G + h] = bsz;
       bmats[size_t(p) * G + h] = EmuSetMat{bsz, N, K, h};  // one row exponent per (h, bc) over every p
       if (N)
-        for (int k = 0; k < K; ++k) {
-          const bool vr = k < H.vcnt[g];
-          brows.push_back(T3BRow{bsz, p, h, vr ? 0 : 1, vr ? H.voff[g] + k : H.ooff[g] + k - H.vcnt[g], k, K});
-        }
+        for (int k = H.vcnt[g]; k < K; ++k) brows.push_back(T3BRow{bsz, p, h, H.ooff[g] + k - H.vcnt[g], k, K});
       bsz += int64_t(K) * N;
     }
   cplx* Bbuf = (cplx*)sc.get(sizeof(cplx) * size_t(std::max<int64_t>(bsz, 1)));
+  {  // the <bc||ep> columns, from the context's integrals
+    const IntRef VVVO{{SP_VIRT, SP_VIRT, SP_VIRT, SP_OCC}};
+    const Gathered gv = held(VVVO);
+    if (gv.n_chunks) {
+      int64_t* d_boff = (int64_t*)sc.get(sizeof(int64_t) * boff.size());
+      upload_async(c, d_boff, boff.data(), sizeof(int64_t) * boff.size());
+      k_t3_gather_bt<<<unsigned(gv.n_chunks), T3_THREADS, 0, c.stream>>>(Bbuf, gv.t->d + size_t(inst) * gv.t->is,
+                                                                         gv.tasks, gv.chunks, DT.T, d_boff, o, v);
+      KCHECK(c);
+    }
+  }
   if (!brows.empty()) {
     T3BRow* d_rows = (T3BRow*)sc.get(sizeof(T3BRow) * brows.size());
     upload(c, d_rows, brows.data(), sizeof(T3BRow) * brows.size());
-    k_t3_brows<<<unsigned(brows.size()), T3_THREADS, 0, c.stream>>>(Bbuf, d_rows, DT.T, t2d, o, v, c.n_gen, seed, scale,
-                                                                     real);
+    k_t3_brows<<<unsigned(brows.size()), T3_THREADS, 0, c.stream>>>(Bbuf, d_rows, DT.T, t2d, o, v);
     KCHECK(c);
   }
   if (emulated) {
@@ -662,9 +710,34 @@ void ccsd_t(Ctx& c, int inst, int block, exp_t3_info* info, double* per_triple) 
   // block size: the largest whose segment and Y^T buffers fit the budget
   const int64_t budget = int64_t(1) << 30;  // complex elements (16 GiB)
   const int nbmax = std::max(1, std::min(o, block > 0 ? block : 64));
+  // a lower bound of one triple's Y elements (the smallest over the triples' irreps):
+  // a block size whose largest batch times it exceeds the budget is skipped unprobed
+  int64_t per = INT64_MAX;
+  for (int gijk = 0; gijk < G; ++gijk) {
+    int64_t y = 0;
+    for (int h = 0; h < G; ++h) y += int64_t(H.npair[h]) * H.vcnt[((gijk - h) % G + G) % G];
+    per = std::min(per, y);
+  }
+  auto most_triples = [&](int cand) {  // triples in the largest batch of block size cand
+    const int nblk = (o + cand - 1) / cand;
+    auto sz = [&](int b) { return int64_t(std::min((b + 1) * cand, o) - b * cand); };
+    int64_t m = 0;
+    for (int I = 0; I < nblk; ++I)
+      for (int J = I; J < nblk; ++J)
+        for (int K = J; K < nblk; ++K) {
+          int64_t t;
+          if (I < J && J < K) t = sz(I) * sz(J) * sz(K);
+          else if (I == J && J < K) t = sz(I) * (sz(I) - 1) / 2 * sz(K);
+          else if (I < J) t = sz(I) * sz(J) * (sz(J) - 1) / 2;
+          else t = choose3(sz(I));
+          m = std::max(m, t);
+        }
+    return m;
+  };
   int nb = 1;
   int64_t max_s = 0, max_y = 0;
   for (int cand = nbmax; cand >= 1; --cand) {
+    if (block == 0 && cand > 1 && per > 0 && most_triples(cand) > budget / per) continue;
     const int nblk = (o + cand - 1) / cand;
     int64_t ms = 0, my = 0;
     BlockPlan probe;

@@ -65,7 +65,6 @@ struct T3Tables {
   int G = 1;
   const int* go = nullptr;     // [o] irrep of each occupied spinor
   const int* gv = nullptr;     // [v] irrep of each virtual spinor
-  const int* girr = nullptr;   // [o + v] irrep of each global spinor index
   const int* voff = nullptr;   // [G] first virtual of each irrep
   const int* vcnt = nullptr;   // [G]
   const int* ooff = nullptr;   // [G]
@@ -396,7 +395,7 @@ namespace {
 
 struct HostTables {
   int o = 0, v = 0, G = 1;
-  std::vector<int> go, gv, girr, voff, vcnt, ooff, ocnt, npair, poff;
+  std::vector<int> go, gv, voff, vcnt, ooff, ocnt, npair, poff;
   std::vector<int32_t> pairs, pidx;
 };
 
@@ -417,8 +416,6 @@ HostTables host_tables(const Ctx& c) {
     for (int k = 0; k < SO.cnt[g]; ++k) H.go[SO.off[g] + k] = g;
     for (int k = 0; k < SV.cnt[g]; ++k) H.gv[SV.off[g] + k] = g;
   }
-  H.girr = H.go;
-  H.girr.insert(H.girr.end(), H.gv.begin(), H.gv.end());
   // pair-packed virtual pairs b < c, grouped by pair irrep, b-major inside a group
   H.npair.assign(H.G, 0);
   H.poff.assign(H.G, 0);
@@ -451,7 +448,7 @@ DevTables upload_tables(Ctx& c, const HostTables& H) {
     buf.insert(buf.end(), x.begin(), x.end());
     return at;
   };
-  const size_t a_go = put(H.go), a_gv = put(H.gv), a_girr = put(H.girr), a_voff = put(H.voff), a_vcnt = put(H.vcnt),
+  const size_t a_go = put(H.go), a_gv = put(H.gv), a_voff = put(H.voff), a_vcnt = put(H.vcnt),
                a_ooff = put(H.ooff), a_ocnt = put(H.ocnt), a_npair = put(H.npair), a_poff = put(H.poff);
   const size_t a_pairs = buf.size();
   buf.insert(buf.end(), H.pairs.begin(), H.pairs.end());
@@ -464,7 +461,6 @@ DevTables upload_tables(Ctx& c, const HostTables& H) {
   D.T.G = H.G;
   D.T.go = p + a_go;
   D.T.gv = p + a_gv;
-  D.T.girr = p + a_girr;
   D.T.voff = p + a_voff;
   D.T.vcnt = p + a_vcnt;
   D.T.ooff = p + a_ooff;

@@ -261,21 +261,26 @@ typedef struct {
  *   c_ijk^abc = P(i/jk) P(a/bc) [ sum_e <bc||ei> t_jk^ae - sum_m <ma||jk> t_im^bc ],
  *   d_ijk^abc = P(i/jk) P(a/bc) t_i^a <bc||jk>,  P(p/qr) f = f - f(p<->q) - f(p<->r),
  *   E(T) = sum over i<j<k, a<b<c of conj(c + d) c / (e_i + e_j + e_k - e_a - e_b - e_c).
- * The connected contractions run as symmetry-blocked grouped products in the
- * context's precision (EXP_EMU_BF16: the BF16-sliced emulation with n_slices slices;
- * EXP_FP64: the FP64 kernel).  The permutations, the disconnected term, the
+ * The connected contractions run as one product per triple and pair irrep of (b, c)
+ * (the three terms' K concatenated), grouped per batch of triples, in the context's
+ * precision (EXP_EMU_BF16: the BF16-sliced emulation with n_slices slices; EXP_FP64:
+ * the FP64 kernel).  The permutations, the disconnected term, the
  * denominators and the energy terms run in FP64 under EXP_FP64 and in double-single
  * FP32 (about 48 bits) under EXP_EMU_BF16; the sums over elements and triples are FP64
  * in fixed order, so the result does not depend on the work
- * decomposition.  block: occupied spinors per block of the schedule (0: the largest
- * whose block products fit the scratch budget; a larger value than n_occ means
- * n_occ); every block size gives the same bits.  info (host, nullable) receives E(T)
+ * decomposition.  block: occupied spinors per block of the schedule (a batch is the
+ * triples of one block triple; 0: the largest block size whose batch outputs fit the
+ * scratch budget; a larger value than n_occ means n_occ); every block size gives the
+ * same bits.  info (host, nullable) receives E(T)
  * and the work counts;
  * per_triple (host, nullable, 2 * n_triples doubles) receives each triple's
  * (re, im) energy at index C(k,3) + C(j,2) + i of its i<j<k (spinor order of the
- * config).  Needs about 16 GiB of scratch for the block products at most, plus
+ * config).  Needs about 16 GiB of scratch for a batch's product outputs at most, plus
  * dense t2 and <bc||jk> (n_occ^2 n_virt^2 each) and the fixed operands
- * (n_occ n_virt^2 (n_virt + n_occ) / (2 G)).  Synchronises.  ESTATE before
+ * (n_occ n_virt^2 (n_virt + n_occ) / (2 G)); the integrals <bc||ep> and <ma||qr> it
+ * reads in a layout the context did not hold yet stay in the context's integral cache
+ * (n_virt^3 n_occ / G and n_occ^3 n_virt / G complex elements per instance).
+ * Synchronises.  ESTATE before
  * exp_init_integrals or before any amplitudes exist, and for a context with an
  * active space; EINVAL for inst out of range, block < 0 or more than 65535 virtual
  * spinors;

@@ -30,7 +30,8 @@
 //
 // Operands.  The integrals are the context's own: <bc||jk> copied out of its driver
 // integral, <ma||qr> and <bc||ep> gathered from layouts it caches (derived by a permute
-// from a held layout of the same symmetry family); t1 and t2 from its amplitudes.
+// from a held layout of the same symmetry family, else drawn once); t1 and t2 from its
+// amplitudes.
 //
 // Schedule.  The members Bt_{p,h} are written and, in the emulated precision, sliced
 // once, all members of one h sharing one exponent per row bc.  The occupied spinors
@@ -39,7 +40,7 @@
 // of one (triple, h) sharing one exponent per column a), one grouped launch forms Y
 // for every (triple, h) of the batch -- each product accumulating its three segments
 // exactly, on the tensor cores -- then one CTA per triple and pair irrep of (b, c)
-// forms c (three Y per P(a/bc) term), d, D and its energy.  Fixed-order sums over the
+// forms c from three Y elements (the P(a/bc) terms), d, D and its energy.  Fixed-order sums over the
 // pair irreps, then over the triples, give the per-triple energies and E(T): the
 // result does not depend on the batching.  The element arithmetic runs in FP64 under
 // EXP_FP64 (where the three segments are three FP64 product launches into Y) and in

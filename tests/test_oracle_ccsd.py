@@ -148,26 +148,29 @@ def test_gauge_rotated_real_instance():
     assert abs(E_g.imag) < 1e-12
 
 
-def test_symmetry_blocked_equals_c1_and_forbidden_stay_zero():
-    """A Z_4 problem solved densely: amplitudes of forbidden blocks stay exactly 0,
-    and the result equals the same Hamiltonian with the labels ignored (C1)."""
-    prob = syn.make_problem(19, 4, 12, G=4)
+@pytest.mark.parametrize("seed,no,nv,G", [(19, 4, 12, 4), (1604, 8, 32, 16)])
+def test_symmetry_blocked_equals_c1_and_forbidden_stay_zero(seed, no, nv, G):
+    """A Z_G problem solved densely (Z16: most irreps hold no occupied spinor): amplitudes
+    of forbidden blocks stay exactly 0, and the result equals the same Hamiltonian with
+    the labels ignored (C1)."""
+    prob = syn.make_problem(seed, no, nv, G=G)
     V = integrals.integrals(prob)
     f = integrals.fock(prob)
-    b = ccsd.Blocks(V, f, 4)
+    b = ccsd.Blocks(V, f, no)
     t1, t2, E, _, conv, _ = ccsd.solve(b, tol=1e-11)
     assert conv
     g = prob.irrep_of
-    go, gv = g[:4], g[4:]
-    forb1 = (gv[None, :] - go[:, None]) % 4 != 0
+    go, gv = g[:no], g[no:]
+    forb1 = (gv[None, :] - go[:, None]) % G != 0
     forb2 = (gv[None, None, :, None] + gv[None, None, None, :]
-             - go[:, None, None, None] - go[None, :, None, None]) % 4 != 0
+             - go[:, None, None, None] - go[None, :, None, None]) % G != 0
+    assert np.any(forb2)
     assert np.all(t1[forb1] == 0) and np.all(t2[forb2] == 0)
     # spinor order permuted (labels ignored): the same physics in C1 ordering
-    perm_o = np.random.default_rng(1).permutation(4)
-    perm_v = np.random.default_rng(2).permutation(12)
-    perm = np.concatenate([perm_o, 4 + perm_v])
+    perm_o = np.random.default_rng(1).permutation(no)
+    perm_v = np.random.default_rng(2).permutation(nv)
+    perm = np.concatenate([perm_o, no + perm_v])
     Vp = V[np.ix_(perm, perm, perm, perm)]
     fp = f[np.ix_(perm, perm)]
-    Ep = ccsd.solve(ccsd.Blocks(Vp, fp, 4), tol=1e-11)[2]
+    Ep = ccsd.solve(ccsd.Blocks(Vp, fp, no), tol=1e-11)[2]
     assert abs(Ep - E) < 1e-12
